@@ -1,0 +1,163 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module only draws data; it holds none of the method's arithmetic, so the
+GPU library and the FP64 oracle can both consume its output.  The paper's two
+datasets (the malware corpus of Experiment 1 and the Home Depot TF-IDF set of
+Experiment 2) are not available; these generators stand in for them.
+
+Workloads (the sigma index i runs 1..r):
+
+* ``fp64_small``   2,000 x 500, X = A diag(10 * 0.85^i) B^T + N(0, 0.01^2),
+                   r = 30, FP64, k = 20, Gaussian Omega.
+* ``fp32_sparse``  200,000 x 4,096, sigma_i = 1/i over r = 512,
+                   noise N(0, 1e-3^2), FP32, k = 128, very sparse Omega p = 64.
+* ``bf16_dense``   1,000,000 x 8,192, sigma_i = exp(-i/200) over r = 1,024,
+                   noise N(0, 1e-3^2), stored BF16, k = 256, Gaussian Omega.
+* ``e4m3_binary``  4,600,000 x 4,096 binary features, column rates
+                   p_j ~ Beta(0.5, 9.5) (5 % mean density), stored FP8 E4M3,
+                   k = 256, very sparse Omega p = 64.
+
+A and B are orthonormal (reduced QR of Gaussian draws).  Rows of the noise
+are drawn in fixed chunks from per-chunk generators, so the same seed gives
+the same matrix for any chunking on a given device type.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    m: int
+    n: int
+    k: int
+    dtype: str           # storage / arithmetic type of X: "f64", "f32", "bf16", "e4m3"
+    omega: str           # "gaussian" or "sparse"
+    p: int = 0           # very sparse parameter (Sec. I-A)
+    r: int = 0
+    noise: float = 0.0
+    spectrum: str = ""
+    data_seed: int = 1
+    omega_seed: int = 0
+    extra: dict = field(default_factory=dict)
+
+    def sigmas(self) -> np.ndarray:
+        i = np.arange(1, self.r + 1, dtype=np.float64)
+        if self.spectrum == "geom0.85":
+            return 10.0 * 0.85 ** i
+        if self.spectrum == "powerlaw1":
+            return 1.0 / i
+        if self.spectrum == "exp200":
+            return np.exp(-i / 200.0)
+        raise ValueError(self.spectrum)
+
+    def scaled(self, m: int | None = None, n: int | None = None, k: int | None = None) -> "Workload":
+        """Same generator recipe at other sizes (rank clipped to min(m, n))."""
+        mm = self.m if m is None else m
+        nn = self.n if n is None else n
+        kk = self.k if k is None else k
+        r = min(self.r, mm, nn) if self.r else 0
+        return Workload(self.name, mm, nn, kk, self.dtype, self.omega, self.p, r, self.noise,
+                        self.spectrum, self.data_seed, self.omega_seed, dict(self.extra))
+
+
+WORKLOADS = {
+    "fp64_small": Workload("fp64_small", 2000, 500, 20, "f64", "gaussian", 0, 30, 0.01, "geom0.85", 1, 0),
+    "fp32_sparse": Workload("fp32_sparse", 200_000, 4096, 128, "f32", "sparse", 64, 512, 1e-3, "powerlaw1", 2, 0),
+    "bf16_dense": Workload("bf16_dense", 1_000_000, 8192, 256, "bf16", "gaussian", 0, 1024, 1e-3, "exp200", 3, 0),
+    "e4m3_binary": Workload("e4m3_binary", 4_600_000, 4096, 256, "e4m3", "sparse", 64, 0, 0.0, "", 4, 0,
+                            {"beta_a": 0.5, "beta_b": 9.5}),
+}
+
+TORCH_DTYPES = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16,
+                "e4m3": torch.float8_e4m3fn}
+
+
+def _orthonormal(rows: int, r: int, gen: torch.Generator, device) -> torch.Tensor:
+    g = torch.randn(rows, r, generator=gen, dtype=torch.float64 if device == "cpu" else torch.float32,
+                    device=device)
+    q, _ = torch.linalg.qr(g, mode="reduced")
+    return q
+
+
+def lowrank_plus_noise(w: Workload, device="cpu", chunk_rows: int = 65536,
+                       out: torch.Tensor | None = None) -> torch.Tensor:
+    """X = A diag(sigma) B^T + noise, rounded once to the storage dtype.
+
+    CPU generation is FP64 throughout; on a GPU the factors and noise are FP32
+    (the rounding to the storage type dominates either way).  Returns an
+    (m, n) row-major tensor on ``device`` in ``TORCH_DTYPES[w.dtype]``.
+    """
+    dev = torch.device(device)
+    dev_key = "cpu" if dev.type == "cpu" else dev
+    work = torch.float64 if dev.type == "cpu" else torch.float32
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(int(w.data_seed) * 1_000_003 + 17)
+    A = _orthonormal(w.m, w.r, gen, dev_key).to(work)
+    B = _orthonormal(w.n, w.r, gen, dev_key).to(work)
+    sig = torch.as_tensor(w.sigmas(), dtype=work, device=dev)
+    BS = (B * sig).T.contiguous()  # r x n
+    X = out if out is not None else torch.empty(w.m, w.n, dtype=TORCH_DTYPES[w.dtype], device=dev)
+    for c0 in range(0, w.m, chunk_rows):
+        c1 = min(w.m, c0 + chunk_rows)
+        g = torch.Generator(device=dev)
+        g.manual_seed(int(w.data_seed) * 7_919 + 1 + c0 // chunk_rows)
+        blk = A[c0:c1] @ BS
+        if w.noise:
+            blk += w.noise * torch.randn(c1 - c0, w.n, generator=g, dtype=work, device=dev)
+        X[c0:c1] = blk.to(X.dtype)
+    return X
+
+
+def beta_rates(w: Workload) -> np.ndarray:
+    """Column Bernoulli rates p_j ~ Beta(a, b), FP64, host-seeded."""
+    rng = np.random.Generator(np.random.PCG64(int(w.data_seed) * 104_729 + 5))
+    return rng.beta(w.extra.get("beta_a", 0.5), w.extra.get("beta_b", 9.5), size=w.n)
+
+
+def binary_features(w: Workload, device="cpu", chunk_rows: int = 262144,
+                    out: torch.Tensor | None = None) -> torch.Tensor:
+    """X_ij = [u_ij < p_j] with p_j ~ Beta(a, b): mostly-binary sparse features
+    shaped like Experiment 1's corpus.  Stored as ``TORCH_DTYPES[w.dtype]``."""
+    dev = torch.device(device)
+    rates = torch.as_tensor(beta_rates(w), dtype=torch.float32, device=dev)
+    X = out if out is not None else torch.empty(w.m, w.n, dtype=TORCH_DTYPES[w.dtype], device=dev)
+    for c0 in range(0, w.m, chunk_rows):
+        c1 = min(w.m, c0 + chunk_rows)
+        g = torch.Generator(device=dev)
+        g.manual_seed(int(w.data_seed) * 15_485_863 + 3 + c0 // chunk_rows)
+        u = torch.rand(c1 - c0, w.n, generator=g, dtype=torch.float32, device=dev)
+        X[c0:c1] = (u < rates).to(torch.float32).to(X.dtype)
+    return X
+
+
+def generate(w: Workload, device="cpu") -> torch.Tensor:
+    """The data matrix X of a workload."""
+    if w.dtype == "e4m3":
+        return binary_features(w, device)
+    return lowrank_plus_noise(w, device)
+
+
+def rank_r_exact(m: int, n: int, r: int, seed: int, dtype=torch.float64) -> tuple:
+    """Noise-free X = A diag(sigma) B^T with sigma_i = 2^-i (i = 1..r).
+
+    Returns (X, B): B spans the exact principal subspace.
+    """
+    gen = torch.Generator()
+    gen.manual_seed(seed)
+    A = _orthonormal(m, r, gen, "cpu")
+    B = _orthonormal(n, r, gen, "cpu")
+    sig = torch.tensor([2.0 ** -i for i in range(1, r + 1)], dtype=torch.float64)
+    X = (A * sig) @ B.T
+    return X.to(dtype), B
+
+
+def serving_rows(seed: int, count: int, lo: int = 1, hi: int = 65536) -> np.ndarray:
+    """Log-uniform request row counts in [lo, hi] (serving workload)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return np.floor(np.exp(rng.uniform(math.log(lo), math.log(hi + 1), size=count))).astype(np.int64)
