@@ -1,0 +1,324 @@
+"""Benchmark: Lazy SPCA fit throughput on one GB300 (and N replicas under torchrun).
+
+Workload (one step = one whole Lazy SPCA fit, every pass of the hot path):
+fp32_sparse -- X of 200,000 x 4,096 FP32 (sigma_i = 1/i over rank 512 plus
+N(0, 1e-3^2) noise), k = 128, very sparse Omega with p = 64.  X (3.28 GB)
+is larger than L2, so no flush is needed between steps.
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Lazy SPCA fit samples/s & HBM-roofline frac vs SPCA on GB300; serve p50/p99 ms"
+WORKLOAD = "fp32_sparse"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        pw = [num(r[3]) for r in rows if num(r[3]) is not None]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(pw) if pw else None}
+
+
+def cpu_baseline(rows: int, reps_seconds: float = 10.0) -> dict:
+    """The FP64 oracle as it stands, on a bounded sample of the workload."""
+    import numpy as np
+
+    from oracle import lspca as O
+    from oracle import philox as P
+    from paper_1709_07175_gb300 import synthetic as S
+    w = S.WORKLOADS[WORKLOAD].scaled(m=rows)
+    X = S.generate(w).double().numpy()
+    Om = P.omega_sparse(w.omega_seed, w.n, w.k, w.p)
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        O.lspca_fit(X, Om, route="eig")
+        reps += 1
+        if time.perf_counter() - t0 >= reps_seconds:
+            break
+    dt = time.perf_counter() - t0
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": rows * reps / dt, "unit": "samples/s", "cores": cores, "kind": "oracle",
+            "sample": f"{rows} rows x {w.n} of the {WORKLOAD} workload (same recipe), k={w.k}, "
+                      f"{reps} fit(s) in {dt:.1f} s; FP64 numpy, BLAS threads = host default",
+            "np": np.__version__}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    from oracle import lspca as O
+    from oracle import philox as P
+    from paper_1709_07175_gb300 import synthetic as S
+    rows = args.ref_rows
+    w = S.WORKLOADS[WORKLOAD].scaled(m=rows)
+    X = S.generate(w).double().numpy()
+    Om = P.omega_sparse(w.omega_seed, w.n, w.k, w.p)
+    for _ in range(args.warmup):
+        O.lspca_fit(X, Om, route="eig")
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.lspca_fit(X, Om, route="eig")
+    dt = time.perf_counter() - t0
+    val = rows * args.steps / dt
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    full = S.WORKLOADS[WORKLOAD]
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "samples/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{WORKLOAD} {full.m}x{full.n} k={full.k} very sparse p={full.p}",
+                       "m": full.m, "n": full.n, "k": full.k},
+            "cpu_baseline": {"value": val, "unit": "samples/s", "cores": cores, "kind": "oracle",
+                             "sample": f"each step: one oracle fit of {rows} rows x {w.n} (same recipe)"},
+            "e2e": {"value": val, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args):
+    import torch
+
+    from paper_1709_07175_gb300 import build as B
+    from paper_1709_07175_gb300 import lspca as L
+    from paper_1709_07175_gb300 import synthetic as S
+
+    ws, rank, local = _dist()
+    B.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist_mod
+        dist_mod.init_process_group("nccl")
+        dist = dist_mod
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    w = S.WORKLOADS[WORKLOAD]
+    if args.m:
+        w = w.scaled(m=args.m)
+    # weak scaling: each rank fits its own independent problem (different data seed)
+    from dataclasses import replace
+    w = replace(w, data_seed=w.data_seed + 1000 * rank)
+    X = S.generate(w, device=f"cuda:{local}")
+    torch.cuda.synchronize()
+    ctx = L.Context(local)
+    om = L.omega("sparse", w.omega_seed, w.p)
+    stream = torch.cuda.current_stream()
+    V = torch.empty(w.n, w.k, dtype=torch.float32, device=X.device)
+    sigma = torch.empty(w.k, dtype=torch.float64, device=X.device)
+    rk = torch.empty(1, dtype=torch.int32, device=X.device)
+
+    def step(fn=L.lspca_fit):
+        rc = fn(ctx.handle, X, w.k, om, 0, V, sigma, None, rk, stream)
+        if rc != L.OK:
+            raise L.LspcaError(rc, fn.__name__)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: device-resident inputs
+    L.lspca_profile(ctx.handle, True)
+    launches0 = ctx.launch_count()
+    clocks = Clocks(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    launches = ctx.launch_count() - launches0
+    pass_ms, calls = L.lspca_profile_read(ctx.handle)
+    L.lspca_profile(ctx.handle, False)
+    if dist is not None:
+        t = torch.tensor([ms], device=X.device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = w.m * ws * args.steps / (ms / 1e3)
+
+    # ---- SPCA comparison path (same workload, same launch configuration)
+    for _ in range(2):
+        step(L.spca_fit)
+    torch.cuda.synchronize()
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    nsp = max(3, min(args.steps, 10))
+    s0.record(stream)
+    for _ in range(nsp):
+        step(L.spca_fit)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    spca_ms = s0.elapsed_time(s1) / nsp
+
+    # ---- end to end through the public API: pinned host X -> device, fit, V and sigma back
+    Xh = torch.empty(X.shape, dtype=X.dtype, pin_memory=True)
+    Xh.copy_(X)
+    Vh = torch.empty(V.shape, dtype=V.dtype, pin_memory=True)
+    sh = torch.empty(sigma.shape, dtype=sigma.dtype, pin_memory=True)
+    ne2e = max(3, min(args.steps, 5))
+
+    def e2e_step():
+        X.copy_(Xh, non_blocking=True)
+        step()
+        Vh.copy_(V, non_blocking=True)
+        sh.copy_(sigma, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(ne2e):
+        e2e_step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = t0.elapsed_time(t1) / ne2e
+    if dist is not None:
+        t = torch.tensor([e2e_ms], device=X.device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    # ---- roofline of the dominant kernel
+    names = ["omega", "sketch", "chain_main", "chain_reduce", "qr", "small", "total"]
+    per = {nm: pass_ms[i] / max(calls, 1) for i, nm in enumerate(names)}
+    x_bytes = w.m * w.n * 4
+    u_bytes = w.m * w.k * 4
+    alg = {"sketch": x_bytes + u_bytes, "chain_main": x_bytes + u_bytes}
+    dom = max(alg, key=lambda nm: per[nm])
+    peak, peak_kind = _peaks()
+    achieved = alg[dom] / (per[dom] / 1e3) / 1e9
+    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+            "bytes_per_launch": alg[dom], "ms_per_launch": per[dom]}
+
+    line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{WORKLOAD} {w.m}x{w.n} k={w.k} very sparse p={w.p}", "m": w.m, "n": w.n,
+                       "k": w.k, "x_bytes": x_bytes, "l2": "inputs larger than L2 (no flush)"},
+            "roofline": roof,
+            "fit_roofline_frac": {"lazy": (x_bytes / (peak * 1e9)) / (ms_step / 1e3),
+                                  "spca": (x_bytes / (peak * 1e9)) / (spca_ms / 1e3)},
+            "spca": {"ms_per_step": spca_ms, "samples_per_s": w.m * ws / (spca_ms / 1e3),
+                     "lazy_speedup": spca_ms / ms_step},
+            "passes_ms": per,
+            "e2e": {"value": w.m * ws / (e2e_ms / 1e3), "unit": "samples/s",
+                    "h2d_bytes_per_step": x_bytes, "d2h_bytes_per_step": w.n * w.k * 4 + w.k * 8,
+                    "ms_per_step": e2e_ms},
+            "gpu_launches": launches,
+            "clocks": clk}
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_rows, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--m", type=int, default=0, help="override the row count (smaller runs)")
+    ap.add_argument("--cpu-rows", type=int, default=50_000)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--ref-rows", type=int, default=20_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,212 @@
+/*
+ * lspca.h -- C ABI of the GB300 Lazy stochastic PCA library (liblspca.so).
+ *
+ * Method: Wojnowicz, Nguyen, Li, Zhao, "Lazy stochastic principal component
+ * analysis", arXiv 1709.07175.  Notation of the paper: X is m x n with the
+ * samples as rows (Sec. I-A), Omega is n x l with l = k (no oversampling, as
+ * in Experiment 1), U = X Omega (Eq. 1, c = 1), F = U^T X, V is n x k, and
+ * the reduction is Y = X V (Sec. III-B.2, Eq. "dim_reduction_maps").
+ *
+ * Conventions for every entry point
+ * ---------------------------------
+ * - All matrices are row-major.  X has leading dimension ldx (elements,
+ *   ldx >= n); ldx * sizeof(element) must be a multiple of 16 bytes and X
+ *   16-byte aligned (pad rows otherwise).  V is n x k (ld k), Y is m x k
+ *   (ld k), U is m x k (ld k), F is k x n (ld n), G is k x k (ld k).
+ * - The "result type" of a path is FP64 when X is LSPCA_F64 and FP32
+ *   otherwise; V, U and Y are stored in the result type.
+ * - Pointers marked [dev] are device pointers on the context's device; the
+ *   caller owns them and keeps them alive until the stream has completed.
+ *   Pointers marked [host] are host pointers.
+ * - Calls are asynchronous: they enqueue on `stream` (a cudaStream_t, NULL =
+ *   legacy default stream) and return.  Outputs are valid after the stream
+ *   has been synchronised.  Device-side failures (non-finite input, a wait
+ *   that gave up) are recorded in a status word of the context; they are
+ *   returned by lspca_sync_status() or by any call given a non-NULL report.
+ * - No call throws; every call returns an lspca_status.  No call falls back
+ *   to the host: every step runs in the library's CUDA kernels.
+ * - A context serialises its workspace: calls on one context must be issued
+ *   from one host thread at a time (they may use different streams only if
+ *   the caller orders them).
+ * - X is never centred (Sec. I-B: uncentred principal components).
+ */
+#ifndef LSPCA_H
+#define LSPCA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lspca_ctx lspca_ctx;
+
+/* Return codes. */
+typedef enum {
+  LSPCA_OK = 0,
+  LSPCA_ERR_INVALID = 1,        /* bad argument or unsupported combination      */
+  LSPCA_ERR_NOMEM = 2,          /* workspace would exceed the context's budget  */
+  LSPCA_WARN_RANK_DEFICIENT = 3,/* success, but rank < k (see rank rule)        */
+  LSPCA_ERR_NUMERIC = 4,        /* NaN/Inf in X, or a numeric failure           */
+  LSPCA_ERR_TIMEOUT = 5,        /* a bounded device or host wait gave up        */
+  LSPCA_ERR_CUDA = 6,           /* a CUDA runtime/driver call failed            */
+  LSPCA_ERR_BUSY = 7            /* serving: no free slot / over budget right now */
+} lspca_status;
+
+/* Element type of X (and the arithmetic the passes run in). */
+typedef enum {
+  LSPCA_F64 = 0,   /* FP64 SIMT throughout                                          */
+  LSPCA_F32 = 1,   /* FP32 X; U in FP32; F on tensor cores with split-FP16 products */
+  LSPCA_BF16 = 2,  /* BF16 X; BF16 tensor cores, split-BF16 U for F                 */
+  LSPCA_E4M3 = 3   /* FP8 E4M3 X (binary features); needs very sparse Omega         */
+} lspca_dtype;
+
+/* The random test matrix Omega (Sec. I-A). */
+typedef enum {
+  LSPCA_OMEGA_GAUSSIAN = 0,     /* Omega_ij ~ N(0, 1) i.i.d.                                   */
+  LSPCA_OMEGA_VERY_SPARSE = 1   /* Omega_ij in {-1, 0, +1} w.p. {1/2p, 1 - 1/p, 1/2p} (Li et al.) */
+} lspca_omega_kind;
+
+/* Omega is generated on the device from a Philox4x32-10 stream (Salmon et al.,
+ * SC'11): entry (i, j) uses counter (i, j / 4, tag, 0) and key (seed mod 2^32,
+ * seed / 2^32); word j % 4 feeds column j.  Gaussian (tag 0): Box-Muller on
+ * word pairs (w0,w1) -> columns 4b (cos), 4b+1 (sin), (w2,w3) -> 4b+2, 4b+3,
+ * u = (w + 1/2) 2^-32, FP64 then rounded to FP32 (and to BF16 on the BF16
+ * path).  Very sparse (tag 1): T = floor(2^32 / 2p), w < T -> -1,
+ * T <= w < 2T -> +1, else 0.  p is ignored for the Gaussian kind.          */
+typedef struct {
+  int32_t kind;    /* lspca_omega_kind */
+  uint32_t p;      /* very sparse parameter, p >= 1 */
+  uint64_t seed;
+} lspca_omega;
+
+/* Flags of the fit calls. */
+enum {
+  LSPCA_WANT_GRAM = 2,     /* also return G = U^T U (k x k, FP64)            */
+  LSPCA_FORCE_SIMT = 16    /* run the plain SIMT kernels instead of the
+                              tensor-core ones (cross-checks; slow)          */
+};
+
+/* Per-call report, filled only when a non-NULL pointer is given; the call then
+ * synchronises `stream` before returning.                                    */
+typedef struct {
+  double ms_total;        /* host wall time of the call incl. synchronisation */
+  double ms_sketch;       /* device time of pass S (U = X Omega)               */
+  double ms_chain;        /* device time of pass F (F = U^T X [, G])           */
+  double ms_small;        /* device time of the k x k step                     */
+  double ms_qr;           /* SPCA only: TSQR and R^-T F                        */
+  double bytes_x;         /* bytes of X read per pass                          */
+  int32_t rank;           /* numerical rank (rank rule)                         */
+  int32_t device_status;  /* status word read from the device                  */
+  int32_t sweeps;         /* Jacobi sweeps of the k x k eigensolve              */
+  int32_t reserved;
+} lspca_report;
+
+/* ------------------------------------------------------------------------- */
+
+/* Create a context on `device`.  hbm_budget_bytes caps the library-owned
+ * workspace (0 = 3/4 of the free device memory at creation).  The workspace
+ * is allocated lazily and grown on demand up to the budget.
+ * Errors: LSPCA_ERR_INVALID (out == NULL, bad device), LSPCA_ERR_CUDA.      */
+int lspca_create(lspca_ctx** out, int device, size_t hbm_budget_bytes);
+
+/* Destroy a context; synchronises its device and frees its workspace.      */
+int lspca_destroy(lspca_ctx* ctx);
+
+/* Lazy SPCA fit, Algorithm 2 / 4 (table of Sec. III):
+ *   U = X Omega; F = U^T X (Alg. 4's slice sum F += U_s^T X_s over row tiles);
+ *   truncated SVD of F by the eigen route of the table footnote:
+ *   F F^T = W Lambda W^T, D = Lambda^1/2, V = F^T W D^-1.
+ * X      [dev]  m x n, element type xt, leading dimension ldx.
+ * k             target dimension, 1 <= k <= min(m, n, 256).
+ * V      [dev]  n x k output in the result type: columns are the approximate right singular
+ *               vectors V^l in descending sigma order; each column's largest-
+ *               magnitude entry is positive; columns beyond the rank are 0.
+ * sigma  [dev]  k FP64 output: singular values of U^T X (0 beyond the rank).
+ * gram   [dev]  k x k FP64 output G = U^T U when flags has LSPCA_WANT_GRAM
+ *               (may be NULL otherwise).
+ * rank   [dev]  int32 output (nullable): numerical rank, lambda_i >
+ *               max(m, n) 2^-52 lambda_1.
+ * rep    [host] nullable report; non-NULL synchronises the stream.
+ * Errors: LSPCA_ERR_INVALID (NULL pointers, k out of range, ldx < n,
+ * misaligned X/ldx, E4M3 with a Gaussian Omega, p == 0 for very sparse),
+ * LSPCA_ERR_NOMEM, LSPCA_ERR_NUMERIC (with rep: NaN/Inf found in X),
+ * LSPCA_WARN_RANK_DEFICIENT (with rep), LSPCA_ERR_CUDA.                     */
+int lspca_fit(lspca_ctx* ctx, const void* X, int32_t xt, int64_t m, int64_t n, int64_t ldx,
+              int32_t k, lspca_omega om, uint32_t flags, void* V, double* sigma, double* gram,
+              int32_t* rank, void* stream, lspca_report* rep);
+
+/* SPCA fit, the comparison path: Algorithm 1 in its streaming form,
+ * Algorithm 3 (table of Sec. III; Eq. "approx_svd"): U = X Omega; R from a
+ * tall-skinny Householder QR of U (row blocks, then a reduction tree of the
+ * stacked R factors: Algorithm 3's qr([R; U_s]) in parallel form);
+ * F = R^-T U^T X (= Q^T X); truncated SVD of F by the same eigen route.
+ * Arguments and errors as lspca_fit; sigma receives Sigma^s of Q^T X and
+ * V receives V^s.  `gram` (with LSPCA_WANT_GRAM) receives U^T U.           */
+int spca_fit(lspca_ctx* ctx, const void* X, int32_t xt, int64_t m, int64_t n, int64_t ldx,
+             int32_t k, lspca_omega om, uint32_t flags, void* V, double* sigma, double* gram,
+             int32_t* rank, void* stream, lspca_report* rep);
+
+/* Reduction map pi(x) = V^T x for every row: Y = X V (Sec. III-B.2).
+ * X [dev] m x n (xt, ldx); V [dev] n x k and Y [dev] m x k (output), both
+ * in the result type.  F32 X runs split-FP16 tensor-core products (X and V
+ * split into hi + lo parts), BF16/E4M3 X split-BF16 V, F64 X FP64 SIMT.
+ * 1 <= k <= 256.
+ * Errors: LSPCA_ERR_INVALID, LSPCA_ERR_NOMEM, LSPCA_ERR_CUDA.               */
+int lspca_project(lspca_ctx* ctx, const void* X, int32_t xt, int64_t m, int64_t n, int64_t ldx,
+                  const void* V, int32_t k, void* Y, void* stream);
+
+/* ---- step-level entry points (the passes of lspca_fit, for tests) ----- */
+
+/* Write Omega (n x k row-major) as generated on the device.  t selects the
+ * output element type: LSPCA_F64 (the FP32-rounded values, or exact +-1/0),
+ * LSPCA_F32, or LSPCA_BF16 (BF16-rounded, as the BF16 path uses it).
+ * out [dev].  Errors: LSPCA_ERR_INVALID, LSPCA_ERR_CUDA.                    */
+int lspca_omega_materialize(lspca_ctx* ctx, lspca_omega om, int64_t n, int32_t k, int32_t t,
+                            void* out, void* stream);
+
+/* Pass S: U = X Omega (Eq. 1, c = 1; Algorithm 2 step 1).  U [dev] m x k,
+ * FP64 when xt == LSPCA_F64, else FP32.  Errors as lspca_fit.               */
+int lspca_sketch(lspca_ctx* ctx, const void* X, int32_t xt, int64_t m, int64_t n, int64_t ldx,
+                 int32_t k, lspca_omega om, uint32_t flags, void* U, void* stream);
+
+/* Pass F: F = U^T X (Algorithm 2 step 2; Algorithm 4's slice sum) and, when
+ * G != NULL, G = U^T U.  U [dev] m x k (FP64 if xt == LSPCA_F64, else FP32);
+ * F [dev] k x n FP64; G [dev] k x k FP64 or NULL.                           */
+int lspca_chain(lspca_ctx* ctx, const void* X, int32_t xt, int64_t m, int64_t n, int64_t ldx,
+                const void* U, int32_t k, uint32_t flags, double* F, double* G, void* stream);
+
+/* The k x k step (table footnote): H = F F^T, H = W Lambda W^T (descending),
+ * sigma = Lambda^1/2, V = F^T W D^-1, sign and rank rules as lspca_fit.
+ * F [dev] k x n FP64; V [dev] n x k output, FP64 when vt == LSPCA_F64, FP32
+ * when vt == LSPCA_F32; sigma [dev] k FP64; rank [dev] nullable; m is the
+ * row count of X (used by the rank rule only).                             */
+int lspca_decompose(lspca_ctx* ctx, const double* F, int32_t k, int64_t n, int64_t m, int32_t vt, void* V,
+                    double* sigma, int32_t* rank, void* stream);
+
+/* Synchronise `stream`, return and clear the device status word:
+ * LSPCA_OK, LSPCA_ERR_NUMERIC or LSPCA_ERR_TIMEOUT.                         */
+int lspca_sync_status(lspca_ctx* ctx, void* stream);
+
+/* Human-readable text of a status code (static storage).                   */
+const char* lspca_strerror(int status);
+
+/* Number of kernels this library has launched on this context (a counter
+ * kept by the host side; used to report launch counts).                    */
+int64_t lspca_launch_count(lspca_ctx* ctx);
+
+/* Pass timing without synchronisation: with profiling enabled every fit
+ * records CUDA events between its kernels on its stream (up to 4096 calls
+ * are kept); lspca_profile_read synchronises the device and returns the
+ * summed device milliseconds ms7[0..6] = {Omega generation (+ X scan),
+ * pass-S kernel, pass-F main kernel, pass-F reduction, SPCA QR + R^-T F,
+ * k x k step, whole call} and the number of calls.  enable = 0 stops and
+ * resets.                                                                   */
+int lspca_profile(lspca_ctx* ctx, int enable);
+int lspca_profile_read(lspca_ctx* ctx, double* ms7, int64_t* calls);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LSPCA_H */

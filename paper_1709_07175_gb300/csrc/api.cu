@@ -1,0 +1,518 @@
+// C ABI of liblspca: context, workspace, argument checks and the orchestration of
+// the passes (declared in include/lspca.h).
+#include <chrono>
+#include <functional>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "tc.h"
+
+using namespace lspca;
+
+struct lspca_ctx {
+  int device = 0;
+  size_t budget = 0;
+  void* ws = nullptr;
+  size_t ws_size = 0;
+  int* d_status = nullptr;    // device status word
+  float* d_absmax = nullptr;  // [0] max|X|, [1] max|U|
+  int32_t* d_rank = nullptr;  // rank when the caller passes none
+  int64_t launches = 0;
+  int num_sms = 0;
+  cudaEvent_t ev[6] = {};
+  // profiling ring: 5 events per call
+  bool profiling = false;
+  std::vector<cudaEvent_t> pev;
+  int64_t pcalls = 0;
+};
+
+namespace {
+
+// Bump allocator over the context workspace (256-byte aligned pieces).
+struct Plan {
+  char* base = nullptr;
+  size_t off = 0;
+  void* take(size_t bytes) {
+    off = (off + 255) & ~(size_t)255;
+    void* p = base ? base + off : nullptr;
+    off += bytes;
+    return p;
+  }
+};
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? LSPCA_OK : LSPCA_ERR_CUDA; }
+
+int ensure_ws(lspca_ctx* ctx, size_t bytes, cudaStream_t stream) {
+  if (bytes > ctx->budget) return LSPCA_ERR_NOMEM;
+  if (bytes <= ctx->ws_size) return LSPCA_OK;
+  cudaError_t e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return LSPCA_ERR_CUDA;
+  if (ctx->ws) cudaFree(ctx->ws);
+  ctx->ws = nullptr;
+  ctx->ws_size = 0;
+  size_t want = bytes + bytes / 4;
+  if (want > ctx->budget) want = ctx->budget;
+  e = cudaMalloc(&ctx->ws, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    e = cudaMalloc(&ctx->ws, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      ctx->ws = nullptr;
+      return LSPCA_ERR_NOMEM;
+    }
+    want = bytes;
+  }
+  ctx->ws_size = want;
+  return LSPCA_OK;
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+int check_x(const void* X, int xt, int64_t m, int64_t n, int64_t ldx) {
+  if (!X) return LSPCA_ERR_INVALID;
+  if (xt < LSPCA_F64 || xt > LSPCA_E4M3) return LSPCA_ERR_INVALID;
+  if (m < 1 || n < 1 || ldx < n) return LSPCA_ERR_INVALID;
+  if (!aligned16(X) || (ldx * (int64_t)dtype_size(xt)) % 16 != 0) return LSPCA_ERR_INVALID;
+  return LSPCA_OK;
+}
+
+int check_omega(const lspca_omega& om, int xt) {
+  if (om.kind != LSPCA_OMEGA_GAUSSIAN && om.kind != LSPCA_OMEGA_VERY_SPARSE) return LSPCA_ERR_INVALID;
+  if (om.kind == LSPCA_OMEGA_VERY_SPARSE && om.p == 0) return LSPCA_ERR_INVALID;
+  if (xt == LSPCA_E4M3 && om.kind != LSPCA_OMEGA_VERY_SPARSE) return LSPCA_ERR_INVALID;
+  return LSPCA_OK;
+}
+
+size_t acc_size(int xt) { return xt == LSPCA_F64 ? 8 : 4; }
+int acc_dt(int xt) { return xt == LSPCA_F64 ? LSPCA_F64 : LSPCA_F32; }
+
+double ev_ms(cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+    cudaGetLastError();
+    return 0.0;
+  }
+  return (double)ms;
+}
+
+// ---- pass S -----------------------------------------------------------------
+struct SketchBufs {
+  int32_t* counts = nullptr;
+  int32_t* col_ptr = nullptr;
+  int32_t* entries = nullptr;
+  void* omega = nullptr;  // dense Omega (n x k, result type) for the SIMT path
+  void* omega_t = nullptr;  // dense Omega^T (k x n BF16) for the tensor-core path
+};
+
+void plan_sketch(Plan& P, SketchBufs& b, int xt, int64_t n, int k, const lspca_omega& om, bool tc) {
+  if (om.kind == LSPCA_OMEGA_VERY_SPARSE) {
+    b.counts = (int32_t*)P.take((size_t)k * 4);
+    b.col_ptr = (int32_t*)P.take((size_t)(k + 1) * 4);
+    b.entries = (int32_t*)P.take((size_t)n * k * 4);
+  } else if (tc) {
+    b.omega_t = P.take((size_t)n * k * 2);
+  } else {
+    b.omega = P.take((size_t)n * k * acc_size(xt));
+  }
+}
+
+using Mark = std::function<void(int)>;
+
+void run_sketch(lspca_ctx* ctx, Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_t ldx, int k,
+                const lspca_omega& om, bool tc, SketchBufs& b, void* U, const Mark& mark) {
+  if (om.kind == LSPCA_OMEGA_VERY_SPARSE) {
+    launch_omega_csc(L, om, n, k, b.counts, b.col_ptr, b.entries);
+    mark(1);
+    launch_sketch_sparse(L, X, xt, m, n, ldx, k, b.col_ptr, b.entries, U, k, ctx->d_absmax, ctx->d_status);
+    mark(2);
+    return;
+  }
+  if (tc) {
+    launch_omega_dense(L, om, n, k, LSPCA_BF16, b.omega_t, n, true, true);
+    launch_scan_x(L, X, xt, m, n, ldx, ctx->d_absmax, ctx->d_status);
+    mark(1);
+    tc_sketch_bf16(L, X, m, n, ldx, b.omega_t, k, (float*)U, ctx->d_absmax + 1);
+    mark(2);
+    return;
+  }
+  const bool bf = xt == LSPCA_BF16;
+  launch_omega_dense(L, om, n, k, acc_dt(xt), b.omega, k, false, bf);
+  launch_scan_x(L, X, xt, m, n, ldx, ctx->d_absmax, ctx->d_status);
+  mark(1);
+  launch_gemm_simt(L, m, k, n, X, xt, ldx, false, b.omega, acc_dt(xt), k, false, U, xt == LSPCA_F64, k, 0, 1,
+                   xt == LSPCA_F64, false);
+  mark(2);
+}
+
+// ---- pass F -----------------------------------------------------------------
+struct ChainBufs {
+  double* Fpart = nullptr;
+  double* Gpart = nullptr;
+  int f_splits = 1, g_splits = 1;
+  TcChainWs tcw;
+};
+
+int simt_splits(int64_t rows, int64_t cols, int64_t K, int num_sms) {
+  const int64_t tiles = ((rows + 63) / 64) * ((cols + 63) / 64);
+  int64_t s = (2 * num_sms + tiles - 1) / tiles;
+  if (s > 64) s = 64;
+  if (s > K / 64) s = K / 64;
+  if (s < 1) s = 1;
+  return (int)s;
+}
+
+void plan_chain(Plan& P, ChainBufs& b, int xt, int64_t m, int64_t n, int k, bool want_g, bool tc, int num_sms) {
+  if (tc) {
+    plan_tc_chain(P.base ? P.base + ((P.off + 255) & ~(size_t)255) : nullptr, b.tcw, xt, m, n, k, want_g, num_sms);
+    P.take(b.tcw.bytes);
+    return;
+  }
+  b.f_splits = simt_splits(k, n, m, num_sms);
+  b.Fpart = (double*)P.take((size_t)b.f_splits * k * n * 8);
+  if (want_g) {
+    b.g_splits = simt_splits(k, k, m, num_sms);
+    b.Gpart = (double*)P.take((size_t)b.g_splits * k * k * 8);
+  }
+}
+
+void run_chain(lspca_ctx* ctx, Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_t ldx, const void* U,
+               int k, bool tc, ChainBufs& b, double* F, double* G, const Mark& mark) {
+  if (tc) {
+    tc_chain_main(L, X, xt, m, n, ldx, (const float*)U, k, b.tcw, ctx->d_absmax, G != nullptr);
+    mark(3);
+    tc_chain_reduce(L, n, k, b.tcw, F, G);
+    mark(4);
+    return;
+  }
+  const bool f64 = xt == LSPCA_F64;
+  launch_gemm_simt(L, k, n, m, U, acc_dt(xt), k, true, X, xt, ldx, false, b.Fpart, true, n, (int64_t)k * n, b.f_splits,
+                   f64, false);
+  if (G)
+    launch_gemm_simt(L, k, k, m, U, acc_dt(xt), k, true, U, acc_dt(xt), k, false, b.Gpart, true, k, (int64_t)k * k,
+                     b.g_splits, f64, false);
+  mark(3);
+  launch_reduce_splits(L, b.Fpart, b.f_splits, (int64_t)k * n, (int64_t)k * n, F);
+  if (G) launch_reduce_splits(L, b.Gpart, b.g_splits, (int64_t)k * k, (int64_t)k * k, G);
+  mark(4);
+}
+
+bool use_tc_chain(int xt, uint32_t flags) {
+  return !(flags & LSPCA_FORCE_SIMT) && (xt == LSPCA_F32 || xt == LSPCA_BF16) && tc_available();
+}
+bool use_tc_sketch(int xt, const lspca_omega& om, uint32_t flags) {
+  return !(flags & LSPCA_FORCE_SIMT) && xt == LSPCA_BF16 && om.kind == LSPCA_OMEGA_GAUSSIAN && tc_available();
+}
+
+int fit_impl(lspca_ctx* ctx, const void* X, int32_t xt, int64_t m, int64_t n, int64_t ldx, int32_t k, lspca_omega om,
+             uint32_t flags, void* V, double* sigma, double* gram, int32_t* rank, void* stream, lspca_report* rep,
+             bool spca) {
+  if (!ctx) return LSPCA_ERR_INVALID;
+  int st = check_x(X, xt, m, n, ldx);
+  if (st) return st;
+  if ((st = check_omega(om, xt))) return st;
+  if (k < 1 || k > 256 || k > m || k > n || !V || !sigma) return LSPCA_ERR_INVALID;
+  const bool want_g = (flags & LSPCA_WANT_GRAM) != 0;
+  if (want_g && !gram) return LSPCA_ERR_INVALID;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return LSPCA_ERR_CUDA;
+  const auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t s = (cudaStream_t)stream;
+  Launcher L{s, &ctx->launches, ctx->num_sms};
+  const bool tc_s = use_tc_sketch(xt, om, flags);
+  const bool tc_f = use_tc_chain(xt, flags);
+  const size_t asz = acc_size(xt);
+
+  SketchBufs sb;
+  ChainBufs cb;
+  SmallWs sw;
+  void *U = nullptr, *small = nullptr, *qrws = nullptr;
+  double *F = nullptr, *G = nullptr, *R = nullptr;
+  auto plan = [&](Plan& P) {
+    U = P.take((size_t)m * k * asz);
+    plan_sketch(P, sb, xt, n, k, om, tc_s);
+    F = (double*)P.take((size_t)k * n * 8);
+    G = (double*)P.take((size_t)k * k * 8);
+    plan_chain(P, cb, xt, m, n, k, want_g, tc_f, ctx->num_sms);
+    small = P.take(small_ws_bytes(k, n, nullptr));
+    if (spca) {
+      qrws = P.take(tsqr_ws_bytes(m, k));
+      R = (double*)P.take((size_t)k * k * 8);
+    }
+  };
+  Plan p0;
+  plan(p0);
+  if ((st = ensure_ws(ctx, p0.off + 4096, s))) return st;
+  Plan p1;
+  p1.base = (char*)ctx->ws;
+  plan(p1);
+  carve_small_ws(sw, small, k, n);
+
+  cudaEvent_t* pe = nullptr;
+  if (ctx->profiling && ctx->pcalls < (int64_t)ctx->pev.size() / 7) pe = &ctx->pev[(size_t)ctx->pcalls++ * 7];
+  // report events: 0 start, 1 after pass S, 2 after pass F, 3 after QR, 4 end
+  static const int rep_slot[7] = {0, -1, 1, -1, 2, 3, 4};
+  Mark mark = [&](int i) {
+    if (rep && rep_slot[i] >= 0) cudaEventRecord(ctx->ev[rep_slot[i]], s);
+    if (pe) cudaEventRecord(pe[i], s);
+  };
+  cudaMemsetAsync(ctx->d_absmax, 0, 2 * sizeof(float), s);
+  mark(0);
+  run_sketch(ctx, L, X, xt, m, n, ldx, k, om, tc_s, sb, U, mark);
+  run_chain(ctx, L, X, xt, m, n, ldx, U, k, tc_f, cb, F, want_g ? G : nullptr, mark);
+  if (spca) {
+    launch_tsqr(L, U, xt == LSPCA_F64, m, k, qrws, R);
+    launch_trsm_rt(L, R, k, F, n);
+  }
+  mark(5);
+  int32_t* rk = rank ? rank : ctx->d_rank;
+  launch_decompose(L, sw, F, k, n, m, xt == LSPCA_F64, V, sigma, rk, ctx->d_status);
+  if (want_g) cudaMemcpyAsync(gram, G, (size_t)k * k * 8, cudaMemcpyDeviceToDevice, s);
+  mark(6);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return LSPCA_ERR_CUDA;
+  if (!rep) return LSPCA_OK;
+
+  memset(rep, 0, sizeof(*rep));
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return LSPCA_ERR_CUDA;
+  rep->ms_sketch = ev_ms(ctx->ev[0], ctx->ev[1]);
+  rep->ms_chain = ev_ms(ctx->ev[1], ctx->ev[2]);
+  rep->ms_qr = ev_ms(ctx->ev[2], ctx->ev[3]);
+  rep->ms_small = ev_ms(ctx->ev[3], ctx->ev[4]);
+  rep->bytes_x = (double)m * n * dtype_size(xt);
+  int32_t hr = 0, hst = 0, hsw = 0;
+  cudaMemcpy(&hr, rk, 4, cudaMemcpyDeviceToHost);
+  cudaMemcpy(&hst, ctx->d_status, 4, cudaMemcpyDeviceToHost);
+  cudaMemcpy(&hsw, sw.sweeps, 4, cudaMemcpyDeviceToHost);
+  cudaMemsetAsync(ctx->d_status, 0, 4, s);
+  cudaStreamSynchronize(s);
+  rep->rank = hr;
+  rep->device_status = hst;
+  rep->sweeps = hsw;
+  rep->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (hst & ST_NONFINITE) return LSPCA_ERR_NUMERIC;
+  if (hst & ST_TIMEOUT) return LSPCA_ERR_TIMEOUT;
+  if (hst & ST_NUMERIC) return LSPCA_ERR_NUMERIC;
+  if (hr < k) return LSPCA_WARN_RANK_DEFICIENT;
+  return LSPCA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lspca_create(lspca_ctx** out, int device, size_t hbm_budget_bytes) {
+  if (!out) return LSPCA_ERR_INVALID;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+    cudaGetLastError();
+    return LSPCA_ERR_CUDA;
+  }
+  if (device < 0 || device >= ndev) return LSPCA_ERR_INVALID;
+  if (cudaSetDevice(device) != cudaSuccess) return LSPCA_ERR_CUDA;
+  lspca_ctx* c = new lspca_ctx();
+  c->device = device;
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  size_t fr = 0, tot = 0;
+  cudaMemGetInfo(&fr, &tot);
+  c->budget = hbm_budget_bytes ? hbm_budget_bytes : fr / 4 * 3;
+  if (cudaMalloc(&c->d_status, 256) != cudaSuccess) {
+    delete c;
+    return LSPCA_ERR_CUDA;
+  }
+  cudaMemset(c->d_status, 0, 256);
+  c->d_absmax = reinterpret_cast<float*>(reinterpret_cast<char*>(c->d_status) + 64);
+  c->d_rank = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(c->d_status) + 128);
+  for (auto& e : c->ev) cudaEventCreate(&e);
+  *out = c;
+  return LSPCA_OK;
+}
+
+int lspca_destroy(lspca_ctx* ctx) {
+  if (!ctx) return LSPCA_ERR_INVALID;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->d_status) cudaFree(ctx->d_status);
+  for (auto& e : ctx->ev)
+    if (e) cudaEventDestroy(e);
+  for (auto& e : ctx->pev) cudaEventDestroy(e);
+  delete ctx;
+  return LSPCA_OK;
+}
+
+int lspca_fit(lspca_ctx* ctx, const void* X, int32_t xt, int64_t m, int64_t n, int64_t ldx, int32_t k, lspca_omega om,
+              uint32_t flags, void* V, double* sigma, double* gram, int32_t* rank, void* stream, lspca_report* rep) {
+  return fit_impl(ctx, X, xt, m, n, ldx, k, om, flags, V, sigma, gram, rank, stream, rep, false);
+}
+
+int spca_fit(lspca_ctx* ctx, const void* X, int32_t xt, int64_t m, int64_t n, int64_t ldx, int32_t k, lspca_omega om,
+             uint32_t flags, void* V, double* sigma, double* gram, int32_t* rank, void* stream, lspca_report* rep) {
+  return fit_impl(ctx, X, xt, m, n, ldx, k, om, flags, V, sigma, gram, rank, stream, rep, true);
+}
+
+int lspca_project(lspca_ctx* ctx, const void* X, int32_t xt, int64_t m, int64_t n, int64_t ldx, const void* V,
+                  int32_t k, void* Y, void* stream) {
+  if (!ctx) return LSPCA_ERR_INVALID;
+  int st = check_x(X, xt, m, n, ldx);
+  if (st) return st;
+  if (!V || !Y || k < 1 || k > 256) return LSPCA_ERR_INVALID;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return LSPCA_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  Launcher L{s, &ctx->launches, ctx->num_sms};
+  if (xt != LSPCA_F64 && tc_available()) {
+    TcProjectWs pw;
+    Plan p0;
+    plan_tc_project(nullptr, pw, xt, n, k);
+    p0.take(pw.bytes);
+    if ((st = ensure_ws(ctx, p0.off + 4096, s))) return st;
+    plan_tc_project((char*)ctx->ws, pw, xt, n, k);
+    tc_project(L, X, xt, m, n, ldx, (const float*)V, k, pw, (float*)Y);
+  } else {
+    launch_gemm_simt(L, m, k, n, X, xt, ldx, false, V, acc_dt(xt), k, false, Y, xt == LSPCA_F64, k, 0, 1,
+                     xt == LSPCA_F64, false);
+  }
+  return cuda_status(cudaGetLastError());
+}
+
+int lspca_omega_materialize(lspca_ctx* ctx, lspca_omega om, int64_t n, int32_t k, int32_t t, void* out,
+                            void* stream) {
+  if (!ctx || !out || n < 1 || k < 1) return LSPCA_ERR_INVALID;
+  if (t != LSPCA_F64 && t != LSPCA_F32 && t != LSPCA_BF16) return LSPCA_ERR_INVALID;
+  if (om.kind != LSPCA_OMEGA_GAUSSIAN && om.kind != LSPCA_OMEGA_VERY_SPARSE) return LSPCA_ERR_INVALID;
+  if (om.kind == LSPCA_OMEGA_VERY_SPARSE && om.p == 0) return LSPCA_ERR_INVALID;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return LSPCA_ERR_CUDA;
+  Launcher L{(cudaStream_t)stream, &ctx->launches, ctx->num_sms};
+  launch_omega_dense(L, om, n, k, t, out, k, false, t == LSPCA_BF16);
+  return cuda_status(cudaGetLastError());
+}
+
+int lspca_sketch(lspca_ctx* ctx, const void* X, int32_t xt, int64_t m, int64_t n, int64_t ldx, int32_t k,
+                 lspca_omega om, uint32_t flags, void* U, void* stream) {
+  if (!ctx) return LSPCA_ERR_INVALID;
+  int st = check_x(X, xt, m, n, ldx);
+  if (st) return st;
+  if ((st = check_omega(om, xt))) return st;
+  if (!U || k < 1 || k > 256) return LSPCA_ERR_INVALID;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return LSPCA_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  Launcher L{s, &ctx->launches, ctx->num_sms};
+  const bool tc = use_tc_sketch(xt, om, flags);
+  SketchBufs sb;
+  Plan p0;
+  plan_sketch(p0, sb, xt, n, k, om, tc);
+  if ((st = ensure_ws(ctx, p0.off + 4096, s))) return st;
+  Plan p1;
+  p1.base = (char*)ctx->ws;
+  plan_sketch(p1, sb, xt, n, k, om, tc);
+  cudaMemsetAsync(ctx->d_absmax, 0, 2 * sizeof(float), s);
+  run_sketch(ctx, L, X, xt, m, n, ldx, k, om, tc, sb, U, [](int) {});
+  return cuda_status(cudaGetLastError());
+}
+
+int lspca_chain(lspca_ctx* ctx, const void* X, int32_t xt, int64_t m, int64_t n, int64_t ldx, const void* U, int32_t k,
+                uint32_t flags, double* F, double* G, void* stream) {
+  if (!ctx) return LSPCA_ERR_INVALID;
+  int st = check_x(X, xt, m, n, ldx);
+  if (st) return st;
+  if (!U || !F || k < 1 || k > 256) return LSPCA_ERR_INVALID;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return LSPCA_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  Launcher L{s, &ctx->launches, ctx->num_sms};
+  const bool tc = use_tc_chain(xt, flags);
+  ChainBufs cb;
+  Plan p0;
+  plan_chain(p0, cb, xt, m, n, k, G != nullptr, tc, ctx->num_sms);
+  if ((st = ensure_ws(ctx, p0.off + 4096, s))) return st;
+  Plan p1;
+  p1.base = (char*)ctx->ws;
+  plan_chain(p1, cb, xt, m, n, k, G != nullptr, tc, ctx->num_sms);
+  if (tc) {
+    // the split-FP16 path scales by powers of two derived from max|X| and max|U|
+    cudaMemsetAsync(ctx->d_absmax, 0, 2 * sizeof(float), s);
+    launch_scan_x(L, X, xt, m, n, ldx, ctx->d_absmax, ctx->d_status);
+    launch_scan_x(L, U, LSPCA_F32, m, k, k, ctx->d_absmax + 1, ctx->d_status);
+  }
+  run_chain(ctx, L, X, xt, m, n, ldx, U, k, tc, cb, F, G, [](int) {});
+  return cuda_status(cudaGetLastError());
+}
+
+int lspca_decompose(lspca_ctx* ctx, const double* F, int32_t k, int64_t n, int64_t m, int32_t vt, void* V,
+                    double* sigma, int32_t* rank, void* stream) {
+  if (!ctx || !F || !V || k < 1 || k > 256 || n < k || m < 1) return LSPCA_ERR_INVALID;
+  if (vt != LSPCA_F64 && vt != LSPCA_F32) return LSPCA_ERR_INVALID;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return LSPCA_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  Launcher L{s, &ctx->launches, ctx->num_sms};
+  int st;
+  const size_t bytes = small_ws_bytes(k, n, nullptr);
+  if ((st = ensure_ws(ctx, bytes + 4096, s))) return st;
+  SmallWs sw;
+  carve_small_ws(sw, ctx->ws, k, n);
+  launch_decompose(L, sw, F, k, n, m, vt == LSPCA_F64, V, sigma, rank ? rank : ctx->d_rank, ctx->d_status);
+  return cuda_status(cudaGetLastError());
+}
+
+int lspca_sync_status(lspca_ctx* ctx, void* stream) {
+  if (!ctx) return LSPCA_ERR_INVALID;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return LSPCA_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return LSPCA_ERR_CUDA;
+  int32_t h = 0;
+  if (cudaMemcpy(&h, ctx->d_status, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return LSPCA_ERR_CUDA;
+  cudaMemset(ctx->d_status, 0, 4);
+  if (h & ST_NONFINITE) return LSPCA_ERR_NUMERIC;
+  if (h & ST_TIMEOUT) return LSPCA_ERR_TIMEOUT;
+  if (h & ST_NUMERIC) return LSPCA_ERR_NUMERIC;
+  return LSPCA_OK;
+}
+
+const char* lspca_strerror(int status) {
+  switch (status) {
+    case LSPCA_OK: return "ok";
+    case LSPCA_ERR_INVALID: return "invalid argument";
+    case LSPCA_ERR_NOMEM: return "workspace exceeds the context's HBM budget";
+    case LSPCA_WARN_RANK_DEFICIENT: return "rank deficient (rank < k)";
+    case LSPCA_ERR_NUMERIC: return "non-finite input or numeric failure";
+    case LSPCA_ERR_TIMEOUT: return "a bounded wait gave up";
+    case LSPCA_ERR_CUDA: return "CUDA error";
+    case LSPCA_ERR_BUSY: return "busy: no free slot or over budget";
+    default: return "unknown status";
+  }
+}
+
+int64_t lspca_launch_count(lspca_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+int lspca_profile(lspca_ctx* ctx, int enable) {
+  if (!ctx) return LSPCA_ERR_INVALID;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return LSPCA_ERR_CUDA;
+  cudaDeviceSynchronize();
+  for (auto& e : ctx->pev) cudaEventDestroy(e);
+  ctx->pev.clear();
+  ctx->pcalls = 0;
+  ctx->profiling = enable != 0;
+  if (enable) {
+    ctx->pev.resize(4096 * 7);
+    for (auto& e : ctx->pev)
+      if (cudaEventCreate(&e) != cudaSuccess) return LSPCA_ERR_CUDA;
+  }
+  return LSPCA_OK;
+}
+
+int lspca_profile_read(lspca_ctx* ctx, double* ms7, int64_t* calls) {
+  if (!ctx || !ms7) return LSPCA_ERR_INVALID;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return LSPCA_ERR_CUDA;
+  if (cudaDeviceSynchronize() != cudaSuccess) return LSPCA_ERR_CUDA;
+  for (int i = 0; i < 7; ++i) ms7[i] = 0.0;
+  for (int64_t c = 0; c < ctx->pcalls; ++c) {
+    cudaEvent_t* e = &ctx->pev[(size_t)c * 7];
+    for (int i = 0; i < 6; ++i) ms7[i] += ev_ms(e[i], e[i + 1]);
+    ms7[6] += ev_ms(e[0], e[6]);
+  }
+  if (calls) *calls = ctx->pcalls;
+  return LSPCA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,77 @@
+// Host-side launchers of liblspca's kernels (internal interface between the
+// C-ABI layer and the kernel translation units).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/lspca.h"
+
+namespace lspca {
+
+struct Launcher {
+  cudaStream_t stream;
+  int64_t* counter;
+  int num_sms;
+  void count(int n) { *counter += n; }
+};
+
+// ---- K0: Omega ------------------------------------------------------------
+void launch_omega_dense(Launcher& L, const lspca_omega& om, int64_t n, int k, int out_dt, void* out, int64_t ld,
+                        bool transposed, bool bf16_round);
+void launch_omega_csc(Launcher& L, const lspca_omega& om, int64_t n, int k, int32_t* counts, int32_t* col_ptr,
+                      int32_t* entries);
+
+// ---- generic SIMT GEMM ------------------------------------------------------
+// C[s][M x N] = sum over K-range s of op(A) op(B), one partial per split s
+// (stride c_split_stride).  op(A)(r, kk) = a_trans ? A[kk*lda + r] : A[r*lda + kk],
+// op(B)(kk, c) = b_trans ? B[c*ldb + kk] : B[kk*ldb + c].
+// Element types: ta/tb in {F64, F32, BF16, E4M3} (lspca_dtype); acc_f64 selects
+// FP64 accumulation; c_f64 selects an FP64 (else FP32) output.
+void launch_gemm_simt(Launcher& L, int64_t M, int64_t N, int64_t K, const void* A, int ta, int64_t lda, bool a_trans,
+                      const void* B, int tb, int64_t ldb, bool b_trans, void* C, bool c_f64, int64_t ldc,
+                      int64_t c_split_stride, int splits, bool acc_f64, bool small_tiles);
+
+// out[e] = sum_{s < splits} part[s * stride + e] in FP64, fixed order; count elements.
+void launch_reduce_splits(Launcher& L, const double* part, int splits, int64_t stride, int64_t count, double* out);
+
+// ---- K1: pass S -----------------------------------------------------------
+// U = X Omega with very sparse Omega (CSC lists); U is FP64 for F64 X, else FP32.
+// absmax[0] |= max|X|, absmax[1] |= max|U| (FP32 bit-pattern max); status |= ST_NONFINITE.
+void launch_sketch_sparse(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_t ldx, int k,
+                          const int32_t* col_ptr, const int32_t* entries, void* U, int64_t ldu, float* absmax,
+                          int* status);
+// Scan X for NaN/Inf and its largest magnitude (dense-Omega paths).
+void launch_scan_x(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_t ldx, float* absmax, int* status);
+
+// ---- K3: the k x k step ---------------------------------------------------
+struct SmallWs {
+  double* Hpart;   // splits x k x k
+  double* H;       // k x k
+  float* h32;      // k x k (global Jacobi scratch when k > 128)
+  float* w32;      // k x k
+  double* Xa;      // k x k
+  double* Xb;      // k x k
+  double* Rm;      // k x k
+  double* T;       // k x k
+  double* S;       // k x k
+  double* E;       // k x k
+  double* lam;     // k
+  double* scal;    // 8 scalars
+  double* Vd;      // n x k
+  int32_t* sweeps; // 1
+  int h_splits;
+};
+size_t small_ws_bytes(int k, int64_t n, int* h_splits);
+void carve_small_ws(SmallWs& w, void* base, int k, int64_t n);
+void launch_decompose(Launcher& L, SmallWs& w, const double* F, int k, int64_t n, int64_t m, bool v_f64, void* V,
+                      double* sigma, int32_t* rank, int* status);
+
+// ---- K4: TSQR (SPCA) ------------------------------------------------------
+size_t tsqr_ws_bytes(int64_t m, int k);
+// R (k x k FP64, upper triangular) of U (m x k, FP64 if u_f64 else FP32).
+void launch_tsqr(Launcher& L, const void* U, bool u_f64, int64_t m, int k, void* ws, double* R);
+// F <- R^-T F in place (F k x n FP64).
+void launch_trsm_rt(Launcher& L, const double* R, int k, double* F, int64_t n);
+
+}  // namespace lspca

@@ -1,0 +1,260 @@
+// K1, pass S for the very sparse Omega (Sec. I-A): U = X Omega (Eq. 1, c = 1).
+//
+// U[r, c] = sum over the nonzeros (j, s) of column c of Omega of s * X[r, j].
+// Omega has about n/p nonzeros per column, so the sketch is a gather-add: it
+// is bound by streaming X from HBM, not by arithmetic.
+//
+// One persistent CTA per SM (512 threads) walks row tiles of 32 rows; each tile
+// is streamed in column chunks of W elements with 16-byte loads held in
+// registers one step ahead.  A chunk is stored transposed, Xt[j][r] with a
+// pitch of 33, so that the gather -- lane = row, all lanes reading the same
+// feature j -- is free of bank conflicts; the lane mapping of the stores
+// (EPV rows x 32/EPV vectors per warp instruction, EPV = elements per vector)
+// makes the transposing stores conflict-free as well.  Each warp owns the Omega
+// columns c = warp + 16 t and walks their sorted index lists, one entry per
+// column per round so that the lists' loads overlap.  A finished tile is staged
+// through shared memory and written with coalesced row stores.
+//
+// Summation of each U entry runs over j in increasing order in the
+// accumulation type (FP64 for FP64 X, else FP32): deterministic.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace lspca {
+
+template <int DT>
+struct SketchCfg {
+  using T = typename XType<DT>::T;
+  using Acc = typename XType<DT>::Acc;
+  static constexpr int EPV = 16 / (int)sizeof(T);               // elements per 16-byte vector
+  static constexpr int W = sizeof(Acc) == 8 ? 128 : 512;         // chunk width in elements
+  static constexpr int ROWS = 32;
+  static constexpr int THREADS = 512;
+  static constexpr int VPT = ROWS * W / EPV / THREADS;           // vectors per thread per chunk
+  static constexpr int RG = 32 / EPV;                            // row groups per chunk
+  static constexpr int PITCH = ROWS + 1;
+  static constexpr int MAX_CPW = 16;                             // k <= 256 -> 16 columns per warp
+  static constexpr int ENT_CACHE = 12288;                        // Omega entries cached in SMEM
+  static size_t smem_bytes(int k, bool cache_entries) {
+    return (size_t)(2 * W * PITCH + ROWS * (k + 1)) * sizeof(Acc) +
+           (cache_entries ? (size_t)ENT_CACHE * 4 + (size_t)(k + 1) * 4 : 0);
+  }
+};
+
+template <int DT>
+__global__ void __launch_bounds__(512, 1)
+    sketch_sparse_kernel(const void* __restrict__ Xv, int64_t m, int64_t n, int64_t ldx, int k,
+                         const int32_t* __restrict__ col_ptr_g, const int32_t* __restrict__ entries_g,
+                         void* __restrict__ Uv, int64_t ldu, float* absmax, int* status) {
+  using C = SketchCfg<DT>;
+  using T = typename C::T;
+  using Acc = typename C::Acc;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Acc* buf0 = reinterpret_cast<Acc*>(smem_raw);
+  Acc* buf1 = buf0 + C::W * C::PITCH;
+  Acc* us = buf1 + C::W * C::PITCH;
+  int32_t* ent_s = reinterpret_cast<int32_t*>(us + C::ROWS * (k + 1));
+  int32_t* cp_s = ent_s + C::ENT_CACHE;
+
+  const T* X = reinterpret_cast<const T*>(Xv);
+  Acc* U = reinterpret_cast<Acc*>(Uv);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int rr = lane % C::EPV, cc = lane / C::EPV;
+
+  const int32_t* entries = entries_g;
+  const int32_t* col_ptr = col_ptr_g;
+  const int nnz = col_ptr_g[k];
+  if (nnz <= C::ENT_CACHE) {
+    for (int e = tid; e < nnz; e += C::THREADS) ent_s[e] = entries_g[e];
+    for (int e = tid; e <= k; e += C::THREADS) cp_s[e] = col_ptr_g[e];
+    entries = ent_s;
+    col_ptr = cp_s;
+  }
+
+  const int64_t ntiles = (m + C::ROWS - 1) / C::ROWS;
+  const int nchunks = (int)((n + C::W - 1) / C::W);
+  const int64_t my_tiles = ((int64_t)blockIdx.x < ntiles) ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  const int64_t steps = my_tiles * nchunks;
+  __syncthreads();
+  if (steps == 0) return;
+
+  uint4 regs[C::VPT];
+  float amax = 0.f, amax_u = 0.f;
+  bool bad = false;
+  Acc acc[C::MAX_CPW];
+  int pos[C::MAX_CPW], pend[C::MAX_CPW];
+
+  auto tile_of = [&](int64_t st) -> int64_t { return (int64_t)blockIdx.x + (st / nchunks) * gridDim.x; };
+
+  auto load = [&](int64_t st) {
+    const int64_t r0 = tile_of(st) * C::ROWS;
+    const int64_t j0 = (int64_t)(st % nchunks) * C::W;
+#pragma unroll
+    for (int q = 0; q < C::VPT; ++q) {
+      const int s = q * 16 + warp;
+      const int row = (s % C::RG) * C::EPV + rr;
+      const int vc = (s / C::RG) * (32 / C::EPV) + cc;
+      const int64_t gr = r0 + row, gj = j0 + (int64_t)vc * C::EPV;
+      if (gr < m && gj < n)
+        regs[q] = __ldg(reinterpret_cast<const uint4*>(X + gr * ldx + gj));
+      else
+        regs[q] = make_uint4(0u, 0u, 0u, 0u);
+    }
+  };
+
+  auto store = [&](int64_t st, Acc* buf) {
+    const int64_t j0 = (int64_t)(st % nchunks) * C::W;
+#pragma unroll
+    for (int q = 0; q < C::VPT; ++q) {
+      const int s = q * 16 + warp;
+      const int row = (s % C::RG) * C::EPV + rr;
+      const int vc = (s / C::RG) * (32 / C::EPV) + cc;
+      const T* e = reinterpret_cast<const T*>(&regs[q]);
+#pragma unroll
+      for (int u = 0; u < C::EPV; ++u) {
+        const int jl = vc * C::EPV + u;
+        Acc v = XType<DT>::to_acc(e[u]);
+        if (j0 + jl >= n) v = Acc(0);
+        if (!finite_acc(v)) bad = true;
+        amax = fmaxf(amax, (float)abs_acc(v));
+        buf[jl * C::PITCH + row] = v;
+      }
+    }
+  };
+
+  const int cpw = (k + 15) / 16;
+  load(0);
+  store(0, buf0);
+  __syncthreads();
+  for (int64_t st = 0; st < steps; ++st) {
+    Acc* cur = (st & 1) ? buf1 : buf0;
+    Acc* nxt = (st & 1) ? buf0 : buf1;
+    const int chunk = (int)(st % nchunks);
+    const int64_t j0 = (int64_t)chunk * C::W;
+    if (chunk == 0) {
+#pragma unroll
+      for (int t = 0; t < C::MAX_CPW; ++t) {
+        const int c = warp + 16 * t;
+        const bool ok = (t < cpw) && (c < k);
+        pos[t] = ok ? col_ptr[c] : 0;
+        pend[t] = ok ? col_ptr[c + 1] : 0;
+        acc[t] = Acc(0);
+      }
+    }
+    if (st + 1 < steps) load(st + 1);
+    // gather: one entry per live column per round
+    const int jend = (int)(j0 + C::W);
+    unsigned live = 0;
+#pragma unroll
+    for (int t = 0; t < C::MAX_CPW; ++t) live |= (pos[t] < pend[t]) ? (1u << t) : 0u;
+    while (live) {
+#pragma unroll
+      for (int t = 0; t < C::MAX_CPW; ++t) {
+        if (live & (1u << t)) {
+          const int32_t e = entries[pos[t]];
+          const int j = (e > 0 ? e : -e) - 1;
+          if (j < jend) {
+            const Acc v = cur[(j - (int)j0) * C::PITCH + lane];
+            acc[t] += (e > 0) ? v : -v;
+            ++pos[t];
+            if (pos[t] >= pend[t]) live &= ~(1u << t);
+          } else {
+            live &= ~(1u << t);
+          }
+        }
+      }
+    }
+    const bool last = (chunk == nchunks - 1);
+    if (last) {
+#pragma unroll
+      for (int t = 0; t < C::MAX_CPW; ++t) {
+        const int c = warp + 16 * t;
+        if (t < cpw && c < k) us[lane * (k + 1) + c] = acc[t];
+      }
+    }
+    if (st + 1 < steps) store(st + 1, nxt);
+    __syncthreads();
+    if (last) {
+      const int64_t r0 = tile_of(st) * C::ROWS;
+      for (int e = tid; e < C::ROWS * k; e += C::THREADS) {
+        const int r = e / k, c = e % k;
+        if (r0 + r < m) {
+          const Acc v = us[r * (k + 1) + c];
+          amax_u = fmaxf(amax_u, (float)abs_acc(v));
+          U[(r0 + r) * ldu + c] = v;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  amax = warp_max(amax);
+  amax_u = warp_max(amax_u);
+  const unsigned anybad = __ballot_sync(0xffffffffu, bad);
+  if (lane == 0) {
+    atomic_max_nonneg(absmax, amax);
+    atomic_max_nonneg(absmax + 1, amax_u);
+    if (anybad) atomicOr(status, ST_NONFINITE);
+  }
+}
+
+template <int DT>
+static void sketch_sparse_dispatch(Launcher& L, const void* X, int64_t m, int64_t n, int64_t ldx, int k,
+                                   const int32_t* col_ptr, const int32_t* entries, void* U, int64_t ldu, float* absmax,
+                                   int* status) {
+  using C = SketchCfg<DT>;
+  const size_t smem = C::smem_bytes(k, true);
+  cudaFuncSetAttribute(sketch_sparse_kernel<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int64_t ntiles = (m + C::ROWS - 1) / C::ROWS;
+  const int grid = (int)(ntiles < L.num_sms ? ntiles : L.num_sms);
+  sketch_sparse_kernel<DT><<<grid, C::THREADS, smem, L.stream>>>(X, m, n, ldx, k, col_ptr, entries, U, ldu, absmax,
+                                                                  status);
+  L.count(1);
+}
+
+void launch_sketch_sparse(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_t ldx, int k,
+                          const int32_t* col_ptr, const int32_t* entries, void* U, int64_t ldu, float* absmax,
+                          int* status) {
+  switch (xt) {
+    case LSPCA_F64: sketch_sparse_dispatch<LSPCA_F64>(L, X, m, n, ldx, k, col_ptr, entries, U, ldu, absmax, status); break;
+    case LSPCA_F32: sketch_sparse_dispatch<LSPCA_F32>(L, X, m, n, ldx, k, col_ptr, entries, U, ldu, absmax, status); break;
+    case LSPCA_BF16: sketch_sparse_dispatch<LSPCA_BF16>(L, X, m, n, ldx, k, col_ptr, entries, U, ldu, absmax, status); break;
+    case LSPCA_E4M3: sketch_sparse_dispatch<LSPCA_E4M3>(L, X, m, n, ldx, k, col_ptr, entries, U, ldu, absmax, status); break;
+  }
+}
+
+// Scan X for NaN/Inf and its largest magnitude (the dense-Omega paths, where the
+// sketch runs on tensor cores or as a plain GEMM and does not see every element).
+template <int DT>
+__global__ void scan_x_kernel(const void* __restrict__ Xv, int64_t m, int64_t n, int64_t ldx, float* absmax,
+                              int* status) {
+  using T = typename XType<DT>::T;
+  const T* X = reinterpret_cast<const T*>(Xv);
+  float amax = 0.f;
+  bool bad = false;
+  const int64_t total = m * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / n, c = e % n;
+    const float v = (float)XType<DT>::to_acc(X[r * ldx + c]);
+    if (!isfinite(v)) bad = true;
+    amax = fmaxf(amax, fabsf(v));
+  }
+  amax = warp_max(amax);
+  const unsigned anybad = __ballot_sync(0xffffffffu, bad);
+  if ((threadIdx.x & 31) == 0) {
+    atomic_max_nonneg(absmax, amax);
+    if (anybad) atomicOr(status, ST_NONFINITE);
+  }
+}
+
+void launch_scan_x(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_t ldx, float* absmax, int* status) {
+  const int threads = 256, blocks = 4 * L.num_sms;
+  switch (xt) {
+    case LSPCA_F64: scan_x_kernel<LSPCA_F64><<<blocks, threads, 0, L.stream>>>(X, m, n, ldx, absmax, status); break;
+    case LSPCA_F32: scan_x_kernel<LSPCA_F32><<<blocks, threads, 0, L.stream>>>(X, m, n, ldx, absmax, status); break;
+    case LSPCA_BF16: scan_x_kernel<LSPCA_BF16><<<blocks, threads, 0, L.stream>>>(X, m, n, ldx, absmax, status); break;
+    case LSPCA_E4M3: scan_x_kernel<LSPCA_E4M3><<<blocks, threads, 0, L.stream>>>(X, m, n, ldx, absmax, status); break;
+  }
+  L.count(1);
+}
+
+}  // namespace lspca

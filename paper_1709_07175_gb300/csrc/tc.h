@@ -1,0 +1,42 @@
+// Tensor-core (tcgen05 / TMEM / TMA) passes of liblspca, sm_103a.
+#pragma once
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include "kernels.h"
+
+namespace lspca {
+
+// True when the current device runs the tcgen05 kernels (compute capability 10.3).
+bool tc_available();
+
+// Pass F on tensor cores: F = U^T X and optionally G = U^T U.
+struct TcChainWs {
+  size_t bytes = 0;
+  double* Fpart = nullptr;  // chunks x k x n partials
+  double* Gpart = nullptr;  // chunks x k x k partials
+  float* scales = nullptr;  // device scalars
+  int chunks = 1;
+  int64_t rows_per_chunk = 0;
+};
+void plan_tc_chain(char* base, TcChainWs& w, int xt, int64_t m, int64_t n, int k, bool want_g, int num_sms);
+void tc_chain_main(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_t ldx, const float* U, int k,
+                   TcChainWs& w, const float* absmax, bool want_g);
+void tc_chain_reduce(Launcher& L, int64_t n, int k, TcChainWs& w, double* F, double* G);
+
+// Pass S on tensor cores for BF16 X and a Gaussian Omega (Omega^T k x n BF16).
+void tc_sketch_bf16(Launcher& L, const void* X, int64_t m, int64_t n, int64_t ldx, const void* omega_t, int k,
+                    float* U, float* absmax_u);
+
+// Y = X V on tensor cores.
+struct TcProjectWs {
+  size_t bytes = 0;
+  void* vhi = nullptr;  // k x n (V^T, high part)
+  void* vlo = nullptr;  // k x n (V^T, low part)
+};
+void plan_tc_project(char* base, TcProjectWs& w, int xt, int64_t n, int k);
+void tc_project(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_t ldx, const float* V, int k,
+                TcProjectWs& w, float* Y);
+
+}  // namespace lspca

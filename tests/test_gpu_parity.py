@@ -1,0 +1,323 @@
+"""GPU parity: the CUDA library, called through its C ABI, against the FP64 oracle.
+
+Both sides consume the same seeded inputs (paper_1709_07175_gb300.synthetic);
+each side generates Omega itself (Philox4x32-10 from its published
+definition).  Tolerances (written in each test):
+
+* Omega: very sparse bit-exact; Gaussian within 1 FP32 ulp.
+* FP64 path (workload fp64_small): reduced data Y within 1e-10 (relative
+  Frobenius, Procrustes-aligned), sigma within 1e-10 relative.
+* FP32 path (fp32_sparse at reduced m): Y within 1e-5 (Procrustes-aligned).
+  The reduced data is unique only up to an orthogonal k x k factor when
+  singular values nearly coincide (Prop. 3 and the footnote of Sec. III-B.2),
+  so the binding comparison aligns with the orthogonal Procrustes factor;
+  the per-column sign-aligned error and the subspace sine are reported.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import lspca as O
+from oracle import metrics as M
+from oracle import philox as P
+from paper_1709_07175_gb300 import lspca as L
+from paper_1709_07175_gb300 import synthetic as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1709_07175_gb300 import build
+    build.build()
+    c = L.Context(0)
+    yield c
+    c.close()
+
+
+def _omega_np(w):
+    if w.omega == "gaussian":
+        return P.omega_gaussian(w.omega_seed, w.n, w.k)
+    return P.omega_sparse(w.omega_seed, w.n, w.k, w.p)
+
+
+def _om(w):
+    return L.omega(w.omega, w.omega_seed, w.p)
+
+
+C1 = S.WORKLOADS["fp64_small"]
+C2S = S.WORKLOADS["fp32_sparse"].scaled(m=3001)          # 94 row tiles, ragged tail
+C2R = S.WORKLOADS["fp32_sparse"].scaled(m=2049, n=1000)   # ragged chunk and ragged rows
+
+
+@pytest.fixture(scope="module")
+def data():
+    out = {}
+    for w in (C1, C2S, C2R):
+        X = S.generate(w)
+        Om = _omega_np(w)
+        Xd = X.double().numpy()
+        fit = O.lspca_fit(Xd, Om, route="eig")
+        out[w.name + str(w.m) + "x" + str(w.n)] = (w, X, Xd, Om, fit)
+    return out
+
+
+def _get(data, w):
+    return data[w.name + str(w.m) + "x" + str(w.n)]
+
+
+# ------------------------------------------------------------------ Omega
+
+@pytest.mark.parametrize("n,k,p,seed", [(4096, 128, 64, 0), (1000, 37, 3, 12345678901), (513, 256, 64, 7)])
+def test_sparse_omega_bit_exact(ctx, n, k, p, seed):
+    om = L.omega("sparse", seed, p)
+    g = ctx.omega(om, n, k, torch.float64).cpu().numpy()
+    ref = P.omega_sparse(seed, n, k, p)
+    assert np.array_equal(g, ref)
+
+
+@pytest.mark.parametrize("n,k,seed", [(8192, 256, 0), (500, 20, 0), (77, 9, 2 ** 40 + 3)])
+def test_gaussian_omega_within_one_ulp(ctx, n, k, seed):
+    om = L.omega("gaussian", seed)
+    g = ctx.omega(om, n, k, torch.float32).cpu().numpy()
+    ref = P.omega_gaussian(seed, n, k).astype(np.float32)
+    gi = g.view(np.int32).astype(np.int64)
+    ri = ref.view(np.int32).astype(np.int64)
+    assert np.max(np.abs(gi - ri)) <= 1
+    # the BF16 form is the round-to-nearest-even of the FP32 value
+    gb = ctx.omega(om, n, k, torch.bfloat16).float().cpu().numpy()
+    assert np.array_equal(gb, torch.from_numpy(g).to(torch.bfloat16).float().numpy())
+
+
+# ------------------------------------------------------------------ pass S
+
+def test_sketch_fp64(ctx, data):
+    w, X, Xd, Om, fit = _get(data, C1)
+    U = ctx.sketch(X.cuda(), w.k, _om(w)).cpu().numpy()
+    ref = fit["U"]
+    assert np.linalg.norm(U - ref) / np.linalg.norm(ref) < 1e-13
+
+
+@pytest.mark.parametrize("wl", [C2S, C2R])
+def test_sketch_sparse_fp32(ctx, data, wl):
+    w, X, Xd, Om, fit = _get(data, wl)
+    U = ctx.sketch(X.cuda(), w.k, _om(w)).double().cpu().numpy()
+    ref = fit["U"]
+    # sequential FP32 sum of the nnz_c signed terms: |err| <= nnz_c u sum|terms|
+    bound = (np.abs(Xd) @ np.abs(Om)) * (np.count_nonzero(Om, axis=0) * 2.0 ** -24) + 1e-30
+    assert np.all(np.abs(U - ref) <= bound)
+
+
+# ------------------------------------------------------------------ pass F
+
+def test_chain_fp64(ctx, data):
+    w, X, Xd, Om, fit = _get(data, C1)
+    U = torch.from_numpy(fit["U"]).cuda()
+    F, G = ctx.chain(X.cuda(), U, want_gram=True)
+    F = F.cpu().numpy()
+    G = G.cpu().numpy()
+    assert np.linalg.norm(F - fit["F"]) / np.linalg.norm(fit["F"]) < 1e-13
+    assert np.linalg.norm(G - fit["G"]) / np.linalg.norm(fit["G"]) < 1e-13
+
+
+@pytest.mark.parametrize("wl", [C2S, C2R])
+def test_chain_fp32(ctx, data, wl):
+    w, X, Xd, Om, fit = _get(data, wl)
+    U32 = torch.from_numpy(fit["U"]).float()
+    Ud = U32.double().numpy()
+    F, G = ctx.chain(X.cuda(), U32.cuda(), want_gram=True)
+    Fref = Ud.T @ Xd
+    Gref = Ud.T @ Ud
+    # FP32 accumulation within a split, FP64 across splits
+    assert np.linalg.norm(F.cpu().numpy() - Fref) / np.linalg.norm(Fref) < 2e-6
+    assert np.linalg.norm(G.cpu().numpy() - Gref) / np.linalg.norm(Gref) < 2e-6
+
+
+# ------------------------------------------------------------------ the k x k step
+
+@pytest.mark.parametrize("wl", [C1, C2S])
+def test_decompose_matches_oracle_eig_route(ctx, data, wl):
+    w, X, Xd, Om, fit = _get(data, wl)
+    F = torch.from_numpy(fit["F"]).cuda()
+    V, sigma, rank = ctx.decompose(F, w.m, torch.float64)
+    V = V.cpu().numpy()
+    sigma = sigma.cpu().numpy()
+    assert int(rank.item()) == fit["rank"] == w.k
+    assert np.max(np.abs(sigma - fit["sigma"]) / fit["sigma"]) < 1e-11
+    assert np.abs(V.T @ V - np.eye(w.k)).max() < 1e-11
+    assert M.max_sine(fit["V"], V) < 1e-10
+    # columns with a clear gap agree individually (sign rule applied on both sides)
+    s = fit["sigma"]
+    gap = np.minimum(np.r_[np.inf, -np.diff(s)], np.r_[-np.diff(s), np.inf]) / s[0]
+    sep = gap > 1e-3
+    assert np.abs(V[:, sep] - fit["V"][:, sep]).max() < 1e-8
+
+
+# ------------------------------------------------------------------ full fits
+
+def _report_errors(Y, Yref, V, Vref):
+    return {"procrustes": M.procrustes_rel(Y, Yref), "signaligned": M.signaligned_rel(Y, Yref),
+            "sine": M.max_sine(Vref, V), "chordal": M.chordal(Vref, V)}
+
+
+def test_fit_fp64_parity(ctx, data):
+    w, X, Xd, Om, fit = _get(data, C1)
+    Xg = X.cuda()
+    r = ctx.fit(Xg, w.k, _om(w))
+    assert r.status == L.OK and r.report["rank"] == w.k
+    V = r.V.cpu().numpy()
+    Y = ctx.project(Xg, r.V).cpu().numpy()
+    Yref = O.project(Xd, fit["V"])
+    e = _report_errors(Y, Yref, V, fit["V"])
+    print("fp64_small", e)
+    assert e["procrustes"] < 1e-10
+    assert e["sine"] < 1e-10
+    assert np.max(np.abs(r.sigma.cpu().numpy() - fit["sigma"]) / fit["sigma"]) < 1e-10
+    # the FP64 path has well separated singular values: per-column agreement too
+    assert e["signaligned"] < 1e-8
+
+
+@pytest.mark.parametrize("wl", [C2S, C2R])
+def test_fit_fp32_parity(ctx, data, wl):
+    w, X, Xd, Om, fit = _get(data, wl)
+    Xg = X.cuda()
+    r = ctx.fit(Xg, w.k, _om(w))
+    assert r.status == L.OK
+    V = r.V.double().cpu().numpy()
+    Y = ctx.project(Xg, r.V).double().cpu().numpy()
+    Yref = O.project(Xd, fit["V"])
+    e = _report_errors(Y, Yref, V, fit["V"])
+    print(w.name, w.m, w.n, e)
+    assert e["procrustes"] < 1e-5
+    assert e["sine"] < 1e-4
+    assert np.max(np.abs(r.sigma.cpu().numpy() - fit["sigma"]) / fit["sigma"]) < 1e-5
+
+
+def test_fit_is_deterministic(ctx, data):
+    w, X, Xd, Om, fit = _get(data, C2S)
+    Xg = X.cuda()
+    a = ctx.fit(Xg, w.k, _om(w))
+    b = ctx.fit(Xg, w.k, _om(w))
+    assert torch.equal(a.V, b.V) and torch.equal(a.sigma, b.sigma)
+
+
+def test_force_simt_agrees(ctx, data):
+    w, X, Xd, Om, fit = _get(data, C2S)
+    Xg = X.cuda()
+    a = ctx.fit(Xg, w.k, _om(w))
+    b = ctx.fit(Xg, w.k, _om(w), flags=L.FORCE_SIMT)
+    Ya = ctx.project(Xg, a.V).double().cpu().numpy()
+    Yb = ctx.project(Xg, b.V).double().cpu().numpy()
+    assert M.procrustes_rel(Ya, Yb) < 1e-5
+
+
+# ------------------------------------------------------------------ SPCA path
+
+def test_spca_fp64_parity_and_prop2(ctx, data):
+    w, X, Xd, Om, fit = _get(data, C1)
+    Xg = X.cuda()
+    sp = O.spca_fit(Xd, Om, route="eig")
+    r = ctx.spca(Xg, w.k, _om(w))
+    Vs = r.V.cpu().numpy()
+    assert M.max_sine(sp["V"], Vs) < 1e-10
+    assert np.max(np.abs(r.sigma.cpu().numpy() - sp["sigma"]) / sp["sigma"]) < 1e-9
+    # Prop. 2 on the GPU: V^s and V^l span the same subspace
+    rl = ctx.fit(Xg, w.k, _om(w))
+    assert M.max_sine(rl.V.cpu().numpy(), Vs) < 1e-10
+    # Prop. 3: equal pairwise distances in the reduced space
+    Ys = ctx.project(Xg, r.V).cpu().numpy()
+    Yl = ctx.project(Xg, rl.V).cpu().numpy()
+    rng = np.random.default_rng(0)
+    i, j = rng.integers(0, w.m, 2000), rng.integers(0, w.m, 2000)
+    keep = i != j
+    ds = np.linalg.norm(Ys[i[keep]] - Ys[j[keep]], axis=1)
+    dl = np.linalg.norm(Yl[i[keep]] - Yl[j[keep]], axis=1)
+    assert np.max(np.abs(ds - dl) / dl) < 1e-10
+
+
+def test_spca_fp32_parity(ctx, data):
+    w, X, Xd, Om, fit = _get(data, C2S)
+    Xg = X.cuda()
+    sp = O.spca_fit(Xd, Om, route="eig")
+    r = ctx.spca(Xg, w.k, _om(w))
+    Y = ctx.project(Xg, r.V).double().cpu().numpy()
+    Yref = O.project(Xd, sp["V"])
+    assert M.procrustes_rel(Y, Yref) < 1e-5
+    assert np.max(np.abs(r.sigma.cpu().numpy() - sp["sigma"]) / sp["sigma"]) < 1e-4
+
+
+# ------------------------------------------------------------------ projection
+
+@pytest.mark.parametrize("wl,tol", [(C1, 1e-13), (C2S, 2e-6), (C2R, 2e-6)])
+def test_project_matches_oracle(ctx, data, wl, tol):
+    w, X, Xd, Om, fit = _get(data, wl)
+    rt = torch.float64 if w.dtype == "f64" else torch.float32
+    V = torch.from_numpy(fit["V"]).to(rt)
+    Y = ctx.project(X.cuda(), V.cuda()).double().cpu().numpy()
+    Yref = Xd @ V.double().numpy()
+    assert np.linalg.norm(Y - Yref) / np.linalg.norm(Yref) < tol
+
+
+# ------------------------------------------------------------------ edge cases
+
+def test_rank_deficient_input(ctx):
+    X, B = S.rank_r_exact(4000, 1000, 5, seed=3)
+    Xg = X.cuda()
+    r = ctx.fit(Xg, 8, L.omega("gaussian", 9))
+    assert r.status == L.WARN_RANK_DEFICIENT
+    assert r.report["rank"] == 5 and int(r.rank.item()) == 5
+    V = r.V.cpu().numpy()
+    assert np.all(V[:, 5:] == 0) and np.all(r.sigma.cpu().numpy()[5:] == 0)
+    assert M.max_sine(B.numpy(), V[:, :5]) < 1e-9
+
+
+def test_nonfinite_input_is_reported(ctx):
+    w = C1
+    X = S.generate(w).clone()
+    X[17, 3] = float("nan")
+    V = torch.empty(w.n, w.k, dtype=torch.float64, device="cuda")
+    sig = torch.empty(w.k, dtype=torch.float64, device="cuda")
+    rep = L.lspca_report()
+    rc = L.lspca_fit(ctx.handle, X.cuda(), w.k, _om(w), 0, V, sig, None, None, None, rep)
+    assert rc == L.ERR_NUMERIC
+    assert ctx.sync_status() == L.OK  # the report consumed the status word
+
+
+@pytest.mark.parametrize("bad", ["k0", "kbig", "ldx", "omega_p0", "e4m3_gauss", "null_v"])
+def test_invalid_arguments(ctx, bad):
+    X = torch.zeros(64, 32, dtype=torch.float32, device="cuda")
+    V = torch.empty(32, 4, dtype=torch.float32, device="cuda")
+    sig = torch.empty(4, dtype=torch.float64, device="cuda")
+    lib = L.load()
+    om = L.omega("gaussian", 0)
+    args = dict(x=X.data_ptr(), xt=L.LSPCA_F32, m=64, n=32, ldx=32, k=4, om=om, v=V.data_ptr())
+    if bad == "k0":
+        args["k"] = 0
+    elif bad == "kbig":
+        args["k"] = 33
+    elif bad == "ldx":
+        args["ldx"] = 31
+    elif bad == "omega_p0":
+        args["om"] = L.omega("sparse", 0, 0)
+    elif bad == "e4m3_gauss":
+        args["xt"] = L.LSPCA_E4M3
+    elif bad == "null_v":
+        args["v"] = None
+    rc = lib.lspca_fit(ctx.handle, args["x"], args["xt"], args["m"], args["n"], args["ldx"], args["k"], args["om"], 0,
+                       args["v"], sig.data_ptr(), None, None, None, None)
+    assert rc == L.ERR_INVALID
+
+
+def test_alg4_slicing_invariance(ctx, data):
+    """Algorithm 4: F summed over horizontal slices equals F of the whole (FP64 path)."""
+    w, X, Xd, Om, fit = _get(data, C1)
+    Xg = X.cuda()
+    U = ctx.sketch(Xg, w.k, _om(w))
+    F, _ = ctx.chain(Xg, U)
+    parts = [0, 333, 1000, 1999, w.m]
+    Fs = sum(ctx.chain(Xg[a:b], U[a:b])[0] for a, b in zip(parts[:-1], parts[1:]))
+    assert torch.allclose(F, Fs, rtol=1e-12, atol=1e-12 * F.abs().max().item())
