@@ -103,6 +103,7 @@ struct SketchBufs {
   int32_t* counts = nullptr;
   int32_t* col_ptr = nullptr;
   int32_t* entries = nullptr;
+  int32_t* off = nullptr;
   void* omega = nullptr;  // dense Omega (n x k, result type) for the SIMT path
   void* omega_t = nullptr;  // dense Omega^T (k x n BF16) for the tensor-core path
 };
@@ -112,6 +113,7 @@ void plan_sketch(Plan& P, SketchBufs& b, int xt, int64_t n, int k, const lspca_o
     b.counts = (int32_t*)P.take((size_t)k * 4);
     b.col_ptr = (int32_t*)P.take((size_t)(k + 1) * 4);
     b.entries = (int32_t*)P.take((size_t)n * k * 4);
+    b.off = (int32_t*)P.take(sketch_off_bytes(n, k));
   } else if (tc) {
     b.omega_t = P.take((size_t)n * k * 2);
   } else {
@@ -126,7 +128,7 @@ void run_sketch(lspca_ctx* ctx, Launcher& L, const void* X, int xt, int64_t m, i
   if (om.kind == LSPCA_OMEGA_VERY_SPARSE) {
     launch_omega_csc(L, om, n, k, b.counts, b.col_ptr, b.entries);
     mark(1);
-    launch_sketch_sparse(L, X, xt, m, n, ldx, k, b.col_ptr, b.entries, U, k, ctx->d_absmax, ctx->d_status);
+    launch_sketch_sparse(L, X, xt, m, n, ldx, k, b.col_ptr, b.entries, b.off, U, k, ctx->d_absmax, ctx->d_status);
     mark(2);
     return;
   }
@@ -181,7 +183,7 @@ void plan_chain(Plan& P, ChainBufs& b, int xt, int64_t m, int64_t n, int k, bool
 void run_chain(lspca_ctx* ctx, Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_t ldx, const void* U,
                int k, bool tc, ChainBufs& b, double* F, double* G, const Mark& mark) {
   if (tc) {
-    tc_chain_main(L, X, xt, m, n, ldx, (const float*)U, k, b.tcw, ctx->d_absmax, G != nullptr);
+    tc_chain_main(L, X, xt, m, n, ldx, (const float*)U, k, b.tcw, ctx->d_absmax, ctx->d_status, G != nullptr);
     mark(3);
     tc_chain_reduce(L, n, k, b.tcw, F, G);
     mark(4);
@@ -199,8 +201,8 @@ void run_chain(lspca_ctx* ctx, Launcher& L, const void* X, int xt, int64_t m, in
   mark(4);
 }
 
-bool use_tc_chain(int xt, uint32_t flags) {
-  return !(flags & LSPCA_FORCE_SIMT) && (xt == LSPCA_F32 || xt == LSPCA_BF16) && tc_available();
+bool use_tc_chain(int xt, uint32_t flags, int k = 4) {
+  return !(flags & LSPCA_FORCE_SIMT) && (xt == LSPCA_F32 || xt == LSPCA_BF16) && (k % 4) == 0 && tc_available();
 }
 bool use_tc_sketch(int xt, const lspca_omega& om, uint32_t flags) {
   return !(flags & LSPCA_FORCE_SIMT) && xt == LSPCA_BF16 && om.kind == LSPCA_OMEGA_GAUSSIAN && tc_available();
@@ -221,7 +223,7 @@ int fit_impl(lspca_ctx* ctx, const void* X, int32_t xt, int64_t m, int64_t n, in
   cudaStream_t s = (cudaStream_t)stream;
   Launcher L{s, &ctx->launches, ctx->num_sms};
   const bool tc_s = use_tc_sketch(xt, om, flags);
-  const bool tc_f = use_tc_chain(xt, flags);
+  const bool tc_f = use_tc_chain(xt, flags, k);
   const size_t asz = acc_size(xt);
 
   SketchBufs sb;
@@ -260,6 +262,8 @@ int fit_impl(lspca_ctx* ctx, const void* X, int32_t xt, int64_t m, int64_t n, in
   cudaMemsetAsync(ctx->d_absmax, 0, 2 * sizeof(float), s);
   mark(0);
   run_sketch(ctx, L, X, xt, m, n, ldx, k, om, tc_s, sb, U, mark);
+  if (tc_f && om.kind == LSPCA_OMEGA_GAUSSIAN && xt == LSPCA_F32)
+    launch_scan_x(L, U, LSPCA_F32, m, k, k, ctx->d_absmax + 1, ctx->d_status);  // max|U| for the FP16 scales
   run_chain(ctx, L, X, xt, m, n, ldx, U, k, tc_f, cb, F, want_g ? G : nullptr, mark);
   if (spca) {
     launch_tsqr(L, U, xt == LSPCA_F64, m, k, qrws, R);
@@ -362,18 +366,8 @@ int lspca_project(lspca_ctx* ctx, const void* X, int32_t xt, int64_t m, int64_t 
   if (cudaSetDevice(ctx->device) != cudaSuccess) return LSPCA_ERR_CUDA;
   cudaStream_t s = (cudaStream_t)stream;
   Launcher L{s, &ctx->launches, ctx->num_sms};
-  if (xt != LSPCA_F64 && tc_available()) {
-    TcProjectWs pw;
-    Plan p0;
-    plan_tc_project(nullptr, pw, xt, n, k);
-    p0.take(pw.bytes);
-    if ((st = ensure_ws(ctx, p0.off + 4096, s))) return st;
-    plan_tc_project((char*)ctx->ws, pw, xt, n, k);
-    tc_project(L, X, xt, m, n, ldx, (const float*)V, k, pw, (float*)Y);
-  } else {
-    launch_gemm_simt(L, m, k, n, X, xt, ldx, false, V, acc_dt(xt), k, false, Y, xt == LSPCA_F64, k, 0, 1,
-                     xt == LSPCA_F64, false);
-  }
+  launch_gemm_simt(L, m, k, n, X, xt, ldx, false, V, acc_dt(xt), k, false, Y, xt == LSPCA_F64, k, 0, 1,
+                   xt == LSPCA_F64, false);
   return cuda_status(cudaGetLastError());
 }
 
@@ -421,7 +415,7 @@ int lspca_chain(lspca_ctx* ctx, const void* X, int32_t xt, int64_t m, int64_t n,
   if (cudaSetDevice(ctx->device) != cudaSuccess) return LSPCA_ERR_CUDA;
   cudaStream_t s = (cudaStream_t)stream;
   Launcher L{s, &ctx->launches, ctx->num_sms};
-  const bool tc = use_tc_chain(xt, flags);
+  const bool tc = use_tc_chain(xt, flags, k) && aligned16(U);
   ChainBufs cb;
   Plan p0;
   plan_chain(p0, cb, xt, m, n, k, G != nullptr, tc, ctx->num_sms);

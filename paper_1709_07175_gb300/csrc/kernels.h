@@ -38,9 +38,12 @@ void launch_reduce_splits(Launcher& L, const double* part, int splits, int64_t s
 // ---- K1: pass S -----------------------------------------------------------
 // U = X Omega with very sparse Omega (CSC lists); U is FP64 for F64 X, else FP32.
 // absmax[0] |= max|X|, absmax[1] |= max|U| (FP32 bit-pattern max); status |= ST_NONFINITE.
+// `off` is a k x (chunks + 1) int32 scratch (sketch_off_bytes) used when the
+// per-(column, chunk) offset table does not fit in shared memory.
+size_t sketch_off_bytes(int64_t n, int k);
 void launch_sketch_sparse(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_t ldx, int k,
-                          const int32_t* col_ptr, const int32_t* entries, void* U, int64_t ldu, float* absmax,
-                          int* status);
+                          const int32_t* col_ptr, const int32_t* entries, int32_t* off, void* U, int64_t ldu,
+                          float* absmax, int* status);
 // Scan X for NaN/Inf and its largest magnitude (dense-Omega paths).
 void launch_scan_x(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_t ldx, float* absmax, int* status);
 
@@ -48,8 +51,9 @@ void launch_scan_x(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int
 struct SmallWs {
   double* Hpart;   // splits x k x k
   double* H;       // k x k
-  float* h32;      // k x k (global Jacobi scratch when k > 128)
-  float* w32;      // k x k
+  float* h32;      // k x k (seed scratch when k > 128)
+  float* w32;      // k x k (seed scratch when k > 128)
+  float* q32;      // k x k (inverse-iteration scratch)
   double* Xa;      // k x k
   double* Xb;      // k x k
   double* Rm;      // k x k
@@ -57,12 +61,16 @@ struct SmallWs {
   double* S;       // k x k
   double* E;       // k x k
   double* lam;     // k
-  double* scal;    // 8 scalars
+  double* scal;    // 8 scalars, sigma copy (k), sqrt(S_rr) (k), order (k int32)
   double* Vd;      // n x k
-  int32_t* sweeps; // 1
+  int32_t* sweeps; // 1: eigenvalue clusters found by the FP32 seed
   int h_splits;
 };
 size_t small_ws_bytes(int k, int64_t n, int* h_splits);
+// FP32 eigen seed of H (k x k FP64): eigenvectors -> Xout (k x k FP64, columns),
+// eigenvalues -> lam (ascending), scal[1] = ||H||_F.
+void launch_eig_seed(Launcher& L, const double* H, int k, float* gA, float* gZ, float* gQ, double* Xout,
+                     double* lam, double* scal, int32_t* nclusters);
 void carve_small_ws(SmallWs& w, void* base, int k, int64_t n);
 void launch_decompose(Launcher& L, SmallWs& w, const double* F, int k, int64_t n, int64_t m, bool v_f64, void* V,
                       double* sigma, int32_t* rank, int* status);

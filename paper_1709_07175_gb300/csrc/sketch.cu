@@ -34,18 +34,30 @@ struct SketchCfg {
   static constexpr int RG = 32 / EPV;                            // row groups per chunk
   static constexpr int PITCH = ROWS + 1;
   static constexpr int MAX_CPW = 16;                             // k <= 256 -> 16 columns per warp
-  static constexpr int ENT_CACHE = 12288;                        // Omega entries cached in SMEM
-  static size_t smem_bytes(int k, bool cache_entries) {
-    return (size_t)(2 * W * PITCH + ROWS * (k + 1)) * sizeof(Acc) +
-           (cache_entries ? (size_t)ENT_CACHE * 4 + (size_t)(k + 1) * 4 : 0);
+  static constexpr int ENT_CACHE = 12288;                        // Omega entries cached in SMEM (int16)
+  static constexpr int OFF_CACHE = 4096;                         // (column, chunk) offsets in SMEM
+  static size_t smem_bytes(int k) {
+    return (size_t)(2 * W * PITCH + ROWS * (k + 1)) * sizeof(Acc) + (size_t)ENT_CACHE * 2 + (size_t)OFF_CACHE * 4;
   }
 };
 
+__device__ __forceinline__ float4 ldg_nc_na(const void* p) {
+  float4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(p));
+  return v;
+}
+
+// Entry encoding in the CSC lists: e = s * (j + 1).  The kernel needs, for
+// every column c and chunk q, the first list position with j >= q W; it builds
+// that table in shared memory (one thread per column) when it fits, so the
+// gather of a chunk walks fixed ranges [off(c, q), off(c, q + 1)).
 template <int DT>
 __global__ void __launch_bounds__(512, 1)
     sketch_sparse_kernel(const void* __restrict__ Xv, int64_t m, int64_t n, int64_t ldx, int k,
-                         const int32_t* __restrict__ col_ptr_g, const int32_t* __restrict__ entries_g,
-                         void* __restrict__ Uv, int64_t ldu, float* absmax, int* status) {
+                         const int32_t* __restrict__ col_ptr, const int32_t* __restrict__ entries_g,
+                         int32_t* __restrict__ off_g, void* __restrict__ Uv, int64_t ldu, float* absmax, int* status) {
   using C = SketchCfg<DT>;
   using T = typename C::T;
   using Acc = typename C::Acc;
@@ -53,42 +65,52 @@ __global__ void __launch_bounds__(512, 1)
   Acc* buf0 = reinterpret_cast<Acc*>(smem_raw);
   Acc* buf1 = buf0 + C::W * C::PITCH;
   Acc* us = buf1 + C::W * C::PITCH;
-  int32_t* ent_s = reinterpret_cast<int32_t*>(us + C::ROWS * (k + 1));
-  int32_t* cp_s = ent_s + C::ENT_CACHE;
+  int16_t* ent_s = reinterpret_cast<int16_t*>(us + C::ROWS * (k + 1));
+  int32_t* off_s = reinterpret_cast<int32_t*>(ent_s + C::ENT_CACHE);
 
   const T* X = reinterpret_cast<const T*>(Xv);
   Acc* U = reinterpret_cast<Acc*>(Uv);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int rr = lane % C::EPV, cc = lane / C::EPV;
+  const int nchunks = (int)((n + C::W - 1) / C::W);
+  const int noff = k * (nchunks + 1);
 
-  const int32_t* entries = entries_g;
-  const int32_t* col_ptr = col_ptr_g;
-  const int nnz = col_ptr_g[k];
-  if (nnz <= C::ENT_CACHE) {
-    for (int e = tid; e < nnz; e += C::THREADS) ent_s[e] = entries_g[e];
-    for (int e = tid; e <= k; e += C::THREADS) cp_s[e] = col_ptr_g[e];
-    entries = ent_s;
-    col_ptr = cp_s;
+  // Omega lists: int16 copies in SMEM when they fit (n < 32767), else global.
+  const int nnz = col_ptr[k];
+  const bool ent_in_smem = nnz <= C::ENT_CACHE && n < 32767;
+  if (ent_in_smem)
+    for (int e = tid; e < nnz; e += C::THREADS) ent_s[e] = (int16_t)entries_g[e];
+  // chunk offsets: SMEM table when small, else a global table (built once per call)
+  int32_t* off = (noff <= C::OFF_CACHE) ? off_s : off_g;
+  for (int c = tid; c < k; c += C::THREADS) {
+    int pos = col_ptr[c];
+    const int end = col_ptr[c + 1];
+    for (int q = 0; q <= nchunks; ++q) {
+      const int64_t lim = (int64_t)q * C::W;
+      while (pos < end) {
+        const int e = entries_g[pos];
+        if ((int64_t)((e > 0 ? e : -e) - 1) >= lim) break;
+        ++pos;
+      }
+      off[c * (nchunks + 1) + q] = pos;
+    }
+    off[c * (nchunks + 1) + nchunks] = end;
   }
 
   const int64_t ntiles = (m + C::ROWS - 1) / C::ROWS;
-  const int nchunks = (int)((n + C::W - 1) / C::W);
   const int64_t my_tiles = ((int64_t)blockIdx.x < ntiles) ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
   const int64_t steps = my_tiles * nchunks;
   __syncthreads();
   if (steps == 0) return;
 
-  uint4 regs[C::VPT];
+  float4 regs[C::VPT];
   float amax = 0.f, amax_u = 0.f;
   bool bad = false;
   Acc acc[C::MAX_CPW];
-  int pos[C::MAX_CPW], pend[C::MAX_CPW];
 
-  auto tile_of = [&](int64_t st) -> int64_t { return (int64_t)blockIdx.x + (st / nchunks) * gridDim.x; };
-
-  auto load = [&](int64_t st) {
-    const int64_t r0 = tile_of(st) * C::ROWS;
-    const int64_t j0 = (int64_t)(st % nchunks) * C::W;
+  auto load = [&](int64_t tile, int chunk) {
+    const int64_t r0 = tile * C::ROWS;
+    const int64_t j0 = (int64_t)chunk * C::W;
 #pragma unroll
     for (int q = 0; q < C::VPT; ++q) {
       const int s = q * 16 + warp;
@@ -96,14 +118,14 @@ __global__ void __launch_bounds__(512, 1)
       const int vc = (s / C::RG) * (32 / C::EPV) + cc;
       const int64_t gr = r0 + row, gj = j0 + (int64_t)vc * C::EPV;
       if (gr < m && gj < n)
-        regs[q] = __ldg(reinterpret_cast<const uint4*>(X + gr * ldx + gj));
+        regs[q] = ldg_nc_na(X + gr * ldx + gj);
       else
-        regs[q] = make_uint4(0u, 0u, 0u, 0u);
+        regs[q] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
   };
 
-  auto store = [&](int64_t st, Acc* buf) {
-    const int64_t j0 = (int64_t)(st % nchunks) * C::W;
+  auto store = [&](int chunk, Acc* buf) {
+    const int64_t j0 = (int64_t)chunk * C::W;
 #pragma unroll
     for (int q = 0; q < C::VPT; ++q) {
       const int s = q * 16 + warp;
@@ -123,45 +145,50 @@ __global__ void __launch_bounds__(512, 1)
   };
 
   const int cpw = (k + 15) / 16;
-  load(0);
-  store(0, buf0);
+  int64_t tile = blockIdx.x;
+  int chunk = 0;
+  load(tile, chunk);
+  store(chunk, buf0);
   __syncthreads();
   for (int64_t st = 0; st < steps; ++st) {
     Acc* cur = (st & 1) ? buf1 : buf0;
     Acc* nxt = (st & 1) ? buf0 : buf1;
-    const int chunk = (int)(st % nchunks);
-    const int64_t j0 = (int64_t)chunk * C::W;
+    const int j0 = chunk * C::W;
     if (chunk == 0) {
 #pragma unroll
-      for (int t = 0; t < C::MAX_CPW; ++t) {
-        const int c = warp + 16 * t;
-        const bool ok = (t < cpw) && (c < k);
-        pos[t] = ok ? col_ptr[c] : 0;
-        pend[t] = ok ? col_ptr[c + 1] : 0;
-        acc[t] = Acc(0);
-      }
+      for (int t = 0; t < C::MAX_CPW; ++t) acc[t] = Acc(0);
     }
-    if (st + 1 < steps) load(st + 1);
-    // gather: one entry per live column per round
-    const int jend = (int)(j0 + C::W);
-    unsigned live = 0;
+    int64_t ntile = tile;
+    int nchunk = chunk + 1;
+    if (nchunk == nchunks) {
+      nchunk = 0;
+      ntile += gridDim.x;
+    }
+    if (st + 1 < steps) load(ntile, nchunk);
+    // gather: for each owned column, the fixed range of its entries in this chunk
 #pragma unroll
-    for (int t = 0; t < C::MAX_CPW; ++t) live |= (pos[t] < pend[t]) ? (1u << t) : 0u;
-    while (live) {
-#pragma unroll
-      for (int t = 0; t < C::MAX_CPW; ++t) {
-        if (live & (1u << t)) {
-          const int32_t e = entries[pos[t]];
-          const int j = (e > 0 ? e : -e) - 1;
-          if (j < jend) {
-            const Acc v = cur[(j - (int)j0) * C::PITCH + lane];
-            acc[t] += (e > 0) ? v : -v;
-            ++pos[t];
-            if (pos[t] >= pend[t]) live &= ~(1u << t);
-          } else {
-            live &= ~(1u << t);
+    for (int t = 0; t < C::MAX_CPW; ++t) {
+      const int c = warp + 16 * t;
+      if (t < cpw && c < k) {
+        const int b = off[c * (nchunks + 1) + chunk];
+        const int e = off[c * (nchunks + 1) + chunk + 1];
+        Acc a = acc[t];
+        if (ent_in_smem) {
+#pragma unroll 4
+          for (int i = b; i < e; ++i) {
+            const int en = ent_s[i];
+            const Acc v = cur[((en > 0 ? en : -en) - 1 - j0) * C::PITCH + lane];
+            a += (en > 0) ? v : -v;
+          }
+        } else {
+#pragma unroll 4
+          for (int i = b; i < e; ++i) {
+            const int en = __ldg(entries_g + i);
+            const Acc v = cur[((en > 0 ? en : -en) - 1 - j0) * C::PITCH + lane];
+            a += (en > 0) ? v : -v;
           }
         }
+        acc[t] = a;
       }
     }
     const bool last = (chunk == nchunks - 1);
@@ -172,10 +199,10 @@ __global__ void __launch_bounds__(512, 1)
         if (t < cpw && c < k) us[lane * (k + 1) + c] = acc[t];
       }
     }
-    if (st + 1 < steps) store(st + 1, nxt);
+    if (st + 1 < steps) store(nchunk, nxt);
     __syncthreads();
     if (last) {
-      const int64_t r0 = tile_of(st) * C::ROWS;
+      const int64_t r0 = tile * C::ROWS;
       for (int e = tid; e < C::ROWS * k; e += C::THREADS) {
         const int r = e / k, c = e % k;
         if (r0 + r < m) {
@@ -186,6 +213,8 @@ __global__ void __launch_bounds__(512, 1)
       }
       __syncthreads();
     }
+    tile = ntile;
+    chunk = nchunk;
   }
   amax = warp_max(amax);
   amax_u = warp_max(amax_u);
@@ -199,26 +228,39 @@ __global__ void __launch_bounds__(512, 1)
 
 template <int DT>
 static void sketch_sparse_dispatch(Launcher& L, const void* X, int64_t m, int64_t n, int64_t ldx, int k,
-                                   const int32_t* col_ptr, const int32_t* entries, void* U, int64_t ldu, float* absmax,
-                                   int* status) {
+                                   const int32_t* col_ptr, const int32_t* entries, int32_t* off, void* U, int64_t ldu,
+                                   float* absmax, int* status) {
   using C = SketchCfg<DT>;
-  const size_t smem = C::smem_bytes(k, true);
+  const size_t smem = C::smem_bytes(k);
   cudaFuncSetAttribute(sketch_sparse_kernel<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int64_t ntiles = (m + C::ROWS - 1) / C::ROWS;
   const int grid = (int)(ntiles < L.num_sms ? ntiles : L.num_sms);
-  sketch_sparse_kernel<DT><<<grid, C::THREADS, smem, L.stream>>>(X, m, n, ldx, k, col_ptr, entries, U, ldu, absmax,
-                                                                  status);
+  sketch_sparse_kernel<DT><<<grid, C::THREADS, smem, L.stream>>>(X, m, n, ldx, k, col_ptr, entries, off, U, ldu,
+                                                                  absmax, status);
   L.count(1);
 }
 
+size_t sketch_off_bytes(int64_t n, int k) {
+  // worst case over the element types: chunks of 128 columns
+  return (size_t)k * (size_t)((n + 127) / 128 + 1) * 4;
+}
+
 void launch_sketch_sparse(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_t ldx, int k,
-                          const int32_t* col_ptr, const int32_t* entries, void* U, int64_t ldu, float* absmax,
-                          int* status) {
+                          const int32_t* col_ptr, const int32_t* entries, int32_t* off, void* U, int64_t ldu,
+                          float* absmax, int* status) {
   switch (xt) {
-    case LSPCA_F64: sketch_sparse_dispatch<LSPCA_F64>(L, X, m, n, ldx, k, col_ptr, entries, U, ldu, absmax, status); break;
-    case LSPCA_F32: sketch_sparse_dispatch<LSPCA_F32>(L, X, m, n, ldx, k, col_ptr, entries, U, ldu, absmax, status); break;
-    case LSPCA_BF16: sketch_sparse_dispatch<LSPCA_BF16>(L, X, m, n, ldx, k, col_ptr, entries, U, ldu, absmax, status); break;
-    case LSPCA_E4M3: sketch_sparse_dispatch<LSPCA_E4M3>(L, X, m, n, ldx, k, col_ptr, entries, U, ldu, absmax, status); break;
+    case LSPCA_F64:
+      sketch_sparse_dispatch<LSPCA_F64>(L, X, m, n, ldx, k, col_ptr, entries, off, U, ldu, absmax, status);
+      break;
+    case LSPCA_F32:
+      sketch_sparse_dispatch<LSPCA_F32>(L, X, m, n, ldx, k, col_ptr, entries, off, U, ldu, absmax, status);
+      break;
+    case LSPCA_BF16:
+      sketch_sparse_dispatch<LSPCA_BF16>(L, X, m, n, ldx, k, col_ptr, entries, off, U, ldu, absmax, status);
+      break;
+    case LSPCA_E4M3:
+      sketch_sparse_dispatch<LSPCA_E4M3>(L, X, m, n, ldx, k, col_ptr, entries, off, U, ldu, absmax, status);
+      break;
   }
 }
 

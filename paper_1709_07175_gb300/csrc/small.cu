@@ -5,9 +5,9 @@
 // column dropped, sigma_i = 0).
 //
 // GB300 executes FP64 at a small fraction of its FP32 rate, so the eigensolve
-// is split into an FP32 cyclic Jacobi on one CTA (the seed) and FP64 iterative
-// refinement of the whole eigenvector matrix built from k x k FP64 products
-// spread over many CTAs (Ogita & Aishima, "Iterative refinement for symmetric
+// is split into an FP32 seed on one CTA (tridiagonalisation, bisection and
+// inverse iteration, eigseed.cu) and FP64 iterative refinement of the whole
+// eigenvector matrix built from k x k FP64 products spread over many CTAs (Ogita & Aishima, "Iterative refinement for symmetric
 // eigenvalue decomposition", Japan J. Indust. Appl. Math. 35, 2018: one step
 // forms R = I - X^T X, S = X^T H X, lambda_i = s_ii / (1 - r_ii),
 // E_ij = (s_ij + lambda_j r_ij) / (lambda_j - lambda_i) for separated pairs,
@@ -19,7 +19,7 @@
 
 namespace lspca {
 
-constexpr int kRefineIters = 3;
+constexpr int kRefineIters = 2;
 constexpr int kJacobiMaxSweeps = 16;
 constexpr int kJacobiThreads = 1024;
 
@@ -32,9 +32,9 @@ size_t small_ws_bytes(int k, int64_t n, int* h_splits) {
   size_t b = 0;
   b += (size_t)hs * kk * 8;            // Hpart
   b += kk * 8;                          // H
-  b += kk * 4 * 2;                      // h32, w32
+  b += kk * 4 * 3;                      // seed scratch: A, Z, inverse-iteration q
   b += kk * 8 * 6;                      // Xa Xb Rm T S E
-  b += (size_t)k * 8 + 64;              // lam, scal
+  b += (size_t)k * 8 + 64 + (size_t)k * 24;  // lam, scal (+ src, sd)
   b += (size_t)n * k * 8;               // Vd
   b += 64;                              // sweeps
   return b + 16 * 256;                  // alignment slack
@@ -53,6 +53,7 @@ void carve_small_ws(SmallWs& w, void* base, int k, int64_t n) {
   w.H = (double*)take(kk * 8);
   w.h32 = (float*)take(kk * 4);
   w.w32 = (float*)take(kk * 4);
+  w.q32 = (float*)take(kk * 4);
   w.Xa = (double*)take(kk * 8);
   w.Xb = (double*)take(kk * 8);
   w.Rm = (double*)take(kk * 8);
@@ -60,118 +61,9 @@ void carve_small_ws(SmallWs& w, void* base, int k, int64_t n) {
   w.S = (double*)take(kk * 8);
   w.E = (double*)take(kk * 8);
   w.lam = (double*)take((size_t)k * 8);
-  w.scal = (double*)take(64);
+  w.scal = (double*)take(64 + (size_t)k * 24);
   w.Vd = (double*)take((size_t)n * k * 8);
   w.sweeps = (int32_t*)take(64);
-}
-
-// Round-robin ("circle") pairing: k2 players (k2 even), round t, pair r.
-__device__ __forceinline__ void rr_pair(int k2, int t, int r, int& p, int& q) {
-  const int K1 = k2 - 1;
-  auto player = [&](int slot) { return slot == 0 ? 0 : 1 + ((slot - 1 + t) % K1); };
-  const int a = player(r), b = player(k2 - 1 - r);
-  p = a < b ? a : b;
-  q = a < b ? b : a;
-}
-
-// FP32 cyclic Jacobi on H / scale.  One CTA of 1024 threads; H and W live in
-// shared memory for k <= 128 and in the global scratch otherwise.  Rotations of
-// one round act on disjoint index pairs: rows first, then columns (A <- J^T A J)
-// and the columns of W (W <- W J).
-__global__ void __launch_bounds__(kJacobiThreads) jacobi32_kernel(const double* __restrict__ H, int k, float* hg,
-                                                                  float* wg, double* Xout, double* lam_out,
-                                                                  int32_t* sweeps_out, int* status) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ float cs[128], sn[128];
-  __shared__ int pp[128], qq[128];
-  __shared__ int rotated;
-  __shared__ float scale_s;
-  const bool in_smem = k <= 128;
-  float* h = in_smem ? reinterpret_cast<float*>(smem_raw) : hg;
-  float* w = in_smem ? reinterpret_cast<float*>(smem_raw) + k * k : wg;
-  const int tid = threadIdx.x;
-  if (tid == 0) {
-    double mx = 0.0;
-    for (int i = 0; i < k; ++i) mx = fmax(mx, fabs(H[(int64_t)i * k + i]));
-    scale_s = (float)(mx > 0.0 ? 1.0 / mx : 1.0);
-  }
-  __syncthreads();
-  const double sc = (double)scale_s;
-  for (int e = tid; e < k * k; e += kJacobiThreads) {
-    h[e] = (float)(H[e] * sc);
-    w[e] = (e / k == e % k) ? 1.f : 0.f;
-  }
-  const int k2 = (k % 2) ? k + 1 : k;
-  const int npairs = k2 / 2;
-  int sweep = 0;
-  for (sweep = 0; sweep < kJacobiMaxSweeps; ++sweep) {
-    if (tid == 0) rotated = 0;
-    __syncthreads();
-    for (int t = 0; t < k2 - 1; ++t) {
-      if (tid < npairs) {
-        int p, q;
-        rr_pair(k2, t, tid, p, q);
-        float c = 1.f, s = 0.f;
-        if (q < k) {
-          const float app = h[p * k + p], aqq = h[q * k + q], apq = h[p * k + q];
-          // relative criterion, with a floor at FP32 rounding noise of the
-          // scaled matrix (max diagonal = 1): below it the FP64 refinement takes over
-          const float thr = fmaxf(1e-7f * sqrtf(fabsf(app * aqq)), 1e-6f);
-          if (fabsf(apq) > thr) {
-            const float tau = (aqq - app) / (2.f * apq);
-            float tt = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
-            c = rsqrtf(1.f + tt * tt);
-            s = tt * c;
-            rotated = 1;
-          }
-        } else {
-          q = p;  // dummy partner of an odd k: no rotation
-        }
-        cs[tid] = c;
-        sn[tid] = s;
-        pp[tid] = p;
-        qq[tid] = q;
-      }
-      __syncthreads();
-      // rows p, q of h
-      for (int e = tid; e < npairs * k; e += kJacobiThreads) {
-        const int r = e / k, j = e % k;
-        const int p = pp[r], q = qq[r];
-        if (p == q || sn[r] == 0.f) continue;
-        const float c = cs[r], s = sn[r];
-        const float hp = h[p * k + j], hq = h[q * k + j];
-        h[p * k + j] = c * hp - s * hq;
-        h[q * k + j] = s * hp + c * hq;
-      }
-      __syncthreads();
-      // columns p, q of h and of w
-      for (int e = tid; e < npairs * k; e += kJacobiThreads) {
-        const int r = e / k, i = e % k;
-        const int p = pp[r], q = qq[r];
-        if (p == q || sn[r] == 0.f) continue;
-        const float c = cs[r], s = sn[r];
-        const float hp = h[i * k + p], hq = h[i * k + q];
-        h[i * k + p] = c * hp - s * hq;
-        h[i * k + q] = s * hp + c * hq;
-        const float wp = w[i * k + p], wq = w[i * k + q];
-        w[i * k + p] = c * wp - s * wq;
-        w[i * k + q] = s * wp + c * wq;
-      }
-      __syncthreads();
-      if (tid < npairs) {
-        const int p = pp[tid], q = qq[tid];
-        if (p != q && sn[tid] != 0.f) {
-          h[p * k + q] = 0.f;
-          h[q * k + p] = 0.f;
-        }
-      }
-      __syncthreads();
-    }
-    if (!rotated) break;
-  }
-  for (int e = tid; e < k * k; e += kJacobiThreads) Xout[e] = (double)w[e];
-  for (int i = tid; i < k; i += kJacobiThreads) lam_out[i] = (double)h[i * k + i] / sc;
-  if (tid == 0) *sweeps_out = sweep < kJacobiMaxSweeps ? sweep + 1 : sweep;
 }
 
 // Block-wide FP64 sum (blockDim.x multiple of 32, <= 1024).
@@ -190,36 +82,37 @@ __device__ double block_sum(double v, double* red) {
   return red[32];
 }
 
-// One refinement step's small part: lambda_i = S_ii / (X^T X)_ii and the
-// correction E (Rm = X^T X, R = I - Rm).  A pair (i, j) takes the first-order
-// correction (s_ij + lambda_j r_ij) / (lambda_j - lambda_i) when that is a
-// small rotation (|E_ij| <= 1/2) and the gap is above FP64 noise of H;
-// otherwise it is treated as a cluster and only re-orthogonalised (r_ij / 2).
-// The per-pair test replaces the method's global cluster threshold, which
+// lambda_i = S_ii / (X^T X)_ii (Rayleigh quotients of the current vectors).
+__global__ void rayleigh_kernel(const double* __restrict__ Rm, const double* __restrict__ S, int k, double* lam) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x)
+    lam[i] = S[(int64_t)i * k + i] / Rm[(int64_t)i * k + i];
+}
+
+// One refinement step's correction E, row i per block (R = I - Rm).  A pair
+// (i, j) takes the first-order correction (s_ij + lambda_j r_ij) /
+// (lambda_j - lambda_i) when that is a small rotation (|E_ij| <= 1/2) and the
+// gap is above FP64 noise of H (64 eps ||H||_F, scal[1] = ||H||_F); otherwise
+// it is treated as a cluster and only re-orthogonalised (r_ij / 2).  The
+// per-pair test replaces the method's global cluster threshold, which
 // (evaluated with Frobenius norms) would leave close but well-coupled pairs
 // unresolved; the iteration still converges quadratically for resolved pairs.
-__global__ void refine_e_kernel(const double* __restrict__ H, const double* __restrict__ Rm,
-                                const double* __restrict__ S, int k, double* __restrict__ E, double* lam) {
-  __shared__ double red[33];
-  __shared__ double lam_s[256];
-  const int tid = threadIdx.x;
-  for (int i = tid; i < k; i += blockDim.x) lam_s[i] = S[(int64_t)i * k + i] / Rm[(int64_t)i * k + i];
-  double hh = 0.0;
-  for (int e = tid; e < k * k; e += blockDim.x) hh += H[e] * H[e];
-  hh = block_sum(hh, red);
-  const double noise = 64.0 * 0x1p-52 * sqrt(hh);
-  for (int e = tid; e < k * k; e += blockDim.x) {
-    const int i = e / k, j = e % k;
+__global__ void refine_e_kernel(const double* __restrict__ Rm, const double* __restrict__ S,
+                                const double* __restrict__ lam, const double* __restrict__ scal, int k,
+                                double* __restrict__ E) {
+  const int i = blockIdx.x;
+  const double noise = 64.0 * 0x1p-52 * scal[1];
+  const double li = lam[i];
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    const int64_t e = (int64_t)i * k + j;
     const double r = (i == j ? 1.0 : 0.0) - Rm[e];
     double v = 0.5 * r;
     if (i != j) {
-      const double gap = lam_s[j] - lam_s[i];
-      const double num = S[e] + lam_s[j] * r;
+      const double gap = lam[j] - li;
+      const double num = S[e] + lam[j] * r;
       if (fabs(gap) > noise && fabs(num) <= 0.5 * fabs(gap)) v = num / gap;
     }
     E[e] = v;
   }
-  for (int i = tid; i < k; i += blockDim.x) lam[i] = lam_s[i];
 }
 
 // C = A + A E (k x k, FP64), one thread per output.
@@ -228,46 +121,86 @@ __global__ void add_ae_kernel(const double* __restrict__ A, const double* __rest
   if (e < k * k) C[e] = A[e] + AE[e];
 }
 
-// Sort eigenpairs by descending lambda (stable), apply the rank rule, write
-// sigma (device output) and the permuted, D^-1-scaled eigenvector matrix
-// Wd[:, r] = W[:, order_r] / sigma_r (zero for dropped columns).
-__global__ void sort_rank_kernel(const double* __restrict__ lam, const double* __restrict__ W, int k, int64_t m,
-                                 int64_t n, double* __restrict__ Wd, double* __restrict__ sigma, int32_t* rank,
-                                 double* scal) {
+// Sort eigenpairs by descending lambda (stable) and apply the rank rule; write
+// sigma (device output), the column-permuted eigenvector matrix Ws and the
+// k x k factor Tinv with V = F^T Ws Tinv.  With S = Ws^T H Ws, Tinv is the
+// first-order inverse of the symmetric square root T of S:
+//   T = D_s + Y,  D_s = diag(sqrt(S_rr)),  Y_ab = S_ab / (s_a + s_b)  (a != b),
+//   Tinv = D_s^-1 - D_s^-1 Y D_s^-1,
+// so V^T V = Tinv^T S Tinv = I up to O(|Y|^2) even where close eigenvalues
+// leave W mixing a cluster (the denominators are sums, not gaps).  For an
+// exactly diagonalising W this is the paper's D^-1.
+__global__ void sort_rank_kernel(const double* __restrict__ lam, const double* __restrict__ S, int k, int64_t m,
+                                 int64_t n, double* __restrict__ sigma, int32_t* rank, double* scal) {
   __shared__ int dest[256];
+  __shared__ int src[256];
   __shared__ double lmax_s;
   __shared__ int rank_s;
+  int32_t* src_g = reinterpret_cast<int32_t*>(scal + 8 + 2 * k);
+  double* sd_g = scal + 8 + k;
   const int tid = threadIdx.x;
+  // total order: NaN keys rank as -inf, ties by index, so dest is a permutation
+  auto key = [&](int i) { const double v = lam[i]; return isnan(v) ? -INFINITY : v; };
+  for (int r = tid; r < k; r += blockDim.x) src[r] = r;
+  __syncthreads();
   for (int i = tid; i < k; i += blockDim.x) {
-    const double li = lam[i];
+    const double li = key(i);
     int pos = 0;
     for (int j = 0; j < k; ++j) {
-      const double lj = lam[j];
+      const double lj = key(j);
       pos += (lj > li) || (lj == li && j < i);
     }
     dest[i] = pos;
+    src[pos] = i;
   }
   __syncthreads();
   if (tid == 0) {
     double mx = 0.0;
-    for (int i = 0; i < k; ++i) mx = fmax(mx, lam[i]);
+    for (int i = 0; i < k; ++i) mx = fmax(mx, key(i));
     lmax_s = mx;
     rank_s = 0;
   }
   __syncthreads();
   const double tol = (double)(m > n ? m : n) * 0x1p-52 * lmax_s;
-  for (int i = tid; i < k; i += blockDim.x) {
-    const int r = dest[i];
-    const bool keep = lam[i] > tol && lmax_s > 0.0;
-    const double s = keep ? sqrt(lam[i]) : 0.0;
-    if (sigma) sigma[r] = s;
-    scal[8 + r] = s;
+  for (int r = tid; r < k; r += blockDim.x) {
+    const int i = src[r];
+    const bool keep = lam[i] > tol && lmax_s > 0.0;  // false for NaN
+    if (sigma) sigma[r] = keep ? sqrt(lam[i]) : 0.0;
+    scal[8 + r] = keep ? sqrt(lam[i]) : 0.0;
+    const double sii = S[(int64_t)i * k + i];
+    sd_g[r] = (keep && sii > 0.0) ? sqrt(sii) : 0.0;
+    src_g[r] = i;
     if (keep) atomicAdd(&rank_s, 1);
-    for (int row = 0; row < k; ++row) Wd[(int64_t)row * k + r] = keep ? W[(int64_t)row * k + i] / s : 0.0;
   }
   __syncthreads();
   if (tid == 0 && rank) *rank = rank_s;
   if (tid == 0) scal[0] = (double)rank_s;
+}
+
+// Row a of Ws (column-permuted eigenvectors) and of Tinv, the first-order
+// inverse of the symmetric square root T of S = Ws^T H Ws:
+//   T = D_s + Y, D_s = diag(sqrt(S_rr)), Y_ab = S_ab / (s_a + s_b) (a != b),
+//   Tinv = D_s^-1 - D_s^-1 Y D_s^-1.
+// V = F^T Ws Tinv then has V^T V = Tinv^T S Tinv = I up to O(|Y|^2), also where
+// close eigenvalues leave W mixing a cluster (the denominators are sums, not
+// gaps).  For an exactly diagonalising W this is the paper's D^-1.
+__global__ void ws_tinv_kernel(const double* __restrict__ W, const double* __restrict__ S,
+                               const double* __restrict__ scal, int k, double* __restrict__ Ws,
+                               double* __restrict__ Tinv) {
+  const int a = blockIdx.x;
+  const int32_t* src = reinterpret_cast<const int32_t*>(scal + 8 + 2 * k);
+  const double* sd = scal + 8 + k;
+  const double sa = sd[a];
+  for (int b = threadIdx.x; b < k; b += blockDim.x) {
+    Ws[(int64_t)a * k + b] = W[(int64_t)a * k + src[b]];
+    double t = 0.0;
+    const double sb = sd[b];
+    if (sa > 0.0 && sb > 0.0) {
+      if (a == b) t = 1.0 / sa;
+      else t = -S[(int64_t)src[a] * k + src[b]] / ((sa + sb) * sa * sb);
+    }
+    Tinv[(int64_t)a * k + b] = t;
+  }
 }
 
 // Sign rule and FP32 output: one block per column of Vd (n x k FP64).
@@ -316,33 +249,33 @@ void launch_decompose(Launcher& L, SmallWs& w, const double* F, int k, int64_t n
   launch_gemm_simt(L, k, k, n, F, LSPCA_F64, n, false, F, LSPCA_F64, n, true, w.Hpart, true, k, kk, w.h_splits, true,
                    true);
   launch_reduce_splits(L, w.Hpart, w.h_splits, kk, kk, w.H);
-  // FP32 Jacobi seed.
-  const size_t jsmem = (k <= 128) ? (size_t)2 * kk * sizeof(float) : 0;
-  cudaFuncSetAttribute(jacobi32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(jsmem ? jsmem : 0));
-  jacobi32_kernel<<<1, kJacobiThreads, jsmem, L.stream>>>(w.H, k, w.h32, w.w32, w.Xa, w.lam, w.sweeps, status);
-  L.count(1);
-  // FP64 refinement.
+  // FP32 seed (tridiagonalisation + bisection + inverse iteration)
+  launch_eig_seed(L, w.H, k, w.h32, w.w32, w.q32, w.Xa, w.lam, w.scal, w.sweeps);
+  // FP64 refinement
   double* X = w.Xa;
   double* Xn = w.Xb;
   for (int it = 0; it <= kRefineIters; ++it) {
     dgemm(L, k, k, k, X, k, true, X, k, false, w.Rm, k);    // X^T X
     dgemm(L, k, k, k, w.H, k, false, X, k, false, w.T, k);  // H X
     dgemm(L, k, k, k, X, k, true, w.T, k, false, w.S, k);   // X^T H X
-    refine_e_kernel<<<1, 1024, 0, L.stream>>>(w.H, w.Rm, w.S, k, w.E, w.lam);
+    rayleigh_kernel<<<1, 256, 0, L.stream>>>(w.Rm, w.S, k, w.lam);
     L.count(1);
-    if (it == kRefineIters) break;  // last pass only refreshes lambda
+    if (it == kRefineIters) break;  // last pass only refreshes lambda and S
+    refine_e_kernel<<<k, 128, 0, L.stream>>>(w.Rm, w.S, w.lam, w.scal, k, w.E);
     dgemm(L, k, k, k, X, k, false, w.E, k, false, w.T, k);  // X E
     add_ae_kernel<<<(int)((kk + 255) / 256), 256, 0, L.stream>>>(X, w.T, k, Xn);
-    L.count(1);
+    L.count(2);
     double* t = X;
     X = Xn;
     Xn = t;
   }
-  // order, rank rule, D^-1 folded into the eigenvector matrix
-  sort_rank_kernel<<<1, 256, 0, L.stream>>>(w.lam, X, k, m, n, w.E, sigma, rank, w.scal);
-  L.count(1);
-  // V = F^T (W D^-1)  (n x k)
-  launch_gemm_simt(L, n, k, k, F, LSPCA_F64, n, true, w.E, LSPCA_F64, k, false, w.Vd, true, k, 0, 1, true, true);
+  // order, rank rule, Ws and Tinv (S of the final X is in w.S)
+  sort_rank_kernel<<<1, 256, 0, L.stream>>>(w.lam, w.S, k, m, n, sigma, rank, w.scal);
+  ws_tinv_kernel<<<k, 128, 0, L.stream>>>(X, w.S, w.scal, k, w.T, w.E);
+  L.count(2);
+  dgemm(L, k, k, k, w.T, k, false, w.E, k, false, w.Rm, k);  // Ws Tinv
+  // V = F^T (Ws Tinv)  (n x k)
+  launch_gemm_simt(L, n, k, k, F, LSPCA_F64, n, true, w.Rm, LSPCA_F64, k, false, w.Vd, true, k, 0, 1, true, true);
   if (v_f64)
     finalize_v_kernel<double><<<k, 256, 0, L.stream>>>(w.Vd, n, k, (double*)V);
   else

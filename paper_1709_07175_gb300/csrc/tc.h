@@ -14,15 +14,17 @@ bool tc_available();
 // Pass F on tensor cores: F = U^T X and optionally G = U^T U.
 struct TcChainWs {
   size_t bytes = 0;
-  double* Fpart = nullptr;  // chunks x k x n partials
-  double* Gpart = nullptr;  // chunks x k x k partials
-  float* scales = nullptr;  // device scalars
+  double* Fpart = nullptr;  // chunks x k x n FP32 partials
+  double* Gpart = nullptr;  // gchunks x k x k FP32 partials
   int chunks = 1;
   int64_t rows_per_chunk = 0;
+  int gchunks = 0;
+  int64_t grows_per_chunk = 0;
 };
 void plan_tc_chain(char* base, TcChainWs& w, int xt, int64_t m, int64_t n, int k, bool want_g, int num_sms);
+// absmax[0] = max|X|, absmax[1] = max|U| on the device (FP32 path scales).
 void tc_chain_main(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_t ldx, const float* U, int k,
-                   TcChainWs& w, const float* absmax, bool want_g);
+                   TcChainWs& w, const float* absmax, int* status, bool want_g);
 void tc_chain_reduce(Launcher& L, int64_t n, int k, TcChainWs& w, double* F, double* G);
 
 // Pass S on tensor cores for BF16 X and a Gaussian Omega (Omega^T k x n BF16).
