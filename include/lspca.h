@@ -185,6 +185,28 @@ int lspca_chain(lspca_ctx* ctx, const void* X, int32_t xt, int64_t m, int64_t n,
 int lspca_decompose(lspca_ctx* ctx, const double* F, int32_t k, int64_t n, int64_t m, int32_t vt, void* V,
                     double* sigma, int32_t* rank, void* stream);
 
+/* Pass F without any allocation (the paper has no counterpart: this serves
+ * callers that may not allocate device memory, e.g. code running inside a
+ * framework that owns all GPU memory through its own pool, or loops that
+ * cannot afford the device synchronisation cudaMalloc/cudaFree imply).
+ * Computes F = U^T X exactly as lspca_chain's tensor-core path (FP32 X:
+ * split-FP16 products; BF16 X: split-BF16 U), without a context.
+ * X [dev] m x n, xt LSPCA_F32 or LSPCA_BF16; U [dev] m x k FP32 (ld k);
+ * 4 <= k <= 256, k a multiple of 4; F [dev] k x n FP64 output;
+ * status [dev] int32 output (nullable): zeroed, then the device status bits
+ * (2 = a bounded wait inside the kernel gave up); stream as elsewhere.
+ * Scratch: a 16 MiB device array inside the library, held by every GPU that
+ * loads the library until the process exits; k * n * 4 bytes of it must hold
+ * one chunk's partial sums (k * n <= 4,194,240), else LSPCA_ERR_NOMEM.  The
+ * first call on a device looks up the array's device address, so make it
+ * before any stream capture.  Every call shares the array: calls whose
+ * executions overlap on the GPU race on it and must be ordered by the caller.
+ * Allocates nothing (no cudaMalloc, cudaFree or allocating library call).
+ * Errors: LSPCA_ERR_INVALID (NULL or misaligned pointers, k or xt out of
+ * range, no sm_103 device), LSPCA_ERR_NOMEM (k * n too large), LSPCA_ERR_CUDA. */
+int lspca_chain_noalloc(const void* X, int32_t xt, int64_t m, int64_t n, int64_t ldx, const float* U, int32_t k,
+                        double* F, int32_t* status, void* stream);
+
 /* Synchronise `stream`, return and clear the device status word:
  * LSPCA_OK, LSPCA_ERR_NUMERIC or LSPCA_ERR_TIMEOUT.                         */
 int lspca_sync_status(lspca_ctx* ctx, void* stream);

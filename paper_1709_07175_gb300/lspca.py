@@ -71,6 +71,7 @@ _SIGS = {
     "lspca_sync_status": (ctypes.c_int, [_P, _P]),
     "lspca_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "lspca_launch_count": (ctypes.c_int64, [_P]),
+    "lspca_chain_noalloc": (ctypes.c_int, [_P, _I32, _I64, _I64, _I64, _P, _I32, _P, _P, _P]),
     "lspca_profile": (ctypes.c_int, [_P, ctypes.c_int]),
     "lspca_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64)]),
 }
@@ -171,6 +172,11 @@ def lspca_sketch(ctx, X, k, om, flags, U, stream=None) -> int:
 def lspca_chain(ctx, X, U, k, flags, F, G=None, stream=None) -> int:
     x, xt, m, n, ldx = _xargs(X)
     return load().lspca_chain(ctx, x, xt, m, n, ldx, _ptr(U), k, flags, _ptr(F), _ptr(G), _stream(stream))
+
+
+def lspca_chain_noalloc(X, U, k, F, status=None, stream=None) -> int:
+    x, xt, m, n, ldx = _xargs(X)
+    return load().lspca_chain_noalloc(x, xt, m, n, ldx, _ptr(U), k, _ptr(F), _ptr(status), _stream(stream))
 
 
 def lspca_decompose(ctx, F, k, n, m, vt, V, sigma, rank=None, stream=None) -> int:
