@@ -104,18 +104,21 @@ struct SketchBufs {
   int32_t* col_ptr = nullptr;
   int32_t* entries = nullptr;
   int32_t* off = nullptr;
-  void* omega = nullptr;  // dense Omega (n x k, result type) for the SIMT path
-  void* omega_t = nullptr;  // dense Omega^T (k x n BF16) for the tensor-core path
+  void* omega = nullptr;  // dense Omega (n x k, result type) for the SIMT / tensor-core paths
+  TcProjectWs pw;         // tensor-core path: pre-split tiles of Omega
 };
 
 void plan_sketch(Plan& P, SketchBufs& b, int xt, int64_t n, int k, const lspca_omega& om, bool tc) {
-  if (om.kind == LSPCA_OMEGA_VERY_SPARSE) {
+  if (tc) {
+    b.omega = P.take((size_t)n * k * 4);
+    char* base = P.base ? P.base + ((P.off + 255) & ~(size_t)255) : nullptr;
+    plan_tc_project(base, b.pw, xt, n, k);
+    P.take(b.pw.bytes);
+  } else if (om.kind == LSPCA_OMEGA_VERY_SPARSE) {
     b.counts = (int32_t*)P.take((size_t)k * 4);
     b.col_ptr = (int32_t*)P.take((size_t)(k + 1) * 4);
     b.entries = (int32_t*)P.take((size_t)n * k * 4);
     b.off = (int32_t*)P.take(sketch_off_bytes(n, k));
-  } else if (tc) {
-    b.omega_t = P.take((size_t)n * k * 2);
   } else {
     b.omega = P.take((size_t)n * k * acc_size(xt));
   }
@@ -125,18 +128,20 @@ using Mark = std::function<void(int)>;
 
 void run_sketch(lspca_ctx* ctx, Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_t ldx, int k,
                 const lspca_omega& om, bool tc, SketchBufs& b, void* U, const Mark& mark) {
+  if (tc) {
+    // dense Omega (BF16-rounded for BF16 X, exact +-1/0 for the very sparse kind)
+    // through the tensor-core reduction-map kernel: U = X Omega
+    launch_omega_dense(L, om, n, k, LSPCA_F32, b.omega, k, false, xt == LSPCA_BF16);
+    launch_scan_x(L, X, xt, m, n, ldx, ctx->d_absmax, ctx->d_status);
+    mark(1);
+    tc_project(L, X, xt, m, n, ldx, (const float*)b.omega, k, b.pw, (float*)U, ctx->d_status);
+    mark(2);
+    return;
+  }
   if (om.kind == LSPCA_OMEGA_VERY_SPARSE) {
     launch_omega_csc(L, om, n, k, b.counts, b.col_ptr, b.entries);
     mark(1);
     launch_sketch_sparse(L, X, xt, m, n, ldx, k, b.col_ptr, b.entries, b.off, U, k, ctx->d_absmax, ctx->d_status);
-    mark(2);
-    return;
-  }
-  if (tc) {
-    launch_omega_dense(L, om, n, k, LSPCA_BF16, b.omega_t, n, true, true);
-    launch_scan_x(L, X, xt, m, n, ldx, ctx->d_absmax, ctx->d_status);
-    mark(1);
-    tc_sketch_bf16(L, X, m, n, ldx, b.omega_t, k, (float*)U, ctx->d_absmax + 1);
     mark(2);
     return;
   }
@@ -202,10 +207,14 @@ void run_chain(lspca_ctx* ctx, Launcher& L, const void* X, int xt, int64_t m, in
 }
 
 bool use_tc_chain(int xt, uint32_t flags, int k = 4) {
-  return !(flags & LSPCA_FORCE_SIMT) && (xt == LSPCA_F32 || xt == LSPCA_BF16) && (k % 4) == 0 && tc_available();
+  return !(flags & LSPCA_FORCE_SIMT) && xt != LSPCA_F64 && (k % 4) == 0 && tc_available();
 }
+// Dense-Omega sketches run on the tensor-core reduction-map kernel; the very
+// sparse Omega on FP32/BF16 X keeps the gather kernel (HBM-bound, no MMA work).
 bool use_tc_sketch(int xt, const lspca_omega& om, uint32_t flags) {
-  return !(flags & LSPCA_FORCE_SIMT) && xt == LSPCA_BF16 && om.kind == LSPCA_OMEGA_GAUSSIAN && tc_available();
+  if ((flags & LSPCA_FORCE_SIMT) || !tc_available()) return false;
+  if (om.kind == LSPCA_OMEGA_GAUSSIAN) return xt == LSPCA_F32 || xt == LSPCA_BF16;
+  return xt == LSPCA_E4M3;
 }
 
 int fit_impl(lspca_ctx* ctx, const void* X, int32_t xt, int64_t m, int64_t n, int64_t ldx, int32_t k, lspca_omega om,
@@ -262,7 +271,7 @@ int fit_impl(lspca_ctx* ctx, const void* X, int32_t xt, int64_t m, int64_t n, in
   cudaMemsetAsync(ctx->d_absmax, 0, 2 * sizeof(float), s);
   mark(0);
   run_sketch(ctx, L, X, xt, m, n, ldx, k, om, tc_s, sb, U, mark);
-  if (tc_f && om.kind == LSPCA_OMEGA_GAUSSIAN && xt == LSPCA_F32)
+  if (tc_f && xt == LSPCA_F32 && (tc_s || om.kind == LSPCA_OMEGA_GAUSSIAN))
     launch_scan_x(L, U, LSPCA_F32, m, k, k, ctx->d_absmax + 1, ctx->d_status);  // max|U| for the FP16 scales
   run_chain(ctx, L, X, xt, m, n, ldx, U, k, tc_f, cb, F, want_g ? G : nullptr, mark);
   if (spca) {
@@ -366,8 +375,16 @@ int lspca_project(lspca_ctx* ctx, const void* X, int32_t xt, int64_t m, int64_t 
   if (cudaSetDevice(ctx->device) != cudaSuccess) return LSPCA_ERR_CUDA;
   cudaStream_t s = (cudaStream_t)stream;
   Launcher L{s, &ctx->launches, ctx->num_sms};
-  launch_gemm_simt(L, m, k, n, X, xt, ldx, false, V, acc_dt(xt), k, false, Y, xt == LSPCA_F64, k, 0, 1,
-                   xt == LSPCA_F64, false);
+  if (xt != LSPCA_F64 && tc_available() && aligned16(V)) {
+    TcProjectWs pw;
+    plan_tc_project(nullptr, pw, xt, n, k);
+    if ((st = ensure_ws(ctx, pw.bytes + 4096, s))) return st;
+    plan_tc_project((char*)ctx->ws, pw, xt, n, k);
+    tc_project(L, X, xt, m, n, ldx, (const float*)V, k, pw, (float*)Y, ctx->d_status);
+  } else {
+    launch_gemm_simt(L, m, k, n, X, xt, ldx, false, V, acc_dt(xt), k, false, Y, xt == LSPCA_F64, k, 0, 1,
+                     xt == LSPCA_F64, false);
+  }
   return cuda_status(cudaGetLastError());
 }
 

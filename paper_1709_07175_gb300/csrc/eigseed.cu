@@ -16,7 +16,9 @@
 //      what the FP64 refinement corrects);
 //   4. back-transformation W = Q Z.
 // H is scaled by 1 / max|H_ii| first.  Matrices live in shared memory for
-// k <= 128 and in a global scratch otherwise.
+// k <= 128 and in a global scratch otherwise; Householder vectors are copied
+// to a contiguous vector before use (a column of the row-major matrix would
+// bank-conflict on every read).
 #include "common.cuh"
 #include "kernels.h"
 
@@ -40,13 +42,13 @@ __device__ __forceinline__ float block_sum_f(float v, float* red) {
 }
 
 // Number of eigenvalues of T (d, e) smaller than x (Sturm count).
-__device__ int sturm_count(const float* d, const float* e2, int k, float x, float pivmin) {
+__device__ __forceinline__ int sturm_count(const float* d, const float* e2, int k, float x, float pivmin) {
   int c = 0;
   float q = d[0] - x;
   if (fabsf(q) < pivmin) q = -pivmin;
   c += q < 0.f;
   for (int i = 1; i < k; ++i) {
-    q = d[i] - x - e2[i - 1] / q;
+    q = d[i] - x - __fdividef(e2[i - 1], q);
     if (fabsf(q) < pivmin) q = -pivmin;
     c += q < 0.f;
   }
@@ -56,22 +58,25 @@ __device__ int sturm_count(const float* d, const float* e2, int k, float x, floa
 // One inverse-iteration solve (T - lam I) z <- z with the LDL^T factorisation
 // (no pivoting; tiny pivots replaced by -pivmin), then normalisation.
 // q is per-thread scratch of length k.
-__device__ void inv_iter(const float* d, const float* e, int k, float lam, float pivmin, float* z, float* q,
+__device__ __forceinline__ void inv_iter(const float* d, const float* e, int k, float lam, float pivmin, float* z, float* q,
                          int zstride) {
   // factor: q_0 = d_0 - lam, q_i = d_i - lam - e_{i-1}^2 / q_{i-1}; L_i = e_{i-1} / q_{i-1}
   float qi = d[0] - lam;
   if (fabsf(qi) < pivmin) qi = -pivmin;
   q[0] = qi;
   for (int i = 1; i < k; ++i) {
-    qi = d[i] - lam - e[i - 1] * e[i - 1] / qi;
+    qi = d[i] - lam - __fdividef(e[i - 1] * e[i - 1], qi);
     if (fabsf(qi) < pivmin) qi = -pivmin;
     q[i] = qi;
   }
   // forward: L y = z  (L unit lower bidiagonal, L_i = e_{i-1}/q_{i-1})
-  for (int i = 1; i < k; ++i) z[i * zstride] -= (e[i - 1] / q[i - 1]) * z[(i - 1) * zstride];
+  for (int i = 1; i < k; ++i) z[i * zstride] -= __fdividef(e[i - 1], q[i - 1]) * z[(i - 1) * zstride];
   // diagonal and backward: D L^T x = y
-  z[(k - 1) * zstride] /= q[k - 1];
-  for (int i = k - 2; i >= 0; --i) z[i * zstride] = z[i * zstride] / q[i] - (e[i] / q[i]) * z[(i + 1) * zstride];
+  z[(k - 1) * zstride] = __fdividef(z[(k - 1) * zstride], q[k - 1]);
+  for (int i = k - 2; i >= 0; --i) {
+    const float rq = __fdividef(1.f, q[i]);
+    z[i * zstride] = z[i * zstride] * rq - (e[i] * rq) * z[(i + 1) * zstride];
+  }
   float nrm = 0.f;
   for (int i = 0; i < k; ++i) nrm = fmaf(z[i * zstride], z[i * zstride], nrm);
   if (!(nrm > 0.f) || !isfinite(nrm)) {
@@ -84,19 +89,19 @@ __device__ void inv_iter(const float* d, const float* e, int k, float lam, float
   for (int i = 0; i < k; ++i) z[i * zstride] *= inv;
 }
 
-__global__ void __launch_bounds__(kSeedThreads) eig_seed_kernel(const double* __restrict__ H, int k, float* gA,
+__global__ void __launch_bounds__(kSeedThreads, 1) eig_seed_kernel(const double* __restrict__ H, int k, float* gA,
                                                                 float* gZ, float* gQ, double* __restrict__ Xout,
                                                                 double* __restrict__ lam_out, double* scal,
                                                                 int32_t* nclusters) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ float red[33];
-  __shared__ float dv[256], ev[256], e2v[256], betav[256], wl[256], pv[256], lamv[256];
+  __shared__ float dv[256], ev[256], e2v[256], betav[256], wl[256], pv[256], lamv[256], vv_s[256];
   __shared__ float coef[4];
   __shared__ int clstart[257];
   const bool sm = k <= 128;
   float* A = sm ? reinterpret_cast<float*>(smem_raw) : gA;         // k x k row-major
   float* Z = sm ? reinterpret_cast<float*>(smem_raw) + k * k : gZ;  // k x k, column j = eigenvector j
-  float* Qs = gQ;                                                   // k x k inverse-iteration scratch (global)
+  float* Qs = sm ? reinterpret_cast<float*>(smem_raw) + 2 * k * k : gQ;  // inverse-iteration scratch, one row per cluster
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kSeedThreads / 32;
 
   // scale and load; ||H||_F for the refinement's noise floor
@@ -154,25 +159,29 @@ __global__ void __launch_bounds__(kSeedThreads) eig_seed_kernel(const double* __
     __syncthreads();
     const float beta = betav[j];
     if (beta != 0.f) {
-      // p = beta A' v, A' = A[j+1:, j+1:], v = A[j+1:, j]; one warp per row
+      // v (column j below the diagonal) into a contiguous vector: the column is
+      // strided by k in SMEM and would bank-conflict on every read
+      for (int r = tid; r < n1; r += kSeedThreads) vv_s[r] = A[(j + 1 + r) * k + j];
+      __syncthreads();
+      // p = beta A' v, A' = A[j+1:, j+1:]; one warp per row
       for (int r = warp; r < n1; r += nw) {
         const float* row = A + (j + 1 + r) * k + (j + 1);
         float acc = 0.f;
-        for (int l = lane; l < n1; l += 32) acc = fmaf(row[l], A[(j + 1 + l) * k + j], acc);
+        for (int l = lane; l < n1; l += 32) acc = fmaf(row[l], vv_s[l], acc);
         acc = warp_sumf(acc);
         if (lane == 0) pv[r] = beta * acc;
       }
       __syncthreads();
       float pt = 0.f;
-      for (int r = tid; r < n1; r += kSeedThreads) pt = fmaf(pv[r], A[(j + 1 + r) * k + j], pt);
+      for (int r = tid; r < n1; r += kSeedThreads) pt = fmaf(pv[r], vv_s[r], pt);
       const float ptv = block_sum_f(pt, red);
       const float K = 0.5f * beta * ptv;
-      for (int r = tid; r < n1; r += kSeedThreads) wl[r] = pv[r] - K * A[(j + 1 + r) * k + j];
+      for (int r = tid; r < n1; r += kSeedThreads) wl[r] = pv[r] - K * vv_s[r];
       __syncthreads();
-      for (int idx = tid; idx < n1 * n1; idx += kSeedThreads) {
-        const int r = idx / n1, c = idx % n1;
-        const float vr = A[(j + 1 + r) * k + j], vc = A[(j + 1 + c) * k + j];
-        A[(j + 1 + r) * k + (j + 1 + c)] -= vr * wl[c] + wl[r] * vc;
+      for (int r = warp; r < n1; r += nw) {
+        const float vr = vv_s[r], wr = wl[r];
+        float* row = A + (j + 1 + r) * k + (j + 1);
+        for (int c = lane; c < n1; c += 32) row[c] -= vr * wl[c] + wr * vv_s[c];
       }
       __syncthreads();
     }
@@ -271,21 +280,24 @@ __global__ void __launch_bounds__(kSeedThreads) eig_seed_kernel(const double* __
     const float beta = betav[j];
     if (beta == 0.f) continue;
     const int n1 = k - j - 1;
-    // w_c = v^T Z[j+1:, c] for every column c; 8 threads per column
+    for (int r = tid; r < n1; r += kSeedThreads) vv_s[r] = A[(j + 1 + r) * k + j];
+    __syncthreads();
+    // w_c = beta v^T Z[j+1:, c] for every column c; 8 threads per column
     for (int cbase = 0; cbase < k; cbase += kSeedThreads / 8) {
       const int c = cbase + tid / 8, g = tid & 7;
       float acc = 0.f;
       if (c < k)
-        for (int r = g; r < n1; r += 8) acc = fmaf(A[(j + 1 + r) * k + j], Z[(j + 1 + r) * k + c], acc);
+        for (int r = g; r < n1; r += 8) acc = fmaf(vv_s[r], Z[(j + 1 + r) * k + c], acc);
       acc += __shfl_xor_sync(0xffffffffu, acc, 1);
       acc += __shfl_xor_sync(0xffffffffu, acc, 2);
       acc += __shfl_xor_sync(0xffffffffu, acc, 4);
       if (c < k && g == 0) wl[c] = beta * acc;
     }
     __syncthreads();
-    for (int idx = tid; idx < n1 * k; idx += kSeedThreads) {
-      const int r = idx / k, c = idx % k;
-      Z[(j + 1 + r) * k + c] -= A[(j + 1 + r) * k + j] * wl[c];
+    for (int r = warp; r < n1; r += nw) {
+      const float vr = vv_s[r];
+      float* row = Z + (j + 1 + r) * k;
+      for (int c = lane; c < k; c += 32) row[c] -= vr * wl[c];
     }
     __syncthreads();
   }
@@ -293,7 +305,7 @@ __global__ void __launch_bounds__(kSeedThreads) eig_seed_kernel(const double* __
   for (int i = tid; i < k; i += kSeedThreads) lam_out[i] = (double)lamv[i] * hmax_s;
 }
 
-size_t eig_seed_smem(int k) { return k <= 128 ? (size_t)2 * k * k * sizeof(float) : 0; }
+size_t eig_seed_smem(int k) { return k <= 128 ? (size_t)3 * k * k * sizeof(float) : 0; }
 
 void launch_eig_seed(Launcher& L, const double* H, int k, float* gA, float* gZ, float* gQ, double* Xout,
                      double* lam, double* scal, int32_t* nclusters) {

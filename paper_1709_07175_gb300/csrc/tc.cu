@@ -63,7 +63,7 @@ constexpr int THREADS = 13 * 32;
 constexpr uint64_t kWaitNs = 2000000000ull;
 constexpr int SEG = 4;               // k-steps accumulated by the tensor core per segment
 
-enum XKind { XK_F32 = 0, XK_BF16 = 1 };
+enum XKind { XK_F32 = 0, XK_BF16 = 1, XK_E4M3 = 2 };
 
 struct Params {
   const float* U;      // m x k, ld ldu (A source)
@@ -93,7 +93,9 @@ struct Cfg {
   static constexpr uint32_t SBO_B = (BN / 64) * 1024;
   static constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + NB * B_BYTES;
   static constexpr int A_VEC = BK * WA / 4 / CONV_THREADS;        // float4 per thread
-  static constexpr int B_VEC = (XK == XK_F32) ? BK * BN / 4 / CONV_THREADS : BK * BN / 8 / CONV_THREADS;
+  static constexpr int B_VEC = (XK == XK_F32)    ? BK * BN / 4 / CONV_THREADS
+                               : (XK == XK_BF16) ? BK * BN / 8 / CONV_THREADS
+                                                 : BK * BN / 16 / CONV_THREADS;
   // 8 KB of slack after the ring keeps every descriptor-addressed byte inside
   // the allocation
   static constexpr size_t SMEM = 1024 + STAGES * STAGE_BYTES + 256 + 8192;
@@ -223,11 +225,18 @@ __global__ void __launch_bounds__(THREADS, 1) chain_kernel(Params p) {
             rb[q] = ldg_stream16((const float*)p.B + gi * p.ldb + gj);
           else
             rb[q] = make_uint4(0u, 0u, 0u, 0u);
-        } else {
+        } else if (XK == XK_BF16) {
           const int kr = f / (C::BN / 8), mn = (f % (C::BN / 8)) * 8;
           const int64_t gi = i0 + kr, gj = col0 + mn;
           if (gi < i1 && gj < p.nb)
             rb[q] = ldg_stream16((const __nv_bfloat16*)p.B + gi * p.ldb + gj);
+          else
+            rb[q] = make_uint4(0u, 0u, 0u, 0u);
+        } else {
+          const int kr = f / (C::BN / 16), mn = (f % (C::BN / 16)) * 16;
+          const int64_t gi = i0 + kr, gj = col0 + mn;
+          if (gi < i1 && gj < p.nb)
+            rb[q] = ldg_stream16((const uint8_t*)p.B + gi * p.ldb + gj);
           else
             rb[q] = make_uint4(0u, 0u, 0u, 0u);
         }
@@ -263,9 +272,21 @@ __global__ void __launch_bounds__(THREADS, 1) chain_kernel(Params p) {
           const uint32_t off = ptx::mn_sw128_offset(kr, mn, C::SBO_B);
           sts64(b_hi + off, pack4<H>(h0, h1, h2, h3));
           sts64(b_lo + off, pack4<H>(l0, l1, l2, l3));
-        } else {
+        } else if (XK == XK_BF16) {
           const int kr = f / (C::BN / 8), mn = (f % (C::BN / 8)) * 8;
           sts128(b_hi + ptx::mn_sw128_offset(kr, mn, C::SBO_B), rb[q]);
+        } else {
+          // FP8 E4M3 values widen exactly to BF16
+          const int kr = f / (C::BN / 16), mn = (f % (C::BN / 16)) * 16;
+          const __nv_fp8_e4m3* e8 = reinterpret_cast<const __nv_fp8_e4m3*>(&rb[q]);
+          uint32_t w[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            __nv_bfloat162 h2 = __floats2bfloat162_rn(float(e8[2 * u]), float(e8[2 * u + 1]));
+            w[u] = *reinterpret_cast<uint32_t*>(&h2);
+          }
+          sts128(b_hi + ptx::mn_sw128_offset(kr, mn, C::SBO_B), make_uint4(w[0], w[1], w[2], w[3]));
+          sts128(b_hi + ptx::mn_sw128_offset(kr, mn + 8, C::SBO_B), make_uint4(w[4], w[5], w[6], w[7]));
         }
       }
     };
@@ -320,7 +341,7 @@ __global__ void __launch_bounds__(THREADS, 1) chain_kernel(Params p) {
   } else if (warp == MMA_WARP) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      constexpr uint32_t idesc = ptx::idesc_f16(XK == XK_BF16 ? 1 : 0, 128, C::BN, 1, 1);
+      constexpr uint32_t idesc = ptx::idesc_f16(XK == XK_F32 ? 0 : 1, 128, C::BN, 1, 1);
       int64_t step = 0, seg = 0;
       bool ok = true;
       for (int64_t unit = blockIdx.x; unit < units && ok; unit += gridDim.x) {
@@ -535,9 +556,12 @@ void tc_chain_main(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int
   if (xt == LSPCA_F32) {
     if (MH == 1) tcc::launch_chain<tcc::XK_F32, 1>(L, p);
     else tcc::launch_chain<tcc::XK_F32, 2>(L, p);
-  } else {
+  } else if (xt == LSPCA_BF16) {
     if (MH == 1) tcc::launch_chain<tcc::XK_BF16, 1>(L, p);
     else tcc::launch_chain<tcc::XK_BF16, 2>(L, p);
+  } else {
+    if (MH == 1) tcc::launch_chain<tcc::XK_E4M3, 1>(L, p);
+    else tcc::launch_chain<tcc::XK_E4M3, 2>(L, p);
   }
   if (want_g) {
     // G = U^T U: the same kernel with U as the B source (FP32 split path)
@@ -570,9 +594,5 @@ void tc_chain_reduce(Launcher& L, int64_t n, int k, TcChainWs& w, double* F, dou
   }
 }
 
-// Not yet on tensor cores: the BF16 sketch and the projection run the SIMT kernels.
-void tc_sketch_bf16(Launcher&, const void*, int64_t, int64_t, int64_t, const void*, int, float*, float*) {}
-void plan_tc_project(char*, TcProjectWs& w, int, int64_t, int) { w.bytes = 0; }
-void tc_project(Launcher&, const void*, int, int64_t, int64_t, int64_t, const float*, int, TcProjectWs&, float*) {}
 
 }  // namespace lspca

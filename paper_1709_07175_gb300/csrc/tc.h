@@ -27,18 +27,15 @@ void tc_chain_main(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int
                    TcChainWs& w, const float* absmax, int* status, bool want_g);
 void tc_chain_reduce(Launcher& L, int64_t n, int k, TcChainWs& w, double* F, double* G);
 
-// Pass S on tensor cores for BF16 X and a Gaussian Omega (Omega^T k x n BF16).
-void tc_sketch_bf16(Launcher& L, const void* X, int64_t m, int64_t n, int64_t ldx, const void* omega_t, int k,
-                    float* U, float* absmax_u);
-
-// Y = X V on tensor cores.
+// Y = X V on tensor cores (FP32, BF16 or E4M3 X; V and Y FP32, k <= 256).  With V = a
+// dense Omega the same kernel computes the sketch U = X Omega (pass S).
 struct TcProjectWs {
   size_t bytes = 0;
-  void* vhi = nullptr;  // k x n (V^T, high part)
-  void* vlo = nullptr;  // k x n (V^T, low part)
+  void* vhi = nullptr;  // pre-split, pre-swizzled V tiles (per k-step [hi | lo])
+  void* vlo = nullptr;  // device scalars: max|V|, scale t
 };
 void plan_tc_project(char* base, TcProjectWs& w, int xt, int64_t n, int k);
 void tc_project(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_t ldx, const float* V, int k,
-                TcProjectWs& w, float* Y);
+                TcProjectWs& w, float* Y, int* status);
 
 }  // namespace lspca

@@ -54,6 +54,21 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64
   }
 }
 
+// Arrive on `bar` and add `bytes` to its expected transaction count.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// Bulk (non-tensor) asynchronous copy global -> shared, completion counted in
+// bytes on `bar`.  dst, src 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
 // Generic-proxy shared-memory writes -> visible to the async proxy (tcgen05.mma).
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -146,6 +161,14 @@ __device__ __forceinline__ uint32_t mn_sw128_offset(int kr, int mn, uint32_t sbo
   const int r = kr & 7;
   return (uint32_t)(kr >> 3) * sbo + (uint32_t)(mn >> 6) * 1024u + (uint32_t)r * 128u +
          (uint32_t)((((mn & 63) >> 3) ^ r) << 4) + (uint32_t)((mn & 7) << 1);
+}
+
+// Byte offset of 16-bit element (row, kk) inside a K-major SW128 operand tile
+// with 64 K-elements (128 bytes) per row; 8-row groups are 1024 bytes apart.
+__device__ __forceinline__ uint32_t k_sw128_offset(int row, int kk) {
+  const int r = row & 7;
+  return (uint32_t)(row >> 3) * 1024u + (uint32_t)r * 128u + (uint32_t)((((kk & 63) >> 3) ^ r) << 4) +
+         (uint32_t)((kk & 7) << 1);
 }
 
 }  // namespace ptx

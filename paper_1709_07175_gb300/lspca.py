@@ -105,6 +105,8 @@ def _ptr(t) -> int | None:
         return None
     if isinstance(t, int):
         return t
+    if not t.is_contiguous():
+        raise ValueError("tensors passed to liblspca must be row-major contiguous")
     return t.data_ptr()
 
 

@@ -17,9 +17,9 @@ Workloads (the sigma index i runs 1..r):
                    p_j ~ Beta(0.5, 9.5) (5 % mean density), stored FP8 E4M3,
                    k = 256, very sparse Omega p = 64.
 
-A and B are orthonormal (reduced QR of Gaussian draws).  Rows of the noise
-are drawn in fixed chunks from per-chunk generators, so the same seed gives
-the same matrix for any chunking on a given device type.
+A and B are orthonormal (reduced QR of Gaussian draws, on the CPU in FP64 for
+every target device).  Rows of the noise are drawn in fixed chunks from
+per-chunk generators on the target device.
 """
 from __future__ import annotations
 
@@ -78,9 +78,9 @@ TORCH_DTYPES = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat
                 "e4m3": torch.float8_e4m3fn}
 
 
-def _orthonormal(rows: int, r: int, gen: torch.Generator, device) -> torch.Tensor:
-    g = torch.randn(rows, r, generator=gen, dtype=torch.float64 if device == "cpu" else torch.float32,
-                    device=device)
+def _orthonormal(rows: int, r: int, gen: torch.Generator) -> torch.Tensor:
+    """Orthonormal rows x r factor: reduced QR of a Gaussian draw (CPU, FP64)."""
+    g = torch.randn(rows, r, generator=gen, dtype=torch.float64)
     q, _ = torch.linalg.qr(g, mode="reduced")
     return q
 
@@ -89,17 +89,17 @@ def lowrank_plus_noise(w: Workload, device="cpu", chunk_rows: int = 65536,
                        out: torch.Tensor | None = None) -> torch.Tensor:
     """X = A diag(sigma) B^T + noise, rounded once to the storage dtype.
 
-    CPU generation is FP64 throughout; on a GPU the factors and noise are FP32
-    (the rounding to the storage type dominates either way).  Returns an
+    The orthonormal factors A and B always come from the CPU generator in FP64
+    (so every device sees the same factors); the noise is drawn on ``device``
+    (FP64 on the CPU, FP32 on a GPU) from per-chunk generators.  Returns an
     (m, n) row-major tensor on ``device`` in ``TORCH_DTYPES[w.dtype]``.
     """
     dev = torch.device(device)
-    dev_key = "cpu" if dev.type == "cpu" else dev
     work = torch.float64 if dev.type == "cpu" else torch.float32
-    gen = torch.Generator(device=dev)
+    gen = torch.Generator()
     gen.manual_seed(int(w.data_seed) * 1_000_003 + 17)
-    A = _orthonormal(w.m, w.r, gen, dev_key).to(work)
-    B = _orthonormal(w.n, w.r, gen, dev_key).to(work)
+    A = _orthonormal(w.m, w.r, gen).to(device=dev, dtype=work)
+    B = _orthonormal(w.n, w.r, gen).to(device=dev, dtype=work)
     sig = torch.as_tensor(w.sigmas(), dtype=work, device=dev)
     BS = (B * sig).T.contiguous()  # r x n
     X = out if out is not None else torch.empty(w.m, w.n, dtype=TORCH_DTYPES[w.dtype], device=dev)
@@ -150,8 +150,8 @@ def rank_r_exact(m: int, n: int, r: int, seed: int, dtype=torch.float64) -> tupl
     """
     gen = torch.Generator()
     gen.manual_seed(seed)
-    A = _orthonormal(m, r, gen, "cpu")
-    B = _orthonormal(n, r, gen, "cpu")
+    A = _orthonormal(m, r, gen)
+    B = _orthonormal(n, r, gen)
     sig = torch.tensor([2.0 ** -i for i in range(1, r + 1)], dtype=torch.float64)
     X = (A * sig) @ B.T
     return X.to(dtype), B

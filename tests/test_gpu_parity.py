@@ -321,3 +321,86 @@ def test_alg4_slicing_invariance(ctx, data):
     parts = [0, 333, 1000, 1999, w.m]
     Fs = sum(ctx.chain(Xg[a:b], U[a:b])[0] for a, b in zip(parts[:-1], parts[1:]))
     assert torch.allclose(F, Fs, rtol=1e-12, atol=1e-12 * F.abs().max().item())
+
+
+# ------------------------------------------------------------------ tensor-core projection, all X types
+
+@pytest.mark.parametrize("dtype,k,m,n", [("f32", 20, 1000, 500), ("f32", 128, 3001, 4096), ("f32", 200, 777, 1000),
+                                         ("bf16", 64, 2049, 1024), ("bf16", 256, 513, 2048),
+                                         ("e4m3", 256, 1500, 4096), ("e4m3", 128, 4001, 1040)])
+def test_project_tensor_core_paths(ctx, dtype, k, m, n):
+    """Y = X V against the FP64 product of the same stored values (relative Frobenius):
+    FP32 X split-FP16 (per-row scales) 2e-6; BF16 / E4M3 X with split-BF16 V 1e-5."""
+    if dtype == "e4m3":
+        w = S.WORKLOADS["e4m3_binary"].scaled(m=m, n=n, k=k)
+    elif dtype == "bf16":
+        w = S.WORKLOADS["bf16_dense"].scaled(m=m, n=n, k=k)
+    else:
+        w = S.WORKLOADS["fp32_sparse"].scaled(m=m, n=n, k=k)
+    X = S.generate(w)
+    g = torch.Generator().manual_seed(k * 7 + m)
+    V, _ = torch.linalg.qr(torch.randn(n, k, generator=g, dtype=torch.float64))
+    V32 = V.float().contiguous()  # QR returns a column-major Q; the ABI takes row-major V
+    Y = ctx.project(X.cuda(), V32.cuda()).double().cpu().numpy()
+    Yref = X.double().numpy() @ V32.double().numpy()
+    err = np.linalg.norm(Y - Yref) / np.linalg.norm(Yref)
+    assert err < (2e-6 if dtype == "f32" else 1e-5), err
+
+
+# ------------------------------------------------------------------ BF16 and FP8 (binary) workloads
+
+C3S = S.WORKLOADS["bf16_dense"].scaled(m=4001, n=2048)            # k = 256: two 128-row halves of F
+C4S = S.WORKLOADS["e4m3_binary"].scaled(m=5001, n=1024, k=128)
+
+
+def test_fit_bf16_gaussian_parity(ctx):
+    """BF16 X, Gaussian Omega rounded to BF16 (the path's number format), k = 256:
+    Y within 1e-4 (refined low-precision path), Procrustes-aligned."""
+    w = C3S
+    X = S.generate(w)
+    Xd = X.double().numpy()
+    Om = P.bf16_rne(P.omega_gaussian(w.omega_seed, w.n, w.k))
+    fit = O.lspca_fit(Xd, Om, route="eig")
+    Xg = X.cuda()
+    # the sketch itself: BF16 products are exact, FP32 accumulation
+    U = ctx.sketch(Xg, w.k, _om(w)).double().cpu().numpy()
+    assert np.linalg.norm(U - fit["U"]) / np.linalg.norm(fit["U"]) < 1e-6
+    r = ctx.fit(Xg, w.k, _om(w))
+    Y = ctx.project(Xg, r.V).double().cpu().numpy()
+    Yref = O.project(Xd, fit["V"])
+    e = _report_errors(Y, Yref, r.V.double().cpu().numpy(), fit["V"])
+    print("bf16_dense", e)
+    assert e["procrustes"] < 1e-4
+    assert np.max(np.abs(r.sigma.cpu().numpy() - fit["sigma"]) / fit["sigma"]) < 1e-4
+
+
+def test_binary_e4m3_exact_sketch_and_chain(ctx):
+    """Binary X (E4M3) with the very sparse Omega: U = X Omega and F = U^T X are
+    integers and come out bit-exact (FP32 holds integers below 2^24)."""
+    w = C4S
+    X = S.generate(w)
+    Xd = X.float().double().numpy()
+    Om = P.omega_sparse(w.omega_seed, w.n, w.k, w.p)
+    Uref = Xd @ Om
+    Fref = Uref.T @ Xd
+    assert np.abs(Fref).max() < 2 ** 24
+    Xg = X.cuda()
+    U = ctx.sketch(Xg, w.k, _om(w))
+    assert np.array_equal(U.double().cpu().numpy(), Uref)
+    F, _ = ctx.chain(Xg, U)
+    assert np.array_equal(F.cpu().numpy(), Fref)
+
+
+def test_fit_binary_e4m3_parity(ctx):
+    w = C4S
+    X = S.generate(w)
+    Xd = X.float().double().numpy()
+    Om = P.omega_sparse(w.omega_seed, w.n, w.k, w.p)
+    fit = O.lspca_fit(Xd, Om, route="eig")
+    Xg = X.cuda()
+    r = ctx.fit(Xg, w.k, _om(w))
+    Y = ctx.project(Xg, r.V).double().cpu().numpy()
+    Yref = O.project(Xd, fit["V"])
+    e = _report_errors(Y, Yref, r.V.double().cpu().numpy(), fit["V"])
+    print("e4m3_binary", e)
+    assert e["procrustes"] < 1e-4
