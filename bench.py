@@ -119,6 +119,107 @@ def cpu_baseline(rows: int, reps_seconds: float = 10.0) -> dict:
             "np": np.__version__}
 
 
+def serve_bench(L, S, torch, local: int, seconds: float, load: float = 0.8, seed: int = 5) -> dict:
+    """Continuous-batching serving run shaped like the serving workload: three
+    resident V (n = 4096, k in {64, 128, 256}) fitted from BF16 low-rank data,
+    Poisson arrivals of projection requests (log-uniform 1..65,536 BF16 rows)
+    mixed 9:1 with fit requests (m log-uniform 1e4..5e5, n = 4096, k = 128,
+    Gaussian Omega), offered at `load` times the measured unbatched capacity.
+    Latency = completion - arrival on the host clock."""
+    import math
+    import numpy as np
+    dev = torch.device(f"cuda:{local}")
+    n = 4096
+    from dataclasses import replace
+    wsrc = replace(S.WORKLOADS["bf16_dense"].scaled(m=500_000, n=n, k=128), r=64)
+    pool = S.generate(wsrc, device=dev)  # 500k x 4096 BF16 (4.1 GB): fit and projection rows
+    ctx = L.Context(local)
+    fitV = ctx.fit(pool[:20000], 256, L.omega("gaussian", 0), report=False).V
+    Vs = {k: fitV[:, :k].contiguous() for k in (64, 128, 256)}
+    rng = np.random.default_rng(seed)
+    nreq = 600
+    kinds = rng.random(nreq) < 0.1
+    prow = S.serving_rows(seed, nreq)
+    frow = np.floor(np.exp(rng.uniform(math.log(1e4), math.log(5e5), nreq))).astype(np.int64)
+    pk = rng.choice([64, 128, 256], nreq)
+    poff = rng.integers(0, 500_000 - 65_536, nreq)
+    om = L.omega("gaussian", 0)
+
+    def direct(i):
+        if kinds[i]:
+            ctx.fit(pool[: frow[i]], 128, om, report=False)
+        else:
+            X = pool[poff[i]: poff[i] + prow[i]]
+            ctx.project(X, Vs[int(pk[i])])
+
+    # unbatched plain-launch baseline: service time of each request alone
+    for i in range(8):
+        direct(i)
+    torch.cuda.synchronize()
+    svc = np.zeros(nreq)
+    for i in range(nreq):
+        t0 = time.perf_counter()
+        direct(i)
+        torch.cuda.synchronize()
+        svc[i] = time.perf_counter() - t0
+    rate = load / svc.mean()
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, nreq))
+    # baseline latency: one FIFO server with those service times
+    done_b = np.zeros(nreq)
+    tfree = 0.0
+    for i in range(nreq):
+        start = max(arrivals[i], tfree)
+        tfree = start + svc[i]
+        done_b[i] = tfree
+    lat_b = (done_b - arrivals) * 1e3
+
+    srv = L.Server(local, 24 << 30, 64)
+    vid = {k: srv.register_v(V) for k, V in Vs.items()}
+    # warm the server's graphs once per group
+    for k in (64, 128, 256):
+        r, _ = srv.submit_project(vid[k], pool[:300])
+        srv.wait(r)
+        srv.release(r)
+    torch.cuda.synchronize()
+    t_start = time.perf_counter()
+    deadline = t_start + seconds
+    nxt = 0
+    live = {}
+    lat = []
+    rows_done = 0
+    while (nxt < nreq or live) and time.perf_counter() < deadline + 30:
+        now = time.perf_counter() - t_start
+        while nxt < nreq and arrivals[nxt] <= now:
+            if kinds[nxt]:
+                req, V, sig = srv.submit_fit(pool[: frow[nxt]], 128, om)
+                rows = int(frow[nxt])
+            else:
+                req, Y = srv.submit_project(vid[int(pk[nxt])], pool[poff[nxt]: poff[nxt] + prow[nxt]])
+                rows = int(prow[nxt])
+            live[req] = (arrivals[nxt], rows)
+            nxt += 1
+        srv.step()
+        for req in list(live):
+            if srv.done(req):
+                arr, rows = live.pop(req)
+                lat.append((time.perf_counter() - t_start - arr) * 1e3)
+                rows_done += rows
+                srv.release(req)
+        if not live and nxt < nreq:
+            time.sleep(max(0.0, min(1e-3, arrivals[nxt] - (time.perf_counter() - t_start))))
+    wall = time.perf_counter() - t_start
+    torch.cuda.synchronize()
+    srv.close()
+    ctx.close()
+    del pool
+    lat = np.array(lat)
+    return {"load": load, "requests": int(len(lat)), "mix": "9:1 projections:fits",
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "throughput_req_s": len(lat) / wall, "rows_per_s": rows_done / wall,
+            "unbatched": {"p50_ms": float(np.percentile(lat_b, 50)), "p99_ms": float(np.percentile(lat_b, 99)),
+                          "capacity_req_s": 1.0 / svc.mean()}}
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -293,6 +394,14 @@ def run_gpu(args):
                     "ms_per_step": e2e_ms},
             "gpu_launches": launches,
             "clocks": clk}
+    if rank == 0 and args.serve_seconds > 0:
+        del Xh
+        X = None
+        torch.cuda.empty_cache()
+        try:
+            line["serve"] = serve_bench(L, S, torch, local, args.serve_seconds)
+        except Exception as e:  # the fit line above stands on its own
+            line["serve"] = {"error": f"{type(e).__name__}: {e}"}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_rows, args.cpu_seconds)
     if rank == 0:
@@ -313,6 +422,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-rows", type=int, default=20_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=5.0, help="serving run length (0 = skip)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

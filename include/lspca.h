@@ -207,6 +207,48 @@ int lspca_decompose(lspca_ctx* ctx, const double* F, int32_t k, int64_t n, int64
 int lspca_chain_noalloc(const void* X, int32_t xt, int64_t m, int64_t n, int64_t ldx, const float* U, int32_t k,
                         double* F, int32_t* status, void* stream);
 
+/* ---- serving: continuous batching (a request loop on one GPU) ----------
+ * Not in the paper: a runtime that keeps fitted V matrices resident and
+ * serves reduction-map requests (Y = X V, Sec. III-B.2) and Lazy SPCA fits
+ * (Algorithm 4, one slice of 65,536 rows per step) submitted while others
+ * run.  All buffers passed in are device memory owned by the caller and must
+ * stay valid until the request is done.
+ *
+ * lspca_srv_create: server on `device` with its own stream and an HBM arena
+ *   of hbm_budget_bytes (0 = 4 GiB) for fit workspaces and V tiles;
+ *   max_inflight bounds the requests admitted at once.
+ * lspca_srv_register_v: keep V (n x k FP32, row-major, 4 <= k <= 256, k a
+ *   multiple of 4) for projection requests; returns its id.
+ * lspca_srv_submit_project: queue Y[rows x k] = X[rows x n] V (X FP32, BF16
+ *   or E4M3 with leading dimension ldx).
+ * lspca_srv_submit_fit: queue a Lazy SPCA fit of X (m x n, FP32/BF16/E4M3)
+ *   into V (n x k FP32) and sigma (k FP64); LSPCA_ERR_NOMEM if its workspace
+ *   can never fit the arena.
+ * lspca_srv_step: admit queued requests in FIFO order while a slot is free and
+ *   (for fits) the workspace fits the arena, then launch one batch: all
+ *   running projections' 128-row tiles in one table-driven launch per (X type,
+ *   padded k) -- replayed as a captured CUDA graph -- and one slice of every
+ *   running fit.  work_units (nullable) receives tiles + fit slices launched.
+ * lspca_srv_poll: done = 1 once the request's results are complete on the GPU.
+ * lspca_srv_wait: drive steps / wait until done or timeout_ms elapsed
+ *   (LSPCA_ERR_TIMEOUT).
+ * lspca_srv_release: forget a finished request (LSPCA_ERR_BUSY if not done).
+ * Each request's arithmetic depends only on the request (fixed tiles and
+ * slices), so its results are bit-identical alone and in any mix.            */
+typedef struct lspca_srv lspca_srv;
+int lspca_srv_create(lspca_srv** out, int device, size_t hbm_budget_bytes, int32_t max_inflight);
+int lspca_srv_destroy(lspca_srv* srv);
+int lspca_srv_register_v(lspca_srv* srv, const float* V, int64_t n, int32_t k, int32_t* v_id);
+int lspca_srv_submit_project(lspca_srv* srv, int32_t v_id, const void* X, int32_t xt, int64_t rows, int64_t ldx,
+                             float* Y, int64_t* req);
+int lspca_srv_submit_fit(lspca_srv* srv, const void* X, int32_t xt, int64_t m, int64_t n, int64_t ldx, int32_t k,
+                         lspca_omega om, float* V, double* sigma, int64_t* req);
+int lspca_srv_step(lspca_srv* srv, int32_t* work_units);
+int lspca_srv_poll(lspca_srv* srv, int64_t req, int32_t* done);
+int lspca_srv_wait(lspca_srv* srv, int64_t req, int32_t timeout_ms);
+int lspca_srv_release(lspca_srv* srv, int64_t req);
+int64_t lspca_srv_launch_count(lspca_srv* srv);
+
 /* Synchronise `stream`, return and clear the device status word:
  * LSPCA_OK, LSPCA_ERR_NUMERIC or LSPCA_ERR_TIMEOUT.                         */
 int lspca_sync_status(lspca_ctx* ctx, void* stream);

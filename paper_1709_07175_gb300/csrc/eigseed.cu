@@ -5,8 +5,8 @@
 // O(k^3) flops with O(k) synchronisations:
 //   1. Householder tridiagonalisation  H = Q T Q^T  (reflectors kept in the
 //      lower triangle, as in LAPACK's sytrd);
-//   2. eigenvalues of T by bisection on Sturm counts, run as 8-way
-//      multisection by 8 lanes per eigenvalue;
+//   2. eigenvalues of T by bisection on Sturm counts, one thread per
+//      eigenvalue, 30 halvings of the Gershgorin interval (FP32 resolution);
 //   3. eigenvectors of T by two steps of inverse iteration with an LDL^T solve
 //      of T - lambda I; eigenvalues closer than 1e-5 ||T|| form a cluster whose
 //      vectors are computed in order by one thread and Gram-Schmidt
@@ -24,7 +24,7 @@
 
 namespace lspca {
 
-constexpr int kSeedThreads = 1024;
+constexpr int kSeedThreads = 512;
 
 __device__ __forceinline__ float block_sum_f(float v, float* red) {
   v = warp_sumf(v);
@@ -59,7 +59,7 @@ __device__ __forceinline__ int sturm_count(const float* d, const float* e2, int 
 // (no pivoting; tiny pivots replaced by -pivmin), then normalisation.
 // q is per-thread scratch of length k.
 __device__ __forceinline__ void inv_iter(const float* d, const float* e, int k, float lam, float pivmin, float* z, float* q,
-                         int zstride) {
+                         int zstride, int qstride) {
   // factor: q_0 = d_0 - lam, q_i = d_i - lam - e_{i-1}^2 / q_{i-1}; L_i = e_{i-1} / q_{i-1}
   float qi = d[0] - lam;
   if (fabsf(qi) < pivmin) qi = -pivmin;
@@ -67,14 +67,14 @@ __device__ __forceinline__ void inv_iter(const float* d, const float* e, int k, 
   for (int i = 1; i < k; ++i) {
     qi = d[i] - lam - __fdividef(e[i - 1] * e[i - 1], qi);
     if (fabsf(qi) < pivmin) qi = -pivmin;
-    q[i] = qi;
+    q[i * qstride] = qi;
   }
   // forward: L y = z  (L unit lower bidiagonal, L_i = e_{i-1}/q_{i-1})
-  for (int i = 1; i < k; ++i) z[i * zstride] -= __fdividef(e[i - 1], q[i - 1]) * z[(i - 1) * zstride];
+  for (int i = 1; i < k; ++i) z[i * zstride] -= __fdividef(e[i - 1], q[(i - 1) * qstride]) * z[(i - 1) * zstride];
   // diagonal and backward: D L^T x = y
-  z[(k - 1) * zstride] = __fdividef(z[(k - 1) * zstride], q[k - 1]);
+  z[(k - 1) * zstride] = __fdividef(z[(k - 1) * zstride], q[(k - 1) * qstride]);
   for (int i = k - 2; i >= 0; --i) {
-    const float rq = __fdividef(1.f, q[i]);
+    const float rq = __fdividef(1.f, q[i * qstride]);
     z[i * zstride] = z[i * zstride] * rq - (e[i] * rq) * z[(i + 1) * zstride];
   }
   float nrm = 0.f;
@@ -96,6 +96,7 @@ __global__ void __launch_bounds__(kSeedThreads, 1) eig_seed_kernel(const double*
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ float red[33];
   __shared__ float dv[256], ev[256], e2v[256], betav[256], wl[256], pv[256], lamv[256], vv_s[256];
+  __shared__ float gpart[512];
   __shared__ float coef[4];
   __shared__ int clstart[257];
   const bool sm = k <= 128;
@@ -216,25 +217,16 @@ __global__ void __launch_bounds__(kSeedThreads, 1) eig_seed_kernel(const double*
   __syncthreads();
   const float tnorm = coef[2], pivmin = coef[3];
 
-  // ---- 2. eigenvalues by multisection (8 lanes per eigenvalue, ascending index)
-  for (int base = 0; base < k; base += kSeedThreads / 8) {
-    const int idx = base + tid / 8, g = tid & 7;
+  // ---- 2. eigenvalues by bisection (one thread per eigenvalue, ascending index)
+  for (int idx = tid; idx < k; idx += kSeedThreads) {
     float lo = coef[0], hi = coef[1];
-    for (int it = 0; it < 12; ++it) {
-      const float x = lo + (hi - lo) * (float)(g + 1) / 9.f;
-      const int c = (idx < k) ? sturm_count(dv, e2v, k, x, pivmin) : 0;
-      const unsigned gm = 0xFFu << (lane & ~7);
-      const unsigned above = __ballot_sync(0xffffffffu, c > idx) & gm;
-      // first sample whose count exceeds idx bounds the eigenvalue from above
-      const int first = above ? (__ffs(above) - 1) - (lane & ~7) : 8;
-      const float xf = __shfl_sync(0xffffffffu, x, (lane & ~7) + (first < 8 ? first : 7));
-      const float xp = __shfl_sync(0xffffffffu, x, (lane & ~7) + (first > 0 ? first - 1 : 0));
-      const float nlo = first == 0 ? lo : xp;
-      const float nhi = first < 8 ? xf : hi;
-      lo = nlo;
-      hi = nhi;
+#pragma unroll 1
+    for (int it = 0; it < 30; ++it) {
+      const float mid = 0.5f * (lo + hi);
+      if (sturm_count(dv, e2v, k, mid, pivmin) > idx) hi = mid;
+      else lo = mid;
     }
-    if (idx < k && g == 0) lamv[idx] = 0.5f * (lo + hi);
+    lamv[idx] = 0.5f * (lo + hi);
   }
   __syncthreads();
 
@@ -251,14 +243,14 @@ __global__ void __launch_bounds__(kSeedThreads, 1) eig_seed_kernel(const double*
   const int ncl = clstart[256];
   for (int cl = tid; cl < ncl; cl += kSeedThreads) {
     const int i0 = clstart[cl], i1 = clstart[cl + 1];
-    float* q = Qs + (size_t)cl * k;
+    float* q = Qs + cl;  // element i at q[i * k]: the threads of a warp (clusters) hit consecutive banks
     for (int i = i0; i < i1; ++i) {
       // deterministic start vector, then two solves with Gram-Schmidt against
       // the cluster's earlier vectors after each
       for (int r = 0; r < k; ++r) Z[r * k + i] = 1.f + 0.5f * __sinf(0.7f * (float)(r + 3 * i) + 0.3f);
       const float lam = lamv[i];
       for (int rep = 0; rep < 2; ++rep) {
-        inv_iter(dv, ev, k, lam, pivmin, Z + i, q, k);
+        inv_iter(dv, ev, k, lam, pivmin, Z + i, q, k, k);
         for (int pj = (i - 32 > i0 ? i - 32 : i0); pj < i; ++pj) {
           float dot = 0.f;
           for (int r = 0; r < k; ++r) dot = fmaf(Z[r * k + pj], Z[r * k + i], dot);
@@ -282,16 +274,22 @@ __global__ void __launch_bounds__(kSeedThreads, 1) eig_seed_kernel(const double*
     const int n1 = k - j - 1;
     for (int r = tid; r < n1; r += kSeedThreads) vv_s[r] = A[(j + 1 + r) * k + j];
     __syncthreads();
-    // w_c = beta v^T Z[j+1:, c] for every column c; 8 threads per column
-    for (int cbase = 0; cbase < k; cbase += kSeedThreads / 8) {
-      const int c = cbase + tid / 8, g = tid & 7;
-      float acc = 0.f;
-      if (c < k)
-        for (int r = g; r < n1; r += 8) acc = fmaf(vv_s[r], Z[(j + 1 + r) * k + c], acc);
-      acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-      acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-      acc += __shfl_xor_sync(0xffffffffu, acc, 4);
-      if (c < k && g == 0) wl[c] = beta * acc;
+    // w_c = beta v^T Z[j+1:, c]: thread = (row group g, column c), consecutive
+    // threads take consecutive columns (conflict-free), partials summed via SMEM
+    {
+      const int groups = kSeedThreads / k;  // 4 for k = 128, 2 for k = 256
+      for (int t = tid; t < groups * k; t += kSeedThreads) {
+        const int c = t % k, g = t / k;
+        float acc = 0.f;
+        for (int r = g; r < n1; r += groups) acc = fmaf(vv_s[r], Z[(j + 1 + r) * k + c], acc);
+        gpart[g * k + c] = acc;
+      }
+      __syncthreads();
+      for (int c = tid; c < k; c += kSeedThreads) {
+        float acc = 0.f;
+        for (int g = 0; g < groups; ++g) acc += gpart[g * k + c];
+        wl[c] = beta * acc;
+      }
     }
     __syncthreads();
     for (int r = warp; r < n1; r += nw) {

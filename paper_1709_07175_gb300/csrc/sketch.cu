@@ -226,6 +226,222 @@ __global__ void __launch_bounds__(512, 1)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Wide variant for 4-byte accumulation (FP32/BF16/E4M3 X) and k <= 128.
+//
+// Tiles of 128 rows; each lane owns 4 consecutive rows, so one 16-byte shared
+// load of Xt[j][4 lane .. 4 lane + 3] serves 4 rows of one gather.  Chunks of
+// W4 = 128 columns; Xt pitch 132 floats (16-byte aligned rows).  The global
+// loads of a warp instruction cover 16 rows x 2 vectors, which makes the
+// transposing 4-byte stores bank-conflict-free for FP32 (2-way for 2- and
+// 1-byte types).  The Omega entries of every (column, chunk) are re-encoded in
+// shared memory as the byte offset of row j of the chunk, with the sign in bit
+// 31, so a gather is: load code, mask, 16-byte load, sign, four FMAs.
+// NaN/Inf detection and max|X| use one integer max over |bits| per element.
+constexpr int W4 = 128;
+constexpr int P4 = 132;
+constexpr int R4 = 128;
+constexpr int ENT4 = 10240;
+constexpr int OFF4 = 4608;
+
+static size_t smem4_bytes() { return (size_t)2 * W4 * P4 * 4 + (size_t)ENT4 * 4 + (size_t)OFF4 * 4; }
+
+template <int DT>
+__global__ void __launch_bounds__(512, 1)
+    sketch_sparse4_kernel(const void* __restrict__ Xv, int64_t m, int64_t n, int64_t ldx, int k,
+                          const int32_t* __restrict__ col_ptr, const int32_t* __restrict__ entries_g,
+                          int32_t* __restrict__ off_g, int32_t* __restrict__ code_g, float* __restrict__ U,
+                          int64_t ldu, float* absmax, int* status) {
+  using T = typename XType<DT>::T;
+  constexpr int EPV = 16 / (int)sizeof(T);
+  constexpr int VPT = R4 * W4 / EPV / 512;  // 16-byte vectors per thread per chunk
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* buf0 = reinterpret_cast<float*>(smem_raw);
+  float* buf1 = buf0 + W4 * P4;
+  int32_t* code_s = reinterpret_cast<int32_t*>(buf1 + W4 * P4);
+  int32_t* off_s = code_s + ENT4;
+
+  const T* X = reinterpret_cast<const T*>(Xv);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nchunks = (int)((n + W4 - 1) / W4);
+  const int noff = k * (nchunks + 1);
+  const int nnz = col_ptr[k];
+  const bool code_in_smem = nnz <= ENT4;
+  int32_t* codes = code_in_smem ? code_s : code_g;
+  int32_t* off = (noff <= OFF4) ? off_s : off_g;
+  // re-encode: code = sign bit | byte offset of row (j mod W4) inside a chunk buffer
+  for (int e = tid; e < nnz; e += 512) {
+    const int en = entries_g[e];
+    const int j = (en > 0 ? en : -en) - 1;
+    codes[e] = (en < 0 ? (int)0x80000000 : 0) | ((j % W4) * P4 * 4);
+  }
+  for (int c = tid; c < k; c += 512) {
+    int pos = col_ptr[c];
+    const int end = col_ptr[c + 1];
+    for (int q = 0; q < nchunks; ++q) {
+      off[c * (nchunks + 1) + q] = pos;
+      const int64_t lim = (int64_t)(q + 1) * W4;
+      while (pos < end) {
+        const int en = entries_g[pos];
+        if ((int64_t)((en > 0 ? en : -en) - 1) >= lim) break;
+        ++pos;
+      }
+    }
+    off[c * (nchunks + 1) + nchunks] = end;
+  }
+  const int64_t ntiles = (m + R4 - 1) / R4;
+  const int64_t my_tiles = ((int64_t)blockIdx.x < ntiles) ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  const int64_t steps = my_tiles * nchunks;
+  __syncthreads();
+  if (steps == 0) return;
+
+  // per-thread load slots: warp-instruction slot s = q * 16 + warp covers rows
+  // (s % 8) * 16 + (lane % 16) and vector column (s / 8) * 2 + lane / 16
+  const int lr = lane & 15, lh = lane >> 4;
+  uint4 regs[VPT];
+  uint32_t mxb = 0u;
+  float acc[8][4];
+  const int cpw = (k + 15) / 16;
+
+  auto load = [&](int64_t tile, int chunk) {
+    const int64_t r0 = tile * R4, j0 = (int64_t)chunk * W4;
+#pragma unroll
+    for (int q = 0; q < VPT; ++q) {
+      const int s = q * 16 + warp;
+      const int row = (s % 8) * 16 + lr;
+      const int vc = (s / 8) * 2 + lh;
+      const int64_t gr = r0 + row, gj = j0 + (int64_t)vc * EPV;
+      if (gr < m && gj < n)
+        asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(regs[q].x), "=r"(regs[q].y), "=r"(regs[q].z), "=r"(regs[q].w)
+                     : "l"(X + gr * ldx + gj));
+      else
+        regs[q] = make_uint4(0u, 0u, 0u, 0u);
+    }
+  };
+  auto store = [&](int chunk, float* buf) {
+    const int64_t j0 = (int64_t)chunk * W4;
+    const bool tail = j0 + W4 > n;
+#pragma unroll
+    for (int q = 0; q < VPT; ++q) {
+      const int s = q * 16 + warp;
+      const int row = (s % 8) * 16 + lr;
+      const int vc = (s / 8) * 2 + lh;
+      const T* e = reinterpret_cast<const T*>(&regs[q]);
+#pragma unroll
+      for (int u = 0; u < EPV; ++u) {
+        const int jl = vc * EPV + u;
+        float v = XType<DT>::to_acc(e[u]);
+        if (tail && j0 + jl >= n) v = 0.f;
+        mxb = max(mxb, __float_as_uint(v) & 0x7fffffffu);
+        buf[jl * P4 + row] = v;
+      }
+    }
+  };
+
+  int64_t tile = blockIdx.x;
+  int chunk = 0;
+  load(tile, chunk);
+  store(chunk, buf0);
+  __syncthreads();
+  for (int64_t st = 0; st < steps; ++st) {
+    float* cur = (st & 1) ? buf1 : buf0;
+    float* nxt = (st & 1) ? buf0 : buf1;
+    if (chunk == 0) {
+#pragma unroll
+      for (int t = 0; t < 8; ++t)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) acc[t][r] = 0.f;
+    }
+    int64_t ntile = tile;
+    int nchunk = chunk + 1;
+    if (nchunk == nchunks) {
+      nchunk = 0;
+      ntile += gridDim.x;
+    }
+    if (st + 1 < steps) load(ntile, nchunk);
+    const char* cur_lane = reinterpret_cast<const char*>(cur) + lane * 16;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int c = warp + 16 * t;
+      if (t < cpw && c < k) {
+        const int b = off[c * (nchunks + 1) + chunk];
+        const int e = off[c * (nchunks + 1) + chunk + 1];
+        float a0 = acc[t][0], a1 = acc[t][1], a2 = acc[t][2], a3 = acc[t][3];
+#pragma unroll 4
+        for (int i = b; i < e; ++i) {
+          const int code = codes[i];
+          const float4 v = *reinterpret_cast<const float4*>(cur_lane + (code & 0x7fffffff));
+          const float sg = __int_as_float((code & (int)0x80000000) | 0x3f800000);
+          a0 = fmaf(sg, v.x, a0);
+          a1 = fmaf(sg, v.y, a1);
+          a2 = fmaf(sg, v.z, a2);
+          a3 = fmaf(sg, v.w, a3);
+        }
+        acc[t][0] = a0;
+        acc[t][1] = a1;
+        acc[t][2] = a2;
+        acc[t][3] = a3;
+      }
+    }
+    const bool last = (chunk == nchunks - 1);
+    if (st + 1 < steps) store(nchunk, nxt);
+    __syncthreads();
+    if (last) {
+      // stage the tile's U through the buffer just consumed (free until the next
+      // step's store) and write rows coalesced
+      float* us = cur;
+      const int ldp = k + 1;
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int c = warp + 16 * t;
+        if (t < cpw && c < k) {
+#pragma unroll
+          for (int r = 0; r < 4; ++r) us[(4 * lane + r) * ldp + c] = acc[t][r];
+        }
+      }
+      __syncthreads();
+      const int64_t r0 = tile * R4;
+      float umx = 0.f;
+      for (int e = tid; e < R4 * k; e += 512) {
+        const int r = e / k, c = e - r * k;
+        if (r0 + r < m) {
+          const float v = us[r * ldp + c];
+          umx = fmaxf(umx, fabsf(v));
+          U[(r0 + r) * ldu + c] = v;
+        }
+      }
+      umx = warp_max(umx);
+      if (lane == 0) atomic_max_nonneg(absmax + 1, umx);
+      __syncthreads();
+    }
+    tile = ntile;
+    chunk = nchunk;
+  }
+  // one integer max over |bits| covers both max|X| and NaN/Inf (bits >= 0x7f800000)
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mxb = max(mxb, __shfl_xor_sync(0xffffffffu, mxb, o));
+  if (lane == 0) {
+    if (mxb >= 0x7f800000u) atomicOr(status, ST_NONFINITE);
+    else atomic_max_nonneg(absmax, __uint_as_float(mxb));
+  }
+}
+
+template <int DT>
+static bool sketch_sparse4_dispatch(Launcher& L, const void* X, int64_t m, int64_t n, int64_t ldx, int k,
+                                    const int32_t* col_ptr, const int32_t* entries, int32_t* off, int32_t* codes,
+                                    float* U, int64_t ldu, float* absmax, int* status) {
+  if (k > 128) return false;
+  const size_t smem = smem4_bytes();
+  cudaFuncSetAttribute(sketch_sparse4_kernel<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int64_t ntiles = (m + R4 - 1) / R4;
+  const int grid = (int)(ntiles < L.num_sms ? ntiles : L.num_sms);
+  sketch_sparse4_kernel<DT><<<grid, 512, smem, L.stream>>>(X, m, n, ldx, k, col_ptr, entries, off, codes, U, ldu,
+                                                            absmax, status);
+  L.count(1);
+  return true;
+}
+
 template <int DT>
 static void sketch_sparse_dispatch(Launcher& L, const void* X, int64_t m, int64_t n, int64_t ldx, int k,
                                    const int32_t* col_ptr, const int32_t* entries, int32_t* off, void* U, int64_t ldu,
@@ -241,8 +457,14 @@ static void sketch_sparse_dispatch(Launcher& L, const void* X, int64_t m, int64_
 }
 
 size_t sketch_off_bytes(int64_t n, int k) {
-  // worst case over the element types: chunks of 128 columns
-  return (size_t)k * (size_t)((n + 127) / 128 + 1) * 4;
+  // worst case over the element types: chunks of 128 columns; plus room for
+  // the re-encoded entry codes (n * k int32) of the wide kernel
+  return (size_t)k * (size_t)((n + 127) / 128 + 1) * 4 + 256 + (size_t)n * k * 4;
+}
+
+static int32_t* codes_area(int32_t* off, int64_t n, int k) {
+  const size_t a = ((size_t)k * (size_t)((n + 127) / 128 + 1) * 4 + 255) & ~(size_t)255;
+  return reinterpret_cast<int32_t*>(reinterpret_cast<char*>(off) + a);
 }
 
 void launch_sketch_sparse(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_t ldx, int k,
@@ -253,13 +475,19 @@ void launch_sketch_sparse(Launcher& L, const void* X, int xt, int64_t m, int64_t
       sketch_sparse_dispatch<LSPCA_F64>(L, X, m, n, ldx, k, col_ptr, entries, off, U, ldu, absmax, status);
       break;
     case LSPCA_F32:
-      sketch_sparse_dispatch<LSPCA_F32>(L, X, m, n, ldx, k, col_ptr, entries, off, U, ldu, absmax, status);
+      if (!sketch_sparse4_dispatch<LSPCA_F32>(L, X, m, n, ldx, k, col_ptr, entries, off, codes_area(off, n, k),
+                                              (float*)U, ldu, absmax, status))
+        sketch_sparse_dispatch<LSPCA_F32>(L, X, m, n, ldx, k, col_ptr, entries, off, U, ldu, absmax, status);
       break;
     case LSPCA_BF16:
-      sketch_sparse_dispatch<LSPCA_BF16>(L, X, m, n, ldx, k, col_ptr, entries, off, U, ldu, absmax, status);
+      if (!sketch_sparse4_dispatch<LSPCA_BF16>(L, X, m, n, ldx, k, col_ptr, entries, off, codes_area(off, n, k),
+                                               (float*)U, ldu, absmax, status))
+        sketch_sparse_dispatch<LSPCA_BF16>(L, X, m, n, ldx, k, col_ptr, entries, off, U, ldu, absmax, status);
       break;
     case LSPCA_E4M3:
-      sketch_sparse_dispatch<LSPCA_E4M3>(L, X, m, n, ldx, k, col_ptr, entries, off, U, ldu, absmax, status);
+      if (!sketch_sparse4_dispatch<LSPCA_E4M3>(L, X, m, n, ldx, k, col_ptr, entries, off, codes_area(off, n, k),
+                                               (float*)U, ldu, absmax, status))
+        sketch_sparse_dispatch<LSPCA_E4M3>(L, X, m, n, ldx, k, col_ptr, entries, off, U, ldu, absmax, status);
       break;
   }
 }

@@ -35,6 +35,30 @@ struct TcProjectWs {
   void* vlo = nullptr;  // device scalars: max|V|, scale t
 };
 void plan_tc_project(char* base, TcProjectWs& w, int xt, int64_t n, int k);
+
+// Serving batches: one 128-row tile of one request per table entry; all tiles
+// of a launch share the X type and NPAD = k rounded up to 64.
+struct TcProjUnit {
+  const void* X;
+  int64_t ldx;
+  int64_t m;      // rows of the request
+  int64_t row0;   // first row of this tile
+  int64_t n;
+  int32_t k;
+  int32_t pad;
+  const uint8_t* vt;     // V tiles of the request's V (tc_tile_v)
+  const float* vscale;   // V scale (FP32 X) in the V tiles' scalar slot
+  float* Y;              // m x k output of the request
+};
+size_t tc_tile_v_bytes(int64_t n, int k);
+// Split and tile V for X type xt; scal: 2 device floats (max|V|, scale).
+void tc_tile_v(Launcher& L, int xt, const float* V, int64_t n, int k, void* tiles, float* scal, int* status);
+// Y = X V with V already split and tiled by tc_tile_v (vscale = its scale slot).
+void tc_project_pretiled(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_t ldx, const void* tiles,
+                         const float* vscale, int k, float* Y, int* status);
+// One persistent launch over *d_count (<= max_tiles) table entries.
+void tc_project_batch(Launcher& L, int xt, int k, const TcProjUnit* d_units, const int* d_count, int max_tiles,
+                      int* status);
 void tc_project(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_t ldx, const float* V, int k,
                 TcProjectWs& w, float* Y, int* status);
 

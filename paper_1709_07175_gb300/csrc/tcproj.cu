@@ -53,7 +53,46 @@ struct Params {
   const float* vscale;  // device: t (FP32 path) at [0]
   float* Y;             // m x k FP32
   int* status;
+  const TcProjUnit* units;  // table mode (serving batches): tiles of many requests
+  const int* nunits;        // device count of the table
 };
+
+// The tile being processed: from the single matrix, or from the table.
+struct TileInfo {
+  const void* X;
+  int64_t ldx, m, row0, n;
+  int k;
+  const uint8_t* vt;
+  const float* vscale;
+  float* Y;
+};
+
+__device__ __forceinline__ TileInfo tile_info(const Params& p, int64_t t) {
+  TileInfo ti;
+  if (p.units) {
+    const TcProjUnit& u = p.units[t];
+    ti.X = u.X;
+    ti.ldx = u.ldx;
+    ti.m = u.m;
+    ti.row0 = u.row0;
+    ti.n = u.n;
+    ti.k = u.k;
+    ti.vt = u.vt;
+    ti.vscale = u.vscale;
+    ti.Y = u.Y;
+  } else {
+    ti.X = p.X;
+    ti.ldx = p.ldx;
+    ti.m = p.m;
+    ti.row0 = t * 128;
+    ti.n = p.n;
+    ti.k = p.k;
+    ti.vt = p.vt;
+    ti.vscale = p.vscale;
+    ti.Y = p.Y;
+  }
+  return ti;
+}
 
 template <int XK, int NT>
 struct Cfg {
@@ -95,8 +134,7 @@ __global__ void __launch_bounds__(THREADS, 1) project_kernel(Params p) {
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t tiles = (p.m + 127) / 128;
-  const int nks = (int)((p.n + BK - 1) / BK);
+  const int64_t tiles = p.units ? (int64_t)*p.nunits : (p.m + 127) / 128;
 
   if (tid == 0) {
     for (int s = 0; s < C::STAGES; ++s) {
@@ -125,7 +163,7 @@ __global__ void __launch_bounds__(THREADS, 1) project_kernel(Params p) {
     // ------------------------------------------------------------ converters
     constexpr int NV = (XK == XK_F32) ? 8 : (XK == XK_BF16 ? 4 : 2);  // 16-byte vectors per thread per k-step
     uint4 r[NV], rn[NV];
-    auto load = [&](int64_t tile, int ks, uint4 (&dst)[NV]) {
+    auto load = [&](const TileInfo& ti, int ks, uint4 (&dst)[NV]) {
 #pragma unroll
       for (int q = 0; q < NV; ++q) {
         const int f = tid + CONV_THREADS * q;
@@ -133,9 +171,9 @@ __global__ void __launch_bounds__(THREADS, 1) project_kernel(Params p) {
         if (XK == XK_F32) { row = f / 16; col = (f % 16) * 4; }
         else if (XK == XK_BF16) { row = f / 8; col = (f % 8) * 8; }
         else { row = f / 4; col = (f % 4) * 16; }
-        const int64_t gr = tile * 128 + row, gc = (int64_t)ks * BK + col;
-        if (gr < p.m && gc < p.n) {
-          const char* src = (const char*)p.X + (gr * p.ldx + gc) * (XK == XK_F32 ? 4 : (XK == XK_BF16 ? 2 : 1));
+        const int64_t gr = ti.row0 + row, gc = (int64_t)ks * BK + col;
+        if (gr < ti.m && gc < ti.n) {
+          const char* src = (const char*)ti.X + (gr * ti.ldx + gc) * (XK == XK_F32 ? 4 : (XK == XK_BF16 ? 2 : 1));
           asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
                        : "=r"(dst[q].x), "=r"(dst[q].y), "=r"(dst[q].z), "=r"(dst[q].w)
                        : "l"(src));
@@ -144,7 +182,7 @@ __global__ void __launch_bounds__(THREADS, 1) project_kernel(Params p) {
         }
       }
     };
-    auto store = [&](uint32_t st, int slot, int ks) {
+    auto store = [&](uint32_t st, int slot, int ks, int64_t ncols) {
       const uint32_t a_hi = st + 2 * C::B_BYTES, a_lo = a_hi + C::A_BYTES;
 #pragma unroll
       for (int q = 0; q < NV; ++q) {
@@ -157,7 +195,7 @@ __global__ void __launch_bounds__(THREADS, 1) project_kernel(Params p) {
           const int64_t gc = (int64_t)ks * BK + col;
 #pragma unroll
           for (int u = 0; u < 4; ++u)
-            if (gc + u >= p.n) v[u] = 0.f;
+            if (gc + u >= ncols) v[u] = 0.f;
           float mx = fmaxf(fmaxf(fabsf(v[0]), fabsf(v[1])), fmaxf(fabsf(v[2]), fabsf(v[3])));
 #pragma unroll
           for (int o = 1; o < 16; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -179,11 +217,11 @@ __global__ void __launch_bounds__(THREADS, 1) project_kernel(Params p) {
           const int row = f / 8, col = (f % 8) * 8;
           uint4 v = r[q];
           const int64_t gc = (int64_t)ks * BK + col;
-          if (gc + 8 > p.n) {
+          if (gc + 8 > ncols) {
             uint16_t* e = reinterpret_cast<uint16_t*>(&v);
 #pragma unroll
             for (int u = 0; u < 8; ++u)
-              if (gc + u >= p.n) e[u] = 0;
+              if (gc + u >= ncols) e[u] = 0;
           }
           asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a_hi + ptx::k_sw128_offset(row, col)),
                        "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
@@ -195,8 +233,8 @@ __global__ void __launch_bounds__(THREADS, 1) project_kernel(Params p) {
           uint32_t w[8];
 #pragma unroll
           for (int u = 0; u < 8; ++u) {
-            float a = (gc + 2 * u < p.n) ? float(e8[2 * u]) : 0.f;
-            float b = (gc + 2 * u + 1 < p.n) ? float(e8[2 * u + 1]) : 0.f;
+            float a = (gc + 2 * u < ncols) ? float(e8[2 * u]) : 0.f;
+            float b = (gc + 2 * u + 1 < ncols) ? float(e8[2 * u + 1]) : 0.f;
             __nv_bfloat162 h2 = __floats2bfloat162_rn(a, b);
             w[u] = *reinterpret_cast<uint32_t*>(&h2);
           }
@@ -213,8 +251,10 @@ __global__ void __launch_bounds__(THREADS, 1) project_kernel(Params p) {
     int ks = 0;
     int64_t step = 0;
     if (tile < tiles) {
-      load(tile, ks, r);
+      TileInfo ti = tile_info(p, tile), tn = ti;
+      load(ti, ks, r);
       while (true) {
+        const int nks = (int)((ti.n + BK - 1) / BK);
         int64_t ntile = tile;
         int nks_next = ks + 1;
         if (nks_next >= nks) {
@@ -222,7 +262,10 @@ __global__ void __launch_bounds__(THREADS, 1) project_kernel(Params p) {
           ntile += gridDim.x;
         }
         const bool more = ntile < tiles;
-        if (more) load(ntile, nks_next, rn);
+        if (more) {
+          if (ntile != tile) tn = tile_info(p, ntile);
+          load(ntile != tile ? tn : ti, nks_next, rn);
+        }
         const int s = (int)(step % C::STAGES);
         const uint32_t ph = (uint32_t)((step / C::STAGES) & 1);
         if (!ptx::mbar_wait(&empty[s], ph ^ 1u, kWaitNs)) {
@@ -233,14 +276,15 @@ __global__ void __launch_bounds__(THREADS, 1) project_kernel(Params p) {
         const uint32_t st = sbase + s * C::STAGE_BYTES;
         if (warp == 0 && lane == 0) {
           ptx::mbar_arrive_expect_tx(&full[s], 2 * C::B_BYTES);
-          ptx::bulk_g2s(st, p.vt + (size_t)ks * 2 * C::B_BYTES, 2 * C::B_BYTES, &full[s]);
+          ptx::bulk_g2s(st, ti.vt + (size_t)ks * 2 * C::B_BYTES, 2 * C::B_BYTES, &full[s]);
         }
-        store(st, (int)(step % C::RING), ks);
+        store(st, (int)(step % C::RING), ks, ti.n);
         ptx::fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) ptx::mbar_arrive(&full[s]);
         ++step;
         if (!more) break;
+        if (ntile != tile) ti = tn;
         tile = ntile;
         ks = nks_next;
 #pragma unroll
@@ -254,6 +298,7 @@ __global__ void __launch_bounds__(THREADS, 1) project_kernel(Params p) {
       int64_t step = 0;
       bool ok = true;
       for (int64_t tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+        const int nks = (int)((tile_info(p, tile).n + BK - 1) / BK);
         for (int ks = 0; ks < nks; ++ks, ++step) {
           if (!ptx::mbar_wait(acce, (uint32_t)((step & 1) ^ 1), kWaitNs)) {
             fail();
@@ -295,12 +340,14 @@ __global__ void __launch_bounds__(THREADS, 1) project_kernel(Params p) {
     // ------------------------------------------------------------ epilogue
     const int e = warp - EPI_WARP0;
     const uint32_t lane_base = (uint32_t)(32 * e) << 16;
-    const float inv_t = (XK == XK_F32) ? 1.f / *p.vscale : 1.f;
     int64_t step = 0;
     bool ok = true;
     for (int64_t tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+      const TileInfo ti = tile_info(p, tile);
+      const float inv_t = (XK == XK_F32) ? 1.f / *ti.vscale : 1.f;
+      const int nks = (int)((ti.n + BK - 1) / BK);
       const int row = 32 * e + lane;
-      const int64_t grow = tile * 128 + row;
+      const int64_t grow = ti.row0 + row;
       for (int ks = 0; ks < nks; ++ks, ++step) {
         if (!ptx::mbar_wait(accf, (uint32_t)(step & 1), kWaitNs) || aborted()) {
           if (!aborted()) fail();
@@ -325,9 +372,9 @@ __global__ void __launch_bounds__(THREADS, 1) project_kernel(Params p) {
           }
           if (!last) {
             ptx::tmem_st32(tmem + lane_base + (uint32_t)(C::NPAD + c0), sacc);
-          } else if (grow < p.m) {
-            float* dst = p.Y + grow * p.k + c0;
-            if (c0 + 32 <= p.k && (p.k % 4) == 0) {
+          } else if (grow < ti.m) {
+            float* dst = ti.Y + grow * ti.k + c0;
+            if (c0 + 32 <= ti.k && (ti.k % 4) == 0) {
 #pragma unroll
               for (int q = 0; q < 32; q += 4)
                 *reinterpret_cast<float4*>(dst + q) = make_float4(__uint_as_float(sacc[q]), __uint_as_float(sacc[q + 1]),
@@ -336,7 +383,7 @@ __global__ void __launch_bounds__(THREADS, 1) project_kernel(Params p) {
             } else {
 #pragma unroll
               for (int q = 0; q < 32; ++q)
-                if (c0 + q < p.k) dst[q] = __uint_as_float(sacc[q]);
+                if (c0 + q < ti.k) dst[q] = __uint_as_float(sacc[q]);
             }
           }
         }
@@ -394,22 +441,22 @@ __global__ void tile_v_kernel(const float* __restrict__ V, int64_t n, int k, int
 }
 
 template <int XK, int NT>
-static void launch_project(Launcher& L, const Params& p) {
+static void launch_project(Launcher& L, const Params& p, int max_tiles) {
   using C = Cfg<XK, NT>;
   cudaFuncSetAttribute(project_kernel<XK, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-  const int64_t tiles = (p.m + 127) / 128;
-  const int grid = (int)(tiles < L.num_sms ? tiles : L.num_sms);
+  const int64_t tiles = p.units ? max_tiles : (p.m + 127) / 128;
+  const int grid = (int)(tiles < L.num_sms ? (tiles > 0 ? tiles : 1) : L.num_sms);
   project_kernel<XK, NT><<<grid, THREADS, C::SMEM, L.stream>>>(p);
   L.count(1);
 }
 
 template <int XK>
-static void launch_project_nt(Launcher& L, const Params& p, int nt) {
+static void launch_project_nt(Launcher& L, const Params& p, int nt, int max_tiles) {
   switch (nt) {
-    case 1: launch_project<XK, 1>(L, p); break;
-    case 2: launch_project<XK, 2>(L, p); break;
-    case 3: launch_project<XK, 3>(L, p); break;
-    default: launch_project<XK, 4>(L, p); break;
+    case 1: launch_project<XK, 1>(L, p, max_tiles); break;
+    case 2: launch_project<XK, 2>(L, p, max_tiles); break;
+    case 3: launch_project<XK, 3>(L, p, max_tiles); break;
+    default: launch_project<XK, 4>(L, p, max_tiles); break;
   }
 }
 
@@ -456,10 +503,62 @@ void tc_project(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_
   p.vscale = scal + 1;
   p.Y = Y;
   p.status = status;
+  p.units = nullptr;
+  p.nunits = nullptr;
   const int nt = npad / 64;
-  if (xt == LSPCA_F32) tcp::launch_project_nt<tcp::XK_F32>(L, p, nt);
-  else if (xt == LSPCA_BF16) tcp::launch_project_nt<tcp::XK_BF16>(L, p, nt);
-  else tcp::launch_project_nt<tcp::XK_E4M3>(L, p, nt);
+  if (xt == LSPCA_F32) tcp::launch_project_nt<tcp::XK_F32>(L, p, nt, 0);
+  else if (xt == LSPCA_BF16) tcp::launch_project_nt<tcp::XK_BF16>(L, p, nt, 0);
+  else tcp::launch_project_nt<tcp::XK_E4M3>(L, p, nt, 0);
+}
+
+void tc_project_pretiled(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_t ldx, const void* tiles,
+                         const float* vscale, int k, float* Y, int* status) {
+  tcp::Params p{};
+  p.X = X;
+  p.ldx = ldx;
+  p.m = m;
+  p.n = n;
+  p.k = k;
+  p.vt = (const uint8_t*)tiles;
+  p.vscale = vscale;
+  p.Y = Y;
+  p.status = status;
+  p.units = nullptr;
+  p.nunits = nullptr;
+  const int nt = (k + 63) / 64;
+  if (xt == LSPCA_F32) tcp::launch_project_nt<tcp::XK_F32>(L, p, nt, 0);
+  else if (xt == LSPCA_BF16) tcp::launch_project_nt<tcp::XK_BF16>(L, p, nt, 0);
+  else tcp::launch_project_nt<tcp::XK_E4M3>(L, p, nt, 0);
+}
+
+size_t tc_tile_v_bytes(int64_t n, int k) {
+  const int npad = (k + 63) / 64 * 64;
+  return (size_t)((n + tcp::BK - 1) / tcp::BK) * 2 * tcp::BK * npad * 2;
+}
+
+void tc_tile_v(Launcher& L, int xt, const float* V, int64_t n, int k, void* tiles, float* scal, int* status) {
+  const int npad = (k + 63) / 64 * 64;
+  const bool f16 = xt == LSPCA_F32;
+  cudaMemsetAsync(scal, 0, 8, L.stream);
+  if (f16) launch_scan_x(L, V, LSPCA_F32, n, k, k, scal, status);
+  const int64_t nks = (n + tcp::BK - 1) / tcp::BK;
+  const int64_t total = nks * tcp::BK * npad;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 16 * L.num_sms) blocks = 16 * L.num_sms;
+  tcp::tile_v_kernel<<<blocks, 256, 0, L.stream>>>(V, n, k, npad, f16 ? 1 : 0, scal, scal + 1, (uint8_t*)tiles);
+  L.count(1);
+}
+
+void tc_project_batch(Launcher& L, int xt, int k, const TcProjUnit* d_units, const int* d_count, int max_tiles,
+                      int* status) {
+  tcp::Params p{};
+  p.units = d_units;
+  p.nunits = d_count;
+  p.status = status;
+  const int nt = (k + 63) / 64;
+  if (xt == LSPCA_F32) tcp::launch_project_nt<tcp::XK_F32>(L, p, nt, max_tiles);
+  else if (xt == LSPCA_BF16) tcp::launch_project_nt<tcp::XK_BF16>(L, p, nt, max_tiles);
+  else tcp::launch_project_nt<tcp::XK_E4M3>(L, p, nt, max_tiles);
 }
 
 }  // namespace lspca

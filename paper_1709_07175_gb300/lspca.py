@@ -72,6 +72,17 @@ _SIGS = {
     "lspca_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "lspca_launch_count": (ctypes.c_int64, [_P]),
     "lspca_chain_noalloc": (ctypes.c_int, [_P, _I32, _I64, _I64, _I64, _P, _I32, _P, _P, _P]),
+    "lspca_srv_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, _SZ, _I32]),
+    "lspca_srv_destroy": (ctypes.c_int, [_P]),
+    "lspca_srv_register_v": (ctypes.c_int, [_P, _P, _I64, _I32, ctypes.POINTER(_I32)]),
+    "lspca_srv_submit_project": (ctypes.c_int, [_P, _I32, _P, _I32, _I64, _I64, _P, ctypes.POINTER(_I64)]),
+    "lspca_srv_submit_fit": (ctypes.c_int, [_P, _P, _I32, _I64, _I64, _I64, _I32, lspca_omega, _P, _P,
+                                            ctypes.POINTER(_I64)]),
+    "lspca_srv_step": (ctypes.c_int, [_P, ctypes.POINTER(_I32)]),
+    "lspca_srv_poll": (ctypes.c_int, [_P, _I64, ctypes.POINTER(_I32)]),
+    "lspca_srv_wait": (ctypes.c_int, [_P, _I64, _I32]),
+    "lspca_srv_release": (ctypes.c_int, [_P, _I64]),
+    "lspca_srv_launch_count": (ctypes.c_int64, [_P]),
     "lspca_profile": (ctypes.c_int, [_P, ctypes.c_int]),
     "lspca_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64)]),
 }
@@ -208,6 +219,126 @@ def lspca_profile_read(ctx):
     if rc:
         raise LspcaError(rc, "lspca_profile_read")
     return list(ms), calls.value
+
+
+# ---- serving ------------------------------------------------------------------
+
+def lspca_srv_create(device: int = 0, hbm_budget_bytes: int = 0, max_inflight: int = 64) -> int:
+    h = _P()
+    rc = load().lspca_srv_create(ctypes.byref(h), device, hbm_budget_bytes, max_inflight)
+    if rc:
+        raise LspcaError(rc, "lspca_srv_create")
+    return h.value
+
+
+def lspca_srv_destroy(srv) -> int:
+    return load().lspca_srv_destroy(srv)
+
+
+def lspca_srv_register_v(srv, V) -> int:
+    vid = _I32()
+    rc = load().lspca_srv_register_v(srv, _ptr(V), V.shape[0], V.shape[1], ctypes.byref(vid))
+    if rc:
+        raise LspcaError(rc, "lspca_srv_register_v")
+    return vid.value
+
+
+def lspca_srv_submit_project(srv, v_id, X, Y) -> tuple:
+    x, xt, m, n, ldx = _xargs(X)
+    req = _I64()
+    rc = load().lspca_srv_submit_project(srv, v_id, x, xt, m, ldx, _ptr(Y), ctypes.byref(req))
+    return rc, req.value
+
+
+def lspca_srv_submit_fit(srv, X, k, om, V, sigma) -> tuple:
+    x, xt, m, n, ldx = _xargs(X)
+    req = _I64()
+    rc = load().lspca_srv_submit_fit(srv, x, xt, m, n, ldx, k, om, _ptr(V), _ptr(sigma), ctypes.byref(req))
+    return rc, req.value
+
+
+def lspca_srv_step(srv) -> tuple:
+    u = _I32()
+    rc = load().lspca_srv_step(srv, ctypes.byref(u))
+    return rc, u.value
+
+
+def lspca_srv_poll(srv, req) -> tuple:
+    d = _I32()
+    rc = load().lspca_srv_poll(srv, req, ctypes.byref(d))
+    return rc, bool(d.value)
+
+
+def lspca_srv_wait(srv, req, timeout_ms: int = 60000) -> int:
+    return load().lspca_srv_wait(srv, req, timeout_ms)
+
+
+def lspca_srv_release(srv, req) -> int:
+    return load().lspca_srv_release(srv, req)
+
+
+def lspca_srv_launch_count(srv) -> int:
+    return load().lspca_srv_launch_count(srv)
+
+
+class Server:
+    """Continuous-batching server (lspca_srv_*): projections and fits."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, max_inflight: int = 64):
+        self.handle = lspca_srv_create(device, hbm_budget_bytes, max_inflight)
+        self.device = device
+        self._keep = {}
+
+    def close(self):
+        if self.handle:
+            lspca_srv_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def register_v(self, V) -> int:
+        vid = lspca_srv_register_v(self.handle, V)
+        self._keep[("v", vid)] = V
+        return vid
+
+    def submit_project(self, v_id, X):
+        k = self._keep[("v", v_id)].shape[1]
+        Y = torch.empty(X.shape[0], k, dtype=torch.float32, device=X.device)
+        rc, req = lspca_srv_submit_project(self.handle, v_id, X, Y)
+        _check(rc, "lspca_srv_submit_project")
+        self._keep[req] = (X, Y)
+        return req, Y
+
+    def submit_fit(self, X, k, om):
+        V = torch.empty(X.shape[1], k, dtype=torch.float32, device=X.device)
+        sigma = torch.empty(k, dtype=torch.float64, device=X.device)
+        rc, req = lspca_srv_submit_fit(self.handle, X, k, om, V, sigma)
+        _check(rc, "lspca_srv_submit_fit")
+        self._keep[req] = (X, V, sigma)
+        return req, V, sigma
+
+    def step(self) -> int:
+        rc, u = lspca_srv_step(self.handle)
+        _check(rc, "lspca_srv_step")
+        return u
+
+    def done(self, req) -> bool:
+        rc, d = lspca_srv_poll(self.handle, req)
+        _check(rc, "lspca_srv_poll")
+        return d
+
+    def wait(self, req, timeout_ms: int = 60000):
+        _check(lspca_srv_wait(self.handle, req, timeout_ms), "lspca_srv_wait")
+
+    def release(self, req):
+        rc = lspca_srv_release(self.handle, req)
+        if rc == OK:
+            self._keep.pop(req, None)
+        return rc
 
 
 # ---- a small convenience wrapper (allocates outputs with torch) --------------
