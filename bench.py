@@ -220,6 +220,16 @@ def serve_bench(L, S, torch, local: int, seconds: float, load: float = 0.8, seed
                           "capacity_req_s": 1.0 / svc.mean()}}
 
 
+# DRAM bytes (read + write) per row of X of one launch, from one ncu capture at
+# 50,000 rows of the same workload (profiles/sketch_sparse4_fp32_50000x4096.md,
+# profiles/chain_kernel_fp32_50000x4096.md); traffic grows in proportion to the
+# rows.  Set an entry to None when its kernel changes until it is captured again.
+TRAFFIC_PER_ROW = {
+    "sketch": (819.383808e6 + 7.583488e6) / 50000,
+    "chain_main": (846.242048e6 + 24.446976e6) / 50000,
+}
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -375,7 +385,8 @@ def run_gpu(args):
     peak, peak_kind = _peaks()
     achieved = alg[dom] / (per[dom] / 1e3) / 1e9
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+            "frac": achieved / peak, "peak_kind": peak_kind,
+            "traffic": (TRAFFIC_PER_ROW[dom] * w.m if TRAFFIC_PER_ROW.get(dom) else None),
             "bytes_per_launch": alg[dom], "ms_per_launch": per[dom]}
 
     line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": ws, "steps": args.steps,

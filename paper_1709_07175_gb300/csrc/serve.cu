@@ -16,8 +16,12 @@
 //   of rows (sketch of the slice, pass F of the slice, F += F_slice in FP64);
 //   after the last slice the k x k step produces V and sigma.  Slices are fixed
 //   per request, so a fit's arithmetic does not depend on what else runs.
-// * A batch records one event; the requests it completes are done when that
-//   event has completed (lspca_srv_poll / lspca_srv_wait with a bounded wait).
+// * Projections run on a high-priority stream and fit slices on a low-priority
+//   one, so a projection waits for at most the fit kernel that occupies the
+//   SMs when it arrives, not for the fit slices queued behind it.
+// * A batch records one event per stream; the requests it completes are done
+//   when that event has completed (lspca_srv_poll / lspca_srv_wait with a
+//   bounded wait).
 #include <algorithm>
 #include <chrono>
 #include <cstring>
@@ -89,7 +93,8 @@ using namespace lspca;
 struct lspca_srv {
   int device = 0;
   int num_sms = 0;
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;   // fits (low priority)
+  cudaStream_t pstream = nullptr;  // projections (high priority)
   char* arena = nullptr;
   size_t arena_size = 0;
   std::map<size_t, size_t> free_blocks;  // offset -> size
@@ -284,7 +289,14 @@ int lspca_srv_create(lspca_srv** out, int device, size_t hbm_budget_bytes, int32
   s->device = device;
   s->max_inflight = max_inflight;
   cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, device);
-  if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
+  int least = 0, greatest = 0;
+  cudaDeviceGetStreamPriorityRange(&least, &greatest);
+  if (cudaStreamCreateWithPriority(&s->stream, cudaStreamNonBlocking, least) != cudaSuccess) {
+    delete s;
+    return LSPCA_ERR_CUDA;
+  }
+  if (cudaStreamCreateWithPriority(&s->pstream, cudaStreamNonBlocking, greatest) != cudaSuccess) {
+    cudaStreamDestroy(s->stream);
     delete s;
     return LSPCA_ERR_CUDA;
   }
@@ -292,6 +304,7 @@ int lspca_srv_create(lspca_srv** out, int device, size_t hbm_budget_bytes, int32
   if (cudaMalloc(&s->arena, hbm_budget_bytes) != cudaSuccess) {
     cudaGetLastError();
     cudaStreamDestroy(s->stream);
+    cudaStreamDestroy(s->pstream);
     delete s;
     return LSPCA_ERR_NOMEM;
   }
@@ -317,6 +330,7 @@ int lspca_srv_destroy(lspca_srv* s) {
   if (!s) return LSPCA_ERR_INVALID;
   cudaSetDevice(s->device);
   cudaStreamSynchronize(s->stream);
+  cudaStreamSynchronize(s->pstream);
   for (int g = 0; g < kGroups; ++g) {
     for (int b = 0; b < 2; ++b) {
       if (s->gexec[g][b]) cudaGraphExecDestroy(s->gexec[g][b]);
@@ -335,6 +349,7 @@ int lspca_srv_destroy(lspca_srv* s) {
   cudaFree(s->arena);
   cudaFree(s->d_status);
   cudaStreamDestroy(s->stream);
+  cudaStreamDestroy(s->pstream);
   delete s;
   return LSPCA_OK;
 }
@@ -404,7 +419,8 @@ int lspca_srv_submit_fit(lspca_srv* s, const void* X, int32_t xt, int64_t m, int
 int lspca_srv_step(lspca_srv* s, int32_t* work_units) {
   if (!s) return LSPCA_ERR_INVALID;
   if (cudaSetDevice(s->device) != cudaSuccess) return LSPCA_ERR_CUDA;
-  Launcher L{s->stream, &s->launches, s->num_sms};
+  Launcher L{s->stream, &s->launches, s->num_sms};    // fits
+  Launcher Lp{s->pstream, &s->launches, s->num_sms};  // projections
   retire(s);
   // 1. admission, FIFO: a slot, and for fits an arena block
   while (!s->queue.empty() && s->inflight < s->max_inflight) {
@@ -418,7 +434,7 @@ int lspca_srv_step(lspca_srv* s, int32_t* work_units) {
   int units = 0;
   // 2. projection tiles of all running projections, grouped by (X type, padded k)
   int cnt[kGroups] = {};
-  std::vector<int64_t> finishing;
+  std::vector<int64_t> finishing, pfinishing;
   for (int64_t id : s->running) {
     Req& r = s->reqs[id];
     if (r.kind != KIND_PROJECT || r.finishing) continue;
@@ -429,7 +445,7 @@ int lspca_srv_step(lspca_srv* s, int32_t* work_units) {
       const size_t bytes = tc_tile_v_bytes(v.n, v.k) + 256;
       if (!arena_alloc(s, bytes, &off)) continue;  // wait for memory
       v.tiles_off[xi] = off;
-      tc_tile_v(L, r.xt, v.V, v.n, v.k, s->arena + off + 256, (float*)(s->arena + off), s->d_status);
+      tc_tile_v(Lp, r.xt, v.V, v.n, v.k, s->arena + off + 256, (float*)(s->arena + off), s->d_status);
       v.ready[xi] = true;
     }
     const int g = group_of(r.xt, r.k);
@@ -452,7 +468,7 @@ int lspca_srv_step(lspca_srv* s, int32_t* work_units) {
     }
     if (r.next >= r.rows) {
       r.finishing = true;
-      finishing.push_back(id);
+      pfinishing.push_back(id);
     }
   }
   for (int g = 0; g < kGroups; ++g) {
@@ -465,34 +481,34 @@ int lspca_srv_step(lspca_srv* s, int32_t* work_units) {
     if (!s->warmed[g]) {
       // first batch of the group: direct launch (sets kernel attributes), then capture
       cudaMemcpyAsync(s->d_units[g], s->h_units[g][b], sizeof(TcProjUnit) * kMaxTiles, cudaMemcpyHostToDevice,
-                      s->stream);
-      cudaMemcpyAsync(s->d_count[g], s->h_count[g][b], sizeof(int), cudaMemcpyHostToDevice, s->stream);
-      tc_project_batch(L, xt, k, s->d_units[g], s->d_count[g], kMaxTiles, s->d_status);
+                      s->pstream);
+      cudaMemcpyAsync(s->d_count[g], s->h_count[g][b], sizeof(int), cudaMemcpyHostToDevice, s->pstream);
+      tc_project_batch(Lp, xt, k, s->d_units[g], s->d_count[g], kMaxTiles, s->d_status);
       for (int bb = 0; bb < 2; ++bb) {
         cudaGraph_t graph = nullptr;
         int64_t dummy = 0;
-        Launcher Lc{s->stream, &dummy, s->num_sms};
-        if (cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) break;
+        Launcher Lc{s->pstream, &dummy, s->num_sms};
+        if (cudaStreamBeginCapture(s->pstream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) break;
         cudaMemcpyAsync(s->d_units[g], s->h_units[g][bb], sizeof(TcProjUnit) * kMaxTiles, cudaMemcpyHostToDevice,
-                        s->stream);
-        cudaMemcpyAsync(s->d_count[g], s->h_count[g][bb], sizeof(int), cudaMemcpyHostToDevice, s->stream);
+                        s->pstream);
+        cudaMemcpyAsync(s->d_count[g], s->h_count[g][bb], sizeof(int), cudaMemcpyHostToDevice, s->pstream);
         tc_project_batch(Lc, xt, k, s->d_units[g], s->d_count[g], kMaxTiles, s->d_status);
-        if (cudaStreamEndCapture(s->stream, &graph) != cudaSuccess || !graph) break;
+        if (cudaStreamEndCapture(s->pstream, &graph) != cudaSuccess || !graph) break;
         if (cudaGraphInstantiate(&s->gexec[g][bb], graph, 0) != cudaSuccess) s->gexec[g][bb] = nullptr;
         cudaGraphDestroy(graph);
       }
       cudaGetLastError();
       s->warmed[g] = true;
     } else if (s->gexec[g][b]) {
-      cudaGraphLaunch(s->gexec[g][b], s->stream);
+      cudaGraphLaunch(s->gexec[g][b], s->pstream);
       s->launches += 1;
     } else {
       cudaMemcpyAsync(s->d_units[g], s->h_units[g][b], sizeof(TcProjUnit) * kMaxTiles, cudaMemcpyHostToDevice,
-                      s->stream);
-      cudaMemcpyAsync(s->d_count[g], s->h_count[g][b], sizeof(int), cudaMemcpyHostToDevice, s->stream);
-      tc_project_batch(L, xt, k, s->d_units[g], s->d_count[g], kMaxTiles, s->d_status);
+                      s->pstream);
+      cudaMemcpyAsync(s->d_count[g], s->h_count[g][b], sizeof(int), cudaMemcpyHostToDevice, s->pstream);
+      tc_project_batch(Lp, xt, k, s->d_units[g], s->d_count[g], kMaxTiles, s->d_status);
     }
-    cudaEventRecord(s->buf_ev[g][b], s->stream);
+    cudaEventRecord(s->buf_ev[g][b], s->pstream);
     s->flip[g] ^= 1;
   }
   // 3. one Algorithm-4 slice of every running fit
@@ -505,7 +521,12 @@ int lspca_srv_step(lspca_srv* s, int32_t* work_units) {
     if (r.finishing) finishing.push_back(id);
   }
   // 4. completion events of the requests this batch finishes (one event each,
-  //    recorded after the batch's last launch)
+  //    recorded after the batch's last launch on the request's stream)
+  for (int64_t id : pfinishing) {
+    Req& r = s->reqs[id];
+    r.ev = take_event(s);
+    cudaEventRecord(r.ev, s->pstream);
+  }
   for (int64_t id : finishing) {
     Req& r = s->reqs[id];
     r.ev = take_event(s);
