@@ -3,10 +3,12 @@
 // The FP64 refinement that follows (small.cu) needs eigenvectors accurate to
 // well under a radian per pair; a standard dense symmetric route gives them in
 // O(k^3) flops with O(k) synchronisations:
-//   1. Householder tridiagonalisation  H = Q T Q^T  (reflectors kept in the
-//      lower triangle, as in LAPACK's sytrd);
-//   2. eigenvalues of T by bisection on Sturm counts, one thread per
-//      eigenvalue, 30 halvings of the Gershgorin interval (FP32 resolution);
+//   1. Householder tridiagonalisation  H = Q T Q^T; the reflector of step j
+//      is kept in row j right of the diagonal (the trailing block is updated
+//      whole, so row j equals column j and is read contiguously);
+//   2. eigenvalues of T by multisection on Sturm counts: 4 threads per
+//      eigenvalue (2 for k > 128) split the bracket into 5 (3) parts per
+//      round, to the resolution of 30 halvings of the Gershgorin interval;
 //   3. eigenvectors of T by two steps of inverse iteration with an LDL^T solve
 //      of T - lambda I; eigenvalues closer than 1e-5 ||T|| form a cluster whose
 //      vectors are computed in order by one thread and Gram-Schmidt
@@ -16,30 +18,15 @@
 //      what the FP64 refinement corrects);
 //   4. back-transformation W = Q Z.
 // H is scaled by 1 / max|H_ii| first.  Matrices live in shared memory for
-// k <= 128 and in a global scratch otherwise; Householder vectors are copied
-// to a contiguous vector before use (a column of the row-major matrix would
-// bank-conflict on every read).
+// k <= 128 and in a global scratch otherwise.  Steps 1 and 4 map thread t to
+// (group t / kp, column t % kp), kp = 128 or 256, so consecutive lanes touch
+// consecutive addresses and every step needs at most four block barriers.
 #include "common.cuh"
 #include "kernels.h"
 
 namespace lspca {
 
 constexpr int kSeedThreads = 512;
-
-__device__ __forceinline__ float block_sum_f(float v, float* red) {
-  v = warp_sumf(v);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) red[wid] = v;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    float s = (threadIdx.x < (int)(blockDim.x >> 5)) ? red[threadIdx.x] : 0.f;
-    s = warp_sumf(s);
-    if (threadIdx.x == 0) red[32] = s;
-  }
-  __syncthreads();
-  return red[32];
-}
 
 // Number of eigenvalues of T (d, e) smaller than x (Sturm count).
 __device__ __forceinline__ int sturm_count(const float* d, const float* e2, int k, float x, float pivmin) {
@@ -89,20 +76,204 @@ __device__ __forceinline__ void inv_iter(const float* d, const float* e, int k, 
   for (int i = 0; i < k; ++i) z[i * zstride] *= inv;
 }
 
+// Register-resident forms of steps 1 and 4 for k <= 128: thread t owns the
+// entries (r, c) with c = t mod 128 and r = t / 128 + 4 i, i = 0..31, of the
+// matrix being reduced (step 1) or back-transformed (step 4).  Vectors indexed
+// by row are also kept "permuted", x[(r mod 4) * 32 + r / 4], so that a thread
+// reads the 32 entries of its rows with eight 16-byte broadcast loads.
+// Vectors are zero outside the active range, which makes every update a plain
+// multiply-add over all 32 rows (no predicates).
+__device__ __forceinline__ int perm_idx(int r) { return (r & 3) * 32 + (r >> 2); }
+
+// Step 1: tridiagonalisation.  A (k x k, row-major, already scaled) is read
+// from `Asrc`; the reflectors are left in Vh (row j: permuted v_j) and d, e,
+// beta in dv, ev, betav.  Four barriers per reflector.
+__device__ void tridiag_regs(const float* Asrc, int k, float* Vh, float* dv, float* ev, float* betav, float* rowbuf,
+                             float* vfl, float* wl, float* vperm, float* wperm, float* gpart) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tr = tid & 127, tg = tid >> 7;
+  float a[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    const int r = tg + 4 * i;
+    a[i] = (r < k && tr < k) ? Asrc[r * k + tr] : 0.f;
+  }
+  if (tg == 0) rowbuf[tr] = a[0];  // row 0
+  __syncthreads();
+  for (int j = 0; j + 2 < k; ++j) {
+    // a. warp 0: reflector of row j (x = A[j][j+1..k-1])
+    if (warp == 0) {
+      float sq = 0.f;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int r = lane + 32 * q;
+        const float x = (r >= j + 2 && r < k) ? rowbuf[r] : 0.f;
+        sq = fmaf(x, x, sq);
+      }
+      sq = warp_sumf(sq);
+      const float x0 = rowbuf[j + 1];
+      const float nrm = sqrtf(x0 * x0 + sq);
+      float alpha = 0.f, beta = 0.f, v0 = x0;
+      if (nrm > 0.f) {
+        alpha = x0 >= 0.f ? -nrm : nrm;
+        v0 = x0 - alpha;
+        const float vv = v0 * v0 + sq;
+        beta = vv > 0.f ? 2.f / vv : 0.f;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int r = lane + 32 * q;
+        const float v = r == j + 1 ? v0 : ((r > j + 1 && r < k) ? rowbuf[r] : 0.f);
+        vfl[r] = v;
+        vperm[perm_idx(r)] = v;
+        Vh[j * 128 + perm_idx(r)] = v;
+      }
+      if (lane == 0) {
+        dv[j] = rowbuf[j];
+        ev[j] = (nrm > 0.f) ? alpha : x0;
+        betav[j] = beta;
+      }
+    }
+    __syncthreads();
+    const float beta = betav[j];
+    // b. partial p_c = sum over the thread's rows of A[r][c] v_r
+    {
+      const float4* vp = reinterpret_cast<const float4*>(vperm + tg * 32);
+      float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float4 v = vp[q];
+        s0 = fmaf(a[4 * q], v.x, s0);
+        s1 = fmaf(a[4 * q + 1], v.y, s1);
+        s0 = fmaf(a[4 * q + 2], v.z, s0);
+        s1 = fmaf(a[4 * q + 3], v.w, s1);
+      }
+      gpart[tg * 128 + tr] = s0 + s1;
+    }
+    __syncthreads();
+    // c. warp 0: p = beta A' v, K = beta p.v / 2, w = p - K v (zero outside rows j+1..k-1)
+    if (warp == 0) {
+      float pr[4], pv = 0.f;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int r = lane + 32 * q;
+        const bool act = r > j && r < k;
+        const float p = act ? beta * (gpart[r] + gpart[128 + r] + gpart[256 + r] + gpart[384 + r]) : 0.f;
+        pr[q] = p;
+        pv = fmaf(p, vfl[r], pv);
+      }
+      pv = warp_sumf(pv);
+      const float K = 0.5f * beta * pv;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int r = lane + 32 * q;
+        const float w = (r > j && r < k) ? pr[q] - K * vfl[r] : 0.f;
+        wl[r] = w;
+        wperm[perm_idx(r)] = w;
+      }
+    }
+    __syncthreads();
+    // d. A -= v w^T + w v^T; the owners of row j + 1 publish it for the next step
+    {
+      const float vc = vfl[tr], wc = wl[tr];
+      const float4* vp = reinterpret_cast<const float4*>(vperm + tg * 32);
+      const float4* wp = reinterpret_cast<const float4*>(wperm + tg * 32);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float4 v = vp[q], w = wp[q];
+        a[4 * q] -= v.x * wc + w.x * vc;
+        a[4 * q + 1] -= v.y * wc + w.y * vc;
+        a[4 * q + 2] -= v.z * wc + w.z * vc;
+        a[4 * q + 3] -= v.w * wc + w.w * vc;
+      }
+#pragma unroll
+      for (int i = 0; i < 32; ++i)
+        if (tg + 4 * i == j + 1) rowbuf[tr] = a[i];
+    }
+    __syncthreads();
+  }
+  // the last 2 x 2 block (rows k-2, k-1), or the whole matrix when k < 3
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    const int r = tg + 4 * i;
+    if (r == k - 2 && tr < k) gpart[tr] = a[i];
+    if (r == k - 1 && tr < k) gpart[128 + tr] = a[i];
+  }
+  __syncthreads();
+  if (tid == 0) {
+    if (k >= 2) {
+      dv[k - 2] = gpart[k - 2];
+      ev[k - 2] = gpart[128 + k - 2];
+      betav[k - 2] = 0.f;
+    }
+    dv[k - 1] = gpart[128 + k - 1];
+    betav[k - 1] = 0.f;
+  }
+  __syncthreads();
+}
+
+// Step 4: Z <- H_0 H_1 ... H_{k-3} Z with the reflectors left in Vh by
+// tridiag_regs; Z (k x k, row-major, column i = eigenvector i of T) is read
+// from and written back to `Z`.  Two barriers per reflector.
+__device__ void backtransform_regs(float* Z, int k, const float* Vh, const float* betav, float* gpart) {
+  const int tid = threadIdx.x;
+  const int tr = tid & 127, tg = tid >> 7;
+  float z[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    const int r = tg + 4 * i;
+    z[i] = (r < k && tr < k) ? Z[r * k + tr] : 0.f;
+  }
+  for (int j = k - 3; j >= 0; --j) {
+    const float beta = betav[j];
+    if (beta == 0.f) continue;  // uniform
+    const float4* vp = reinterpret_cast<const float4*>(Vh + j * 128 + tg * 32);
+    float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const float4 v = vp[q];
+      s0 = fmaf(v.x, z[4 * q], s0);
+      s1 = fmaf(v.y, z[4 * q + 1], s1);
+      s0 = fmaf(v.z, z[4 * q + 2], s0);
+      s1 = fmaf(v.w, z[4 * q + 3], s1);
+    }
+    gpart[tg * 128 + tr] = s0 + s1;
+    __syncthreads();
+    const float wc = beta * (gpart[tr] + gpart[128 + tr] + gpart[256 + tr] + gpart[384 + tr]);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const float4 v = vp[q];
+      z[4 * q] -= v.x * wc;
+      z[4 * q + 1] -= v.y * wc;
+      z[4 * q + 2] -= v.z * wc;
+      z[4 * q + 3] -= v.w * wc;
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    const int r = tg + 4 * i;
+    if (r < k && tr < k) Z[r * k + tr] = z[i];
+  }
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(kSeedThreads, 1) eig_seed_kernel(const double* __restrict__ H, int k, float* gA,
                                                                 float* gZ, float* gQ, double* __restrict__ Xout,
                                                                 double* __restrict__ lam_out, double* scal,
                                                                 int32_t* nclusters) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ float red[33];
-  __shared__ float dv[256], ev[256], e2v[256], betav[256], wl[256], pv[256], lamv[256], vv_s[256];
-  __shared__ float gpart[512];
+  __shared__ float dv[256], ev[256], e2v[256], betav[256], wl[256], pv_s[256], lamv[256], vv_s[256];
+  __shared__ float gpart[kSeedThreads];
   __shared__ float coef[4];
   __shared__ int clstart[257];
   const bool sm = k <= 128;
-  float* A = sm ? reinterpret_cast<float*>(smem_raw) : gA;         // k x k row-major
-  float* Z = sm ? reinterpret_cast<float*>(smem_raw) + k * k : gZ;  // k x k, column j = eigenvector j
-  float* Qs = sm ? reinterpret_cast<float*>(smem_raw) + 2 * k * k : gQ;  // inverse-iteration scratch, one row per cluster
+  // k <= 128: A (scaled H, then the reflectors, 128 k floats), Z, Qs in SMEM
+  float* A = sm ? reinterpret_cast<float*>(smem_raw) : gA;               // k x k row-major
+  float* Z = sm ? reinterpret_cast<float*>(smem_raw) + 128 * k : gZ;     // k x k, column j = eigenvector j
+  float* Qs = sm ? Z + k * k : gQ;  // inverse-iteration scratch, one row per cluster
+  __shared__ __align__(16) float vperm[128], wperm[128];
+  __shared__ float rowbuf[128], vfl[128];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kSeedThreads / 32;
 
   // scale and load; ||H||_F for the refinement's noise floor
@@ -133,70 +304,103 @@ __global__ void __launch_bounds__(kSeedThreads, 1) eig_seed_kernel(const double*
   }
   __syncthreads();
 
-  // ---- 1. tridiagonalisation
-  for (int j = 0; j + 2 < k; ++j) {
-    const int n1 = k - j - 1;
-    float part = 0.f;
-    for (int i = j + 2 + tid; i < k; i += kSeedThreads) {
-      const float x = A[i * k + j];
-      part = fmaf(x, x, part);
-    }
-    const float sig = block_sum_f(part, red);
-    if (tid == 0) {
-      const float x0 = A[(j + 1) * k + j];
-      const float nrm = sqrtf(x0 * x0 + sig);
-      float alpha = 0.f, beta = 0.f;
-      if (nrm > 0.f) {
-        alpha = x0 >= 0.f ? -nrm : nrm;
-        const float v0 = x0 - alpha;
-        const float vv = v0 * v0 + sig;
-        beta = vv > 0.f ? 2.f / vv : 0.f;
-        A[(j + 1) * k + j] = v0;
+  // ---- 1. tridiagonalisation: in registers for k <= 128 (tridiag_regs),
+  // else the form below over the SMEM/global matrix
+  const int kp = k <= 128 ? 128 : 256;  // padded width: thread t = (t / kp, t % kp)
+  const int GR = kSeedThreads / kp;      // 4 or 2 groups
+  const int tr = tid % kp, tg = tid / kp;
+  if (sm) {
+    tridiag_regs(A, k, A, dv, ev, betav, rowbuf, vfl, wl, vperm, wperm, gpart);
+  } else {
+    // Step j reflects the trailing block
+    // A' = A[j+1:, j+1:] with H = I - beta v v^T built from row j (equal to
+    // column j: the trailing block is kept whole and symmetric).  Four barriers
+    // per step:
+    //   a. warp 0: norm of row j right of the diagonal, alpha, beta, v (stored
+    //      back into row j for the back-transformation and into vv_s);
+    //   b. p = A' v: thread (g, r) sums a quarter (k <= 128) or half of the
+    //      terms of p_r, reading A'[l][r] = A'[r][l] along rows (consecutive
+    //      lanes, consecutive addresses);
+    //   c. warp 0: p = beta sum of the partials, K = beta p.v / 2, w = p - K v;
+    //   d. A' -= v w^T + w v^T, thread (g, c) over rows r = g mod GR.
+    for (int j = 0; j + 2 < k; ++j) {
+      const int n1 = k - j - 1;
+      float* rowj = A + j * k + (j + 1);  // row j right of the diagonal (length n1)
+      if (warp == 0) {
+        float sq = 0.f;
+        for (int r = 1 + lane; r < n1; r += 32) sq = fmaf(rowj[r], rowj[r], sq);
+        sq = warp_sumf(sq);
+        const float x0 = rowj[0];
+        const float nrm = sqrtf(x0 * x0 + sq);
+        float alpha = 0.f, beta = 0.f, v0 = x0;
+        if (nrm > 0.f) {
+          alpha = x0 >= 0.f ? -nrm : nrm;
+          v0 = x0 - alpha;
+          const float vv = v0 * v0 + sq;
+          beta = vv > 0.f ? 2.f / vv : 0.f;
+        }
+        for (int r = lane; r < n1; r += 32) vv_s[r] = r == 0 ? v0 : rowj[r];
+        __syncwarp();
+        if (lane == 0) {
+          dv[j] = A[j * k + j];
+          ev[j] = (nrm > 0.f) ? alpha : x0;
+          betav[j] = beta;
+          rowj[0] = v0;
+        }
       }
-      dv[j] = A[j * k + j];
-      ev[j] = (nrm > 0.f) ? alpha : x0;
-      betav[j] = beta;
+      __syncthreads();
+      const float beta = betav[j];
+      if (beta == 0.f) continue;  // uniform: the block is already reduced here
+      const float* Ap = A + (j + 1) * k + (j + 1);
+      {
+        const int chunk = (n1 + GR - 1) / GR;
+        const int l0 = tg * chunk, l1 = min(n1, l0 + chunk);
+        float a0 = 0.f, a1 = 0.f;
+        if (tr < n1) {
+          int l = l0;
+          for (; l + 1 < l1; l += 2) {
+            a0 = fmaf(Ap[l * k + tr], vv_s[l], a0);
+            a1 = fmaf(Ap[(l + 1) * k + tr], vv_s[l + 1], a1);
+          }
+          if (l < l1) a0 = fmaf(Ap[l * k + tr], vv_s[l], a0);
+        }
+        gpart[tg * kp + tr] = a0 + a1;
+      }
+      __syncthreads();
+      if (warp == 0) {
+        float pv = 0.f;
+        for (int r = lane; r < n1; r += 32) {
+          float s = 0.f;
+          for (int g = 0; g < GR; ++g) s += gpart[g * kp + r];
+          s *= beta;
+          pv_s[r] = s;
+          pv = fmaf(s, vv_s[r], pv);
+        }
+        pv = warp_sumf(pv);
+        const float K = 0.5f * beta * pv;
+        for (int r = lane; r < n1; r += 32) wl[r] = pv_s[r] - K * vv_s[r];
+      }
+      __syncthreads();
+      if (tr < n1) {
+        const float vc = vv_s[tr], wc = wl[tr];
+        for (int r = tg; r < n1; r += GR) {
+          float* a = A + (j + 1 + r) * k + (j + 1) + tr;
+          *a -= vv_s[r] * wc + wl[r] * vc;
+        }
+      }
+      __syncthreads();
+    }
+    if (tid == 0) {
+      if (k >= 2) {
+        dv[k - 2] = A[(k - 2) * k + (k - 2)];
+        ev[k - 2] = A[(k - 1) * k + (k - 2)];
+      }
+      dv[k - 1] = A[(k - 1) * k + (k - 1)];
+      if (k >= 2) betav[k - 2] = 0.f;
+      betav[k - 1] = 0.f;
     }
     __syncthreads();
-    const float beta = betav[j];
-    if (beta != 0.f) {
-      // v (column j below the diagonal) into a contiguous vector: the column is
-      // strided by k in SMEM and would bank-conflict on every read
-      for (int r = tid; r < n1; r += kSeedThreads) vv_s[r] = A[(j + 1 + r) * k + j];
-      __syncthreads();
-      // p = beta A' v, A' = A[j+1:, j+1:]; one warp per row
-      for (int r = warp; r < n1; r += nw) {
-        const float* row = A + (j + 1 + r) * k + (j + 1);
-        float acc = 0.f;
-        for (int l = lane; l < n1; l += 32) acc = fmaf(row[l], vv_s[l], acc);
-        acc = warp_sumf(acc);
-        if (lane == 0) pv[r] = beta * acc;
-      }
-      __syncthreads();
-      float pt = 0.f;
-      for (int r = tid; r < n1; r += kSeedThreads) pt = fmaf(pv[r], vv_s[r], pt);
-      const float ptv = block_sum_f(pt, red);
-      const float K = 0.5f * beta * ptv;
-      for (int r = tid; r < n1; r += kSeedThreads) wl[r] = pv[r] - K * vv_s[r];
-      __syncthreads();
-      for (int r = warp; r < n1; r += nw) {
-        const float vr = vv_s[r], wr = wl[r];
-        float* row = A + (j + 1 + r) * k + (j + 1);
-        for (int c = lane; c < n1; c += 32) row[c] -= vr * wl[c] + wr * vv_s[c];
-      }
-      __syncthreads();
-    }
   }
-  if (tid == 0) {
-    if (k >= 2) {
-      dv[k - 2] = A[(k - 2) * k + (k - 2)];
-      ev[k - 2] = A[(k - 1) * k + (k - 2)];
-    }
-    dv[k - 1] = A[(k - 1) * k + (k - 1)];
-    if (k >= 2) betav[k - 2] = 0.f;
-    betav[k - 1] = 0.f;
-  }
-  __syncthreads();
   for (int i = tid; i < k; i += kSeedThreads) e2v[i] = (i + 1 < k) ? ev[i] * ev[i] : 0.f;
 
   // Gershgorin interval, ||T||, pivmin
@@ -217,16 +421,28 @@ __global__ void __launch_bounds__(kSeedThreads, 1) eig_seed_kernel(const double*
   __syncthreads();
   const float tnorm = coef[2], pivmin = coef[3];
 
-  // ---- 2. eigenvalues by bisection (one thread per eigenvalue, ascending index)
-  for (int idx = tid; idx < k; idx += kSeedThreads) {
+  // ---- 2. eigenvalues by multisection: GR threads (lanes of one warp) per
+  // eigenvalue evaluate Sturm counts at GR interior points of the bracket,
+  // which shrinks by GR + 1 per round ((GR + 1)^rounds >= 2^30, the
+  // resolution of 30 halvings of the Gershgorin interval).
+  {
+    const int idx = tid / GR, q = tid % GR;
+    const int rounds = GR == 4 ? 13 : 19;
+    const float den = (float)(GR + 1);
     float lo = coef[0], hi = coef[1];
 #pragma unroll 1
-    for (int it = 0; it < 30; ++it) {
-      const float mid = 0.5f * (lo + hi);
-      if (sturm_count(dv, e2v, k, mid, pivmin) > idx) hi = mid;
-      else lo = mid;
+    for (int it = 0; it < rounds; ++it) {
+      const float x = lo + (hi - lo) * (float)(q + 1) / den;
+      const bool above = idx < k && sturm_count(dv, e2v, k, x, pivmin) > idx;
+      const unsigned ball = __ballot_sync(0xffffffffu, above);
+      const unsigned grp = (ball >> ((lane / GR) * GR)) & ((1u << GR) - 1u);
+      const int first = grp ? __ffs((int)grp) - 1 : GR;  // first point with count > idx
+      const float nlo = first == 0 ? lo : lo + (hi - lo) * (float)first / den;
+      const float nhi = first == GR ? hi : lo + (hi - lo) * (float)(first + 1) / den;
+      lo = nlo;
+      hi = nhi;
     }
-    lamv[idx] = 0.5f * (lo + hi);
+    if (q == 0 && idx < k) lamv[idx] = 0.5f * (lo + hi);
   }
   __syncthreads();
 
@@ -267,43 +483,39 @@ __global__ void __launch_bounds__(kSeedThreads, 1) eig_seed_kernel(const double*
   }
   __syncthreads();
 
-  // ---- 4. back-transformation: Z <- H_0 H_1 ... H_{k-3} Z
-  for (int j = k - 3; j >= 0; --j) {
-    const float beta = betav[j];
-    if (beta == 0.f) continue;
-    const int n1 = k - j - 1;
-    for (int r = tid; r < n1; r += kSeedThreads) vv_s[r] = A[(j + 1 + r) * k + j];
-    __syncthreads();
-    // w_c = beta v^T Z[j+1:, c]: thread = (row group g, column c), consecutive
-    // threads take consecutive columns (conflict-free), partials summed via SMEM
-    {
-      const int groups = kSeedThreads / k;  // 4 for k = 128, 2 for k = 256
-      for (int t = tid; t < groups * k; t += kSeedThreads) {
-        const int c = t % k, g = t / k;
-        float acc = 0.f;
-        for (int r = g; r < n1; r += groups) acc = fmaf(vv_s[r], Z[(j + 1 + r) * k + c], acc);
-        gpart[g * k + c] = acc;
+  // ---- 4. back-transformation Z <- H_0 H_1 ... H_{k-3} Z, last reflector
+  // first; v_j is row j of A right of the diagonal.  Thread (g, c), two
+  // barriers per reflector:
+  //   1. partial of w_c = v^T Z[j+1:, c] over the rows r = g mod GR;
+  //   2. w_c = beta (sum of the GR partials of column c), then
+  //      Z[j+1+r][c] -= v_r w_c over the same rows.
+  if (sm) {
+    backtransform_regs(Z, k, A, betav, gpart);
+  } else {
+    for (int j = k - 3; j >= 0; --j) {
+      const float beta = betav[j];
+      if (beta == 0.f) continue;
+      const int n1 = k - j - 1;
+      const float* v = A + j * k + (j + 1);
+      float acc = 0.f;
+      if (tr < k)
+        for (int r = tg; r < n1; r += GR) acc = fmaf(v[r], Z[(j + 1 + r) * k + tr], acc);
+      gpart[tg * kp + tr] = acc;
+      __syncthreads();
+      if (tr < k) {
+        float wc = 0.f;
+        for (int g = 0; g < GR; ++g) wc += gpart[g * kp + tr];
+        wc *= beta;
+        for (int r = tg; r < n1; r += GR) Z[(j + 1 + r) * k + tr] -= v[r] * wc;
       }
       __syncthreads();
-      for (int c = tid; c < k; c += kSeedThreads) {
-        float acc = 0.f;
-        for (int g = 0; g < groups; ++g) acc += gpart[g * k + c];
-        wl[c] = beta * acc;
-      }
     }
-    __syncthreads();
-    for (int r = warp; r < n1; r += nw) {
-      const float vr = vv_s[r];
-      float* row = Z + (j + 1 + r) * k;
-      for (int c = lane; c < k; c += 32) row[c] -= vr * wl[c];
-    }
-    __syncthreads();
   }
   for (int e = tid; e < k * k; e += kSeedThreads) Xout[e] = (double)Z[e];
   for (int i = tid; i < k; i += kSeedThreads) lam_out[i] = (double)lamv[i] * hmax_s;
 }
 
-size_t eig_seed_smem(int k) { return k <= 128 ? (size_t)3 * k * k * sizeof(float) : 0; }
+size_t eig_seed_smem(int k) { return k <= 128 ? ((size_t)128 * k + (size_t)2 * k * k) * sizeof(float) : 0; }
 
 void launch_eig_seed(Launcher& L, const double* H, int k, float* gA, float* gZ, float* gQ, double* Xout,
                      double* lam, double* scal, int32_t* nclusters) {

@@ -19,6 +19,8 @@
 // accumulation type (FP64 for FP64 X, else FP32): deterministic.
 #include "common.cuh"
 #include "kernels.h"
+#include "tc_ptx.cuh"
+#include "tma.h"
 
 namespace lspca {
 
@@ -456,6 +458,296 @@ static void sketch_sparse_dispatch(Launcher& L, const void* X, int64_t m, int64_
   L.count(1);
 }
 
+
+// ---------------------------------------------------------------------------
+// Streaming variant for FP32 / BF16 X and k <= 128 with an asynchronous copy
+// ring (the form the dispatcher prefers).
+//
+// Row tiles of R5 = 128 rows are streamed in steps of W5 = 64 columns.  One
+// thread issues each step as tiled TMA copies (boxes of 128 rows x 128 bytes
+// with the 128-byte swizzle; rows past m and columns past n arrive as zeros)
+// into a ring of S stages, S steps ahead, so the loads stay in flight while the
+// CTA gathers.  With the swizzle, 8 consecutive rows at the same 16-byte
+// column chunk fall on 8 different bank groups, so a warp reading 32 rows x 16
+// bytes is conflict-free.  Each step the whole CTA transposes its stage into
+// Xt[j][r] (FP32, pitch R5; consecutive lanes = consecutive rows, so the
+// 4-byte stores are conflict-free) and then gathers from Xt exactly as the
+// kernel above: lane = 4 consecutive rows, one 16-byte load per Omega entry.
+// Xt is double-buffered, so one barrier per step orders the transpose of step
+// s + 1 after every warp's gather of step s - 1, and the refill of a ring
+// stage after every warp's transpose of it.  Warp w owns the Omega columns
+// [w cpw, (w + 1) cpw), cpw = ceil(k / 16): a finished tile's row of U is cpw
+// consecutive floats per thread, written as 16-byte stores.
+// Entry codes are 16 bits: sign in bit 15, byte offset of row (j mod W5) of
+// Xt in bits 0..14 (in shared memory when Omega has at most ENT5 nonzeros,
+// else in a global scratch), stored chunk-major: the entries of (step chunk q,
+// column c) follow those of (q, c - 1), ascending in j, so the begin offsets
+// of a warp's cpw columns in a chunk are cpw + 1 consecutive words that lanes
+// 0..cpw load at once and the gather loop receives by shuffles.
+// A wait on a stage gives up after 2 s: the CTA records ST_TIMEOUT, waits
+// (bounded) for its copies in flight and returns.
+constexpr int R5 = 128;
+constexpr int W5 = 64;
+constexpr int ENT5 = 12288;
+constexpr int PTR5 = 8704;  // max nch * k + 1 (chunk-major begin offsets)
+
+template <int DT>
+struct Sk5 {
+  using T = typename XType<DT>::T;
+  static constexpr int ELEM = (int)sizeof(T);
+  static constexpr int BOXW = 128 / ELEM;              // columns per 128-byte swizzled box row
+  static constexpr int NBOX = W5 / BOXW;               // boxes per step (2 for FP32, 1 for BF16)
+  static constexpr int BOX_BYTES = R5 * 128;
+  static constexpr int STAGE = NBOX * BOX_BYTES;
+  static constexpr int S = ELEM == 4 ? 3 : 5;          // ring stages
+  static constexpr int CHUNKS = W5 * ELEM / 16;        // 16-byte chunks per staged row
+  static constexpr int EPC = 16 / ELEM;                // elements per chunk
+  static constexpr size_t XT_OFF = (size_t)S * STAGE;
+  static constexpr size_t CODE_OFF = XT_OFF + (size_t)2 * W5 * R5 * 4;
+  static constexpr size_t PTR_OFF = CODE_OFF + (size_t)ENT5 * 2;
+  static constexpr size_t RED_OFF = PTR_OFF + (size_t)PTR5 * 4;
+  static constexpr size_t BAR_OFF = RED_OFF + 32 * 4;
+  static constexpr size_t SMEM = 1024 + BAR_OFF + 8 * S;  // + alignment of the ring to 1024 bytes
+};
+
+template <int DT>
+__global__ void __launch_bounds__(512, 1)
+    sketch_sparse5_kernel(const __grid_constant__ CUtensorMap tmx, int64_t m, int64_t n, int k,
+                          const int32_t* __restrict__ col_ptr, const int32_t* __restrict__ entries_g,
+                          uint16_t* __restrict__ codes_g, float* __restrict__ U, int64_t ldu, int vec_u,
+                          float* absmax, int* status) {
+  using C = Sk5<DT>;
+  using T = typename C::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* ring = sm;
+  float* xt = reinterpret_cast<float*>(sm + C::XT_OFF);
+  uint32_t* ptr = reinterpret_cast<uint32_t*>(sm + C::PTR_OFF);
+  uint32_t* red = reinterpret_cast<uint32_t*>(sm + C::RED_OFF);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + C::BAR_OFF);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nch = (int)((n + W5 - 1) / W5);
+  const int nnz = col_ptr[k];
+  const int nslot = nch * k;  // (chunk, column) slots, chunk-major
+  uint16_t* codes = nnz <= ENT5 ? reinterpret_cast<uint16_t*>(sm + C::CODE_OFF) : codes_g;
+  // 1. entries per (chunk, column): thread c walks column c (its slots only)
+  for (int i = tid; i <= nslot; i += 512) ptr[i] = 0u;
+  __syncthreads();
+  for (int c = tid; c < k; c += 512)
+    for (int e = col_ptr[c]; e < col_ptr[c + 1]; ++e) {
+      const int en = entries_g[e];
+      const int j = (en > 0 ? en : -en) - 1;
+      ptr[(j / W5) * k + c + 1] += 1u;
+    }
+  __syncthreads();
+  // 2. inclusive scan of ptr[1..nslot] (contiguous segment per thread)
+  {
+    const int per = (nslot + 511) / 512;
+    const int a = 1 + tid * per, b = min(nslot + 1, a + per);
+    uint32_t sum = 0u;
+    for (int i = a; i < b; ++i) sum += ptr[i];
+    uint32_t inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    if (lane == 31) red[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+      uint32_t w = lane < 16 ? red[lane] : 0u;
+#pragma unroll
+      for (int o = 1; o < 16; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += y;
+      }
+      if (lane < 16) red[lane] = w;
+    }
+    __syncthreads();
+    uint32_t run = inc - sum + (warp ? red[warp - 1] : 0u);
+    for (int i = a; i < b; ++i) {
+      run += ptr[i];
+      ptr[i] = run;
+    }
+  }
+  __syncthreads();
+  // 3. codes in chunk-major order, ascending j inside every (chunk, column):
+  // sign in bit 15, byte offset of row (j mod W5) of Xt in bits 0..14
+  for (int c = tid; c < k; c += 512) {
+    int q = -1;
+    uint32_t pos = 0u;
+    for (int e = col_ptr[c]; e < col_ptr[c + 1]; ++e) {
+      const int en = entries_g[e];
+      const int j = (en > 0 ? en : -en) - 1;
+      if (j / W5 != q) {
+        q = j / W5;
+        pos = ptr[q * k + c];
+      }
+      codes[pos++] = (uint16_t)((en < 0 ? 0x8000 : 0) | ((j % W5) * R5 * 4));
+    }
+  }
+  if (tid == 0) {
+    for (int q = 0; q < C::S; ++q) ptx::mbar_init(&full[q], 1);
+    ptx::fence_mbar_init();
+  }
+  const int64_t ntiles = (m + R5 - 1) / R5;
+  const int64_t my_tiles = ((int64_t)blockIdx.x < ntiles) ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  const int64_t steps = my_tiles * nch;
+  __syncthreads();
+  if (steps == 0) return;
+
+  // one thread: step `st` (tile blockIdx.x + (st / nch) gridDim.x, chunk st % nch)
+  // into ring stage st % S as NBOX swizzled boxes of 128 rows x 128 bytes
+  // (rows past m and columns past n arrive as zeros)
+  auto issue = [&](int64_t st) {
+    const int r0 = (int)(((int64_t)blockIdx.x + (st / nch) * gridDim.x) * R5);
+    const int j0 = (int)((st % nch) * W5);
+    const int q = (int)(st % C::S);
+    ptx::fence_proxy_async_smem();  // this stage was last read by generic loads
+    ptx::mbar_arrive_expect_tx(&full[q], (uint32_t)C::STAGE);
+    const uint32_t dst = ptx::smem_u32(ring + (size_t)q * C::STAGE);
+#pragma unroll
+    for (int b = 0; b < C::NBOX; ++b) ptx::tma_load_2d(dst + b * C::BOX_BYTES, &tmx, j0 + b * C::BOXW, r0, &full[q]);
+  };
+  if (tid == 0)
+    for (int64_t st = 0; st < (steps < C::S ? steps : C::S); ++st) issue(st);
+
+  const int cpw = (k + 15) / 16;
+  const int c0 = warp * cpw;
+  float acc[8][4];
+  uint32_t mxb = 0u;
+  float umx = 0.f;
+  for (int64_t st = 0; st < steps; ++st) {
+    const int q = (int)(st % C::S);
+    const int chunk = (int)(st % nch);
+    const int64_t r0 = ((int64_t)blockIdx.x + (st / nch) * gridDim.x) * R5;
+    const bool ok = ptx::mbar_wait(&full[q], (uint32_t)((st / C::S) & 1), 2000000000ull);
+    float* xc = xt + (size_t)(st & 1) * (W5 * R5);
+    if (ok) {
+      // transpose: item = (row, 16-byte chunk); chunk c of box b, row r sits at
+      // b * BOX_BYTES + r * 128 + ((c ^ (r & 7)) << 4) (128-byte swizzle)
+      const unsigned char* stage = ring + (size_t)q * C::STAGE;
+      const int row = tid % R5;
+#pragma unroll
+      for (int qq = 0; qq < R5 * C::CHUNKS / 512; ++qq) {
+        const int ch = tid / R5 + (512 / R5) * qq;
+        const int b = ch / 8, c = ch % 8;
+        const uint4 v = *reinterpret_cast<const uint4*>(stage + b * C::BOX_BYTES + row * 128 + ((c ^ (row & 7)) << 4));
+        const T* e = reinterpret_cast<const T*>(&v);
+        float* dst = xc + ch * C::EPC * R5 + row;
+#pragma unroll
+        for (int u = 0; u < C::EPC; ++u) {
+          const float x = XType<DT>::to_acc(e[u]);
+          mxb = max(mxb, __float_as_uint(x) & 0x7fffffffu);
+          dst[u * R5] = x;
+        }
+      }
+    }
+    if (__syncthreads_or(ok ? 0 : 1)) {
+      if (tid == 0) {
+        atomicOr(status, ST_TIMEOUT);
+        for (int64_t w = st; w < steps && w < st + C::S; ++w)
+          ptx::mbar_wait(&full[w % C::S], (uint32_t)((w / C::S) & 1), 100000000ull);
+      }
+      __syncthreads();
+      return;
+    }
+    if (tid == 0 && st + C::S < steps) issue(st + C::S);
+
+    if (chunk == 0) {
+#pragma unroll
+      for (int t = 0; t < 8; ++t)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) acc[t][r] = 0.f;
+    }
+    const char* xl = reinterpret_cast<const char*>(xc) + lane * 16;
+    // begin offsets of the warp's columns in this chunk: lanes 0..cpw load
+    // ptr[chunk k + c0 + lane] (the last one is the end of column c0 + cpw - 1)
+    const int pi = chunk * k + c0 + lane;
+    const uint32_t myp = ptr[pi <= nslot ? pi : nslot];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int c = c0 + t;
+      const int b = (int)__shfl_sync(0xffffffffu, myp, t);
+      const int e = (int)__shfl_sync(0xffffffffu, myp, t + 1);
+      if (t < cpw && c < k) {
+        float a0 = acc[t][0], a1 = acc[t][1], a2 = acc[t][2], a3 = acc[t][3];
+#pragma unroll 2
+        for (int i = b; i < e; ++i) {
+          const uint32_t code = codes[i];
+          const float4 v = *reinterpret_cast<const float4*>(xl + (code & 0x7fffu));
+          const float sg = __uint_as_float(((code & 0x8000u) << 16) | 0x3f800000u);
+          a0 = fmaf(sg, v.x, a0);
+          a1 = fmaf(sg, v.y, a1);
+          a2 = fmaf(sg, v.z, a2);
+          a3 = fmaf(sg, v.w, a3);
+        }
+        acc[t][0] = a0;
+        acc[t][1] = a1;
+        acc[t][2] = a2;
+        acc[t][3] = a3;
+      }
+    }
+    if (chunk == nch - 1) {
+      // tile done: rows r0 + 4 lane + i, columns c0 .. c0 + cpw - 1 of U
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int64_t r = r0 + 4 * lane + i;
+        if (r >= m) continue;
+        float* dst = U + r * ldu + c0;
+        if (vec_u && (cpw & 3) == 0 && c0 + cpw <= k) {
+#pragma unroll
+          for (int t = 0; t < 8; t += 4)
+            if (t < cpw) {
+              const float4 v = make_float4(acc[t][i], acc[t + 1][i], acc[t + 2][i], acc[t + 3][i]);
+              umx = fmaxf(umx, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+              *reinterpret_cast<float4*>(dst + t) = v;
+            }
+        } else {
+#pragma unroll
+          for (int t = 0; t < 8; ++t)
+            if (t < cpw && c0 + t < k) {
+              umx = fmaxf(umx, fabsf(acc[t][i]));
+              dst[t] = acc[t][i];
+            }
+        }
+      }
+    }
+  }
+  umx = warp_max(umx);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mxb = max(mxb, __shfl_xor_sync(0xffffffffu, mxb, o));
+  if (lane == 0) {
+    atomic_max_nonneg(absmax + 1, umx);
+    if (mxb >= 0x7f800000u) atomicOr(status, ST_NONFINITE);
+    else atomic_max_nonneg(absmax, __uint_as_float(mxb));
+  }
+}
+
+template <int DT>
+static bool sketch_sparse5_dispatch(Launcher& L, const void* X, int64_t m, int64_t n, int64_t ldx, int k,
+                                    const int32_t* col_ptr, const int32_t* entries, int32_t* codes_g, float* U,
+                                    int64_t ldu, float* absmax, int* status) {
+  using C = Sk5<DT>;
+  const int64_t nch = (n + W5 - 1) / W5;
+  // the (chunk, column) begin offsets live in shared memory
+  if (k > 128 || n >= 65536 || m >= ((int64_t)1 << 31) || (int64_t)k * nch + 1 > PTR5) return false;
+  CUtensorMap tm;
+  const CUtensorMapDataType dt = C::ELEM == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  if (!make_tmap_2d_sw128(&tm, X, dt, C::ELEM, (uint64_t)m, (uint64_t)n, (uint64_t)ldx * C::ELEM, R5, C::BOXW))
+    return false;
+  cudaFuncSetAttribute(sketch_sparse5_kernel<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+  const int64_t ntiles = (m + R5 - 1) / R5;
+  const int grid = (int)(ntiles < L.num_sms ? ntiles : L.num_sms);
+  const int vec_u = (((uintptr_t)U & 15u) == 0 && (ldu & 3) == 0) ? 1 : 0;
+  sketch_sparse5_kernel<DT><<<grid, 512, C::SMEM, L.stream>>>(tm, m, n, k, col_ptr, entries,
+                                                              reinterpret_cast<uint16_t*>(codes_g), U, ldu, vec_u,
+                                                              absmax, status);
+  L.count(1);
+  return true;
+}
+
 size_t sketch_off_bytes(int64_t n, int k) {
   // worst case over the element types: chunks of 128 columns; plus room for
   // the re-encoded entry codes (n * k int32) of the wide kernel
@@ -475,12 +767,16 @@ void launch_sketch_sparse(Launcher& L, const void* X, int xt, int64_t m, int64_t
       sketch_sparse_dispatch<LSPCA_F64>(L, X, m, n, ldx, k, col_ptr, entries, off, U, ldu, absmax, status);
       break;
     case LSPCA_F32:
-      if (!sketch_sparse4_dispatch<LSPCA_F32>(L, X, m, n, ldx, k, col_ptr, entries, off, codes_area(off, n, k),
+      if (!sketch_sparse5_dispatch<LSPCA_F32>(L, X, m, n, ldx, k, col_ptr, entries, codes_area(off, n, k),
+                                              (float*)U, ldu, absmax, status) &&
+          !sketch_sparse4_dispatch<LSPCA_F32>(L, X, m, n, ldx, k, col_ptr, entries, off, codes_area(off, n, k),
                                               (float*)U, ldu, absmax, status))
         sketch_sparse_dispatch<LSPCA_F32>(L, X, m, n, ldx, k, col_ptr, entries, off, U, ldu, absmax, status);
       break;
     case LSPCA_BF16:
-      if (!sketch_sparse4_dispatch<LSPCA_BF16>(L, X, m, n, ldx, k, col_ptr, entries, off, codes_area(off, n, k),
+      if (!sketch_sparse5_dispatch<LSPCA_BF16>(L, X, m, n, ldx, k, col_ptr, entries, codes_area(off, n, k),
+                                               (float*)U, ldu, absmax, status) &&
+          !sketch_sparse4_dispatch<LSPCA_BF16>(L, X, m, n, ldx, k, col_ptr, entries, off, codes_area(off, n, k),
                                                (float*)U, ldu, absmax, status))
         sketch_sparse_dispatch<LSPCA_BF16>(L, X, m, n, ldx, k, col_ptr, entries, off, U, ldu, absmax, status);
       break;

@@ -135,9 +135,10 @@ def omega(kind: str | int, seed: int = 0, p: int = 0) -> lspca_omega:
 
 
 def _xargs(X: torch.Tensor):
-    if X.dim() != 2 or X.stride(1) != 1:
-        raise ValueError("X must be a row-major 2-D tensor")
-    return _ptr(X), DTYPE_CODES[X.dtype], X.shape[0], X.shape[1], X.stride(0)
+    """X may be a row-strided view (unit column stride, ldx = stride(0) >= n)."""
+    if X.dim() != 2 or X.stride(1) != 1 or X.stride(0) < X.shape[1]:
+        raise ValueError("X must be a row-major 2-D tensor (unit column stride)")
+    return X.data_ptr(), DTYPE_CODES[X.dtype], X.shape[0], X.shape[1], X.stride(0)
 
 
 # ---- the C entry points, same names -----------------------------------------

@@ -112,6 +112,26 @@ def test_sketch_sparse_fp32(ctx, data, wl):
     assert np.all(np.abs(U - ref) <= bound)
 
 
+@pytest.mark.parametrize("dtype,m,n,ldx,k", [(torch.float32, 777, 1001, 1004, 64),
+                                             (torch.float32, 300, 4096, 4096, 128),
+                                             (torch.bfloat16, 515, 1003, 1008, 100),
+                                             (torch.bfloat16, 129, 2048, 2048, 128)])
+def test_sketch_sparse_strided_and_ragged(ctx, dtype, m, n, ldx, k):
+    """Pass S of the very sparse Omega on FP32 / BF16 X with ragged row tiles,
+    a ragged last column step (n not a multiple of the copy width, X rows
+    padded to ldx) and k not a multiple of 16: the FP32 gather sum is within
+    the sequential-summation bound of the FP64 oracle."""
+    w = S.WORKLOADS["fp32_sparse"].scaled(m=m, n=ldx, k=k)
+    base = S.generate(w).to(dtype)
+    X = base.cuda()[:, :n]  # row-strided view, ldx > n where the two differ
+    Xd = base[:, :n].double().numpy()
+    Om = P.omega_sparse(w.omega_seed, n, k, w.p)
+    U = ctx.sketch(X, k, L.omega("sparse", w.omega_seed, w.p)).double().cpu().numpy()
+    ref = O.sketch(Xd, Om)
+    bound = (np.abs(Xd) @ np.abs(Om)) * (np.count_nonzero(Om, axis=0) * 2.0 ** -24) + 1e-30
+    assert np.all(np.abs(U - ref) <= bound)
+
+
 # ------------------------------------------------------------------ pass F
 
 def test_chain_fp64(ctx, data):
