@@ -185,14 +185,15 @@ void plan_chain(Plan& P, ChainBufs& b, int xt, int64_t m, int64_t n, int k, bool
   }
 }
 
-void run_chain(lspca_ctx* ctx, Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_t ldx, const void* U,
-               int k, bool tc, ChainBufs& b, double* F, double* G, const Mark& mark) {
+int run_chain(lspca_ctx* ctx, Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_t ldx, const void* U,
+              int k, bool tc, ChainBufs& b, double* F, double* G, const Mark& mark) {
   if (tc) {
-    tc_chain_main(L, X, xt, m, n, ldx, (const float*)U, k, b.tcw, ctx->d_absmax, ctx->d_status, G != nullptr);
+    if (!tc_chain_main(L, X, xt, m, n, ldx, (const float*)U, k, b.tcw, ctx->d_absmax, ctx->d_status, G != nullptr))
+      return LSPCA_ERR_CUDA;
     mark(3);
     tc_chain_reduce(L, n, k, b.tcw, F, G);
     mark(4);
-    return;
+    return LSPCA_OK;
   }
   const bool f64 = xt == LSPCA_F64;
   launch_gemm_simt(L, k, n, m, U, acc_dt(xt), k, true, X, xt, ldx, false, b.Fpart, true, n, (int64_t)k * n, b.f_splits,
@@ -204,6 +205,7 @@ void run_chain(lspca_ctx* ctx, Launcher& L, const void* X, int xt, int64_t m, in
   launch_reduce_splits(L, b.Fpart, b.f_splits, (int64_t)k * n, (int64_t)k * n, F);
   if (G) launch_reduce_splits(L, b.Gpart, b.g_splits, (int64_t)k * k, (int64_t)k * k, G);
   mark(4);
+  return LSPCA_OK;
 }
 
 bool use_tc_chain(int xt, uint32_t flags, int k = 4) {
@@ -271,9 +273,9 @@ int fit_impl(lspca_ctx* ctx, const void* X, int32_t xt, int64_t m, int64_t n, in
   cudaMemsetAsync(ctx->d_absmax, 0, 2 * sizeof(float), s);
   mark(0);
   run_sketch(ctx, L, X, xt, m, n, ldx, k, om, tc_s, sb, U, mark);
-  if (tc_f && xt == LSPCA_F32 && (tc_s || om.kind == LSPCA_OMEGA_GAUSSIAN))
+  if (tc_f && (xt == LSPCA_F32 || want_g) && (tc_s || om.kind == LSPCA_OMEGA_GAUSSIAN))
     launch_scan_x(L, U, LSPCA_F32, m, k, k, ctx->d_absmax + 1, ctx->d_status);  // max|U| for the FP16 scales
-  run_chain(ctx, L, X, xt, m, n, ldx, U, k, tc_f, cb, F, want_g ? G : nullptr, mark);
+  if ((st = run_chain(ctx, L, X, xt, m, n, ldx, U, k, tc_f, cb, F, want_g ? G : nullptr, mark))) return st;
   if (spca) {
     launch_tsqr(L, U, xt == LSPCA_F64, m, k, qrws, R);
     launch_trsm_rt(L, R, k, F, n);
@@ -446,7 +448,7 @@ int lspca_chain(lspca_ctx* ctx, const void* X, int32_t xt, int64_t m, int64_t n,
     launch_scan_x(L, X, xt, m, n, ldx, ctx->d_absmax, ctx->d_status);
     launch_scan_x(L, U, LSPCA_F32, m, k, k, ctx->d_absmax + 1, ctx->d_status);
   }
-  run_chain(ctx, L, X, xt, m, n, ldx, U, k, tc, cb, F, G, [](int) {});
+  if ((st = run_chain(ctx, L, X, xt, m, n, ldx, U, k, tc, cb, F, G, [](int) {}))) return st;
   return cuda_status(cudaGetLastError());
 }
 

@@ -1,0 +1,685 @@
+// Pass F on sm_103a tensor cores with TMA-fed operands: F = U^T X
+// (Algorithm 4's F += U_s^T X_s, Algorithm 2 step 2) and, optionally, the
+// Gram G = U^T U (Lemma 1 / Prop. 1).
+//
+// D[c, j] = sum over the rows i of one m-chunk of U[i, c] B[i, j], B = X (or U
+// for the Gram): a GEMM whose reduction runs over the rows of two row-major
+// sources, so both operands are MN-major.  M = k (one or two 128-row halves),
+// N = a 256-column (128 when k > 128) tile of B, K = rows.
+//
+// Number formats (the same as the tensor-core reduction map):
+//  * FP32 X: U and X are split into FP16 pairs v s = hi + lo with power-of-two
+//    scales s from max|U| and max|X| (|v s| <= 2^14); three products
+//    hi*hi + hi*lo + lo*hi carry ~22 significant bits.
+//  * BF16 X: X is exact, U is split into a BF16 pair (no scale), two products.
+//  * E4M3 X: widened exactly to BF16, U as a BF16 pair, two products.
+//  * Gram: B = U, both FP16 pairs with the max|U| scale, three products.
+//
+// U is split once per fit by split_u_kernel into two row-major 16-bit arrays
+// (pitch ku = k rounded up to 8), so every CTA loads the A operand with tiled
+// TMA copies (boxes of BK rows x 64 columns, 128-byte swizzle: exactly the
+// MN-major SW128 operand layout; rows past m and columns past k arrive as
+// zeros).  For BF16 X and for the Gram the B operand is loaded the same way
+// and the kernel has no converter warps; FP32 and E4M3 X are converted by
+// converter warps that load X rows with 16-byte global loads one step ahead,
+// while the producer warp prefetches the rows of the step PF_STEPS ahead into
+// L2 with bulk prefetches, so the converters' loads hit L2.
+//
+// Accumulation.  Measured on GB300, the FP32 accumulation of tcgen05.mma into
+// TMEM behaves like round-toward-zero (its error is biased and grows with the
+// number of accumulating instructions), so the tensor core accumulates only
+// segments of SEG k-steps (SEG * BK rows) into TMEM region A; the epilogue
+// warps fold each finished segment into a round-to-nearest FP32 running sum S
+// in TMEM region B and write S, scaled back, as the unit's FP32 partial after
+// its last segment.  Partials of the m-chunks are summed in FP64 in fixed
+// order (tc_chain_reduce).
+//
+// Kernel structure (one persistent CTA per SM; a unit = (m-chunk, N tile)):
+//   warps 0..CW-1      converters (FP32 / E4M3 X only);
+//   warps CW..CW+3     epilogue (one TMEM lane quarter each);
+//   warp  CW+4         TMEM allocation, the thread that issues tcgen05.mma;
+//   warp  CW+5         producer: TMA copies of each stage (lane 0) and L2
+//                      prefetches of X rows (one row per lane).
+// Ring of STAGES shared-memory stages; per stage the mbarriers tfull (TMA
+// bytes), full (converter warps), empty (tcgen05.commit).  Every wait is
+// bounded (2 s of %globaltimer): on expiry the kernel records ST_TIMEOUT,
+// stops issuing work, waits (bounded) for its copies and MMAs in flight and
+// frees TMEM.
+#include "common.cuh"
+#include "tc.h"
+#include "tc_ptx.cuh"
+#include "tma.h"
+
+namespace lspca {
+namespace pf {
+
+constexpr int BK = 32;       // rows (K) per stage
+constexpr int SEG = 4;       // k-steps accumulated by the tensor core per segment
+constexpr int PF_STEPS = 6;  // L2 prefetch distance of the converter modes, in steps
+constexpr uint64_t kWaitNs = 2000000000ull;
+constexpr uint64_t kDrainNs = 100000000ull;
+
+enum Mode { M_F32 = 0, M_BF16 = 1, M_E4M3 = 2, M_GRAM = 3 };
+
+template <int MODE, int MH>
+struct Cfg {
+  static constexpr int BN = 256 / MH;
+  static constexpr int WA = 128 * MH;
+  static constexpr bool CONV = (MODE == M_F32 || MODE == M_E4M3);
+  static constexpr bool F16 = (MODE == M_F32 || MODE == M_GRAM);  // FP16 pairs, else BF16
+  static constexpr int NB = F16 ? 2 : 1;                          // B operand parts
+  static constexpr int CW = CONV ? 8 : 0;
+  static constexpr int CT = CW * 32;
+  static constexpr int EPI0 = CW;
+  static constexpr int MMA_W = CW + 4;
+  static constexpr int PROD_W = CW + 5;
+  static constexpr int THREADS = (CW + 6) * 32;
+  static constexpr uint32_t BOX = BK * 128;        // one TMA box: BK rows x 64 16-bit columns
+  static constexpr uint32_t A_BYTES = BK * WA * 2;  // one part of A
+  static constexpr uint32_t B_BYTES = BK * BN * 2;  // one part of B
+  static constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + NB * B_BYTES;
+  static constexpr int STAGES = STAGE_BYTES <= 32768 ? 6 : 4;
+  static constexpr uint32_t TX = 2 * A_BYTES + (CONV ? 0u : NB * B_BYTES);
+  static constexpr uint32_t SBO_B = (BN / 64) * 1024;  // converter layout of B: K atom groups
+  static constexpr int ELEM = (MODE == M_F32) ? 4 : 1;  // converter modes: bytes per X element
+  static constexpr int B_VEC = CONV ? BK * BN * ELEM / 16 / CT : 1;  // 16-byte loads per thread per step
+  static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES + 256 + 8192;
+  static constexpr uint32_t TMEM_COLS = 512;  // segment accumulator A (MH x BN = 256) + running sum S
+};
+
+struct Params {
+  const void* X;  // B source of the converter modes (row-major, ld ldb)
+  int64_t ldb;
+  int64_t nb;     // columns of the B source
+  int64_t m;
+  int k;
+  int tiles;      // N tiles of the B source
+  int chunks;     // m-chunks
+  int64_t rows_per_chunk;
+  float* part;    // chunks x k x nb FP32 partials
+  const float* amax_b;  // max|B source| (FP32 X and Gram scales)
+  const float* amax_u;  // max|U|
+  int* status;
+};
+
+// Power-of-two scale s with |v s| < 2^14 for |v| <= amax (1 for amax 0 / non-finite).
+__device__ __forceinline__ float pow2_scale(float amax) {
+  if (!(amax > 0.f) || !isfinite(amax)) return 1.f;
+  int e;
+  frexpf(amax, &e);  // amax < 2^e
+  return ldexpf(1.f, 14 - e);
+}
+
+__device__ __forceinline__ uint32_t pack_h2(float a, float b) {
+  __half2 h = __floats2half2_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+__device__ __forceinline__ uint32_t pack_b2(float a, float b) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// (a, b) -> hi pair and lo pair, FP16: hi = fp16(v), lo = fp16(v - hi).
+__device__ __forceinline__ void split_h2(float a, float b, uint32_t& hi, uint32_t& lo) {
+  __half2 h = __floats2half2_rn(a, b);
+  const float2 f = __half22float2(h);
+  hi = *reinterpret_cast<uint32_t*>(&h);
+  lo = pack_h2(a - f.x, b - f.y);
+}
+__device__ __forceinline__ void split_b2(float a, float b, uint32_t& hi, uint32_t& lo) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  const float2 f = __bfloat1622float2(h);
+  hi = *reinterpret_cast<uint32_t*>(&h);
+  lo = pack_b2(a - f.x, b - f.y);
+}
+
+__device__ __forceinline__ void sts64(uint32_t addr, uint32_t x, uint32_t y) {
+  asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(x), "r"(y) : "memory");
+}
+__device__ __forceinline__ void sts128(uint32_t addr, uint4 v) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+               : "memory");
+}
+__device__ __forceinline__ uint4 ldg16(const void* p) {
+  uint4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p));
+  return v;
+}
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// U (m x k FP32, ld k, k % 4 == 0) -> hi, lo (m x ku 16-bit): FP16 pairs of
+// U s (s = pow2_scale(max|U|)) or BF16 pairs of U.
+template <bool F16>
+__global__ void split_u_kernel(const float* __restrict__ U, int64_t m, int k, int64_t ku,
+                               const float* __restrict__ amax, uint16_t* __restrict__ hi, uint16_t* __restrict__ lo) {
+  const float s = F16 ? pow2_scale(*amax) : 1.f;
+  const int k4 = k / 4;
+  const int64_t total = m * k4;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / k4;
+    const int c = (int)(e - r * k4) * 4;
+    const float4 v = __ldg(reinterpret_cast<const float4*>(U + r * k + c));
+    uint32_t h0, l0, h1, l1;
+    if (F16) {
+      split_h2(v.x * s, v.y * s, h0, l0);
+      split_h2(v.z * s, v.w * s, h1, l1);
+    } else {
+      split_b2(v.x, v.y, h0, l0);
+      split_b2(v.z, v.w, h1, l1);
+    }
+    *reinterpret_cast<uint2*>(hi + r * ku + c) = make_uint2(h0, h1);
+    *reinterpret_cast<uint2*>(lo + r * ku + c) = make_uint2(l0, l1);
+  }
+}
+
+template <int MODE, int MH>
+__global__ void __launch_bounds__(Cfg<MODE, MH>::THREADS, 1)
+    passf_kernel(const __grid_constant__ CUtensorMap tm_ahi, const __grid_constant__ CUtensorMap tm_alo,
+                 const __grid_constant__ CUtensorMap tm_bhi, const __grid_constant__ CUtensorMap tm_blo, Params p) {
+  using C = Cfg<MODE, MH>;
+  constexpr int STAGES = C::STAGES;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* tfull = reinterpret_cast<uint64_t*>(smem + STAGES * C::STAGE_BYTES);
+  uint64_t* full = tfull + STAGES;
+  uint64_t* empty = full + STAGES;
+  uint64_t* accf = empty + STAGES;
+  uint64_t* acce = accf + 1;
+  uint64_t* drain = acce + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int units = p.tiles * p.chunks;
+
+  if (tid == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      ptx::mbar_init(&tfull[s], 1);
+      ptx::mbar_init(&full[s], C::CONV ? C::CW : 1);
+      ptx::mbar_init(&empty[s], 1);
+    }
+    ptx::mbar_init(accf, 1);
+    ptx::mbar_init(acce, 4);
+    ptx::mbar_init(drain, 1);
+    *abort_flag = 0;
+    ptx::fence_mbar_init();
+  }
+  if (warp == C::MMA_W) ptx::tmem_alloc(tmem_slot, C::TMEM_COLS);
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t sbase = ptx::smem_u32(smem);
+
+  auto fail = [&]() {
+    atomicOr(p.status, ST_TIMEOUT);
+    atomicExch(abort_flag, 1);
+  };
+  auto aborted = [&]() { return *(volatile int*)abort_flag != 0; };
+  auto unit_rows = [&](int64_t u, int64_t& i0, int64_t& i1) {
+    i0 = (u / p.tiles) * p.rows_per_chunk;
+    i1 = i0 + p.rows_per_chunk;
+    if (i1 > p.m) i1 = p.m;
+  };
+
+  if (warp == C::PROD_W) {
+    // ------------------------------------------------------------ producer
+    int64_t step = 0;
+    bool ok = true;
+    // L2 prefetch cursor (converter modes): the step PF_STEPS ahead of `step`
+    int64_t pu = blockIdx.x, pt = 0;
+    auto advance = [&](int64_t& u, int64_t& t) {
+      int64_t a, b;
+      unit_rows(u, a, b);
+      if (++t >= (b - a + BK - 1) / BK) {
+        u += gridDim.x;
+        t = 0;
+      }
+    };
+    auto prefetch = [&](int64_t u, int64_t t) {
+      if (u >= units) return;
+      int64_t a, b;
+      unit_rows(u, a, b);
+      const int64_t row = a + t * BK + lane;
+      const int64_t col0 = (int64_t)(u % p.tiles) * C::BN;
+      int64_t cols = p.nb - col0;
+      if (cols > C::BN) cols = C::BN;
+      const uint32_t bytes = (uint32_t)(cols * C::ELEM) & ~15u;
+      if (row < b && bytes > 0)
+        prefetch_l2((const uint8_t*)p.X + (row * p.ldb + col0) * C::ELEM, bytes);
+    };
+    if (C::CONV) {
+      for (int i = 0; i < PF_STEPS && pu < units; ++i) {
+        prefetch(pu, pt);
+        advance(pu, pt);
+      }
+    }
+    for (int64_t unit = blockIdx.x; unit < units && ok; unit += gridDim.x) {
+      int64_t i0, i1;
+      unit_rows(unit, i0, i1);
+      const int64_t nsteps = (i1 - i0 + BK - 1) / BK;
+      const int col0 = (int)(unit % p.tiles) * C::BN;
+      for (int64_t t = 0; t < nsteps; ++t, ++step) {
+        const int s = (int)(step % STAGES);
+        const uint32_t ph = (uint32_t)((step / STAGES) & 1);
+        int good = 1;
+        if (lane == 0) {
+          if (!ptx::mbar_wait(&empty[s], ph ^ 1u, kWaitNs)) {
+            fail();
+            good = 0;
+          } else if (aborted()) {
+            good = 0;
+          }
+        }
+        good = __shfl_sync(0xffffffffu, good, 0);
+        if (!good) {
+          ok = false;
+          break;
+        }
+        if (lane == 0) {
+          const uint32_t st = sbase + s * C::STAGE_BYTES;
+          const int y = (int)(i0 + t * BK);
+          ptx::mbar_arrive_expect_tx(&tfull[s], C::TX);
+#pragma unroll
+          for (int b = 0; b < 2 * MH; ++b) {
+            ptx::tma_load_2d(st + b * C::BOX, &tm_ahi, 64 * b, y, &tfull[s]);
+            ptx::tma_load_2d(st + C::A_BYTES + b * C::BOX, &tm_alo, 64 * b, y, &tfull[s]);
+          }
+          if (!C::CONV) {
+            const uint32_t bst = st + 2 * C::A_BYTES;
+#pragma unroll
+            for (int b = 0; b < C::BN / 64; ++b) {
+              ptx::tma_load_2d(bst + b * C::BOX, &tm_bhi, col0 + 64 * b, y, &tfull[s]);
+              if (C::NB == 2) ptx::tma_load_2d(bst + C::B_BYTES + b * C::BOX, &tm_blo, col0 + 64 * b, y, &tfull[s]);
+            }
+          }
+        }
+        if (C::CONV) {
+          prefetch(pu, pt);
+          advance(pu, pt);
+        }
+      }
+    }
+    // bounded wait for the copies of the last stages issued (already complete
+    // on the normal path; in flight when the kernel aborted)
+    if (lane == 0) {
+      for (int64_t w = step - 1; w >= 0 && w >= step - STAGES; --w)
+        ptx::mbar_wait(&tfull[w % STAGES], (uint32_t)((w / STAGES) & 1), kDrainNs);
+    }
+    __syncwarp();
+  } else if (warp < C::CW) {
+    // ------------------------------------------------------------ converters
+    float sb = 1.f;
+    if (MODE == M_F32) sb = pow2_scale(*p.amax_b);
+    uint4 rb[C::B_VEC], rb_n[C::B_VEC];
+    auto load = [&](int64_t i0, int64_t i1, int tile, uint4 (&r)[C::B_VEC]) {
+      const int64_t col0 = (int64_t)tile * C::BN;
+      constexpr int EPV = 16 / C::ELEM;  // elements per 16-byte load
+#pragma unroll
+      for (int q = 0; q < C::B_VEC; ++q) {
+        const int f = tid + C::CT * q;
+        const int kr = f / (C::BN / EPV), mn = (f % (C::BN / EPV)) * EPV;
+        const int64_t gi = i0 + kr, gj = col0 + mn;
+        if (gi < i1 && gj < p.nb)
+          r[q] = ldg16((const uint8_t*)p.X + (gi * p.ldb + gj) * C::ELEM);
+        else
+          r[q] = make_uint4(0u, 0u, 0u, 0u);
+      }
+    };
+    auto store = [&](uint32_t stage_addr, const uint4 (&r)[C::B_VEC]) {
+      const uint32_t b_hi = stage_addr + 2 * C::A_BYTES, b_lo = b_hi + C::B_BYTES;
+#pragma unroll
+      for (int q = 0; q < C::B_VEC; ++q) {
+        const int f = tid + C::CT * q;
+        if (MODE == M_F32) {
+          const int kr = f / (C::BN / 4), mn = (f % (C::BN / 4)) * 4;
+          const float4 v = *reinterpret_cast<const float4*>(&r[q]);
+          uint32_t h0, l0, h1, l1;
+          split_h2(v.x * sb, v.y * sb, h0, l0);
+          split_h2(v.z * sb, v.w * sb, h1, l1);
+          const uint32_t off = ptx::mn_sw128_offset(kr, mn, C::SBO_B);
+          sts64(b_hi + off, h0, h1);
+          sts64(b_lo + off, l0, l1);
+        } else {
+          // E4M3 values widen exactly to BF16
+          const int kr = f / (C::BN / 16), mn = (f % (C::BN / 16)) * 16;
+          const __nv_fp8_e4m3* e8 = reinterpret_cast<const __nv_fp8_e4m3*>(&r[q]);
+          uint32_t w[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) w[u] = pack_b2(float(e8[2 * u]), float(e8[2 * u + 1]));
+          sts128(b_hi + ptx::mn_sw128_offset(kr, mn, C::SBO_B), make_uint4(w[0], w[1], w[2], w[3]));
+          sts128(b_hi + ptx::mn_sw128_offset(kr, mn + 8, C::SBO_B), make_uint4(w[4], w[5], w[6], w[7]));
+        }
+      }
+    };
+    int64_t unit = blockIdx.x, kst = 0, step = 0;
+    int64_t c0, c1;
+    if (unit < units) {
+      unit_rows(unit, c0, c1);
+      load(c0, c1, (int)(unit % p.tiles), rb);
+      while (true) {
+        const int64_t nsteps = (c1 - c0 + BK - 1) / BK;
+        int64_t nunit = unit, nk = kst + 1;
+        if (nk >= nsteps) {
+          nunit = unit + gridDim.x;
+          nk = 0;
+        }
+        int64_t n0 = 0, n1 = 0;
+        const bool more = nunit < units;
+        if (more) {
+          unit_rows(nunit, n0, n1);
+          load(n0 + nk * BK, n1, (int)(nunit % p.tiles), rb_n);
+        }
+        const int s = (int)(step % STAGES);
+        const uint32_t ph = (uint32_t)((step / STAGES) & 1);
+        if (!ptx::mbar_wait(&empty[s], ph ^ 1u, kWaitNs)) {
+          fail();
+          break;
+        }
+        if (aborted()) break;
+        store(sbase + s * C::STAGE_BYTES, rb);
+        ptx::fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(&full[s]);
+        ++step;
+        if (!more) break;
+        unit = nunit;
+        kst = nk;
+        c0 = n0;
+        c1 = n1;
+#pragma unroll
+        for (int q = 0; q < C::B_VEC; ++q) rb[q] = rb_n[q];
+      }
+    }
+  } else if (warp == C::MMA_W) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      constexpr uint32_t idesc = ptx::idesc_f16(C::F16 ? 0 : 1, 128, C::BN, 1, 1);
+      int64_t step = 0, seg = 0;
+      bool ok = true;
+      for (int64_t unit = blockIdx.x; unit < units && ok; unit += gridDim.x) {
+        int64_t i0, i1;
+        unit_rows(unit, i0, i1);
+        const int64_t nsteps = (i1 - i0 + BK - 1) / BK;
+        for (int64_t t = 0; t < nsteps && ok; ++t, ++step) {
+          const bool seg_start = (t % SEG) == 0;
+          if (seg_start) {
+            // wait until the epilogue has folded the previous segment out of A
+            if (!ptx::mbar_wait(acce, (uint32_t)((seg & 1) ^ 1), kWaitNs)) {
+              fail();
+              ok = false;
+              break;
+            }
+            ptx::tc_fence_after();
+          }
+          const int s = (int)(step % STAGES);
+          const uint32_t ph = (uint32_t)((step / STAGES) & 1);
+          bool got = ptx::mbar_wait(&tfull[s], ph, kWaitNs);
+          if (got && C::CONV) got = ptx::mbar_wait(&full[s], ph, kWaitNs);
+          if (!got || aborted()) {
+            if (!aborted()) fail();
+            ok = false;
+            break;
+          }
+          ptx::tc_fence_after();
+          const uint32_t st = sbase + s * C::STAGE_BYTES;
+          const uint32_t a_hi = st, a_lo = st + C::A_BYTES, b_hi = st + 2 * C::A_BYTES, b_lo = b_hi + C::B_BYTES;
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            uint64_t bdh, bdl = 0;
+            if (C::CONV) {
+              bdh = ptx::desc_sw128(b_hi + kk * 2 * C::SBO_B, 1024, C::SBO_B);
+              if (C::NB == 2) bdl = ptx::desc_sw128(b_lo + kk * 2 * C::SBO_B, 1024, C::SBO_B);
+            } else {
+              bdh = ptx::desc_sw128(b_hi + kk * 2048, C::BOX, 1024);
+              if (C::NB == 2) bdl = ptx::desc_sw128(b_lo + kk * 2048, C::BOX, 1024);
+            }
+#pragma unroll
+            for (int h = 0; h < MH; ++h) {
+              const uint32_t d = tmem + (uint32_t)(h * C::BN);
+              const uint64_t adh = ptx::desc_sw128(a_hi + h * 2 * C::BOX + kk * 2048, C::BOX, 1024);
+              const uint64_t adl = ptx::desc_sw128(a_lo + h * 2 * C::BOX + kk * 2048, C::BOX, 1024);
+              const uint32_t acc = (seg_start && kk == 0) ? 0u : 1u;
+              ptx::mma_f16(d, adh, bdh, idesc, acc);
+              if (C::NB == 2) ptx::mma_f16(d, adh, bdl, idesc, 1u);
+              ptx::mma_f16(d, adl, bdh, idesc, 1u);
+            }
+          }
+          ptx::mma_commit(&empty[s]);
+          if ((t % SEG) == SEG - 1 || t == nsteps - 1) {
+            ptx::mma_commit(accf);
+            ++seg;
+          }
+        }
+      }
+      // drain: every MMA issued by this thread completes before TMEM is freed
+      ptx::mma_commit(drain);
+      if (!ptx::mbar_wait(drain, 0u, kWaitNs)) atomicOr(p.status, ST_TIMEOUT);
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int e = warp - C::EPI0;  // TMEM lane quarter
+    float sc = 1.f;
+    if (MODE == M_F32) sc = 1.f / (pow2_scale(*p.amax_u) * pow2_scale(*p.amax_b));
+    if (MODE == M_GRAM) sc = 1.f / (pow2_scale(*p.amax_u) * pow2_scale(*p.amax_u));
+    const uint32_t lane_base = (uint32_t)(32 * e) << 16;
+    constexpr uint32_t S_COL = MH * C::BN;  // running sum S follows the segment accumulator A
+    int64_t seg = 0;
+    bool ok = true;
+    for (int64_t unit = blockIdx.x; unit < units && ok; unit += gridDim.x) {
+      const int tile = (int)(unit % p.tiles);
+      const int64_t ch = unit / p.tiles;
+      int64_t i0, i1;
+      unit_rows(unit, i0, i1);
+      const int64_t nsteps = (i1 - i0 + BK - 1) / BK;
+      const int64_t nseg = (nsteps + SEG - 1) / SEG;
+      for (int64_t g = 0; g < nseg; ++g, ++seg) {
+        if (!ptx::mbar_wait(accf, (uint32_t)(seg & 1), kWaitNs) || aborted()) {
+          if (!aborted()) fail();
+          ok = false;
+          break;
+        }
+        ptx::tc_fence_after();
+        const bool first = g == 0, last = g == nseg - 1;
+#pragma unroll
+        for (int h = 0; h < MH; ++h) {
+          const int c = 128 * h + 32 * e + lane;
+#pragma unroll 1
+          for (int cc = 0; cc < C::BN; cc += 32) {
+            const uint32_t col = (uint32_t)(h * C::BN + cc);
+            uint32_t a[32], r[32];
+            ptx::tmem_ld32(tmem + lane_base + col, a);
+            if (first) {
+#pragma unroll
+              for (int q = 0; q < 32; ++q) r[q] = a[q];
+            } else {
+              ptx::tmem_ld32(tmem + lane_base + S_COL + col, r);
+#pragma unroll
+              for (int q = 0; q < 32; ++q) r[q] = __float_as_uint(__uint_as_float(r[q]) + __uint_as_float(a[q]));
+            }
+            if (!last) {
+              ptx::tmem_st32(tmem + lane_base + S_COL + col, r);
+            } else if (c < p.k) {
+              const int64_t j0 = (int64_t)tile * C::BN + cc;
+              float* dst = p.part + (ch * p.k + c) * p.nb + j0;
+              if (j0 + 32 <= p.nb && (p.nb & 3) == 0) {
+#pragma unroll
+                for (int q = 0; q < 32; q += 4)
+                  *reinterpret_cast<float4*>(dst + q) =
+                      make_float4(__uint_as_float(r[q]) * sc, __uint_as_float(r[q + 1]) * sc,
+                                  __uint_as_float(r[q + 2]) * sc, __uint_as_float(r[q + 3]) * sc);
+              } else {
+#pragma unroll
+                for (int q = 0; q < 32; ++q)
+                  if (j0 + q < p.nb) dst[q] = __uint_as_float(r[q]) * sc;
+              }
+            }
+          }
+        }
+        ptx::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(acce);
+      }
+    }
+  }
+
+  __syncthreads();
+  if (warp == C::MMA_W) {
+    ptx::tc_fence_after();
+    ptx::tmem_dealloc(tmem, C::TMEM_COLS);
+  }
+}
+
+// about four units per CTA, chunks of >= 512 rows, a multiple of BK rows
+void choose_chunks(int64_t m, int tiles, int num_sms, int& chunks, int64_t& rows) {
+  int64_t c = (4LL * num_sms + tiles - 1) / tiles;
+  const int64_t cmax = (m + 511) / 512;
+  if (c > cmax) c = cmax;
+  if (c < 1) c = 1;
+  rows = (m + c - 1) / c;
+  rows = (rows + BK - 1) / BK * BK;
+  chunks = (int)((m + rows - 1) / rows);
+}
+
+template <int MODE, int MH>
+bool launch(Launcher& L, const CUtensorMap& ahi, const CUtensorMap& alo, const CUtensorMap& bhi,
+            const CUtensorMap& blo, const Params& p) {
+  using C = Cfg<MODE, MH>;
+  if (cudaFuncSetAttribute(passf_kernel<MODE, MH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM) !=
+      cudaSuccess)
+    return false;
+  const int units = p.tiles * p.chunks;
+  const int grid = units < L.num_sms ? units : L.num_sms;
+  passf_kernel<MODE, MH><<<grid, C::THREADS, C::SMEM, L.stream>>>(ahi, alo, bhi, blo, p);
+  L.count(1);
+  return true;
+}
+
+template <int MODE>
+bool launch_mh(Launcher& L, int MH, const CUtensorMap& ahi, const CUtensorMap& alo, const CUtensorMap& bhi,
+               const CUtensorMap& blo, const Params& p) {
+  return MH == 1 ? launch<MODE, 1>(L, ahi, alo, bhi, blo, p) : launch<MODE, 2>(L, ahi, alo, bhi, blo, p);
+}
+
+int64_t pitch16(int k) { return ((int64_t)k + 7) / 8 * 8; }
+
+}  // namespace pf
+
+void plan_tc_chain(char* base, TcChainWs& w, int xt, int64_t m, int64_t n, int k, bool want_g, int num_sms) {
+  const int MH = k > 128 ? 2 : 1;
+  const int BN = 256 / MH;
+  const int tiles = (int)((n + BN - 1) / BN);
+  int chunks;
+  int64_t rows;
+  pf::choose_chunks(m, tiles, num_sms, chunks, rows);
+  w.chunks = chunks;
+  w.rows_per_chunk = rows;
+  w.ku = pf::pitch16(k);
+  size_t off = 0;
+  auto take = [&](size_t b) {
+    off = (off + 255) & ~(size_t)255;
+    char* r = base ? base + off : nullptr;
+    off += b;
+    return r;
+  };
+  const size_t split_bytes = (size_t)m * (size_t)w.ku * 2;
+  w.Fpart = (double*)take((size_t)chunks * k * n * 4);  // FP32 partials (typed as bytes)
+  w.uhi = take(split_bytes);
+  w.ulo = take(split_bytes);
+  w.Gpart = nullptr;
+  w.ghi = w.glo = nullptr;
+  w.gchunks = 0;
+  if (want_g) {
+    const int gt = (k + BN - 1) / BN;
+    int gc;
+    int64_t grows;
+    pf::choose_chunks(m, gt, num_sms, gc, grows);
+    w.gchunks = gc;
+    w.grows_per_chunk = grows;
+    w.Gpart = (double*)take((size_t)gc * k * k * 4);
+    if (xt != LSPCA_F32) {
+      // the Gram takes FP16 pairs; BF16 / E4M3 X split U into BF16 pairs for F
+      w.ghi = take(split_bytes);
+      w.glo = take(split_bytes);
+    }
+  }
+  w.bytes = off + 256;
+}
+
+bool tc_chain_main(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_t ldx, const float* U, int k,
+                   TcChainWs& w, const float* absmax, int* status, bool want_g) {
+  const int MH = k > 128 ? 2 : 1;
+  const int BN = 256 / MH;
+  const bool f16 = xt == LSPCA_F32;
+  const int threads = 256;
+  const int64_t total4 = m * (k / 4);
+  int blocks = (int)((total4 + threads - 1) / threads);
+  if (blocks > 8 * L.num_sms) blocks = 8 * L.num_sms;
+  if (f16)
+    pf::split_u_kernel<true><<<blocks, threads, 0, L.stream>>>(U, m, k, w.ku, absmax + 1, (uint16_t*)w.uhi,
+                                                                (uint16_t*)w.ulo);
+  else
+    pf::split_u_kernel<false><<<blocks, threads, 0, L.stream>>>(U, m, k, w.ku, absmax + 1, (uint16_t*)w.uhi,
+                                                                 (uint16_t*)w.ulo);
+  L.count(1);
+  const CUtensorMapDataType adt = f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  CUtensorMap ahi, alo, bhi, blo;
+  if (!make_tmap_2d_sw128(&ahi, w.uhi, adt, 2, (uint64_t)m, (uint64_t)k, (uint64_t)w.ku * 2, pf::BK, 64) ||
+      !make_tmap_2d_sw128(&alo, w.ulo, adt, 2, (uint64_t)m, (uint64_t)k, (uint64_t)w.ku * 2, pf::BK, 64))
+    return false;
+  bhi = ahi;
+  blo = alo;
+  if (xt == LSPCA_BF16 &&
+      !make_tmap_2d_sw128(&bhi, X, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (uint64_t)m, (uint64_t)n, (uint64_t)ldx * 2,
+                          pf::BK, 64))
+    return false;
+  pf::Params p{};
+  p.X = X;
+  p.ldb = ldx;
+  p.nb = n;
+  p.m = m;
+  p.k = k;
+  p.tiles = (int)((n + BN - 1) / BN);
+  p.chunks = w.chunks;
+  p.rows_per_chunk = w.rows_per_chunk;
+  p.part = (float*)w.Fpart;
+  p.amax_b = absmax;
+  p.amax_u = absmax + 1;
+  p.status = status;
+  bool ok;
+  if (xt == LSPCA_F32) ok = pf::launch_mh<pf::M_F32>(L, MH, ahi, alo, bhi, blo, p);
+  else if (xt == LSPCA_BF16) ok = pf::launch_mh<pf::M_BF16>(L, MH, ahi, alo, bhi, blo, p);
+  else ok = pf::launch_mh<pf::M_E4M3>(L, MH, ahi, alo, bhi, blo, p);
+  if (!ok) return false;
+  if (want_g) {
+    // G = U^T U from FP16 pairs of U (the F pairs when X is FP32)
+    CUtensorMap ghi = ahi, glo = alo;
+    if (xt != LSPCA_F32) {
+      pf::split_u_kernel<true><<<blocks, threads, 0, L.stream>>>(U, m, k, w.ku, absmax + 1, (uint16_t*)w.ghi,
+                                                                  (uint16_t*)w.glo);
+      L.count(1);
+      if (!make_tmap_2d_sw128(&ghi, w.ghi, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, (uint64_t)m, (uint64_t)k,
+                              (uint64_t)w.ku * 2, pf::BK, 64) ||
+          !make_tmap_2d_sw128(&glo, w.glo, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, (uint64_t)m, (uint64_t)k,
+                              (uint64_t)w.ku * 2, pf::BK, 64))
+        return false;
+    }
+    pf::Params g = p;
+    g.X = nullptr;
+    g.nb = k;
+    g.tiles = (k + BN - 1) / BN;
+    g.chunks = w.gchunks;
+    g.rows_per_chunk = w.grows_per_chunk;
+    g.part = (float*)w.Gpart;
+    g.amax_b = absmax + 1;
+    if (!pf::launch_mh<pf::M_GRAM>(L, MH, ghi, glo, ghi, glo, g)) return false;
+  }
+  return true;
+}
+
+}  // namespace lspca

@@ -91,7 +91,7 @@ extern "C" int lspca_chain_noalloc(const void* X, int32_t xt, int64_t m, int64_t
   int* dstatus = status ? reinterpret_cast<int*>(status) : reinterpret_cast<int*>((char*)base + 64);
   // chunking of the regular pass, capped by the array's capacity
   TcChainWs w;
-  plan_tc_chain(nullptr, w, xt, m, n, k, false, sms);
+  plan_tc_chain_inline(nullptr, w, xt, m, n, k, false, sms);
   int64_t chunks = w.chunks;
   const int64_t cap_chunks = (int64_t)(part_cap / per_chunk);
   if (chunks > cap_chunks) {
@@ -111,7 +111,7 @@ extern "C" int lspca_chain_noalloc(const void* X, int32_t xt, int64_t m, int64_t
     launch_scan_x(L, X, xt, m, n, ldx, absmax, dstatus);
     launch_scan_x(L, U, LSPCA_F32, m, k, k, absmax + 1, dstatus);
   }
-  tc_chain_main(L, X, xt, m, n, ldx, U, k, w, absmax, dstatus, false);
+  tc_chain_inline_main(L, X, xt, m, n, ldx, U, k, w, absmax, dstatus, false);
   tc_chain_reduce(L, n, k, w, F, nullptr);
   return cudaGetLastError() == cudaSuccess ? LSPCA_OK : LSPCA_ERR_CUDA;
 }

@@ -218,7 +218,7 @@ void fit_prepare(lspca_srv* s, Req& r, Launcher& L) {
   r.prepared = true;
 }
 
-void fit_slice(lspca_srv* s, Req& r, Launcher& L) {
+bool fit_slice(lspca_srv* s, Req& r, Launcher& L) {
   FitLayout F = fit_layout(r, s->num_sms);
   char* b = s->arena + r.ws_off;
   const int64_t r0 = r.next;
@@ -241,7 +241,7 @@ void fit_slice(lspca_srv* s, Req& r, Launcher& L) {
   // pass F of the slice; the chunking depends only on the slice size
   TcChainWs cw;
   plan_tc_chain(b + F.chain, cw, r.xt, rows, r.n, r.k, false, s->num_sms);
-  tc_chain_main(L, Xs, r.xt, rows, r.n, r.ldx, U, r.k, cw, absmax, s->d_status, false);
+  if (!tc_chain_main(L, Xs, r.xt, rows, r.n, r.ldx, U, r.k, cw, absmax, s->d_status, false)) return false;
   tc_chain_reduce(L, r.n, r.k, cw, (double*)(b + F.fslice), nullptr);
   const int64_t cnt = (int64_t)r.k * r.n;
   add_f64_kernel<<<(int)((cnt + 255) / 256 < 4 * s->num_sms ? (cnt + 255) / 256 : 4 * s->num_sms), 256, 0,
@@ -255,6 +255,7 @@ void fit_slice(lspca_srv* s, Req& r, Launcher& L) {
                      (int32_t*)(b + F.misc + 64), s->d_status);
     r.finishing = true;
   }
+  return true;
 }
 
 bool tc_ok(int xt, int k) { return xt != LSPCA_F64 && k >= 4 && k <= 256 && (k % 4) == 0 && tc_available(); }
@@ -516,7 +517,7 @@ int lspca_srv_step(lspca_srv* s, int32_t* work_units) {
     Req& r = s->reqs[id];
     if (r.kind != KIND_FIT || r.finishing) continue;
     if (!r.prepared) fit_prepare(s, r, L);
-    fit_slice(s, r, L);
+    if (!fit_slice(s, r, L)) return LSPCA_ERR_CUDA;
     units += 1;
     if (r.finishing) finishing.push_back(id);
   }

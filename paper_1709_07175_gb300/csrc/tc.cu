@@ -503,7 +503,7 @@ static void choose_chunks(int64_t m, int tiles, int num_sms, int& chunks, int64_
 
 }  // namespace tcc
 
-void plan_tc_chain(char* base, TcChainWs& w, int xt, int64_t m, int64_t n, int k, bool want_g, int num_sms) {
+void plan_tc_chain_inline(char* base, TcChainWs& w, int xt, int64_t m, int64_t n, int k, bool want_g, int num_sms) {
   const int MH = k > 128 ? 2 : 1;
   const int BN = 256 / MH;
   const int tiles = (int)((n + BN - 1) / BN);
@@ -535,8 +535,8 @@ void plan_tc_chain(char* base, TcChainWs& w, int xt, int64_t m, int64_t n, int k
   (void)xt;
 }
 
-void tc_chain_main(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_t ldx, const float* U, int k,
-                   TcChainWs& w, const float* absmax, int* status, bool want_g) {
+void tc_chain_inline_main(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_t ldx, const float* U,
+                          int k, TcChainWs& w, const float* absmax, int* status, bool want_g) {
   const int MH = k > 128 ? 2 : 1;
   tcc::Params p{};
   p.U = U;

@@ -20,11 +20,23 @@ struct TcChainWs {
   int64_t rows_per_chunk = 0;
   int gchunks = 0;
   int64_t grows_per_chunk = 0;
+  int64_t ku = 0;           // pitch (16-bit elements) of the split copies of U
+  void* uhi = nullptr;      // m x ku: hi / lo 16-bit pairs of U (TMA-fed A operand)
+  void* ulo = nullptr;
+  void* ghi = nullptr;      // FP16 pairs of U for the Gram when X is BF16 / E4M3
+  void* glo = nullptr;
 };
+// TMA-fed pass F (chain.cu): U is split once into 16-bit pairs in the workspace.
 void plan_tc_chain(char* base, TcChainWs& w, int xt, int64_t m, int64_t n, int k, bool want_g, int num_sms);
-// absmax[0] = max|X|, absmax[1] = max|U| on the device (FP32 path scales).
-void tc_chain_main(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_t ldx, const float* U, int k,
+// absmax[0] = max|X|, absmax[1] = max|U| on the device (FP32 / Gram scales).
+// Returns false when a tensor map cannot be built or the kernel cannot be configured.
+bool tc_chain_main(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_t ldx, const float* U, int k,
                    TcChainWs& w, const float* absmax, int* status, bool want_g);
+// Pass F with U split inside the kernel (tc.cu): its workspace is the partials
+// only, which a fixed-size scratch array can hold for any m.
+void plan_tc_chain_inline(char* base, TcChainWs& w, int xt, int64_t m, int64_t n, int k, bool want_g, int num_sms);
+void tc_chain_inline_main(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_t ldx, const float* U,
+                          int k, TcChainWs& w, const float* absmax, int* status, bool want_g);
 void tc_chain_reduce(Launcher& L, int64_t n, int k, TcChainWs& w, double* F, double* G);
 
 // Y = X V on tensor cores (FP32, BF16 or E4M3 X; V and Y FP32, k <= 256).  With V = a

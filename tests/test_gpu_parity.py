@@ -157,6 +157,37 @@ def test_chain_fp32(ctx, data, wl):
     assert np.linalg.norm(G.cpu().numpy() - Gref) / np.linalg.norm(Gref) < 2e-6
 
 
+@pytest.mark.parametrize("dtype,m,n,ldx,k", [("f32", 3001, 1000, 1000, 100), ("f32", 2049, 4096, 4096, 256),
+                                             ("f32", 777, 1001, 1004, 20), ("bf16", 3001, 1000, 1000, 100),
+                                             ("bf16", 1025, 2048, 2056, 200), ("e4m3", 1500, 1040, 1040, 64),
+                                             ("e4m3", 700, 4096, 4096, 256)])
+def test_chain_tensor_core_paths(ctx, dtype, m, n, ldx, k):
+    """Pass F (F = U^T X with G = U^T U) on every tensor-core path, with a ragged
+    row tail, a partial last column tile, k below one 128-row half or spanning
+    two, and row-strided X.  Against the FP64 products of the same stored
+    values (relative Frobenius): FP32 X with split-FP16 operands 2e-6; BF16 and
+    E4M3 X (exact) with a split-BF16 U 2e-5; G from FP16 pairs of U 2e-6."""
+    if dtype == "e4m3":
+        w = S.WORKLOADS["e4m3_binary"].scaled(m=m, n=ldx, k=k)
+    elif dtype == "bf16":
+        w = S.WORKLOADS["bf16_dense"].scaled(m=m, n=ldx, k=k)
+    else:
+        w = S.WORKLOADS["fp32_sparse"].scaled(m=m, n=ldx, k=k)
+    base = S.generate(w)
+    X = base.cuda()[:, :n]
+    Xd = base[:, :n].float().double().numpy()
+    Om = P.omega_sparse(w.omega_seed, n, k, 64)
+    U32 = torch.from_numpy(Xd @ Om).float()
+    Ud = U32.double().numpy()
+    F, G = ctx.chain(X, U32.cuda(), want_gram=True)
+    Fref = Ud.T @ Xd
+    Gref = Ud.T @ Ud
+    ef = np.linalg.norm(F.cpu().numpy() - Fref) / np.linalg.norm(Fref)
+    eg = np.linalg.norm(G.cpu().numpy() - Gref) / np.linalg.norm(Gref)
+    assert ef < (2e-6 if dtype == "f32" else 2e-5), ef
+    assert eg < 2e-6, eg
+
+
 # ------------------------------------------------------------------ the k x k step
 
 @pytest.mark.parametrize("wl", [C1, C2S])
