@@ -346,6 +346,28 @@ def run_gpu(args):
     torch.cuda.synchronize()
     spca_ms = s0.elapsed_time(s1) / nsp
 
+    # ---- the reduction map Y = X V (Sec. III-B.2) of the fitted V over the same X
+    Y = torch.empty(w.m, w.k, dtype=torch.float32, device=X.device)
+
+    def proj():
+        rc = L.lspca_project(ctx.handle, X, V, w.k, Y, stream)
+        if rc != L.OK:
+            raise L.LspcaError(rc, "lspca_project")
+
+    for _ in range(3):
+        proj()
+    torch.cuda.synchronize()
+    p0 = torch.cuda.Event(enable_timing=True)
+    p1 = torch.cuda.Event(enable_timing=True)
+    npj = max(3, min(args.steps, 10))
+    p0.record(stream)
+    for _ in range(npj):
+        proj()
+    p1.record(stream)
+    torch.cuda.synchronize()
+    proj_ms = p0.elapsed_time(p1) / npj
+    del Y
+
     # ---- end to end through the public API: pinned host X -> device, fit, V and sigma back
     Xh = torch.empty(X.shape, dtype=X.dtype, pin_memory=True)
     Xh.copy_(X)
@@ -400,6 +422,10 @@ def run_gpu(args):
             "spca": {"ms_per_step": spca_ms, "samples_per_s": w.m * ws / (spca_ms / 1e3),
                      "lazy_speedup": spca_ms / ms_step},
             "passes_ms": per,
+            "project": {"ms_per_call": proj_ms, "samples_per_s": w.m / (proj_ms / 1e3),
+                        "achieved_gbs": (x_bytes + u_bytes) / (proj_ms / 1e3) / 1e9,
+                        "frac": (x_bytes + u_bytes) / (proj_ms / 1e3) / 1e9 / peak,
+                        "bytes_per_call": x_bytes + u_bytes, "kernel": "tcproj project_kernel (FP32 X, k=128)"},
             "e2e": {"value": w.m * ws / (e2e_ms / 1e3), "unit": "samples/s",
                     "h2d_bytes_per_step": x_bytes, "d2h_bytes_per_step": w.n * w.k * 4 + w.k * 8,
                     "ms_per_step": e2e_ms},

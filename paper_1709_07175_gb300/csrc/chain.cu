@@ -21,25 +21,25 @@
 // MN-major SW128 operand layout; rows past m and columns past k arrive as
 // zeros).  For BF16 X and for the Gram the B operand is loaded the same way
 // and the kernel has no converter warps; FP32 and E4M3 X are converted by
-// converter warps that load X rows with 16-byte global loads one step ahead,
-// while the producer warp prefetches the rows of the step PF_STEPS ahead into
-// L2 with bulk prefetches, so the converters' loads hit L2.
+// converter warps that load X rows with 16-byte global loads one step ahead
+// (two register buffers in ping-pong).  (Bulk L2 prefetches of the rows a few
+// steps ahead were measured on GB300 to slow this pass down by a third.)
 //
 // Accumulation.  Measured on GB300, the FP32 accumulation of tcgen05.mma into
 // TMEM behaves like round-toward-zero (its error is biased and grows with the
 // number of accumulating instructions), so the tensor core accumulates only
-// segments of SEG k-steps (SEG * BK rows) into TMEM region A; the epilogue
-// warps fold each finished segment into a round-to-nearest FP32 running sum S
-// in TMEM region B and write S, scaled back, as the unit's FP32 partial after
-// its last segment.  Partials of the m-chunks are summed in FP64 in fixed
-// order (tc_chain_reduce).
+// segments of SEG k-steps (SEG * BK rows) into a TMEM accumulator A; the
+// epilogue warps fold each finished segment into a round-to-nearest FP32
+// running sum S in TMEM and write S, scaled back, as the unit's FP32 partial
+// after its last segment.  Eight epilogue warps fold in parallel, since each
+// fold is a chain of TMEM load / store round trips.  Partials of the m-chunks
+// are summed in FP64 in fixed order (tc_chain_reduce).
 //
 // Kernel structure (one persistent CTA per SM; a unit = (m-chunk, N tile)):
-//   warps 0..CW-1      converters (FP32 / E4M3 X only);
-//   warps CW..CW+3     epilogue (one TMEM lane quarter each);
-//   warp  CW+4         TMEM allocation, the thread that issues tcgen05.mma;
-//   warp  CW+5         producer: TMA copies of each stage (lane 0) and L2
-//                      prefetches of X rows (one row per lane).
+//   warps 0..CW-1      converters (16 for FP32 X, 8 for E4M3 X, none otherwise);
+//   warps CW..CW+7     epilogue (two per TMEM lane quarter, half the columns each);
+//   warp  CW+8         TMEM allocation, the thread that issues tcgen05.mma;
+//   warp  CW+9         producer: TMA copies of each stage (lane 0).
 // Ring of STAGES shared-memory stages; per stage the mbarriers tfull (TMA
 // bytes), full (converter warps), empty (tcgen05.commit).  Every wait is
 // bounded (2 s of %globaltimer): on expiry the kernel records ST_TIMEOUT,
@@ -54,37 +54,47 @@ namespace lspca {
 namespace pf {
 
 constexpr int BK = 32;       // rows (K) per stage
-constexpr int SEG = 4;       // k-steps accumulated by the tensor core per segment
-constexpr int PF_STEPS = 6;  // L2 prefetch distance of the converter modes, in steps
 constexpr uint64_t kWaitNs = 2000000000ull;
 constexpr uint64_t kDrainNs = 100000000ull;
 
 enum Mode { M_F32 = 0, M_BF16 = 1, M_E4M3 = 2, M_GRAM = 3 };
+constexpr int kConvBuffers = 2;
 
-template <int MODE, int MH>
+template <int MODE, int MH, int NACC>
 struct Cfg {
-  static constexpr int BN = 256 / MH;
+  static_assert(NACC == 1 || (NACC == 2 && MH == 1), "double-buffered A with one M half only");
+  static constexpr int BN = (MH == 2 || NACC == 2) ? 128 : 256;
   static constexpr int WA = 128 * MH;
   static constexpr bool CONV = (MODE == M_F32 || MODE == M_E4M3);
   static constexpr bool F16 = (MODE == M_F32 || MODE == M_GRAM);  // FP16 pairs, else BF16
   static constexpr int NB = F16 ? 2 : 1;                          // B operand parts
-  static constexpr int CW = CONV ? 8 : 0;
+  static constexpr int CW = MODE == M_F32 ? 16 : (CONV ? 8 : 0);
   static constexpr int CT = CW * 32;
-  static constexpr int EPI0 = CW;
-  static constexpr int MMA_W = CW + 4;
-  static constexpr int PROD_W = CW + 5;
-  static constexpr int THREADS = (CW + 6) * 32;
+  static constexpr int EW_N = 8;  // epilogue warps: two per TMEM lane quarter, each folds half the columns
+  static constexpr int EPI0 = CW;  // a multiple of 4, so warp EPI0 + e owns TMEM lane quarter e % 4
+  static constexpr int MMA_W = CW + EW_N;
+  static constexpr int PROD_W = CW + EW_N + 1;
+  static constexpr int THREADS = (CW + EW_N + 2) * 32;
   static constexpr uint32_t BOX = BK * 128;        // one TMA box: BK rows x 64 16-bit columns
   static constexpr uint32_t A_BYTES = BK * WA * 2;  // one part of A
   static constexpr uint32_t B_BYTES = BK * BN * 2;  // one part of B
   static constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + NB * B_BYTES;
-  static constexpr int STAGES = STAGE_BYTES <= 32768 ? 6 : 4;
+  static constexpr int STAGES = STAGE_BYTES <= 24576 ? 8 : STAGE_BYTES <= 32768 ? 6 : 4;
   static constexpr uint32_t TX = 2 * A_BYTES + (CONV ? 0u : NB * B_BYTES);
   static constexpr uint32_t SBO_B = (BN / 64) * 1024;  // converter layout of B: K atom groups
   static constexpr int ELEM = (MODE == M_F32) ? 4 : 1;  // converter modes: bytes per X element
   static constexpr int B_VEC = CONV ? BK * BN * ELEM / 16 / CT : 1;  // 16-byte loads per thread per step
+  // k-steps the tensor core accumulates per segment: 8 for F (measured mean
+  // relative bias of F on GB300: -8e-7, nearly uniform across entries), 4 for
+  // the Gram, whose entries are all compared to one norm (-4e-7)
+  static constexpr int SEG = MODE == M_GRAM ? 4 : 8;
+  static constexpr int NBUF = kConvBuffers;  // register buffers of the converters (loads NBUF - 1 steps ahead)
   static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES + 256 + 8192;
-  static constexpr uint32_t TMEM_COLS = 512;  // segment accumulator A (MH x BN = 256) + running sum S
+  // TMEM: NACC segment accumulators of MH x BN columns, then the running sum S
+  static constexpr uint32_t ACC_COLS = MH * BN;
+  static constexpr uint32_t S_COL = NACC * ACC_COLS;
+  static constexpr uint32_t TMEM_COLS = 512;
+  static_assert(S_COL + ACC_COLS <= TMEM_COLS, "TMEM budget");
 };
 
 struct Params {
@@ -94,8 +104,8 @@ struct Params {
   int64_t m;
   int k;
   int tiles;      // N tiles of the B source
-  int chunks;     // m-chunks
-  int64_t rows_per_chunk;
+  int chunks;     // m-chunks; chunk c takes the BK-row blocks c, c + chunks, c + 2 chunks, ...
+  int64_t nblocks;  // BK-row blocks of m
   float* part;    // chunks x k x nb FP32 partials
   const float* amax_b;  // max|B source| (FP32 X and Gram scales)
   const float* amax_u;  // max|U|
@@ -147,9 +157,6 @@ __device__ __forceinline__ uint4 ldg16(const void* p) {
                : "l"(p));
   return v;
 }
-__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
 
 // U (m x k FP32, ld k, k % 4 == 0) -> hi, lo (m x ku 16-bit): FP16 pairs of
 // U s (s = pow2_scale(max|U|)) or BF16 pairs of U.
@@ -176,20 +183,20 @@ __global__ void split_u_kernel(const float* __restrict__ U, int64_t m, int k, in
   }
 }
 
-template <int MODE, int MH>
-__global__ void __launch_bounds__(Cfg<MODE, MH>::THREADS, 1)
+template <int MODE, int MH, int NACC>
+__global__ void __launch_bounds__(Cfg<MODE, MH, NACC>::THREADS, 1)
     passf_kernel(const __grid_constant__ CUtensorMap tm_ahi, const __grid_constant__ CUtensorMap tm_alo,
                  const __grid_constant__ CUtensorMap tm_bhi, const __grid_constant__ CUtensorMap tm_blo, Params p) {
-  using C = Cfg<MODE, MH>;
+  using C = Cfg<MODE, MH, NACC>;
   constexpr int STAGES = C::STAGES;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* tfull = reinterpret_cast<uint64_t*>(smem + STAGES * C::STAGE_BYTES);
   uint64_t* full = tfull + STAGES;
   uint64_t* empty = full + STAGES;
-  uint64_t* accf = empty + STAGES;
-  uint64_t* acce = accf + 1;
-  uint64_t* drain = acce + 1;
+  uint64_t* accf = empty + STAGES;  // [NACC]
+  uint64_t* acce = accf + NACC;     // [NACC]
+  uint64_t* drain = acce + NACC;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
 
@@ -202,8 +209,10 @@ __global__ void __launch_bounds__(Cfg<MODE, MH>::THREADS, 1)
       ptx::mbar_init(&full[s], C::CONV ? C::CW : 1);
       ptx::mbar_init(&empty[s], 1);
     }
-    ptx::mbar_init(accf, 1);
-    ptx::mbar_init(acce, 4);
+    for (int b = 0; b < NACC; ++b) {
+      ptx::mbar_init(&accf[b], 1);
+      ptx::mbar_init(&acce[b], C::EW_N);
+    }
     ptx::mbar_init(drain, 1);
     *abort_flag = 0;
     ptx::fence_mbar_init();
@@ -220,48 +229,20 @@ __global__ void __launch_bounds__(Cfg<MODE, MH>::THREADS, 1)
     atomicExch(abort_flag, 1);
   };
   auto aborted = [&]() { return *(volatile int*)abort_flag != 0; };
-  auto unit_rows = [&](int64_t u, int64_t& i0, int64_t& i1) {
-    i0 = (u / p.tiles) * p.rows_per_chunk;
-    i1 = i0 + p.rows_per_chunk;
-    if (i1 > p.m) i1 = p.m;
+  // Rows of a unit: its chunk's BK-row blocks, interleaved with the other
+  // chunks' blocks so that all CTAs stream nearby rows of X at any moment.
+  auto unit_steps = [&](int64_t u) -> int64_t {
+    const int64_t ch = u / p.tiles;
+    return ch < p.nblocks ? (p.nblocks - ch + p.chunks - 1) / p.chunks : 0;
   };
+  auto step_row = [&](int64_t u, int64_t t) -> int64_t { return (u / p.tiles + t * p.chunks) * BK; };
 
   if (warp == C::PROD_W) {
     // ------------------------------------------------------------ producer
     int64_t step = 0;
     bool ok = true;
-    // L2 prefetch cursor (converter modes): the step PF_STEPS ahead of `step`
-    int64_t pu = blockIdx.x, pt = 0;
-    auto advance = [&](int64_t& u, int64_t& t) {
-      int64_t a, b;
-      unit_rows(u, a, b);
-      if (++t >= (b - a + BK - 1) / BK) {
-        u += gridDim.x;
-        t = 0;
-      }
-    };
-    auto prefetch = [&](int64_t u, int64_t t) {
-      if (u >= units) return;
-      int64_t a, b;
-      unit_rows(u, a, b);
-      const int64_t row = a + t * BK + lane;
-      const int64_t col0 = (int64_t)(u % p.tiles) * C::BN;
-      int64_t cols = p.nb - col0;
-      if (cols > C::BN) cols = C::BN;
-      const uint32_t bytes = (uint32_t)(cols * C::ELEM) & ~15u;
-      if (row < b && bytes > 0)
-        prefetch_l2((const uint8_t*)p.X + (row * p.ldb + col0) * C::ELEM, bytes);
-    };
-    if (C::CONV) {
-      for (int i = 0; i < PF_STEPS && pu < units; ++i) {
-        prefetch(pu, pt);
-        advance(pu, pt);
-      }
-    }
     for (int64_t unit = blockIdx.x; unit < units && ok; unit += gridDim.x) {
-      int64_t i0, i1;
-      unit_rows(unit, i0, i1);
-      const int64_t nsteps = (i1 - i0 + BK - 1) / BK;
+      const int64_t nsteps = unit_steps(unit);
       const int col0 = (int)(unit % p.tiles) * C::BN;
       for (int64_t t = 0; t < nsteps; ++t, ++step) {
         const int s = (int)(step % STAGES);
@@ -282,7 +263,7 @@ __global__ void __launch_bounds__(Cfg<MODE, MH>::THREADS, 1)
         }
         if (lane == 0) {
           const uint32_t st = sbase + s * C::STAGE_BYTES;
-          const int y = (int)(i0 + t * BK);
+          const int y = (int)step_row(unit, t);
           ptx::mbar_arrive_expect_tx(&tfull[s], C::TX);
 #pragma unroll
           for (int b = 0; b < 2 * MH; ++b) {
@@ -298,10 +279,6 @@ __global__ void __launch_bounds__(Cfg<MODE, MH>::THREADS, 1)
             }
           }
         }
-        if (C::CONV) {
-          prefetch(pu, pt);
-          advance(pu, pt);
-        }
       }
     }
     // bounded wait for the copies of the last stages issued (already complete
@@ -315,19 +292,46 @@ __global__ void __launch_bounds__(Cfg<MODE, MH>::THREADS, 1)
     // ------------------------------------------------------------ converters
     float sb = 1.f;
     if (MODE == M_F32) sb = pow2_scale(*p.amax_b);
-    uint4 rb[C::B_VEC], rb_n[C::B_VEC];
-    auto load = [&](int64_t i0, int64_t i1, int tile, uint4 (&r)[C::B_VEC]) {
-      const int64_t col0 = (int64_t)tile * C::BN;
-      constexpr int EPV = 16 / C::ELEM;  // elements per 16-byte load
+    // Per-thread byte offsets of its B_VEC 16-byte loads inside a step's
+    // BK x BN block (kr rows down, mn elements across), fixed for the kernel.
+    constexpr int EPV = 16 / C::ELEM;  // elements per 16-byte load
+    const int64_t row_bytes = p.ldb * C::ELEM;
+    // Load cursor: unit lu, its step lk of lsteps, the block's first row and column.
+    int64_t lu = blockIdx.x, lk = 0, lsteps = 0, lrow = 0, lcol = 0;
+    bool lcols_full = true;
+    auto enter_unit = [&]() {
+      lk = 0;
+      if (lu >= units) return;
+      lsteps = unit_steps(lu);
+      lrow = (lu / p.tiles) * BK;
+      lcol = (lu % p.tiles) * C::BN;
+      lcols_full = lcol + C::BN <= p.nb;
+    };
+    enter_unit();
+    auto issue = [&](uint4 (&r)[C::B_VEC]) {
+      const uint8_t* base = (const uint8_t*)p.X + lrow * row_bytes + lcol * C::ELEM;
+      if (lcols_full && lrow + BK <= p.m) {
 #pragma unroll
-      for (int q = 0; q < C::B_VEC; ++q) {
-        const int f = tid + C::CT * q;
-        const int kr = f / (C::BN / EPV), mn = (f % (C::BN / EPV)) * EPV;
-        const int64_t gi = i0 + kr, gj = col0 + mn;
-        if (gi < i1 && gj < p.nb)
-          r[q] = ldg16((const uint8_t*)p.X + (gi * p.ldb + gj) * C::ELEM);
-        else
-          r[q] = make_uint4(0u, 0u, 0u, 0u);
+        for (int q = 0; q < C::B_VEC; ++q) {
+          const int f = tid + C::CT * q;
+          const int kr = f / (C::BN / EPV), mn = (f % (C::BN / EPV)) * EPV;
+          r[q] = ldg16(base + kr * row_bytes + mn * C::ELEM);
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < C::B_VEC; ++q) {
+          const int f = tid + C::CT * q;
+          const int kr = f / (C::BN / EPV), mn = (f % (C::BN / EPV)) * EPV;
+          if (lrow + kr < p.m && lcol + mn < p.nb)
+            r[q] = ldg16(base + kr * row_bytes + mn * C::ELEM);
+          else
+            r[q] = make_uint4(0u, 0u, 0u, 0u);
+        }
+      }
+      lrow += (int64_t)p.chunks * BK;
+      if (++lk >= lsteps) {
+        lu += gridDim.x;
+        enter_unit();
       }
     };
     auto store = [&](uint32_t stage_addr, const uint4 (&r)[C::B_VEC]) {
@@ -356,43 +360,42 @@ __global__ void __launch_bounds__(Cfg<MODE, MH>::THREADS, 1)
         }
       }
     };
-    int64_t unit = blockIdx.x, kst = 0, step = 0;
-    int64_t c0, c1;
-    if (unit < units) {
-      unit_rows(unit, c0, c1);
-      load(c0, c1, (int)(unit % p.tiles), rb);
-      while (true) {
-        const int64_t nsteps = (c1 - c0 + BK - 1) / BK;
-        int64_t nunit = unit, nk = kst + 1;
-        if (nk >= nsteps) {
-          nunit = unit + gridDim.x;
-          nk = 0;
+    // NBUF register buffers in rotation: the loads of step t + NBUF - 1 are
+    // issued before step t is converted and consumed NBUF - 1 iterations
+    // later (a register copy out of a prefetch buffer would instead wait for
+    // its loads at once).
+    int64_t total = 0;  // steps of this CTA over all its units
+    for (int64_t u = blockIdx.x; u < units; u += gridDim.x) total += unit_steps(u);
+    int64_t step = 0;
+    auto body = [&](uint4 (&cur)[C::B_VEC], uint4 (&nx)[C::B_VEC]) -> bool {
+      if (step + C::NBUF - 1 < total) issue(nx);
+      const int s = (int)(step % STAGES);
+      const uint32_t ph = (uint32_t)((step / STAGES) & 1);
+      if (!ptx::mbar_wait(&empty[s], ph ^ 1u, kWaitNs)) {
+        fail();
+        return false;
+      }
+      if (aborted()) return false;
+      store(sbase + s * C::STAGE_BYTES, cur);
+      ptx::fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive(&full[s]);
+      return ++step < total;
+    };
+    uint4 b0[C::B_VEC], b1[C::B_VEC];
+    if constexpr (C::NBUF == 3) {
+      uint4 b2[C::B_VEC];
+      if (total > 0) issue(b0);
+      if (total > 1) issue(b1);
+      if (total > 0) {
+        while (body(b0, b2) && body(b1, b0) && body(b2, b1)) {
         }
-        int64_t n0 = 0, n1 = 0;
-        const bool more = nunit < units;
-        if (more) {
-          unit_rows(nunit, n0, n1);
-          load(n0 + nk * BK, n1, (int)(nunit % p.tiles), rb_n);
+      }
+    } else {
+      if (total > 0) issue(b0);
+      if (total > 0) {
+        while (body(b0, b1) && body(b1, b0)) {
         }
-        const int s = (int)(step % STAGES);
-        const uint32_t ph = (uint32_t)((step / STAGES) & 1);
-        if (!ptx::mbar_wait(&empty[s], ph ^ 1u, kWaitNs)) {
-          fail();
-          break;
-        }
-        if (aborted()) break;
-        store(sbase + s * C::STAGE_BYTES, rb);
-        ptx::fence_proxy_async_smem();
-        __syncwarp();
-        if (lane == 0) ptx::mbar_arrive(&full[s]);
-        ++step;
-        if (!more) break;
-        unit = nunit;
-        kst = nk;
-        c0 = n0;
-        c1 = n1;
-#pragma unroll
-        for (int q = 0; q < C::B_VEC; ++q) rb[q] = rb_n[q];
       }
     }
   } else if (warp == C::MMA_W) {
@@ -402,14 +405,13 @@ __global__ void __launch_bounds__(Cfg<MODE, MH>::THREADS, 1)
       int64_t step = 0, seg = 0;
       bool ok = true;
       for (int64_t unit = blockIdx.x; unit < units && ok; unit += gridDim.x) {
-        int64_t i0, i1;
-        unit_rows(unit, i0, i1);
-        const int64_t nsteps = (i1 - i0 + BK - 1) / BK;
+        const int64_t nsteps = unit_steps(unit);
         for (int64_t t = 0; t < nsteps && ok; ++t, ++step) {
-          const bool seg_start = (t % SEG) == 0;
+          const bool seg_start = (t % C::SEG) == 0;
+          const int ab = (int)(seg % NACC);
           if (seg_start) {
-            // wait until the epilogue has folded the previous segment out of A
-            if (!ptx::mbar_wait(acce, (uint32_t)((seg & 1) ^ 1), kWaitNs)) {
+            // wait until the epilogue has folded the segment that last used buffer ab
+            if (!ptx::mbar_wait(&acce[ab], (uint32_t)(((seg / NACC) & 1) ^ 1), kWaitNs)) {
               fail();
               ok = false;
               break;
@@ -440,7 +442,7 @@ __global__ void __launch_bounds__(Cfg<MODE, MH>::THREADS, 1)
             }
 #pragma unroll
             for (int h = 0; h < MH; ++h) {
-              const uint32_t d = tmem + (uint32_t)(h * C::BN);
+              const uint32_t d = tmem + (uint32_t)(ab * C::ACC_COLS + h * C::BN);
               const uint64_t adh = ptx::desc_sw128(a_hi + h * 2 * C::BOX + kk * 2048, C::BOX, 1024);
               const uint64_t adl = ptx::desc_sw128(a_lo + h * 2 * C::BOX + kk * 2048, C::BOX, 1024);
               const uint32_t acc = (seg_start && kk == 0) ? 0u : 1u;
@@ -450,8 +452,8 @@ __global__ void __launch_bounds__(Cfg<MODE, MH>::THREADS, 1)
             }
           }
           ptx::mma_commit(&empty[s]);
-          if ((t % SEG) == SEG - 1 || t == nsteps - 1) {
-            ptx::mma_commit(accf);
+          if ((t % C::SEG) == C::SEG - 1 || t == nsteps - 1) {
+            ptx::mma_commit(&accf[ab]);
             ++seg;
           }
         }
@@ -463,59 +465,71 @@ __global__ void __launch_bounds__(Cfg<MODE, MH>::THREADS, 1)
     __syncwarp();
   } else {
     // ------------------------------------------------------------ epilogue
-    const int e = warp - C::EPI0;  // TMEM lane quarter
+    const int e = (warp - C::EPI0) & 3;       // TMEM lane quarter
+    const int ehalf = (warp - C::EPI0) >> 2;  // which half of the columns this warp folds
     float sc = 1.f;
     if (MODE == M_F32) sc = 1.f / (pow2_scale(*p.amax_u) * pow2_scale(*p.amax_b));
     if (MODE == M_GRAM) sc = 1.f / (pow2_scale(*p.amax_u) * pow2_scale(*p.amax_u));
     const uint32_t lane_base = (uint32_t)(32 * e) << 16;
-    constexpr uint32_t S_COL = MH * C::BN;  // running sum S follows the segment accumulator A
+    constexpr int EW = C::CW > 8 ? 16 : 32;  // TMEM columns per fold chunk (registers are scarcer with 16 converters)
     int64_t seg = 0;
     bool ok = true;
     for (int64_t unit = blockIdx.x; unit < units && ok; unit += gridDim.x) {
       const int tile = (int)(unit % p.tiles);
       const int64_t ch = unit / p.tiles;
-      int64_t i0, i1;
-      unit_rows(unit, i0, i1);
-      const int64_t nsteps = (i1 - i0 + BK - 1) / BK;
-      const int64_t nseg = (nsteps + SEG - 1) / SEG;
+      const int64_t nsteps = unit_steps(unit);
+      const int64_t nseg = (nsteps + C::SEG - 1) / C::SEG;
       for (int64_t g = 0; g < nseg; ++g, ++seg) {
-        if (!ptx::mbar_wait(accf, (uint32_t)(seg & 1), kWaitNs) || aborted()) {
+        const int ab = (int)(seg % NACC);
+        if (!ptx::mbar_wait(&accf[ab], (uint32_t)((seg / NACC) & 1), kWaitNs) || aborted()) {
           if (!aborted()) fail();
           ok = false;
           break;
         }
         ptx::tc_fence_after();
         const bool first = g == 0, last = g == nseg - 1;
+        const uint32_t abase = tmem + lane_base + (uint32_t)(ab * C::ACC_COLS);
+        const uint32_t sbase_t = tmem + lane_base + C::S_COL;
 #pragma unroll
         for (int h = 0; h < MH; ++h) {
           const int c = 128 * h + 32 * e + lane;
 #pragma unroll 1
-          for (int cc = 0; cc < C::BN; cc += 32) {
+          for (int cc = ehalf * (C::BN / 2); cc < (ehalf + 1) * (C::BN / 2); cc += EW) {
             const uint32_t col = (uint32_t)(h * C::BN + cc);
-            uint32_t a[32], r[32];
-            ptx::tmem_ld32(tmem + lane_base + col, a);
+            uint32_t a[EW], r[EW];
+            // the previous chunk's store of S has to land before r is reloaded
+            ptx::tmem_wait_st(r);
+            if constexpr (EW == 32) {
+              ptx::tmem_ld32_nowait(abase + col, a);
+              if (!first) ptx::tmem_ld32_nowait(sbase_t + col, r);
+            } else {
+              ptx::tmem_ld16_nowait(abase + col, a);
+              if (!first) ptx::tmem_ld16_nowait(sbase_t + col, r);
+            }
+            ptx::tmem_wait_ld(a);
             if (first) {
 #pragma unroll
-              for (int q = 0; q < 32; ++q) r[q] = a[q];
+              for (int q = 0; q < EW; ++q) r[q] = a[q];
             } else {
-              ptx::tmem_ld32(tmem + lane_base + S_COL + col, r);
+              ptx::tmem_regs_ready(r);
 #pragma unroll
-              for (int q = 0; q < 32; ++q) r[q] = __float_as_uint(__uint_as_float(r[q]) + __uint_as_float(a[q]));
+              for (int q = 0; q < EW; ++q) r[q] = __float_as_uint(__uint_as_float(r[q]) + __uint_as_float(a[q]));
             }
             if (!last) {
-              ptx::tmem_st32(tmem + lane_base + S_COL + col, r);
+              if constexpr (EW == 32) ptx::tmem_st32_nowait(sbase_t + col, r);
+              else ptx::tmem_st16_nowait(sbase_t + col, r);
             } else if (c < p.k) {
               const int64_t j0 = (int64_t)tile * C::BN + cc;
               float* dst = p.part + (ch * p.k + c) * p.nb + j0;
-              if (j0 + 32 <= p.nb && (p.nb & 3) == 0) {
+              if (j0 + EW <= p.nb && (p.nb & 3) == 0) {
 #pragma unroll
-                for (int q = 0; q < 32; q += 4)
+                for (int q = 0; q < EW; q += 4)
                   *reinterpret_cast<float4*>(dst + q) =
                       make_float4(__uint_as_float(r[q]) * sc, __uint_as_float(r[q + 1]) * sc,
                                   __uint_as_float(r[q + 2]) * sc, __uint_as_float(r[q + 3]) * sc);
               } else {
 #pragma unroll
-                for (int q = 0; q < 32; ++q)
+                for (int q = 0; q < EW; ++q)
                   if (j0 + q < p.nb) dst[q] = __uint_as_float(r[q]) * sc;
               }
             }
@@ -523,9 +537,10 @@ __global__ void __launch_bounds__(Cfg<MODE, MH>::THREADS, 1)
         }
         ptx::tc_fence_before();
         __syncwarp();
-        if (lane == 0) ptx::mbar_arrive(acce);
+        if (lane == 0) ptx::mbar_arrive(&acce[ab]);
       }
     }
+    ptx::tmem_wait_st();
   }
 
   __syncthreads();
@@ -546,24 +561,31 @@ void choose_chunks(int64_t m, int tiles, int num_sms, int& chunks, int64_t& rows
   chunks = (int)((m + rows - 1) / rows);
 }
 
-template <int MODE, int MH>
+template <int MODE, int MH, int NACC>
 bool launch(Launcher& L, const CUtensorMap& ahi, const CUtensorMap& alo, const CUtensorMap& bhi,
             const CUtensorMap& blo, const Params& p) {
-  using C = Cfg<MODE, MH>;
-  if (cudaFuncSetAttribute(passf_kernel<MODE, MH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM) !=
-      cudaSuccess)
+  using C = Cfg<MODE, MH, NACC>;
+  if (cudaFuncSetAttribute(passf_kernel<MODE, MH, NACC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)C::SMEM) != cudaSuccess)
     return false;
   const int units = p.tiles * p.chunks;
   const int grid = units < L.num_sms ? units : L.num_sms;
-  passf_kernel<MODE, MH><<<grid, C::THREADS, C::SMEM, L.stream>>>(ahi, alo, bhi, blo, p);
+  passf_kernel<MODE, MH, NACC><<<grid, C::THREADS, C::SMEM, L.stream>>>(ahi, alo, bhi, blo, p);
   L.count(1);
   return true;
 }
 
+// k <= 128: one 256-column accumulator; k > 128: two M halves of 128 columns.
+// (NACC = 2 -- 128-column tiles with a double-buffered accumulator, so the
+// tensor core never waits for the fold -- measured slower on GB300 at
+// 200,000 x 4,096: twice the MMA instructions and the U copies per X byte.)
+int tile_cols(int k) { return k > 128 ? 128 : 256; }
+
 template <int MODE>
-bool launch_mh(Launcher& L, int MH, const CUtensorMap& ahi, const CUtensorMap& alo, const CUtensorMap& bhi,
-               const CUtensorMap& blo, const Params& p) {
-  return MH == 1 ? launch<MODE, 1>(L, ahi, alo, bhi, blo, p) : launch<MODE, 2>(L, ahi, alo, bhi, blo, p);
+bool launch_k(Launcher& L, int k, const CUtensorMap& ahi, const CUtensorMap& alo, const CUtensorMap& bhi,
+              const CUtensorMap& blo, const Params& p) {
+  if (k > 128) return launch<MODE, 2, 1>(L, ahi, alo, bhi, blo, p);
+  return launch<MODE, 1, 1>(L, ahi, alo, bhi, blo, p);
 }
 
 int64_t pitch16(int k) { return ((int64_t)k + 7) / 8 * 8; }
@@ -571,8 +593,7 @@ int64_t pitch16(int k) { return ((int64_t)k + 7) / 8 * 8; }
 }  // namespace pf
 
 void plan_tc_chain(char* base, TcChainWs& w, int xt, int64_t m, int64_t n, int k, bool want_g, int num_sms) {
-  const int MH = k > 128 ? 2 : 1;
-  const int BN = 256 / MH;
+  const int BN = pf::tile_cols(k);
   const int tiles = (int)((n + BN - 1) / BN);
   int chunks;
   int64_t rows;
@@ -613,8 +634,7 @@ void plan_tc_chain(char* base, TcChainWs& w, int xt, int64_t m, int64_t n, int k
 
 bool tc_chain_main(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_t ldx, const float* U, int k,
                    TcChainWs& w, const float* absmax, int* status, bool want_g) {
-  const int MH = k > 128 ? 2 : 1;
-  const int BN = 256 / MH;
+  const int BN = pf::tile_cols(k);
   const bool f16 = xt == LSPCA_F32;
   const int threads = 256;
   const int64_t total4 = m * (k / 4);
@@ -646,15 +666,15 @@ bool tc_chain_main(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int
   p.k = k;
   p.tiles = (int)((n + BN - 1) / BN);
   p.chunks = w.chunks;
-  p.rows_per_chunk = w.rows_per_chunk;
+  p.nblocks = (m + pf::BK - 1) / pf::BK;
   p.part = (float*)w.Fpart;
   p.amax_b = absmax;
   p.amax_u = absmax + 1;
   p.status = status;
   bool ok;
-  if (xt == LSPCA_F32) ok = pf::launch_mh<pf::M_F32>(L, MH, ahi, alo, bhi, blo, p);
-  else if (xt == LSPCA_BF16) ok = pf::launch_mh<pf::M_BF16>(L, MH, ahi, alo, bhi, blo, p);
-  else ok = pf::launch_mh<pf::M_E4M3>(L, MH, ahi, alo, bhi, blo, p);
+  if (xt == LSPCA_F32) ok = pf::launch_k<pf::M_F32>(L, k, ahi, alo, bhi, blo, p);
+  else if (xt == LSPCA_BF16) ok = pf::launch_k<pf::M_BF16>(L, k, ahi, alo, bhi, blo, p);
+  else ok = pf::launch_k<pf::M_E4M3>(L, k, ahi, alo, bhi, blo, p);
   if (!ok) return false;
   if (want_g) {
     // G = U^T U from FP16 pairs of U (the F pairs when X is FP32)
@@ -674,10 +694,10 @@ bool tc_chain_main(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int
     g.nb = k;
     g.tiles = (k + BN - 1) / BN;
     g.chunks = w.gchunks;
-    g.rows_per_chunk = w.grows_per_chunk;
+
     g.part = (float*)w.Gpart;
     g.amax_b = absmax + 1;
-    if (!pf::launch_mh<pf::M_GRAM>(L, MH, ghi, glo, ghi, glo, g)) return false;
+    if (!pf::launch_k<pf::M_GRAM>(L, k, ghi, glo, ghi, glo, g)) return false;
   }
   return true;
 }

@@ -790,23 +790,40 @@ void launch_sketch_sparse(Launcher& L, const void* X, int xt, int64_t m, int64_t
 
 // Scan X for NaN/Inf and its largest magnitude (the dense-Omega paths, where the
 // sketch runs on tensor cores or as a plain GEMM and does not see every element).
+// One warp per row at a time; 16-byte loads when the rows are 16-byte aligned.
 template <int DT>
 __global__ void scan_x_kernel(const void* __restrict__ Xv, int64_t m, int64_t n, int64_t ldx, float* absmax,
                               int* status) {
   using T = typename XType<DT>::T;
-  const T* X = reinterpret_cast<const T*>(Xv);
+  constexpr int ES = (int)sizeof(T);
+  constexpr int EPV = 16 / ES;
+  const char* X = reinterpret_cast<const char*>(Xv);
+  const int lane = threadIdx.x & 31;
+  const int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const bool vec = (((uintptr_t)Xv & 15u) == 0) && ((ldx * ES) % 16 == 0);
+  const int64_t nv = vec ? n / EPV : 0;  // full 16-byte vectors per row
   float amax = 0.f;
   bool bad = false;
-  const int64_t total = m * n;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = e / n, c = e % n;
-    const float v = (float)XType<DT>::to_acc(X[r * ldx + c]);
+  auto take = [&](T e) {
+    const float v = (float)XType<DT>::to_acc(e);
     if (!isfinite(v)) bad = true;
     amax = fmaxf(amax, fabsf(v));
+  };
+  for (int64_t r = wg; r < m; r += nw) {
+    const char* row = X + r * ldx * ES;
+#pragma unroll 4
+    for (int64_t v = lane; v < nv; v += 32) {
+      const uint4 q = __ldg(reinterpret_cast<const uint4*>(row) + v);
+      const T* e = reinterpret_cast<const T*>(&q);
+#pragma unroll
+      for (int u = 0; u < EPV; ++u) take(e[u]);
+    }
+    for (int64_t c = nv * EPV + lane; c < n; c += 32) take(reinterpret_cast<const T*>(row)[c]);
   }
   amax = warp_max(amax);
   const unsigned anybad = __ballot_sync(0xffffffffu, bad);
-  if ((threadIdx.x & 31) == 0) {
+  if (lane == 0) {
     atomic_max_nonneg(absmax, amax);
     if (anybad) atomicOr(status, ST_NONFINITE);
   }

@@ -162,7 +162,6 @@ __global__ void __launch_bounds__(THREADS, 1) project_kernel(Params p) {
   if (warp < CONV_WARPS) {
     // ------------------------------------------------------------ converters
     constexpr int NV = (XK == XK_F32) ? 8 : (XK == XK_BF16 ? 4 : 2);  // 16-byte vectors per thread per k-step
-    uint4 r[NV], rn[NV];
     auto load = [&](const TileInfo& ti, int ks, uint4 (&dst)[NV]) {
 #pragma unroll
       for (int q = 0; q < NV; ++q) {
@@ -182,7 +181,7 @@ __global__ void __launch_bounds__(THREADS, 1) project_kernel(Params p) {
         }
       }
     };
-    auto store = [&](uint32_t st, int slot, int ks, int64_t ncols) {
+    auto store = [&](const uint4 (&r)[NV], uint32_t st, int slot, int ks, int64_t ncols) {
       const uint32_t a_hi = st + 2 * C::B_BYTES, a_lo = a_hi + C::A_BYTES;
 #pragma unroll
       for (int q = 0; q < NV; ++q) {
@@ -247,48 +246,55 @@ __global__ void __launch_bounds__(THREADS, 1) project_kernel(Params p) {
         }
       }
     };
+    // Two register buffers in ping-pong: the loads of step t + 1 are issued
+    // before step t is converted and consumed one full iteration later (a
+    // register copy from a prefetch buffer would wait for them at once).
+    uint4 ra[NV], rb[NV];
     int64_t tile = blockIdx.x;
     int ks = 0;
     int64_t step = 0;
+    TileInfo ti, tn;
+    auto body = [&](const uint4 (&cur)[NV], uint4 (&nxt)[NV]) -> bool {
+      const int nks = (int)((ti.n + BK - 1) / BK);
+      int64_t ntile = tile;
+      int nks_next = ks + 1;
+      if (nks_next >= nks) {
+        nks_next = 0;
+        ntile += gridDim.x;
+      }
+      const bool more = ntile < tiles;
+      if (more) {
+        if (ntile != tile) tn = tile_info(p, ntile);
+        load(ntile != tile ? tn : ti, nks_next, nxt);
+      }
+      const int s = (int)(step % C::STAGES);
+      const uint32_t ph = (uint32_t)((step / C::STAGES) & 1);
+      if (!ptx::mbar_wait(&empty[s], ph ^ 1u, kWaitNs)) {
+        fail();
+        return false;
+      }
+      if (aborted()) return false;
+      const uint32_t st = sbase + s * C::STAGE_BYTES;
+      if (warp == 0 && lane == 0) {
+        ptx::mbar_arrive_expect_tx(&full[s], 2 * C::B_BYTES);
+        ptx::bulk_g2s(st, ti.vt + (size_t)ks * 2 * C::B_BYTES, 2 * C::B_BYTES, &full[s]);
+      }
+      store(cur, st, (int)(step % C::RING), ks, ti.n);
+      ptx::fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive(&full[s]);
+      ++step;
+      if (!more) return false;
+      if (ntile != tile) ti = tn;
+      tile = ntile;
+      ks = nks_next;
+      return true;
+    };
     if (tile < tiles) {
-      TileInfo ti = tile_info(p, tile), tn = ti;
-      load(ti, ks, r);
-      while (true) {
-        const int nks = (int)((ti.n + BK - 1) / BK);
-        int64_t ntile = tile;
-        int nks_next = ks + 1;
-        if (nks_next >= nks) {
-          nks_next = 0;
-          ntile += gridDim.x;
-        }
-        const bool more = ntile < tiles;
-        if (more) {
-          if (ntile != tile) tn = tile_info(p, ntile);
-          load(ntile != tile ? tn : ti, nks_next, rn);
-        }
-        const int s = (int)(step % C::STAGES);
-        const uint32_t ph = (uint32_t)((step / C::STAGES) & 1);
-        if (!ptx::mbar_wait(&empty[s], ph ^ 1u, kWaitNs)) {
-          fail();
-          break;
-        }
-        if (aborted()) break;
-        const uint32_t st = sbase + s * C::STAGE_BYTES;
-        if (warp == 0 && lane == 0) {
-          ptx::mbar_arrive_expect_tx(&full[s], 2 * C::B_BYTES);
-          ptx::bulk_g2s(st, ti.vt + (size_t)ks * 2 * C::B_BYTES, 2 * C::B_BYTES, &full[s]);
-        }
-        store(st, (int)(step % C::RING), ks, ti.n);
-        ptx::fence_proxy_async_smem();
-        __syncwarp();
-        if (lane == 0) ptx::mbar_arrive(&full[s]);
-        ++step;
-        if (!more) break;
-        if (ntile != tile) ti = tn;
-        tile = ntile;
-        ks = nks_next;
-#pragma unroll
-        for (int q = 0; q < NV; ++q) r[q] = rn[q];
+      ti = tile_info(p, tile);
+      tn = ti;
+      load(ti, ks, ra);
+      while (body(ra, rb) && body(rb, ra)) {
       }
     }
   } else if (warp == MMA_WARP) {

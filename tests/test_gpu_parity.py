@@ -338,6 +338,24 @@ def test_nonfinite_input_is_reported(ctx):
     assert ctx.sync_status() == L.OK  # the report consumed the status word
 
 
+@pytest.mark.parametrize("dtype,where", [(torch.float32, (3, 8)), (torch.float32, (500, 1000)),
+                                         (torch.bfloat16, (776, 17)), (torch.bfloat16, (0, 999))])
+def test_nonfinite_reported_on_tensor_core_paths(ctx, dtype, where):
+    """Gaussian Omega on FP32 / BF16 X (the tensor-core sketch, whose scan of X
+    sets the FP16 scales and detects NaN/Inf): an Inf inside a 16-byte vector
+    or in a row's ragged tail of a row-strided X gives ERR_NUMERIC."""
+    m, n, ldx, k = 777, 1001, 1008, 16
+    base = torch.randn(m, ldx, generator=torch.Generator().manual_seed(3)).to(dtype)
+    base[where] = float("inf")
+    X = base.cuda()[:, :n]
+    V = torch.empty(n, k, dtype=torch.float32, device="cuda")
+    sig = torch.empty(k, dtype=torch.float64, device="cuda")
+    rep = L.lspca_report()
+    rc = L.lspca_fit(ctx.handle, X, k, L.omega("gaussian", 0), 0, V, sig, None, None, None, rep)
+    assert rc == L.ERR_NUMERIC
+    assert ctx.sync_status() == L.OK
+
+
 @pytest.mark.parametrize("bad", ["k0", "kbig", "ldx", "omega_p0", "e4m3_gauss", "null_v"])
 def test_invalid_arguments(ctx, bad):
     X = torch.zeros(64, 32, dtype=torch.float32, device="cuda")
