@@ -130,11 +130,12 @@ void run_sketch(lspca_ctx* ctx, Launcher& L, const void* X, int xt, int64_t m, i
                 const lspca_omega& om, bool tc, SketchBufs& b, void* U, const Mark& mark) {
   if (tc) {
     // dense Omega (BF16-rounded for BF16 X, exact +-1/0 for the very sparse kind)
-    // through the tensor-core reduction-map kernel: U = X Omega
+    // through the tensor-core reduction-map kernel: U = X Omega; the kernel also
+    // takes max|X| (NaN / Inf detection) and max|U| as it streams
     launch_omega_dense(L, om, n, k, LSPCA_F32, b.omega, k, false, xt == LSPCA_BF16);
-    launch_scan_x(L, X, xt, m, n, ldx, ctx->d_absmax, ctx->d_status);
     mark(1);
-    tc_project(L, X, xt, m, n, ldx, (const float*)b.omega, k, b.pw, (float*)U, ctx->d_status);
+    tc_project(L, X, xt, m, n, ldx, (const float*)b.omega, k, b.pw, (float*)U, ctx->d_status,
+               om.kind == LSPCA_OMEGA_VERY_SPARSE, ctx->d_absmax, ctx->d_absmax + 1);
     mark(2);
     return;
   }
@@ -211,12 +212,14 @@ int run_chain(lspca_ctx* ctx, Launcher& L, const void* X, int xt, int64_t m, int
 bool use_tc_chain(int xt, uint32_t flags, int k = 4) {
   return !(flags & LSPCA_FORCE_SIMT) && xt != LSPCA_F64 && (k % 4) == 0 && tc_available();
 }
-// Dense-Omega sketches run on the tensor-core reduction-map kernel; the very
-// sparse Omega on FP32/BF16 X keeps the gather kernel (HBM-bound, no MMA work).
+// The sketch of FP32 / BF16 / E4M3 X runs on the tensor-core reduction-map
+// kernel with Omega as its right operand (the very sparse Omega is exact in
+// one FP16 / BF16 piece, so half the products drop out); the gather kernel of
+// the very sparse Omega stays for FP64 X and under LSPCA_FORCE_SIMT.
 bool use_tc_sketch(int xt, const lspca_omega& om, uint32_t flags) {
   if ((flags & LSPCA_FORCE_SIMT) || !tc_available()) return false;
-  if (om.kind == LSPCA_OMEGA_GAUSSIAN) return xt == LSPCA_F32 || xt == LSPCA_BF16;
-  return xt == LSPCA_E4M3;
+  (void)om;
+  return xt == LSPCA_F32 || xt == LSPCA_BF16 || xt == LSPCA_E4M3;
 }
 
 int fit_impl(lspca_ctx* ctx, const void* X, int32_t xt, int64_t m, int64_t n, int64_t ldx, int32_t k, lspca_omega om,
@@ -273,7 +276,7 @@ int fit_impl(lspca_ctx* ctx, const void* X, int32_t xt, int64_t m, int64_t n, in
   cudaMemsetAsync(ctx->d_absmax, 0, 2 * sizeof(float), s);
   mark(0);
   run_sketch(ctx, L, X, xt, m, n, ldx, k, om, tc_s, sb, U, mark);
-  if (tc_f && (xt == LSPCA_F32 || want_g) && (tc_s || om.kind == LSPCA_OMEGA_GAUSSIAN))
+  if (tc_f && !tc_s && om.kind == LSPCA_OMEGA_GAUSSIAN)
     launch_scan_x(L, U, LSPCA_F32, m, k, k, ctx->d_absmax + 1, ctx->d_status);  // max|U| for the FP16 scales
   if ((st = run_chain(ctx, L, X, xt, m, n, ldx, U, k, tc_f, cb, F, want_g ? G : nullptr, mark))) return st;
   if (spca) {

@@ -229,11 +229,10 @@ bool fit_slice(lspca_srv* s, Req& r, Launcher& L) {
   float* absmax = (float*)(b + F.misc);
   cudaMemsetAsync(absmax, 0, 8, L.stream);
   if (fit_tc_sketch(r)) {
-    launch_scan_x(L, Xs, r.xt, rows, r.n, r.ldx, absmax, s->d_status);
-    // U_s = X_s Omega on the reduction-map kernel with the request's pre-tiled Omega
+    // U_s = X_s Omega on the reduction-map kernel with the request's pre-tiled
+    // Omega; the kernel takes max|X_s| (NaN / Inf detection) and max|U_s|
     tc_project_pretiled(L, Xs, r.xt, rows, r.n, r.ldx, b + F.tiles, (const float*)(b + F.scal) + 1, r.k, U,
-                        s->d_status);
-    if (r.xt == LSPCA_F32) launch_scan_x(L, U, LSPCA_F32, rows, r.k, r.k, absmax + 1, s->d_status);
+                        s->d_status, r.om.kind == LSPCA_OMEGA_VERY_SPARSE, absmax, absmax + 1);
   } else {
     launch_sketch_sparse(L, Xs, r.xt, rows, r.n, r.ldx, r.k, (const int32_t*)(b + F.colp), (const int32_t*)(b + F.ent),
                          (int32_t*)(b + F.off), U, r.k, absmax, s->d_status);

@@ -66,12 +66,17 @@ size_t tc_tile_v_bytes(int64_t n, int k);
 // Split and tile V for X type xt; scal: 2 device floats (max|V|, scale).
 void tc_tile_v(Launcher& L, int xt, const float* V, int64_t n, int k, void* tiles, float* scal, int* status);
 // Y = X V with V already split and tiled by tc_tile_v (vscale = its scale slot).
+// exact_v: V is exact in its hi piece (the very sparse Omega), so the products
+// with its lo piece are skipped.  xmax / ymax (nullable): max|X| and max|Y| are
+// folded into them with atomic max; NaN / Inf in X set ST_NONFINITE.
 void tc_project_pretiled(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_t ldx, const void* tiles,
-                         const float* vscale, int k, float* Y, int* status);
+                         const float* vscale, int k, float* Y, int* status, bool exact_v = false,
+                         float* xmax = nullptr, float* ymax = nullptr);
 // One persistent launch over *d_count (<= max_tiles) table entries.
 void tc_project_batch(Launcher& L, int xt, int k, const TcProjUnit* d_units, const int* d_count, int max_tiles,
                       int* status);
 void tc_project(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_t ldx, const float* V, int k,
-                TcProjectWs& w, float* Y, int* status);
+                TcProjectWs& w, float* Y, int* status, bool exact_v = false, float* xmax = nullptr,
+                float* ymax = nullptr);
 
 }  // namespace lspca

@@ -1,5 +1,6 @@
 // Tensor-core reduction map Y = X V (Sec. III-B.2: pi(x) = V^T x for every
-// row) on sm_103a with tcgen05/TMEM.
+// row) on sm_103a with tcgen05/TMEM.  With V = a dense Omega the same kernel
+// computes the sketch U = X Omega (Eq. 1).
 //
 // GEMM view: M = 128 rows of X per tile, N = k padded to a multiple of 64,
 // K = n.  A = the X tile (K-major: rows of X are contiguous in K), B = V
@@ -8,23 +9,38 @@
 // Number formats.
 // * FP32 X: x s_r = hi + lo with FP16 pieces, where s_r is a power of two
 //   chosen per row and per k-step from the row's max |x| in that step (a
-//   half-warp reduction over the 64 values the converter already holds), so no
+//   half-warp reduction over the 64 values the converters already hold), so no
 //   extra pass over X is needed; V t = hi + lo likewise with one power of two
 //   t from max|V|.  Three products hi*hi + hi*lo + lo*hi.
 // * BF16 X: X exact; V split into a BF16 pair; two products.
 // * E4M3 X: values widened exactly to BF16; V split as for BF16.
+// * V exact in its hi piece (the very sparse Omega: entries 0 and +-1): the
+//   products with V's lo piece, which is zero, are skipped and only the hi
+//   tiles are copied.  FP32 X is then split into three BF16 pieces
+//   x = x0 + x1 + x2 (exact: each piece keeps the top 8 bits of an exactly
+//   computed remainder) with no scale, three products, each exact.
 //
-// Accumulation.  The tensor core accumulates one k-step (64 columns) per
-// segment into TMEM region A (FP32 accumulation into TMEM behaves like
-// round-toward-zero on GB300); the epilogue unscales each row of the segment
-// by 1 / (s_r t) and folds it into a round-to-nearest FP32 running sum S in
-// TMEM region B, then writes S as the rows of Y after the last k-step.
+// Accumulation.  FP32 accumulation of tcgen05.mma into TMEM behaves like
+// round-toward-zero on GB300, so the tensor core accumulates short segments
+// into a TMEM accumulator A: one k-step (64 columns) for the FP16 pairs, whose
+// per-row scales change every k-step, SEG k-steps otherwise.  The epilogue unscales
+// each row of a segment by 1 / (s_r t) and folds it into a round-to-nearest
+// FP32 running sum S in TMEM, then writes S as the rows of Y after the last
+// k-step.  For k <= 128 the accumulator is double-buffered, so the tensor
+// core fills one buffer while the epilogue folds the other.
 //
-// Structure (one persistent CTA per SM, 13 warps, as the pass-F kernel):
-// warps 0-7 convert X into the 128B-swizzled K-major A layout (one k-step
-// ahead in registers) and warp 0 lane 0 streams the pre-split, pre-swizzled V
-// tile of the stage with one cp.async.bulk; warps 8-11 run the epilogue;
-// warp 12 allocates TMEM and issues tcgen05.mma.  All waits are bounded.
+// Structure (one persistent CTA per SM):
+//   warps 0..CW-1    converters (16 for FP32 X, else 8): 16-byte loads of the X
+//                    rows of a k-step, one k-step ahead in two register
+//                    buffers in ping-pong, converted into the 128-byte-swizzled
+//                    K-major A layout;
+//   warps CW..CW+3   epilogue: one per TMEM lane quarter;
+//   warp  CW+4       TMEM allocation and the thread that issues tcgen05.mma;
+//   warp  CW+5       producer: one cp.async.bulk of the pre-split,
+//                    pre-swizzled V tile of each stage.
+// All waits are bounded (2 s of %globaltimer): on expiry the kernel records
+// ST_TIMEOUT, stops issuing work, waits (bounded) for its copies and MMAs in
+// flight and frees TMEM.
 #include <type_traits>
 
 #include "common.cuh"
@@ -35,12 +51,8 @@ namespace lspca {
 namespace tcp {
 
 constexpr int BK = 64;
-constexpr int CONV_WARPS = 8;
-constexpr int CONV_THREADS = 256;
-constexpr int EPI_WARP0 = 8;
-constexpr int MMA_WARP = 12;
-constexpr int THREADS = 13 * 32;
 constexpr uint64_t kWaitNs = 2000000000ull;
+constexpr uint64_t kDrainNs = 100000000ull;
 
 enum XKind { XK_F32 = 0, XK_BF16 = 1, XK_E4M3 = 2 };
 
@@ -55,6 +67,8 @@ struct Params {
   int* status;
   const TcProjUnit* units;  // table mode (serving batches): tiles of many requests
   const int* nunits;        // device count of the table
+  float* xmax;              // nullable: max|X| out (NaN / Inf in X set ST_NONFINITE instead)
+  float* ymax;              // nullable: max|Y| out
 };
 
 // The tile being processed: from the single matrix, or from the table.
@@ -94,17 +108,39 @@ __device__ __forceinline__ TileInfo tile_info(const Params& p, int64_t t) {
   return ti;
 }
 
-template <int XK, int NT>
+template <int XK, int NT, bool EXACT_V>
 struct Cfg {
   static constexpr int NPAD = 64 * NT;
-  static constexpr int PA = (XK == XK_F32) ? 2 : 1;            // A parts
-  static constexpr uint32_t A_BYTES = 128 * BK * 2;             // 16 KB
-  static constexpr uint32_t B_BYTES = BK * NPAD * 2;            // one part
+  static constexpr bool F32 = XK == XK_F32;
+  // FP32 X against an exact V: X as three BF16 pieces x0 + x1 + x2 (exactly
+  // x), no scale; FP32 X otherwise: FP16 pair of x s_r with per-row scales
+  static constexpr bool SPL3 = F32 && EXACT_V;
+  static constexpr bool F16 = F32 && !EXACT_V;          // FP16 operands (else BF16)
+  static constexpr int PA = SPL3 ? 3 : (F32 ? 2 : 1);   // A parts
+  static constexpr int PB = EXACT_V ? 1 : 2;            // B parts used
+  static constexpr uint32_t A_BYTES = 128 * BK * 2;     // 16 KB
+  static constexpr uint32_t B_BYTES = BK * NPAD * 2;    // one part
   static constexpr uint32_t SBO_B = NT * 1024;
-  static constexpr uint32_t STAGE_BYTES = 2 * B_BYTES + PA * A_BYTES;
-  static constexpr int STAGES = (STAGE_BYTES * 3 <= 200 * 1024) ? 3 : 2;
-  static constexpr int RING = STAGES + 2;                      // per-row scale ring
+  static constexpr uint32_t STAGE_BYTES = PB * B_BYTES + PA * A_BYTES;  // [B parts | A parts]
+  static constexpr int STAGES = STAGE_BYTES * 4 <= 200 * 1024 ? 4 : STAGE_BYTES * 3 <= 200 * 1024 ? 3 : 2;
+  static constexpr int CW = F32 ? 16 : 8;               // converter warps
+  static constexpr int CT = CW * 32;
+  static constexpr int ES = F32 ? 4 : (XK == XK_BF16 ? 2 : 1);
+  static constexpr int EPV = 16 / ES;                   // elements per 16-byte load
+  static constexpr int VPR = BK / EPV;                  // 16-byte loads per row of a k-step
+  static constexpr int NV = 128 * VPR / CT;             // 16-byte loads per converter thread per k-step
+  static constexpr int EW_N = 4;                        // epilogue warps (one per TMEM lane quarter)
+  static constexpr int EPI0 = CW;                       // a multiple of 4 (TMEM lane quarters)
+  static constexpr int MMA_W = CW + EW_N;
+  static constexpr int PROD_W = CW + EW_N + 1;
+  static constexpr int THREADS = (CW + EW_N + 2) * 32;
+  static constexpr int NACC = NPAD <= 128 ? 2 : 1;      // segment accumulators in TMEM
+  static constexpr uint32_t S_COL = NACC * NPAD;        // running sum S after them
+  static constexpr int SEG = F16 ? 1 : 8;               // k-steps per accumulation segment
+  static constexpr int RING = STAGES + NACC + 1;        // per-row scale slots (FP32 X)
   static constexpr size_t SMEM = 1024 + STAGES * STAGE_BYTES + RING * 128 * 4 + 256 + 8192;
+  static_assert(S_COL + NPAD <= 512, "TMEM budget");
+  static_assert(NV * CT == 128 * VPR, "converter split");
 };
 
 __device__ __forceinline__ float pow2_scale_row(float amax) {
@@ -114,22 +150,50 @@ __device__ __forceinline__ float pow2_scale_row(float amax) {
   return ldexpf(1.f, 14 - e);
 }
 
-__device__ __forceinline__ uint2 pack_half4(float a, float b, float c, float d) {
-  __half2 x = __floats2half2_rn(a, b), y = __floats2half2_rn(c, d);
-  return make_uint2(*reinterpret_cast<uint32_t*>(&x), *reinterpret_cast<uint32_t*>(&y));
+// The power of two 2^(14 - E), E the exponent with amax < 2^E, from the bits
+// of amax (sign cleared): |x| 2^(14 - E) < 2^14 for |x| <= amax.  1 for amax 0
+// or non-finite; clamped to 2^127 for subnormal amax.
+__device__ __forceinline__ float pow2_scale_bits(uint32_t ab) {
+  if (ab == 0u || ab >= 0x7f800000u) return 1.f;
+  const int se = min(max(267 - (int)(ab >> 23), 1), 254);  // biased exponent of the scale
+  return __uint_as_float((uint32_t)se << 23);
 }
 
-template <int XK, int NT>
-__global__ void __launch_bounds__(THREADS, 1) project_kernel(Params p) {
-  using C = Cfg<XK, NT>;
+// (a, b) -> three BF16 pieces each, v = p0 + p1 + p2 exactly for normal FP32 v
+// (each step keeps the top 8 bits of an exactly computed remainder).
+__device__ __forceinline__ void split_b3(float a, float b, uint32_t& p0, uint32_t& p1, uint32_t& p2) {
+  const __nv_bfloat162 h0 = __floats2bfloat162_rn(a, b);
+  const float2 f0 = __bfloat1622float2(h0);
+  const float ra = a - f0.x, rb = b - f0.y;
+  const __nv_bfloat162 h1 = __floats2bfloat162_rn(ra, rb);
+  const float2 f1 = __bfloat1622float2(h1);
+  const __nv_bfloat162 h2 = __floats2bfloat162_rn(ra - f1.x, rb - f1.y);
+  p0 = *reinterpret_cast<const uint32_t*>(&h0);
+  p1 = *reinterpret_cast<const uint32_t*>(&h1);
+  p2 = *reinterpret_cast<const uint32_t*>(&h2);
+}
+
+// (a, b) -> FP16 pairs: hi = fp16(v), lo = fp16(v - hi), two of each packed.
+__device__ __forceinline__ void split_h2(float a, float b, uint32_t& hi, uint32_t& lo) {
+  const __half2 h = __floats2half2_rn(a, b);
+  const float2 f = __half22float2(h);
+  const __half2 l = __floats2half2_rn(a - f.x, b - f.y);
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+template <int XK, int NT, bool EXACT_V>
+__global__ void __launch_bounds__(Cfg<XK, NT, EXACT_V>::THREADS, 1) project_kernel(Params p) {
+  using C = Cfg<XK, NT, EXACT_V>;
+  constexpr int STAGES = C::STAGES;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  float* scales = reinterpret_cast<float*>(smem + C::STAGES * C::STAGE_BYTES);
+  float* scales = reinterpret_cast<float*>(smem + STAGES * C::STAGE_BYTES);
   uint64_t* full = reinterpret_cast<uint64_t*>(scales + C::RING * 128);
-  uint64_t* empty = full + C::STAGES;
-  uint64_t* accf = empty + C::STAGES;
-  uint64_t* acce = accf + 1;
-  uint64_t* drain = acce + 1;
+  uint64_t* empty = full + STAGES;
+  uint64_t* accf = empty + STAGES;  // [NACC]
+  uint64_t* acce = accf + C::NACC;  // [NACC]
+  uint64_t* drain = acce + C::NACC;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
 
@@ -137,17 +201,19 @@ __global__ void __launch_bounds__(THREADS, 1) project_kernel(Params p) {
   const int64_t tiles = p.units ? (int64_t)*p.nunits : (p.m + 127) / 128;
 
   if (tid == 0) {
-    for (int s = 0; s < C::STAGES; ++s) {
-      ptx::mbar_init(&full[s], CONV_WARPS + 1);
+    for (int s = 0; s < STAGES; ++s) {
+      ptx::mbar_init(&full[s], C::CW + 1);  // converter warps + the producer's expect-tx arrival
       ptx::mbar_init(&empty[s], 1);
     }
-    ptx::mbar_init(accf, 1);
-    ptx::mbar_init(acce, 4);
+    for (int b = 0; b < C::NACC; ++b) {
+      ptx::mbar_init(&accf[b], 1);
+      ptx::mbar_init(&acce[b], C::EW_N);
+    }
     ptx::mbar_init(drain, 1);
     *abort_flag = 0;
     ptx::fence_mbar_init();
   }
-  if (warp == MMA_WARP) ptx::tmem_alloc(tmem_slot, 512);
+  if (warp == C::MMA_W) ptx::tmem_alloc(tmem_slot, 512);
   ptx::tc_fence_before();
   __syncthreads();
   ptx::tc_fence_after();
@@ -158,82 +224,134 @@ __global__ void __launch_bounds__(THREADS, 1) project_kernel(Params p) {
     atomicExch(abort_flag, 1);
   };
   auto aborted = [&]() { return *(volatile int*)abort_flag != 0; };
+  auto ksteps = [&](const TileInfo& ti) { return (int)((ti.n + BK - 1) / BK); };
 
-  if (warp < CONV_WARPS) {
+  if (warp == C::PROD_W) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      int64_t step = 0;
+      bool ok = true;
+      for (int64_t tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+        const TileInfo ti = tile_info(p, tile);
+        const int nks = ksteps(ti);
+        for (int ks = 0; ks < nks; ++ks, ++step) {
+          const int s = (int)(step % STAGES);
+          const uint32_t ph = (uint32_t)((step / STAGES) & 1);
+          if (!ptx::mbar_wait(&empty[s], ph ^ 1u, kWaitNs)) {
+            fail();
+            ok = false;
+            break;
+          }
+          if (aborted()) {
+            ok = false;
+            break;
+          }
+          ptx::mbar_arrive_expect_tx(&full[s], C::PB * C::B_BYTES);
+          ptx::bulk_g2s(sbase + s * C::STAGE_BYTES, ti.vt + (size_t)ks * 2 * C::B_BYTES, C::PB * C::B_BYTES,
+                        &full[s]);
+        }
+      }
+      // bounded wait for the copies of the last stages (complete on the
+      // normal path, possibly in flight after an abort)
+      for (int64_t w = step - 1; w >= 0 && w >= step - STAGES; --w)
+        ptx::mbar_wait(&full[w % STAGES], (uint32_t)((w / STAGES) & 1), kDrainNs);
+    }
+    __syncwarp();
+  } else if (warp < C::CW) {
     // ------------------------------------------------------------ converters
-    constexpr int NV = (XK == XK_F32) ? 8 : (XK == XK_BF16 ? 4 : 2);  // 16-byte vectors per thread per k-step
-    auto load = [&](const TileInfo& ti, int ks, uint4 (&dst)[NV]) {
+    // thread tid, load q covers row (tid + CT q) / VPR and the EPV elements at
+    // column ((tid + CT q) % VPR) EPV of the k-step
+    auto load = [&](const TileInfo& ti, int ks, uint4 (&dst)[C::NV]) {
+      const int64_t c0 = (int64_t)ks * BK;
+      const char* base = (const char*)ti.X + (ti.row0 * ti.ldx + c0) * C::ES;
+      const int64_t row_bytes = ti.ldx * C::ES;
+      const bool full_tile = ti.row0 + 128 <= ti.m && c0 + BK <= ti.n;
 #pragma unroll
-      for (int q = 0; q < NV; ++q) {
-        const int f = tid + CONV_THREADS * q;
-        int row, col;
-        if (XK == XK_F32) { row = f / 16; col = (f % 16) * 4; }
-        else if (XK == XK_BF16) { row = f / 8; col = (f % 8) * 8; }
-        else { row = f / 4; col = (f % 4) * 16; }
-        const int64_t gr = ti.row0 + row, gc = (int64_t)ks * BK + col;
-        if (gr < ti.m && gc < ti.n) {
-          const char* src = (const char*)ti.X + (gr * ti.ldx + gc) * (XK == XK_F32 ? 4 : (XK == XK_BF16 ? 2 : 1));
+      for (int q = 0; q < C::NV; ++q) {
+        const int f = tid + C::CT * q;
+        const int row = f / C::VPR, col = (f % C::VPR) * C::EPV;
+        if (full_tile || (ti.row0 + row < ti.m && c0 + col < ti.n)) {
           asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
                        : "=r"(dst[q].x), "=r"(dst[q].y), "=r"(dst[q].z), "=r"(dst[q].w)
-                       : "l"(src));
+                       : "l"(base + row * row_bytes + col * C::ES));
         } else {
           dst[q] = make_uint4(0u, 0u, 0u, 0u);
         }
       }
     };
-    auto store = [&](const uint4 (&r)[NV], uint32_t st, int slot, int ks, int64_t ncols) {
-      const uint32_t a_hi = st + 2 * C::B_BYTES, a_lo = a_hi + C::A_BYTES;
+    uint32_t xb = 0u;  // max over the |x| seen, as FP32 bits (>= 0x7f800000: NaN / Inf)
+    auto store = [&](const uint4 (&r)[C::NV], uint32_t st, int slot, int ks, int64_t ncols) {
+      const uint32_t a_hi = st + C::PB * C::B_BYTES, a_lo = a_hi + C::A_BYTES;
+      const int64_t c0 = (int64_t)ks * BK;
+      const bool tail = c0 + BK > ncols;  // the k-step runs past the last column
 #pragma unroll
-      for (int q = 0; q < NV; ++q) {
-        const int f = tid + CONV_THREADS * q;
-        if (XK == XK_F32) {
-          const int row = f / 16, col = (f % 16) * 4;
+      for (int q = 0; q < C::NV; ++q) {
+        const int f = tid + C::CT * q;
+        const int row = f / C::VPR, col = (f % C::VPR) * C::EPV;
+        if constexpr (C::SPL3) {
           float v[4] = {__uint_as_float(r[q].x), __uint_as_float(r[q].y), __uint_as_float(r[q].z),
                         __uint_as_float(r[q].w)};
-          // zero the tail of a row that ends inside this vector
-          const int64_t gc = (int64_t)ks * BK + col;
+          if (tail) {
 #pragma unroll
-          for (int u = 0; u < 4; ++u)
-            if (gc + u >= ncols) v[u] = 0.f;
-          float mx = fmaxf(fmaxf(fabsf(v[0]), fabsf(v[1])), fmaxf(fabsf(v[2]), fabsf(v[3])));
-#pragma unroll
-          for (int o = 1; o < 16; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-          const float s = pow2_scale_row(mx);
-          if ((f % 16) == 0) scales[slot * 128 + row] = s;
-          float hi[4], lo[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const float xs = v[u] * s;
-            hi[u] = __half2float(__float2half_rn(xs));
-            lo[u] = xs - hi[u];
+            for (int u = 0; u < 4; ++u)
+              if (c0 + col + u >= ncols) v[u] = 0.f;
           }
+          xb = max(xb, max(max(__float_as_uint(v[0]) & 0x7fffffffu, __float_as_uint(v[1]) & 0x7fffffffu),
+                           max(__float_as_uint(v[2]) & 0x7fffffffu, __float_as_uint(v[3]) & 0x7fffffffu)));
+          uint32_t p0[2], p1[2], p2[2];
+          split_b3(v[0], v[1], p0[0], p1[0], p2[0]);
+          split_b3(v[2], v[3], p0[1], p1[1], p2[1]);
           const uint32_t off = ptx::k_sw128_offset(row, col);
-          const uint2 h = pack_half4(hi[0], hi[1], hi[2], hi[3]);
-          const uint2 l = pack_half4(lo[0], lo[1], lo[2], lo[3]);
-          asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a_hi + off), "r"(h.x), "r"(h.y) : "memory");
-          asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a_lo + off), "r"(l.x), "r"(l.y) : "memory");
-        } else if (XK == XK_BF16) {
-          const int row = f / 8, col = (f % 8) * 8;
+          asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a_hi + off), "r"(p0[0]), "r"(p0[1]) : "memory");
+          asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a_lo + off), "r"(p1[0]), "r"(p1[1]) : "memory");
+          asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a_lo + C::A_BYTES + off), "r"(p2[0]), "r"(p2[1])
+                       : "memory");
+        } else if constexpr (XK == XK_F32) {
+          float v[4] = {__uint_as_float(r[q].x), __uint_as_float(r[q].y), __uint_as_float(r[q].z),
+                        __uint_as_float(r[q].w)};
+          if (tail) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              if (c0 + col + u >= ncols) v[u] = 0.f;
+          }
+          uint32_t mb = max(max(__float_as_uint(v[0]) & 0x7fffffffu, __float_as_uint(v[1]) & 0x7fffffffu),
+                            max(__float_as_uint(v[2]) & 0x7fffffffu, __float_as_uint(v[3]) & 0x7fffffffu));
+          xb = max(xb, mb);
+          // the row's 16 loads sit in one half-warp: max over that half
+          static_assert(C::VPR == 16, "one row per half-warp");
+          mb = __reduce_max_sync(lane < 16 ? 0x0000ffffu : 0xffff0000u, mb);
+          const float sc = pow2_scale_bits(mb);
+          if ((f % C::VPR) == 0) scales[slot * 128 + row] = sc;  // FP16 path only
+          uint32_t h0, l0, h1, l1;
+          split_h2(v[0] * sc, v[1] * sc, h0, l0);
+          split_h2(v[2] * sc, v[3] * sc, h1, l1);
+          const uint32_t off = ptx::k_sw128_offset(row, col);
+          asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a_hi + off), "r"(h0), "r"(h1) : "memory");
+          asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a_lo + off), "r"(l0), "r"(l1) : "memory");
+        } else if constexpr (XK == XK_BF16) {
           uint4 v = r[q];
-          const int64_t gc = (int64_t)ks * BK + col;
-          if (gc + 8 > ncols) {
+          if (tail && c0 + col + 8 > ncols) {
             uint16_t* e = reinterpret_cast<uint16_t*>(&v);
 #pragma unroll
             for (int u = 0; u < 8; ++u)
-              if (gc + u >= ncols) e[u] = 0;
+              if (c0 + col + u >= ncols) e[u] = 0;
+          }
+          {
+            const uint32_t m2 = __vmaxu2(__vmaxu2(v.x & 0x7fff7fffu, v.y & 0x7fff7fffu),
+                                         __vmaxu2(v.z & 0x7fff7fffu, v.w & 0x7fff7fffu));
+            xb = max(xb, max(m2 >> 16, m2 & 0xffffu) << 16);  // BF16 bits widen to FP32 bits
           }
           asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a_hi + ptx::k_sw128_offset(row, col)),
                        "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
                        : "memory");
         } else {
-          const int row = f / 4, col = (f % 4) * 16;
-          const int64_t gc = (int64_t)ks * BK + col;
           const __nv_fp8_e4m3* e8 = reinterpret_cast<const __nv_fp8_e4m3*>(&r[q]);
           uint32_t w[8];
 #pragma unroll
           for (int u = 0; u < 8; ++u) {
-            float a = (gc + 2 * u < ncols) ? float(e8[2 * u]) : 0.f;
-            float b = (gc + 2 * u + 1 < ncols) ? float(e8[2 * u + 1]) : 0.f;
+            const float a = (!tail || c0 + col + 2 * u < ncols) ? float(e8[2 * u]) : 0.f;
+            const float b = (!tail || c0 + col + 2 * u + 1 < ncols) ? float(e8[2 * u + 1]) : 0.f;
+            xb = max(xb, max(__float_as_uint(a) & 0x7fffffffu, __float_as_uint(b) & 0x7fffffffu));
             __nv_bfloat162 h2 = __floats2bfloat162_rn(a, b);
             w[u] = *reinterpret_cast<uint32_t*>(&h2);
           }
@@ -246,74 +364,84 @@ __global__ void __launch_bounds__(THREADS, 1) project_kernel(Params p) {
         }
       }
     };
-    // Two register buffers in ping-pong: the loads of step t + 1 are issued
-    // before step t is converted and consumed one full iteration later (a
-    // register copy from a prefetch buffer would wait for them at once).
-    uint4 ra[NV], rb[NV];
+    // Two register buffers in ping-pong: the loads of k-step t + 1 are issued
+    // before k-step t is converted and consumed one full iteration later (a
+    // register copy out of a prefetch buffer would wait for them at once).
+    // The tile's fields are re-read from the parameters (or the table) when
+    // needed rather than held in registers across iterations.
     int64_t tile = blockIdx.x;
-    int ks = 0;
+    int ks = 0, nks = 0;
     int64_t step = 0;
-    TileInfo ti, tn;
-    auto body = [&](const uint4 (&cur)[NV], uint4 (&nxt)[NV]) -> bool {
-      const int nks = (int)((ti.n + BK - 1) / BK);
+    auto body = [&](const uint4 (&cur)[C::NV], uint4 (&nxt)[C::NV]) -> bool {
       int64_t ntile = tile;
       int nks_next = ks + 1;
+      int nks_n = nks;
       if (nks_next >= nks) {
         nks_next = 0;
         ntile += gridDim.x;
       }
       const bool more = ntile < tiles;
       if (more) {
-        if (ntile != tile) tn = tile_info(p, ntile);
-        load(ntile != tile ? tn : ti, nks_next, nxt);
+        const TileInfo tn = tile_info(p, ntile);
+        if (ntile != tile) nks_n = ksteps(tn);
+        load(tn, nks_next, nxt);
       }
-      const int s = (int)(step % C::STAGES);
-      const uint32_t ph = (uint32_t)((step / C::STAGES) & 1);
+      const int s = (int)(step % STAGES);
+      const uint32_t ph = (uint32_t)((step / STAGES) & 1);
       if (!ptx::mbar_wait(&empty[s], ph ^ 1u, kWaitNs)) {
         fail();
         return false;
       }
       if (aborted()) return false;
-      const uint32_t st = sbase + s * C::STAGE_BYTES;
-      if (warp == 0 && lane == 0) {
-        ptx::mbar_arrive_expect_tx(&full[s], 2 * C::B_BYTES);
-        ptx::bulk_g2s(st, ti.vt + (size_t)ks * 2 * C::B_BYTES, 2 * C::B_BYTES, &full[s]);
-      }
-      store(cur, st, (int)(step % C::RING), ks, ti.n);
+      store(cur, sbase + s * C::STAGE_BYTES, (int)(step % C::RING), ks, tile_info(p, tile).n);
       ptx::fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) ptx::mbar_arrive(&full[s]);
       ++step;
       if (!more) return false;
-      if (ntile != tile) ti = tn;
       tile = ntile;
       ks = nks_next;
+      nks = nks_n;
       return true;
     };
+    uint4 ra[C::NV], rb[C::NV];
     if (tile < tiles) {
-      ti = tile_info(p, tile);
-      tn = ti;
-      load(ti, ks, ra);
+      const TileInfo t0 = tile_info(p, tile);
+      nks = ksteps(t0);
+      load(t0, ks, ra);
       while (body(ra, rb) && body(rb, ra)) {
       }
     }
-  } else if (warp == MMA_WARP) {
+    if (p.xmax) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) xb = max(xb, __shfl_xor_sync(0xffffffffu, xb, o));
+      if (lane == 0) {
+        if (xb >= 0x7f800000u) atomicOr(p.status, ST_NONFINITE);
+        else atomic_max_nonneg(p.xmax, __uint_as_float(xb));
+      }
+    }
+  } else if (warp == C::MMA_W) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      constexpr uint32_t idesc = ptx::idesc_f16(XK == XK_F32 ? 0 : 1, 128, C::NPAD, 0, 1);
-      int64_t step = 0;
+      constexpr uint32_t idesc = ptx::idesc_f16(C::F16 ? 0 : 1, 128, C::NPAD, 0, 1);
+      int64_t step = 0, seg = 0;
       bool ok = true;
       for (int64_t tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
-        const int nks = (int)((tile_info(p, tile).n + BK - 1) / BK);
-        for (int ks = 0; ks < nks; ++ks, ++step) {
-          if (!ptx::mbar_wait(acce, (uint32_t)((step & 1) ^ 1), kWaitNs)) {
-            fail();
-            ok = false;
-            break;
+        const int nks = ksteps(tile_info(p, tile));
+        for (int ks = 0; ks < nks && ok; ++ks, ++step) {
+          const bool seg_start = (ks % C::SEG) == 0;
+          const int ab = (int)(seg % C::NACC);
+          if (seg_start) {
+            // wait until the epilogue has folded the segment that last used buffer ab
+            if (!ptx::mbar_wait(&acce[ab], (uint32_t)(((seg / C::NACC) & 1) ^ 1), kWaitNs)) {
+              fail();
+              ok = false;
+              break;
+            }
+            ptx::tc_fence_after();
           }
-          ptx::tc_fence_after();
-          const int s = (int)(step % C::STAGES);
-          const uint32_t ph = (uint32_t)((step / C::STAGES) & 1);
+          const int s = (int)(step % STAGES);
+          const uint32_t ph = (uint32_t)((step / STAGES) & 1);
           if (!ptx::mbar_wait(&full[s], ph, kWaitNs) || aborted()) {
             if (!aborted()) fail();
             ok = false;
@@ -321,21 +449,31 @@ __global__ void __launch_bounds__(THREADS, 1) project_kernel(Params p) {
           }
           ptx::tc_fence_after();
           const uint32_t st = sbase + s * C::STAGE_BYTES;
-          const uint32_t b_hi = st, b_lo = st + C::B_BYTES, a_hi = st + 2 * C::B_BYTES, a_lo = a_hi + C::A_BYTES;
+          const uint32_t b_hi = st, b_lo = st + C::B_BYTES, a_hi = st + C::PB * C::B_BYTES, a_lo = a_hi + C::A_BYTES;
+          const uint32_t d = tmem + (uint32_t)(ab * C::NPAD);
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk) {
             const uint64_t adh = ptx::desc_sw128(a_hi + kk * 32, 16, 1024);
             const uint64_t bdh = ptx::desc_sw128(b_hi + kk * 2 * C::SBO_B, 1024, C::SBO_B);
-            const uint64_t bdl = ptx::desc_sw128(b_lo + kk * 2 * C::SBO_B, 1024, C::SBO_B);
-            ptx::mma_f16(tmem, adh, bdh, idesc, kk > 0 ? 1u : 0u);
-            ptx::mma_f16(tmem, adh, bdl, idesc, 1u);
-            if (XK == XK_F32) {
+            ptx::mma_f16(d, adh, bdh, idesc, (seg_start && kk == 0) ? 0u : 1u);
+            if (!EXACT_V) {
+              const uint64_t bdl = ptx::desc_sw128(b_lo + kk * 2 * C::SBO_B, 1024, C::SBO_B);
+              ptx::mma_f16(d, adh, bdl, idesc, 1u);
+            }
+            if (C::PA >= 2) {
               const uint64_t adl = ptx::desc_sw128(a_lo + kk * 32, 16, 1024);
-              ptx::mma_f16(tmem, adl, bdh, idesc, 1u);
+              ptx::mma_f16(d, adl, bdh, idesc, 1u);
+            }
+            if (C::PA == 3) {
+              const uint64_t ad2 = ptx::desc_sw128(a_lo + C::A_BYTES + kk * 32, 16, 1024);
+              ptx::mma_f16(d, ad2, bdh, idesc, 1u);
             }
           }
           ptx::mma_commit(&empty[s]);
-          ptx::mma_commit(accf);
+          if ((ks % C::SEG) == C::SEG - 1 || ks == nks - 1) {
+            ptx::mma_commit(&accf[ab]);
+            ++seg;
+          }
         }
       }
       ptx::mma_commit(drain);
@@ -344,63 +482,86 @@ __global__ void __launch_bounds__(THREADS, 1) project_kernel(Params p) {
     __syncwarp();
   } else {
     // ------------------------------------------------------------ epilogue
-    const int e = warp - EPI_WARP0;
+    const int e = (warp - C::EPI0) & 3;       // TMEM lane quarter
+    const int ehalf = (warp - C::EPI0) >> 2;  // which share of the columns this warp folds
     const uint32_t lane_base = (uint32_t)(32 * e) << 16;
-    int64_t step = 0;
+    constexpr int EW = 16;  // TMEM columns per fold chunk
+    uint32_t yb = 0u;       // max|Y| written, as FP32 bits
+    int64_t step = 0, seg = 0;
     bool ok = true;
     for (int64_t tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
       const TileInfo ti = tile_info(p, tile);
-      const float inv_t = (XK == XK_F32) ? 1.f / *ti.vscale : 1.f;
-      const int nks = (int)((ti.n + BK - 1) / BK);
+      const float inv_t = C::F16 ? 1.f / *ti.vscale : 1.f;
+      const int nks = ksteps(ti);
+      const int nseg = (nks + C::SEG - 1) / C::SEG;
       const int row = 32 * e + lane;
       const int64_t grow = ti.row0 + row;
-      for (int ks = 0; ks < nks; ++ks, ++step) {
-        if (!ptx::mbar_wait(accf, (uint32_t)(step & 1), kWaitNs) || aborted()) {
+      for (int g = 0; g < nseg; ++g, ++seg) {
+        const int ab = (int)(seg % C::NACC);
+        if (!ptx::mbar_wait(&accf[ab], (uint32_t)((seg / C::NACC) & 1), kWaitNs) || aborted()) {
           if (!aborted()) fail();
           ok = false;
           break;
         }
         ptx::tc_fence_after();
-        const float us = (XK == XK_F32) ? inv_t / scales[(int)(step % C::RING) * 128 + row] : 1.f;
-        const bool first = ks == 0, last = ks == nks - 1;
+        // FP32 X: one k-step per segment, unscaled by its per-row scale
+        const float us = C::F16 ? inv_t / scales[(int)(step % C::RING) * 128 + row] : 1.f;
+        const bool first = g == 0, last = g == nseg - 1;
+        const uint32_t abase = tmem + lane_base + (uint32_t)(ab * C::NPAD);
+        const uint32_t sbase_t = tmem + lane_base + C::S_COL;
 #pragma unroll 1
-        for (int c0 = 0; c0 < C::NPAD; c0 += 32) {
-          uint32_t a[32], sacc[32];
-          ptx::tmem_ld32(tmem + lane_base + (uint32_t)c0, a);
+        constexpr int WCOLS = C::NPAD * 4 / C::EW_N;  // columns folded by one epilogue warp
+        for (int cc = ehalf * WCOLS; cc < (ehalf + 1) * WCOLS; cc += EW) {
+          uint32_t a[EW], r[EW];
+          // the previous chunk's store of S has to land before r is reloaded
+          ptx::tmem_wait_st(r);
+          ptx::tmem_ld16_nowait(abase + (uint32_t)cc, a);
+          if (!first) ptx::tmem_ld16_nowait(sbase_t + (uint32_t)cc, r);
+          ptx::tmem_wait_ld(a);
           if (first) {
 #pragma unroll
-            for (int q = 0; q < 32; ++q) sacc[q] = __float_as_uint(__uint_as_float(a[q]) * us);
+            for (int q = 0; q < EW; ++q) r[q] = __float_as_uint(__uint_as_float(a[q]) * us);
           } else {
-            ptx::tmem_ld32(tmem + lane_base + (uint32_t)(C::NPAD + c0), sacc);
+            ptx::tmem_regs_ready(r);
 #pragma unroll
-            for (int q = 0; q < 32; ++q)
-              sacc[q] = __float_as_uint(fmaf(__uint_as_float(a[q]), us, __uint_as_float(sacc[q])));
+            for (int q = 0; q < EW; ++q)
+              r[q] = __float_as_uint(fmaf(__uint_as_float(a[q]), us, __uint_as_float(r[q])));
           }
           if (!last) {
-            ptx::tmem_st32(tmem + lane_base + (uint32_t)(C::NPAD + c0), sacc);
+            ptx::tmem_st16_nowait(sbase_t + (uint32_t)cc, r);
           } else if (grow < ti.m) {
-            float* dst = ti.Y + grow * ti.k + c0;
-            if (c0 + 32 <= ti.k && (ti.k % 4) == 0) {
+            float* dst = ti.Y + grow * ti.k + cc;
 #pragma unroll
-              for (int q = 0; q < 32; q += 4)
-                *reinterpret_cast<float4*>(dst + q) = make_float4(__uint_as_float(sacc[q]), __uint_as_float(sacc[q + 1]),
-                                                                  __uint_as_float(sacc[q + 2]),
-                                                                  __uint_as_float(sacc[q + 3]));
+            for (int q = 0; q < EW; ++q)
+              if (cc + q < ti.k) yb = max(yb, r[q] & 0x7fffffffu);
+            if (cc + EW <= ti.k && (ti.k % 4) == 0) {
+#pragma unroll
+              for (int q = 0; q < EW; q += 4)
+                *reinterpret_cast<float4*>(dst + q) = make_float4(__uint_as_float(r[q]), __uint_as_float(r[q + 1]),
+                                                                  __uint_as_float(r[q + 2]),
+                                                                  __uint_as_float(r[q + 3]));
             } else {
 #pragma unroll
-              for (int q = 0; q < 32; ++q)
-                if (c0 + q < ti.k) dst[q] = __uint_as_float(sacc[q]);
+              for (int q = 0; q < EW; ++q)
+                if (cc + q < ti.k) dst[q] = __uint_as_float(r[q]);
             }
           }
         }
         ptx::tc_fence_before();
         __syncwarp();
-        if (lane == 0) ptx::mbar_arrive(acce);
+        if (lane == 0) ptx::mbar_arrive(&acce[ab]);
+        step += (g == nseg - 1) ? nks - g * C::SEG : C::SEG;
       }
+    }
+    ptx::tmem_wait_st();
+    if (p.ymax) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) yb = max(yb, __shfl_xor_sync(0xffffffffu, yb, o));
+      if (lane == 0 && yb < 0x7f800000u) atomic_max_nonneg(p.ymax, __uint_as_float(yb));
     }
   }
   __syncthreads();
-  if (warp == MMA_WARP) {
+  if (warp == C::MMA_W) {
     ptx::tc_fence_after();
     ptx::tmem_dealloc(tmem, 512);
   }
@@ -446,23 +607,23 @@ __global__ void tile_v_kernel(const float* __restrict__ V, int64_t n, int k, int
   }
 }
 
-template <int XK, int NT>
+template <int XK, int NT, bool EXACT_V>
 static void launch_project(Launcher& L, const Params& p, int max_tiles) {
-  using C = Cfg<XK, NT>;
-  cudaFuncSetAttribute(project_kernel<XK, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+  using C = Cfg<XK, NT, EXACT_V>;
+  cudaFuncSetAttribute(project_kernel<XK, NT, EXACT_V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
   const int64_t tiles = p.units ? max_tiles : (p.m + 127) / 128;
   const int grid = (int)(tiles < L.num_sms ? (tiles > 0 ? tiles : 1) : L.num_sms);
-  project_kernel<XK, NT><<<grid, THREADS, C::SMEM, L.stream>>>(p);
+  project_kernel<XK, NT, EXACT_V><<<grid, C::THREADS, C::SMEM, L.stream>>>(p);
   L.count(1);
 }
 
-template <int XK>
+template <int XK, bool EXACT_V = false>
 static void launch_project_nt(Launcher& L, const Params& p, int nt, int max_tiles) {
   switch (nt) {
-    case 1: launch_project<XK, 1>(L, p, max_tiles); break;
-    case 2: launch_project<XK, 2>(L, p, max_tiles); break;
-    case 3: launch_project<XK, 3>(L, p, max_tiles); break;
-    default: launch_project<XK, 4>(L, p, max_tiles); break;
+    case 1: launch_project<XK, 1, EXACT_V>(L, p, max_tiles); break;
+    case 2: launch_project<XK, 2, EXACT_V>(L, p, max_tiles); break;
+    case 3: launch_project<XK, 3, EXACT_V>(L, p, max_tiles); break;
+    default: launch_project<XK, 4, EXACT_V>(L, p, max_tiles); break;
   }
 }
 
@@ -484,11 +645,25 @@ void plan_tc_project(char* base, TcProjectWs& w, int xt, int64_t n, int k) {
   (void)xt;
 }
 
+namespace tcp {
+static void launch_xt(Launcher& L, const Params& p, int xt, int nt, int max_tiles, bool exact_v) {
+  if (exact_v) {
+    if (xt == LSPCA_F32) launch_project_nt<XK_F32, true>(L, p, nt, max_tiles);
+    else if (xt == LSPCA_BF16) launch_project_nt<XK_BF16, true>(L, p, nt, max_tiles);
+    else launch_project_nt<XK_E4M3, true>(L, p, nt, max_tiles);
+  } else {
+    if (xt == LSPCA_F32) launch_project_nt<XK_F32>(L, p, nt, max_tiles);
+    else if (xt == LSPCA_BF16) launch_project_nt<XK_BF16>(L, p, nt, max_tiles);
+    else launch_project_nt<XK_E4M3>(L, p, nt, max_tiles);
+  }
+}
+}  // namespace tcp
+
 void tc_project(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_t ldx, const float* V, int k,
-                TcProjectWs& w, float* Y, int* status) {
+                TcProjectWs& w, float* Y, int* status, bool exact_v, float* xmax, float* ymax) {
   const int npad = (k + 63) / 64 * 64;
   float* scal = (float*)w.vlo;
-  const bool f16 = xt == LSPCA_F32;
+  const bool f16 = xt == LSPCA_F32 && !exact_v;  // FP32 X against an exact V takes BF16 tiles
   cudaMemsetAsync(scal, 0, 8, L.stream);
   if (f16) launch_scan_x(L, V, LSPCA_F32, n, k, k, scal, status);
   {
@@ -511,14 +686,14 @@ void tc_project(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_
   p.status = status;
   p.units = nullptr;
   p.nunits = nullptr;
-  const int nt = npad / 64;
-  if (xt == LSPCA_F32) tcp::launch_project_nt<tcp::XK_F32>(L, p, nt, 0);
-  else if (xt == LSPCA_BF16) tcp::launch_project_nt<tcp::XK_BF16>(L, p, nt, 0);
-  else tcp::launch_project_nt<tcp::XK_E4M3>(L, p, nt, 0);
+  p.xmax = xmax;
+  p.ymax = ymax;
+  tcp::launch_xt(L, p, xt, npad / 64, 0, exact_v);
 }
 
 void tc_project_pretiled(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_t ldx, const void* tiles,
-                         const float* vscale, int k, float* Y, int* status) {
+                         const float* vscale, int k, float* Y, int* status, bool exact_v, float* xmax,
+                         float* ymax) {
   tcp::Params p{};
   p.X = X;
   p.ldx = ldx;
@@ -531,10 +706,9 @@ void tc_project_pretiled(Launcher& L, const void* X, int xt, int64_t m, int64_t 
   p.status = status;
   p.units = nullptr;
   p.nunits = nullptr;
-  const int nt = (k + 63) / 64;
-  if (xt == LSPCA_F32) tcp::launch_project_nt<tcp::XK_F32>(L, p, nt, 0);
-  else if (xt == LSPCA_BF16) tcp::launch_project_nt<tcp::XK_BF16>(L, p, nt, 0);
-  else tcp::launch_project_nt<tcp::XK_E4M3>(L, p, nt, 0);
+  p.xmax = xmax;
+  p.ymax = ymax;
+  tcp::launch_xt(L, p, xt, (k + 63) / 64, 0, exact_v);
 }
 
 size_t tc_tile_v_bytes(int64_t n, int k) {
@@ -561,10 +735,7 @@ void tc_project_batch(Launcher& L, int xt, int k, const TcProjUnit* d_units, con
   p.units = d_units;
   p.nunits = d_count;
   p.status = status;
-  const int nt = (k + 63) / 64;
-  if (xt == LSPCA_F32) tcp::launch_project_nt<tcp::XK_F32>(L, p, nt, max_tiles);
-  else if (xt == LSPCA_BF16) tcp::launch_project_nt<tcp::XK_BF16>(L, p, nt, max_tiles);
-  else tcp::launch_project_nt<tcp::XK_E4M3>(L, p, nt, max_tiles);
+  tcp::launch_xt(L, p, xt, (k + 63) / 64, max_tiles, false);
 }
 
 }  // namespace lspca
