@@ -237,17 +237,76 @@ __global__ void finalize_v_kernel(const double* __restrict__ Vd, int64_t n, int 
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) V[i * k + c] = (VT)(sg * Vd[i * k + c]);
 }
 
+// FP64 GEMM for the k x k step: C[z] = op(A) op(B) over the K range of split z,
+// op(A)(r, q) = at ? A[q lda + r] : A[r lda + q], op(B)(q, c) = bt ? B[c ldb + q]
+// : B[q ldb + c].  One CTA per TM x TN output tile (TM TN threads, one output
+// each, four interleaved partial sums); K in slabs of KS staged whole in
+// shared memory.  GB300 issues few FP64 FMAs per SM per clock, so the tiles
+// are small enough to spread even a 128 x 128 product over all SMs.  sym:
+// C is symmetric (op(B) = op(A)^T); only tiles with blockIdx.x <= blockIdx.y
+// run and each also writes its mirror.
+template <int TM, int TN, int KS>
+__global__ void __launch_bounds__(TM* TN) dgemm_tile_kernel(int64_t M, int64_t N, int64_t K, const double* __restrict__ A,
+                                                           int64_t lda, int at, const double* __restrict__ B,
+                                                           int64_t ldb, int bt, double* __restrict__ C, int64_t ldc,
+                                                           int64_t c_split_stride, int64_t kchunk, int sym) {
+  if (sym && blockIdx.x > blockIdx.y) return;
+  __shared__ double As[TM][KS + 1];
+  __shared__ double Bs[TN][KS + 1];
+  const int tid = threadIdx.x;
+  const int r = tid / TN, c = tid % TN;
+  const int64_t i0 = (int64_t)blockIdx.x * TM, j0 = (int64_t)blockIdx.y * TN;
+  const int64_t kb = (int64_t)blockIdx.z * kchunk;
+  const int64_t ke = min(K, kb + kchunk);
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int64_t k0 = kb; k0 < ke; k0 += KS) {
+    for (int e = tid; e < TM * KS; e += TM * TN) {
+      int rr, q;
+      if (at) { q = e / TM; rr = e % TM; } else { rr = e / KS; q = e % KS; }
+      const int64_t gi = i0 + rr, gq = k0 + q;
+      As[rr][q] = (gi < M && gq < ke) ? (at ? A[gq * lda + gi] : A[gi * lda + gq]) : 0.0;
+    }
+    for (int e = tid; e < TN * KS; e += TM * TN) {
+      int cc, q;
+      if (bt) { cc = e / KS; q = e % KS; } else { q = e / TN; cc = e % TN; }
+      const int64_t gj = j0 + cc, gq = k0 + q;
+      Bs[cc][q] = (gj < N && gq < ke) ? (bt ? B[gj * ldb + gq] : B[gq * ldb + gj]) : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int q = 0; q < KS; q += 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[u] = fma(As[r][q + u], Bs[c][q + u], acc[u]);
+    }
+    __syncthreads();
+  }
+  const double v = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+  double* Cs = C + (int64_t)blockIdx.z * c_split_stride;
+  const int64_t gi = i0 + r, gj = j0 + c;
+  if (gi < M && gj < N) {
+    Cs[gi * ldc + gj] = v;
+    if (sym && blockIdx.x != blockIdx.y) Cs[gj * ldc + gi] = v;
+  }
+}
+
 static void dgemm(Launcher& L, int64_t M, int64_t N, int64_t K, const double* A, int64_t lda, bool at, const double* B,
                   int64_t ldb, bool bt, double* C, int64_t ldc) {
-  launch_gemm_simt(L, M, N, K, A, LSPCA_F64, lda, at, B, LSPCA_F64, ldb, bt, C, true, ldc, 0, 1, true, true);
+  dim3 grid((unsigned)((M + 7) / 8), (unsigned)((N + 7) / 8), 1);
+  dgemm_tile_kernel<8, 8, 64><<<grid, 64, 0, L.stream>>>(M, N, K, A, lda, at ? 1 : 0, B, ldb, bt ? 1 : 0, C, ldc, 0,
+                                                          K, 0);
+  L.count(1);
 }
 
 void launch_decompose(Launcher& L, SmallWs& w, const double* F, int k, int64_t n, int64_t m, bool v_f64, void* V,
                       double* sigma, int32_t* rank, int* status) {
   const int64_t kk = (int64_t)k * k;
-  // H = F F^T, split over n, reduced in fixed order.
-  launch_gemm_simt(L, k, k, n, F, LSPCA_F64, n, false, F, LSPCA_F64, n, true, w.Hpart, true, k, kk, w.h_splits, true,
-                   true);
+  // H = F F^T in FP64, split over n, upper tiles mirrored, reduced in fixed order.
+  {
+    const int64_t kchunk = ((n + w.h_splits - 1) / w.h_splits + 63) / 64 * 64;
+    dim3 grid((unsigned)((k + 15) / 16), (unsigned)((k + 15) / 16), (unsigned)w.h_splits);
+    dgemm_tile_kernel<16, 16, 64><<<grid, 256, 0, L.stream>>>(k, k, n, F, n, 0, F, n, 1, w.Hpart, k, kk, kchunk, 1);
+    L.count(1);
+  }
   launch_reduce_splits(L, w.Hpart, w.h_splits, kk, kk, w.H);
   // FP32 seed (tridiagonalisation + bisection + inverse iteration)
   launch_eig_seed(L, w.H, k, w.h32, w.w32, w.q32, w.Xa, w.lam, w.scal, w.sweeps);
@@ -274,8 +333,14 @@ void launch_decompose(Launcher& L, SmallWs& w, const double* F, int k, int64_t n
   ws_tinv_kernel<<<k, 128, 0, L.stream>>>(X, w.S, w.scal, k, w.T, w.E);
   L.count(2);
   dgemm(L, k, k, k, w.T, k, false, w.E, k, false, w.Rm, k);  // Ws Tinv
-  // V = F^T (Ws Tinv)  (n x k)
-  launch_gemm_simt(L, n, k, k, F, LSPCA_F64, n, true, w.Rm, LSPCA_F64, k, false, w.Vd, true, k, 0, 1, true, true);
+  // V = F^T (Ws Tinv)  (n x k): FP64 for an FP64 V; for an FP32 V (the result
+  // type of FP32 / BF16 / E4M3 X) an FP32 product of the FP64 factors rounded
+  // to FP32, summed over K in 16-term slabs (relative error ~1e-7 of an
+  // FP32-rounded result); the factorisation itself stays FP64
+  if (v_f64)
+    launch_gemm_simt(L, n, k, k, F, LSPCA_F64, n, true, w.Rm, LSPCA_F64, k, false, w.Vd, true, k, 0, 1, true, true);
+  else
+    launch_gemm_simt(L, n, k, k, F, LSPCA_F64, n, true, w.Rm, LSPCA_F64, k, false, w.Vd, true, k, 0, 1, false, false);
   if (v_f64)
     finalize_v_kernel<double><<<k, 256, 0, L.stream>>>(w.Vd, n, k, (double*)V);
   else
