@@ -368,7 +368,9 @@ def run_gpu(args):
     proj_ms = p0.elapsed_time(p1) / npj
     del Y
 
-    # ---- end to end through the public API: pinned host X -> device, fit, V and sigma back
+    # ---- end to end through the public API: a host-resident (pinned) X, fitted
+    # by lspca_fit_host (row slices copied to the device while the previous
+    # slice is computed, Algorithm 4), V and sigma copied back
     Xh = torch.empty(X.shape, dtype=X.dtype, pin_memory=True)
     Xh.copy_(X)
     Vh = torch.empty(V.shape, dtype=V.dtype, pin_memory=True)
@@ -376,8 +378,9 @@ def run_gpu(args):
     ne2e = max(3, min(args.steps, 5))
 
     def e2e_step():
-        X.copy_(Xh, non_blocking=True)
-        step()
+        rc = L.lspca_fit_host(ctx.handle, Xh, w.k, om, 0, 0, V, sigma, rk, stream)
+        if rc != L.OK:
+            raise L.LspcaError(rc, "lspca_fit_host")
         Vh.copy_(V, non_blocking=True)
         sh.copy_(sigma, non_blocking=True)
 

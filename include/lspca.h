@@ -148,6 +148,29 @@ int spca_fit(lspca_ctx* ctx, const void* X, int32_t xt, int64_t m, int64_t n, in
              int32_t k, lspca_omega om, uint32_t flags, void* V, double* sigma, double* gram,
              int32_t* rank, void* stream, lspca_report* rep);
 
+/* Lazy SPCA fit of a host-resident X, Algorithm 4 proper (table of Sec. III:
+ * F += U_s^T X_s over row slices X_s; the paper's setting in which X does not
+ * fit in memory).  The slices are copied into two device staging buffers on
+ * a stream of the context while the previous slice's sketch U_s = X_s Omega
+ * and F += U_s^T X_s run on `stream`; then the k x k step runs once, as in
+ * lspca_fit.
+ * Xh     [host] m x n, element type xt (LSPCA_F32, LSPCA_BF16 or LSPCA_E4M3),
+ *               leading dimension ldx; page-locked memory (cudaHostAlloc,
+ *               cudaHostRegister) lets the copies overlap the computation.
+ *               Xh must stay valid and unchanged until the stream completes.
+ * slice_rows    rows per slice (0 = about 256 MB of X per slice); rounded up
+ *               to a multiple of 128 and capped at m.
+ * k             1 <= k <= min(m, n, 256), a multiple of 4.
+ * V, sigma, rank, rep: as lspca_fit (V in FP32).  flags: 0 (no Gram).
+ * The workspace holds two slices, one slice of U and the k x n FP64 F, so
+ * its size does not depend on m.  Slicing changes only the order in which
+ * F's terms are summed (Algorithm 2 = Algorithm 4 up to rounding).
+ * Errors: as lspca_fit; LSPCA_ERR_INVALID also for F64 X, k not a multiple
+ * of 4, LSPCA_WANT_GRAM / LSPCA_FORCE_SIMT in flags, or no sm_103 device.    */
+int lspca_fit_host(lspca_ctx* ctx, const void* Xh, int32_t xt, int64_t m, int64_t n, int64_t ldx, int32_t k,
+                   lspca_omega om, uint32_t flags, int64_t slice_rows, void* V, double* sigma, int32_t* rank,
+                   void* stream, lspca_report* rep);
+
 /* Reduction map pi(x) = V^T x for every row: Y = X V (Sec. III-B.2).
  * X [dev] m x n (xt, ldx); V [dev] n x k and Y [dev] m x k (output), both
  * in the result type.  F32 X runs split-FP16 tensor-core products (X and V

@@ -22,6 +22,10 @@ struct lspca_ctx {
   int64_t launches = 0;
   int num_sms = 0;
   cudaEvent_t ev[6] = {};
+  // host-resident fits: copy stream, per staging buffer "copied" / "consumed" events
+  cudaStream_t cstream = nullptr;
+  cudaEvent_t copied[2] = {};
+  cudaEvent_t consumed[2] = {};
   // profiling ring: 5 events per call
   bool profiling = false;
   std::vector<cudaEvent_t> pev;
@@ -356,6 +360,11 @@ int lspca_destroy(lspca_ctx* ctx) {
   if (ctx->d_status) cudaFree(ctx->d_status);
   for (auto& e : ctx->ev)
     if (e) cudaEventDestroy(e);
+  for (int b = 0; b < 2; ++b) {
+    if (ctx->copied[b]) cudaEventDestroy(ctx->copied[b]);
+    if (ctx->consumed[b]) cudaEventDestroy(ctx->consumed[b]);
+  }
+  if (ctx->cstream) cudaStreamDestroy(ctx->cstream);
   for (auto& e : ctx->pev) cudaEventDestroy(e);
   delete ctx;
   return LSPCA_OK;
@@ -369,6 +378,120 @@ int lspca_fit(lspca_ctx* ctx, const void* X, int32_t xt, int64_t m, int64_t n, i
 int spca_fit(lspca_ctx* ctx, const void* X, int32_t xt, int64_t m, int64_t n, int64_t ldx, int32_t k, lspca_omega om,
              uint32_t flags, void* V, double* sigma, double* gram, int32_t* rank, void* stream, lspca_report* rep) {
   return fit_impl(ctx, X, xt, m, n, ldx, k, om, flags, V, sigma, gram, rank, stream, rep, true);
+}
+
+int lspca_fit_host(lspca_ctx* ctx, const void* Xh, int32_t xt, int64_t m, int64_t n, int64_t ldx, int32_t k,
+                   lspca_omega om, uint32_t flags, int64_t slice_rows, void* V, double* sigma, int32_t* rank,
+                   void* stream, lspca_report* rep) {
+  if (!ctx || !Xh || !V || !sigma) return LSPCA_ERR_INVALID;
+  if (xt != LSPCA_F32 && xt != LSPCA_BF16 && xt != LSPCA_E4M3) return LSPCA_ERR_INVALID;
+  if (m < 1 || n < 1 || ldx < n || (ldx * (int64_t)dtype_size(xt)) % 16 != 0) return LSPCA_ERR_INVALID;
+  int st;
+  if ((st = check_omega(om, xt))) return st;
+  if (k < 1 || k > 256 || k > m || k > n || (k % 4) != 0 || slice_rows < 0) return LSPCA_ERR_INVALID;
+  if (flags & (LSPCA_WANT_GRAM | LSPCA_FORCE_SIMT)) return LSPCA_ERR_INVALID;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return LSPCA_ERR_CUDA;
+  if (!tc_available()) return LSPCA_ERR_INVALID;
+  const auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t s = (cudaStream_t)stream;
+  Launcher L{s, &ctx->launches, ctx->num_sms};
+  const int64_t row_bytes = ldx * (int64_t)dtype_size(xt);
+  if (slice_rows == 0) slice_rows = ((int64_t)256 << 20) / row_bytes;  // ~256 MB slices
+  slice_rows = (slice_rows + 127) / 128 * 128;
+  if (slice_rows < 128) slice_rows = 128;
+  if (slice_rows > m) slice_rows = m;
+  const int64_t nslices = (m + slice_rows - 1) / slice_rows;
+  const bool exact = om.kind == LSPCA_OMEGA_VERY_SPARSE;
+
+  void *stage[2] = {nullptr, nullptr}, *U = nullptr, *omega_d = nullptr, *tiles = nullptr, *small = nullptr;
+  float* scal = nullptr;
+  double* Facc = nullptr;
+  char* chain_base = nullptr;
+  TcChainWs cw_max;
+  auto plan = [&](Plan& P) {
+    for (auto& b : stage) b = P.take((size_t)slice_rows * (size_t)row_bytes);
+    U = P.take((size_t)slice_rows * k * 4);
+    omega_d = P.take((size_t)n * k * 4);
+    tiles = P.take(tc_tile_v_bytes(n, k));
+    scal = (float*)P.take(256);
+    Facc = (double*)P.take((size_t)k * n * 8);
+    small = P.take(small_ws_bytes(k, n, nullptr));
+    plan_tc_chain(nullptr, cw_max, xt, slice_rows, n, k, false, ctx->num_sms);
+    chain_base = (char*)P.take(cw_max.bytes);
+  };
+  Plan p0;
+  plan(p0);
+  if ((st = ensure_ws(ctx, p0.off + 4096, s))) return st;
+  Plan p1;
+  p1.base = (char*)ctx->ws;
+  plan(p1);
+  SmallWs sw;
+  carve_small_ws(sw, small, k, n);
+  if (!ctx->cstream) {
+    if (cudaStreamCreateWithFlags(&ctx->cstream, cudaStreamNonBlocking) != cudaSuccess) return LSPCA_ERR_CUDA;
+    for (int b = 0; b < 2; ++b) {
+      if (cudaEventCreateWithFlags(&ctx->copied[b], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&ctx->consumed[b], cudaEventDisableTiming) != cudaSuccess)
+        return LSPCA_ERR_CUDA;
+    }
+  }
+  // Omega once per fit, tiled for the reduction-map kernel
+  if (rep) cudaEventRecord(ctx->ev[0], s);
+  launch_omega_dense(L, om, n, k, LSPCA_F32, omega_d, k, false, xt == LSPCA_BF16);
+  tc_tile_v(L, xt, (const float*)omega_d, n, k, tiles, scal, ctx->d_status, exact);
+  // the copy stream starts after the work already queued on the caller's stream
+  // (the staging buffers may still be read by a previous call)
+  cudaEventRecord(ctx->consumed[0], s);
+  cudaStreamWaitEvent(ctx->cstream, ctx->consumed[0], 0);
+  for (int64_t si = 0; si < nslices; ++si) {
+    const int b = (int)(si & 1);
+    const int64_t r0 = si * slice_rows;
+    const int64_t rows = (r0 + slice_rows <= m) ? slice_rows : m - r0;
+    // Algorithm 4: copy slice si while the previous slice is computed
+    if (si >= 2) cudaStreamWaitEvent(ctx->cstream, ctx->consumed[b], 0);
+    if (cudaMemcpyAsync(stage[b], (const char*)Xh + r0 * row_bytes, (size_t)(rows * row_bytes),
+                        cudaMemcpyHostToDevice, ctx->cstream) != cudaSuccess)
+      return LSPCA_ERR_CUDA;
+    cudaEventRecord(ctx->copied[b], ctx->cstream);
+    cudaStreamWaitEvent(s, ctx->copied[b], 0);
+    // U_s = X_s Omega (max|X_s|, NaN / Inf, max|U_s| taken on the way); F += U_s^T X_s
+    cudaMemsetAsync(ctx->d_absmax, 0, 2 * sizeof(float), s);
+    tc_project_pretiled(L, stage[b], xt, rows, n, ldx, tiles, scal + 1, k, (float*)U, ctx->d_status, exact,
+                        ctx->d_absmax, ctx->d_absmax + 1);
+    TcChainWs cw;
+    plan_tc_chain(chain_base, cw, xt, rows, n, k, false, ctx->num_sms);
+    if (!tc_chain_main(L, stage[b], xt, rows, n, ldx, (const float*)U, k, cw, ctx->d_absmax, ctx->d_status, false))
+      return LSPCA_ERR_CUDA;
+    tc_chain_reduce(L, n, k, cw, Facc, nullptr, si > 0);
+    cudaEventRecord(ctx->consumed[b], s);
+  }
+  if (rep) cudaEventRecord(ctx->ev[2], s);
+  int32_t* rk = rank ? rank : ctx->d_rank;
+  launch_decompose(L, sw, Facc, k, n, m, false, V, sigma, rk, ctx->d_status);
+  if (rep) cudaEventRecord(ctx->ev[4], s);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return LSPCA_ERR_CUDA;
+  if (!rep) return LSPCA_OK;
+  memset(rep, 0, sizeof(*rep));
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return LSPCA_ERR_CUDA;
+  rep->ms_chain = ev_ms(ctx->ev[0], ctx->ev[2]);  // copies, sketches and pass F of all slices
+  rep->ms_small = ev_ms(ctx->ev[2], ctx->ev[4]);
+  rep->bytes_x = (double)m * n * dtype_size(xt);
+  int32_t hr = 0, hst = 0, hsw = 0;
+  cudaMemcpy(&hr, rk, 4, cudaMemcpyDeviceToHost);
+  cudaMemcpy(&hst, ctx->d_status, 4, cudaMemcpyDeviceToHost);
+  cudaMemcpy(&hsw, sw.sweeps, 4, cudaMemcpyDeviceToHost);
+  cudaMemsetAsync(ctx->d_status, 0, 4, s);
+  cudaStreamSynchronize(s);
+  rep->rank = hr;
+  rep->device_status = hst;
+  rep->sweeps = hsw;
+  rep->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (hst & ST_NONFINITE) return LSPCA_ERR_NUMERIC;
+  if (hst & ST_TIMEOUT) return LSPCA_ERR_TIMEOUT;
+  if (hst & ST_NUMERIC) return LSPCA_ERR_NUMERIC;
+  if (hr < k) return LSPCA_WARN_RANK_DEFICIENT;
+  return LSPCA_OK;
 }
 
 int lspca_project(lspca_ctx* ctx, const void* X, int32_t xt, int64_t m, int64_t n, int64_t ldx, const void* V,

@@ -37,7 +37,8 @@ bool tc_chain_main(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int
 void plan_tc_chain_inline(char* base, TcChainWs& w, int xt, int64_t m, int64_t n, int k, bool want_g, int num_sms);
 void tc_chain_inline_main(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_t ldx, const float* U,
                           int k, TcChainWs& w, const float* absmax, int* status, bool want_g);
-void tc_chain_reduce(Launcher& L, int64_t n, int k, TcChainWs& w, double* F, double* G);
+// F (k x n FP64) = sum of the chunk partials, or F += that sum with accumulate (Algorithm 4's F += U_s^T X_s).
+void tc_chain_reduce(Launcher& L, int64_t n, int k, TcChainWs& w, double* F, double* G, bool accumulate = false);
 
 // Y = X V on tensor cores (FP32, BF16 or E4M3 X; V and Y FP32, k <= 256).  With V = a
 // dense Omega the same kernel computes the sketch U = X Omega (pass S).
@@ -64,7 +65,9 @@ struct TcProjUnit {
 };
 size_t tc_tile_v_bytes(int64_t n, int k);
 // Split and tile V for X type xt; scal: 2 device floats (max|V|, scale).
-void tc_tile_v(Launcher& L, int xt, const float* V, int64_t n, int k, void* tiles, float* scal, int* status);
+// exact_v: V is exact in one piece (the very sparse Omega), tiled for the exact-V products.
+void tc_tile_v(Launcher& L, int xt, const float* V, int64_t n, int k, void* tiles, float* scal, int* status,
+               bool exact_v = false);
 // Y = X V with V already split and tiled by tc_tile_v (vscale = its scale slot).
 // exact_v: V is exact in its hi piece (the very sparse Omega), so the products
 // with its lo piece are skipped.  xmax / ymax (nullable): max|X| and max|Y| are

@@ -716,9 +716,10 @@ size_t tc_tile_v_bytes(int64_t n, int k) {
   return (size_t)((n + tcp::BK - 1) / tcp::BK) * 2 * tcp::BK * npad * 2;
 }
 
-void tc_tile_v(Launcher& L, int xt, const float* V, int64_t n, int k, void* tiles, float* scal, int* status) {
+void tc_tile_v(Launcher& L, int xt, const float* V, int64_t n, int k, void* tiles, float* scal, int* status,
+               bool exact_v) {
   const int npad = (k + 63) / 64 * 64;
-  const bool f16 = xt == LSPCA_F32;
+  const bool f16 = xt == LSPCA_F32 && !exact_v;  // FP32 X against an exact V takes BF16 tiles
   cudaMemsetAsync(scal, 0, 8, L.stream);
   if (f16) launch_scan_x(L, V, LSPCA_F32, n, k, k, scal, status);
   const int64_t nks = (n + tcp::BK - 1) / tcp::BK;

@@ -63,6 +63,8 @@ _SIGS = {
                                  ctypes.POINTER(lspca_report)]),
     "spca_fit": (ctypes.c_int, [_P, _P, _I32, _I64, _I64, _I64, _I32, lspca_omega, _U32, _P, _P, _P, _P, _P,
                                 ctypes.POINTER(lspca_report)]),
+    "lspca_fit_host": (ctypes.c_int, [_P, _P, _I32, _I64, _I64, _I64, _I32, lspca_omega, _U32, _I64, _P, _P, _P,
+                                      _P, ctypes.POINTER(lspca_report)]),
     "lspca_project": (ctypes.c_int, [_P, _P, _I32, _I64, _I64, _I64, _P, _I32, _P, _P]),
     "lspca_omega_materialize": (ctypes.c_int, [_P, lspca_omega, _I64, _I32, _I32, _P, _P]),
     "lspca_sketch": (ctypes.c_int, [_P, _P, _I32, _I64, _I64, _I64, _I32, lspca_omega, _U32, _P, _P]),
@@ -153,6 +155,14 @@ def lspca_create(device: int = 0, hbm_budget_bytes: int = 0) -> int:
 
 def lspca_destroy(ctx: int) -> int:
     return load().lspca_destroy(ctx)
+
+
+def lspca_fit_host(ctx, Xh, k, om, flags, slice_rows, V, sigma, rank=None, stream=None, report=None) -> int:
+    """Xh: a CPU tensor (pinned for overlapped copies); V, sigma, rank: CUDA tensors."""
+    x, xt, m, n, ldx = _xargs(Xh)
+    rep = ctypes.byref(report) if report is not None else None
+    return load().lspca_fit_host(ctx, x, xt, m, n, ldx, k, om, flags, int(slice_rows), _ptr(V), _ptr(sigma),
+                                 _ptr(rank), _stream(stream), rep)
 
 
 def lspca_fit(ctx, X, k, om, flags, V, sigma, gram=None, rank=None, stream=None, report=None) -> int:
@@ -392,6 +402,17 @@ class Context:
 
     def fit(self, X, k, om, flags=0, report=True, stream=None) -> FitResult:
         return self._fit(lspca_fit, X, k, om, flags, report, stream)
+
+    def fit_host(self, Xh, k, om, slice_rows=0, report=True, stream=None) -> FitResult:
+        """Fit a host-resident X (CPU tensor, pinned for overlapped copies) slice by slice."""
+        dev = torch.device(f"cuda:{self.device}")
+        V = torch.empty(Xh.shape[1], k, dtype=torch.float32, device=dev)
+        sigma = torch.empty(k, dtype=torch.float64, device=dev)
+        rank = torch.empty(1, dtype=torch.int32, device=dev)
+        rep = lspca_report() if report else None
+        rc = lspca_fit_host(self.handle, Xh, k, om, 0, slice_rows, V, sigma, rank, stream, rep)
+        _check(rc, "lspca_fit_host", allow=(OK, WARN_RANK_DEFICIENT))
+        return FitResult(V, sigma, rank, None, rc, rep.as_dict() if rep is not None else None)
 
     def spca(self, X, k, om, flags=0, report=True, stream=None) -> FitResult:
         return self._fit(spca_fit, X, k, om, flags, report, stream)
