@@ -384,6 +384,17 @@ def run_gpu(args):
         Vh.copy_(V, non_blocking=True)
         sh.copy_(sigma, non_blocking=True)
 
+    # the host -> device copy floor of this node: one plain copy of the same bytes
+    X.copy_(Xh, non_blocking=True)
+    torch.cuda.synchronize()
+    c0 = torch.cuda.Event(enable_timing=True)
+    c1 = torch.cuda.Event(enable_timing=True)
+    c0.record(stream)
+    X.copy_(Xh, non_blocking=True)
+    c1.record(stream)
+    torch.cuda.synchronize()
+    h2d_ms = c0.elapsed_time(c1)
+
     e2e_step()
     torch.cuda.synchronize()
     barrier()
@@ -431,7 +442,8 @@ def run_gpu(args):
                         "bytes_per_call": x_bytes + u_bytes, "kernel": "tcproj project_kernel (FP32 X, k=128)"},
             "e2e": {"value": w.m * ws / (e2e_ms / 1e3), "unit": "samples/s",
                     "h2d_bytes_per_step": x_bytes, "d2h_bytes_per_step": w.n * w.k * 4 + w.k * 8,
-                    "ms_per_step": e2e_ms},
+                    "ms_per_step": e2e_ms, "api": "lspca_fit_host (pinned host X, row slices overlapped)",
+                    "h2d_copy_ms": h2d_ms, "h2d_copy_gbs": x_bytes / (h2d_ms / 1e3) / 1e9},
             "gpu_launches": launches,
             "clocks": clk}
     if rank == 0 and args.serve_seconds > 0:
