@@ -429,22 +429,20 @@ __global__ void __launch_bounds__(Cfg<MODE, MH, NACC>::THREADS, 1)
           }
           ptx::tc_fence_after();
           const uint32_t st = sbase + s * C::STAGE_BYTES;
-          const uint32_t a_hi = st, a_lo = st + C::A_BYTES, b_hi = st + 2 * C::A_BYTES, b_lo = b_hi + C::B_BYTES;
+          const uint32_t a_hi = st, b_hi = st + 2 * C::A_BYTES;
+          // descriptors of the stage's operands; K slices and M halves are offsets
+          const uint64_t adh0 = ptx::desc_sw128(a_hi, C::BOX, 1024);
+          const uint64_t bdh0 = C::CONV ? ptx::desc_sw128(b_hi, 1024, C::SBO_B) : ptx::desc_sw128(b_hi, C::BOX, 1024);
+          constexpr uint32_t B_KSTEP = C::CONV ? 2 * C::SBO_B : 2048;  // bytes per 16 K-rows of B
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk) {
-            uint64_t bdh, bdl = 0;
-            if (C::CONV) {
-              bdh = ptx::desc_sw128(b_hi + kk * 2 * C::SBO_B, 1024, C::SBO_B);
-              if (C::NB == 2) bdl = ptx::desc_sw128(b_lo + kk * 2 * C::SBO_B, 1024, C::SBO_B);
-            } else {
-              bdh = ptx::desc_sw128(b_hi + kk * 2048, C::BOX, 1024);
-              if (C::NB == 2) bdl = ptx::desc_sw128(b_lo + kk * 2048, C::BOX, 1024);
-            }
+            const uint64_t bdh = ptx::desc_advance(bdh0, kk * B_KSTEP);
+            const uint64_t bdl = ptx::desc_advance(bdh, C::B_BYTES);
 #pragma unroll
             for (int h = 0; h < MH; ++h) {
               const uint32_t d = tmem + (uint32_t)(ab * C::ACC_COLS + h * C::BN);
-              const uint64_t adh = ptx::desc_sw128(a_hi + h * 2 * C::BOX + kk * 2048, C::BOX, 1024);
-              const uint64_t adl = ptx::desc_sw128(a_lo + h * 2 * C::BOX + kk * 2048, C::BOX, 1024);
+              const uint64_t adh = ptx::desc_advance(adh0, h * 2 * C::BOX + kk * 2048);
+              const uint64_t adl = ptx::desc_advance(adh, C::A_BYTES);
               const uint32_t acc = (seg_start && kk == 0) ? 0u : 1u;
               ptx::mma_f16(d, adh, bdh, idesc, acc);
               if (C::NB == 2) ptx::mma_f16(d, adh, bdl, idesc, 1u);

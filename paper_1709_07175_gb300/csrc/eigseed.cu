@@ -214,39 +214,106 @@ __device__ void tridiag_regs(const float* Asrc, int k, float* Vh, float* dv, flo
 
 // Step 4: Z <- H_0 H_1 ... H_{k-3} Z with the reflectors left in Vh by
 // tridiag_regs; Z (k x k, row-major, column i = eigenvector i of T) is read
-// from and written back to `Z`.  Two barriers per reflector.
-__device__ void backtransform_regs(float* Z, int k, const float* Vh, const float* betav, float* gpart) {
-  const int tid = threadIdx.x;
+// from and written back to `Z`.  The reflectors are applied four at a time in
+// compact WY form: H_a H_{a+1} H_{a+2} H_{a+3} = I - V T V^T with V = [v_a ..
+// v_{a+3}] and T 4 x 4 upper triangular (T_ii = beta_i, T[0:i, i] = -beta_i
+// T[0:i, 0:i] V[:, 0:i]^T v_i), so Z <- Z - V (T (V^T Z)) costs two barriers
+// per four reflectors.  The T of every group is formed first, one warp per
+// group.  gp: 16 x 128 floats of partial sums; Tg: 16 floats per group.
+__device__ void backtransform_regs(float* Z, int k, const float* Vh, const float* betav, float* gp, float* Tg) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int tr = tid & 127, tg = tid >> 7;
+  const int nr = k > 2 ? k - 2 : 0;  // reflectors 0 .. nr - 1
+  const int ng = (nr + 3) / 4;
   float z[32];
 #pragma unroll
   for (int i = 0; i < 32; ++i) {
     const int r = tg + 4 * i;
     z[i] = (r < k && tr < k) ? Z[r * k + tr] : 0.f;
   }
-  for (int j = k - 3; j >= 0; --j) {
-    const float beta = betav[j];
-    if (beta == 0.f) continue;  // uniform
-    const float4* vp = reinterpret_cast<const float4*>(Vh + j * 128 + tg * 32);
-    float s0 = 0.f, s1 = 0.f;
+  // T of each group: the six inner products v_l . v_i (l < i) by one warp
+  for (int g = warp; g < ng; g += kSeedThreads / 32) {
+    const int a = 4 * g;
+    float w[6];
+    int t = 0;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const float4 v = vp[q];
-      s0 = fmaf(v.x, z[4 * q], s0);
-      s1 = fmaf(v.y, z[4 * q + 1], s1);
-      s0 = fmaf(v.z, z[4 * q + 2], s0);
-      s1 = fmaf(v.w, z[4 * q + 3], s1);
+    for (int i = 1; i < 4; ++i)
+#pragma unroll
+      for (int l = 0; l < i; ++l) {
+        float d = 0.f;
+        if (a + i < nr) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) d = fmaf(Vh[(a + l) * 128 + lane + 32 * q], Vh[(a + i) * 128 + lane + 32 * q], d);
+        }
+        w[t++] = warp_sumf(d);
+      }
+    if (lane == 0) {
+      float T[4][4] = {};
+      t = 0;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float bi = (a + i < nr) ? betav[a + i] : 0.f;
+        float tmp[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int l = 0; l < i; ++l) tmp[l] = -bi * w[t++];
+        for (int l = 0; l < i; ++l) {
+          float acc = 0.f;
+          for (int m = l; m < i; ++m) acc = fmaf(T[l][m], tmp[m], acc);
+          T[l][i] = acc;
+        }
+        T[i][i] = bi;
+      }
+      for (int i = 0; i < 16; ++i) Tg[g * 16 + i] = T[i / 4][i % 4];
     }
-    gpart[tg * 128 + tr] = s0 + s1;
-    __syncthreads();
-    const float wc = beta * (gpart[tr] + gpart[128 + tr] + gpart[256 + tr] + gpart[384 + tr]);
+  }
+  __syncthreads();
+  for (int g = ng - 1; g >= 0; --g) {
+    const int a = 4 * g;
+    // partial inner products v_{a+i} . z over the thread's 32 rows
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const float4 v = vp[q];
-      z[4 * q] -= v.x * wc;
-      z[4 * q + 1] -= v.y * wc;
-      z[4 * q + 2] -= v.z * wc;
-      z[4 * q + 3] -= v.w * wc;
+    for (int i = 0; i < 4; ++i) {
+      float s0 = 0.f, s1 = 0.f;
+      if (a + i < nr) {
+        const float4* vp = reinterpret_cast<const float4*>(Vh + (a + i) * 128 + tg * 32);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const float4 v = vp[q];
+          s0 = fmaf(v.x, z[4 * q], s0);
+          s1 = fmaf(v.y, z[4 * q + 1], s1);
+          s0 = fmaf(v.z, z[4 * q + 2], s0);
+          s1 = fmaf(v.w, z[4 * q + 3], s1);
+        }
+      }
+      gp[(i * 4 + tg) * 128 + tr] = s0 + s1;
+    }
+    __syncthreads();
+    float S[4], u[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      S[i] = gp[(i * 4) * 128 + tr] + gp[(i * 4 + 1) * 128 + tr] + gp[(i * 4 + 2) * 128 + tr] +
+             gp[(i * 4 + 3) * 128 + tr];
+    const float* T = Tg + g * 16;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      float acc = 0.f;
+#pragma unroll
+      for (int l = i; l < 4; ++l) acc = fmaf(T[i * 4 + l], S[l], acc);
+      u[i] = acc;
+    }
+    // z <- z - V u over the thread's rows
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (a + i < nr) {
+        const float4* vp = reinterpret_cast<const float4*>(Vh + (a + i) * 128 + tg * 32);
+        const float ui = u[i];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const float4 v = vp[q];
+          z[4 * q] -= v.x * ui;
+          z[4 * q + 1] -= v.y * ui;
+          z[4 * q + 2] -= v.z * ui;
+          z[4 * q + 3] -= v.w * ui;
+        }
+      }
     }
     __syncthreads();
   }
@@ -265,6 +332,8 @@ __global__ void __launch_bounds__(kSeedThreads, 1) eig_seed_kernel(const double*
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ float dv[256], ev[256], e2v[256], betav[256], wl[256], pv_s[256], lamv[256], vv_s[256];
   __shared__ float gpart[kSeedThreads];
+  __shared__ __align__(16) float gp16[16 * 128];  // back-transformation partials
+  __shared__ float Tgrp[16 * 32];                  // compact-WY T of each group of four reflectors
   __shared__ float coef[4];
   __shared__ int clstart[257];
   const bool sm = k <= 128;
@@ -278,14 +347,24 @@ __global__ void __launch_bounds__(kSeedThreads, 1) eig_seed_kernel(const double*
 
   // scale and load; ||H||_F for the refinement's noise floor
   __shared__ double hmax_s;
-  if (tid == 0) {
+  __shared__ double hmx[kSeedThreads / 32];
+  {
     double mx = 0.0;
-    for (int i = 0; i < k; ++i) mx = fmax(mx, fabs(H[(int64_t)i * k + i]));
-    hmax_s = mx > 0.0 ? mx : 1.0;
+    for (int i = tid; i < k; i += kSeedThreads) mx = fmax(mx, fabs(H[(int64_t)i * k + i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) hmx[warp] = mx;
+    __syncthreads();
+    if (tid == 0) {
+      double m2 = 0.0;
+      for (int i = 0; i < nw; ++i) m2 = fmax(m2, hmx[i]);
+      hmax_s = m2 > 0.0 ? m2 : 1.0;
+    }
   }
   __syncthreads();
   const double sc = 1.0 / hmax_s;
   double hf = 0.0;
+#pragma unroll 8
   for (int e = tid; e < k * k; e += kSeedThreads) {
     const double h = H[e];
     hf += h * h;
@@ -490,7 +569,7 @@ __global__ void __launch_bounds__(kSeedThreads, 1) eig_seed_kernel(const double*
   //   2. w_c = beta (sum of the GR partials of column c), then
   //      Z[j+1+r][c] -= v_r w_c over the same rows.
   if (sm) {
-    backtransform_regs(Z, k, A, betav, gpart);
+    backtransform_regs(Z, k, A, betav, gp16, Tgrp);
   } else {
     for (int j = k - 3; j >= 0; --j) {
       const float beta = betav[j];

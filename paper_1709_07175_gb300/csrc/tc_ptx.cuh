@@ -247,6 +247,11 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr, uint32_t lbo, uin
   return d;
 }
 
+// The descriptor of the same operand layout `bytes` further on: the start
+// address field holds address >> 4 (shared-memory addresses stay below 2^18,
+// so the field does not carry into the next one).
+__device__ __forceinline__ uint64_t desc_advance(uint64_t d, uint32_t bytes) { return d + (uint64_t)(bytes >> 4); }
+
 // Instruction descriptor of kind::f16: FP32 accumulator, A/B both F16 (bf16 = 0)
 // or both BF16 (bf16 = 1), majorness bits (1 = MN-major), N and M.
 __host__ __device__ constexpr uint32_t idesc_f16(int bf16, int M, int N, int a_mn, int b_mn) {

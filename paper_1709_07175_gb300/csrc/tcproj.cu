@@ -159,18 +159,18 @@ __device__ __forceinline__ float pow2_scale_bits(uint32_t ab) {
   return __uint_as_float((uint32_t)se << 23);
 }
 
-// (a, b) -> three BF16 pieces each, v = p0 + p1 + p2 exactly for normal FP32 v
-// (each step keeps the top 8 bits of an exactly computed remainder).
+// (a, b) -> three BF16 pieces each, v = p0 + p1 + p2 exactly: p0 keeps the top
+// 8 significand bits of v (truncation), p1 the top 8 of the exact remainder and
+// p2 the last at most 8 bits, so every piece is a BF16 without rounding.  The
+// remainders stay normal FP32 numbers (and the pieces exact) for |v| >= 2^-100.
 __device__ __forceinline__ void split_b3(float a, float b, uint32_t& p0, uint32_t& p1, uint32_t& p2) {
-  const __nv_bfloat162 h0 = __floats2bfloat162_rn(a, b);
-  const float2 f0 = __bfloat1622float2(h0);
-  const float ra = a - f0.x, rb = b - f0.y;
-  const __nv_bfloat162 h1 = __floats2bfloat162_rn(ra, rb);
-  const float2 f1 = __bfloat1622float2(h1);
-  const __nv_bfloat162 h2 = __floats2bfloat162_rn(ra - f1.x, rb - f1.y);
-  p0 = *reinterpret_cast<const uint32_t*>(&h0);
-  p1 = *reinterpret_cast<const uint32_t*>(&h1);
-  p2 = *reinterpret_cast<const uint32_t*>(&h2);
+  const uint32_t a0 = __float_as_uint(a) & 0xffff0000u, b0 = __float_as_uint(b) & 0xffff0000u;
+  const float ra = a - __uint_as_float(a0), rb = b - __uint_as_float(b0);
+  const uint32_t a1 = __float_as_uint(ra) & 0xffff0000u, b1 = __float_as_uint(rb) & 0xffff0000u;
+  const float sa = ra - __uint_as_float(a1), sb = rb - __uint_as_float(b1);
+  p0 = __byte_perm(a0, b0, 0x7632);
+  p1 = __byte_perm(a1, b1, 0x7632);
+  p2 = __byte_perm(__float_as_uint(sa), __float_as_uint(sb), 0x7632);
 }
 
 // (a, b) -> FP16 pairs: hi = fp16(v), lo = fp16(v - hi), two of each packed.
@@ -449,25 +449,19 @@ __global__ void __launch_bounds__(Cfg<XK, NT, EXACT_V>::THREADS, 1) project_kern
           }
           ptx::tc_fence_after();
           const uint32_t st = sbase + s * C::STAGE_BYTES;
-          const uint32_t b_hi = st, b_lo = st + C::B_BYTES, a_hi = st + C::PB * C::B_BYTES, a_lo = a_hi + C::A_BYTES;
+          const uint32_t b_hi = st, a_hi = st + C::PB * C::B_BYTES;
           const uint32_t d = tmem + (uint32_t)(ab * C::NPAD);
+          // descriptors of the stage's operands; K slices and pieces are offsets
+          const uint64_t adh0 = ptx::desc_sw128(a_hi, 16, 1024);
+          const uint64_t bdh0 = ptx::desc_sw128(b_hi, 1024, C::SBO_B);
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk) {
-            const uint64_t adh = ptx::desc_sw128(a_hi + kk * 32, 16, 1024);
-            const uint64_t bdh = ptx::desc_sw128(b_hi + kk * 2 * C::SBO_B, 1024, C::SBO_B);
+            const uint64_t adh = ptx::desc_advance(adh0, kk * 32);
+            const uint64_t bdh = ptx::desc_advance(bdh0, kk * 2 * C::SBO_B);
             ptx::mma_f16(d, adh, bdh, idesc, (seg_start && kk == 0) ? 0u : 1u);
-            if (!EXACT_V) {
-              const uint64_t bdl = ptx::desc_sw128(b_lo + kk * 2 * C::SBO_B, 1024, C::SBO_B);
-              ptx::mma_f16(d, adh, bdl, idesc, 1u);
-            }
-            if (C::PA >= 2) {
-              const uint64_t adl = ptx::desc_sw128(a_lo + kk * 32, 16, 1024);
-              ptx::mma_f16(d, adl, bdh, idesc, 1u);
-            }
-            if (C::PA == 3) {
-              const uint64_t ad2 = ptx::desc_sw128(a_lo + C::A_BYTES + kk * 32, 16, 1024);
-              ptx::mma_f16(d, ad2, bdh, idesc, 1u);
-            }
+            if (!EXACT_V) ptx::mma_f16(d, adh, ptx::desc_advance(bdh, C::B_BYTES), idesc, 1u);
+            if (C::PA >= 2) ptx::mma_f16(d, ptx::desc_advance(adh, C::A_BYTES), bdh, idesc, 1u);
+            if (C::PA == 3) ptx::mma_f16(d, ptx::desc_advance(adh, 2 * C::A_BYTES), bdh, idesc, 1u);
           }
           ptx::mma_commit(&empty[s]);
           if ((ks % C::SEG) == C::SEG - 1 || ks == nks - 1) {
