@@ -259,49 +259,81 @@ __global__ void __launch_bounds__(Cfg<XK, NT, EXACT_V>::THREADS, 1) project_kern
     __syncwarp();
   } else if (warp < C::CW) {
     // ------------------------------------------------------------ converters
-    // thread tid, load q covers row (tid + CT q) / VPR and the EPV elements at
-    // column ((tid + CT q) % VPR) EPV of the k-step
-    auto load = [&](const TileInfo& ti, int ks, uint4 (&dst)[C::NV]) {
-      const int64_t c0 = (int64_t)ks * BK;
-      const char* base = (const char*)ti.X + (ti.row0 * ti.ldx + c0) * C::ES;
-      const int64_t row_bytes = ti.ldx * C::ES;
-      const bool full_tile = ti.row0 + 128 <= ti.m && c0 + BK <= ti.n;
+    // Thread tid covers, in every k-step, the EPV elements at column cw of the
+    // rows r0 + RSTEP q (q < NV) of the tile; those rows' swizzled offsets
+    // differ by whole 1024-byte atoms.
+    constexpr int RSTEP = C::CT / C::VPR;
+    static_assert(RSTEP % 8 == 0, "a thread's rows are whole swizzle atoms apart");
+    constexpr uint32_t QOFF = (RSTEP / 8) * 1024u;
+    const int r0 = tid / C::VPR, cw = (tid % C::VPR) * C::EPV;
+    const uint32_t soff = ptx::k_sw128_offset(r0, cw);
+    // Load cursor: tile lt, its k-step lk of lnk; lp = the address of (row r0,
+    // column cw) of k-step lk; lrows = rows of the tile that exist.
+    int64_t lt = blockIdx.x, lrs = 0, ln = 0;
+    int lk = 0, lnk = 0, lrows = 0;
+    const uint8_t* lp = nullptr;
+    auto enter = [&]() {
+      lk = 0;
+      if (lt >= tiles) return;
+      const TileInfo ti = tile_info(p, lt);
+      lnk = ksteps(ti);
+      ln = ti.n;
+      lrows = (int)min(ti.m - ti.row0, (int64_t)128);
+      const int64_t rb = ti.ldx * C::ES;
+      lrs = rb * RSTEP;
+      lp = (const uint8_t*)ti.X + (ti.row0 + r0) * rb + cw * C::ES;
+    };
+    // loads of the cursor's k-step; vc = its columns that exist (BK: all)
+    auto issue = [&](uint4 (&dst)[C::NV], int& vc) {
+      const int64_t left = ln - (int64_t)lk * BK;
+      vc = left >= BK ? BK : (int)left;
+      if (lrows == 128 && vc == BK) {
 #pragma unroll
-      for (int q = 0; q < C::NV; ++q) {
-        const int f = tid + C::CT * q;
-        const int row = f / C::VPR, col = (f % C::VPR) * C::EPV;
-        if (full_tile || (ti.row0 + row < ti.m && c0 + col < ti.n)) {
+        for (int q = 0; q < C::NV; ++q)
           asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
                        : "=r"(dst[q].x), "=r"(dst[q].y), "=r"(dst[q].z), "=r"(dst[q].w)
-                       : "l"(base + row * row_bytes + col * C::ES));
-        } else {
-          dst[q] = make_uint4(0u, 0u, 0u, 0u);
+                       : "l"(lp + q * lrs));
+      } else {
+#pragma unroll
+        for (int q = 0; q < C::NV; ++q) {
+          if (r0 + RSTEP * q < lrows && cw < vc) {
+            asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+                         : "=r"(dst[q].x), "=r"(dst[q].y), "=r"(dst[q].z), "=r"(dst[q].w)
+                         : "l"(lp + q * lrs));
+          } else {
+            dst[q] = make_uint4(0u, 0u, 0u, 0u);
+          }
         }
       }
+      lp += BK * C::ES;
+      if (++lk >= lnk) {
+        lt += gridDim.x;
+        enter();
+      }
     };
-    uint32_t xb = 0u;  // max over the |x| seen, as FP32 bits (>= 0x7f800000: NaN / Inf)
-    auto store = [&](const uint4 (&r)[C::NV], uint32_t st, int slot, int ks, int64_t ncols) {
+    uint32_t xb = 0u;   // max over the |x| seen, as FP32 bits (>= 0x7f800000: NaN / Inf)
+    uint32_t xb2 = 0u;  // three-piece path: max of the BF16 leading pieces' |bits| per half
+    auto store = [&](const uint4 (&r)[C::NV], uint32_t st, int slot, int vc) {
       const uint32_t a_hi = st + C::PB * C::B_BYTES, a_lo = a_hi + C::A_BYTES;
-      const int64_t c0 = (int64_t)ks * BK;
-      const bool tail = c0 + BK > ncols;  // the k-step runs past the last column
+      const bool tail = vc < BK;  // the k-step runs past the last column
 #pragma unroll
       for (int q = 0; q < C::NV; ++q) {
-        const int f = tid + C::CT * q;
-        const int row = f / C::VPR, col = (f % C::VPR) * C::EPV;
+        const uint32_t off = soff + q * QOFF;
         if constexpr (C::SPL3) {
           float v[4] = {__uint_as_float(r[q].x), __uint_as_float(r[q].y), __uint_as_float(r[q].z),
                         __uint_as_float(r[q].w)};
           if (tail) {
 #pragma unroll
             for (int u = 0; u < 4; ++u)
-              if (c0 + col + u >= ncols) v[u] = 0.f;
+              if (cw + u >= vc) v[u] = 0.f;
           }
-          xb = max(xb, max(max(__float_as_uint(v[0]) & 0x7fffffffu, __float_as_uint(v[1]) & 0x7fffffffu),
-                           max(__float_as_uint(v[2]) & 0x7fffffffu, __float_as_uint(v[3]) & 0x7fffffffu)));
           uint32_t p0[2], p1[2], p2[2];
           split_b3(v[0], v[1], p0[0], p1[0], p2[0]);
           split_b3(v[2], v[3], p0[1], p1[1], p2[1]);
-          const uint32_t off = ptx::k_sw128_offset(row, col);
+          // the leading piece keeps x's sign, exponent and top 7 fraction
+          // bits: its max is max|x| rounded toward zero, and NaN / Inf stay
+          // >= 0x7f80
+          xb2 = __vmaxu2(xb2, __vmaxu2(p0[0] & 0x7fff7fffu, p0[1] & 0x7fff7fffu));
           asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a_hi + off), "r"(p0[0]), "r"(p0[1]) : "memory");
           asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a_lo + off), "r"(p1[0]), "r"(p1[1]) : "memory");
           asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a_lo + C::A_BYTES + off), "r"(p2[0]), "r"(p2[1])
@@ -312,106 +344,97 @@ __global__ void __launch_bounds__(Cfg<XK, NT, EXACT_V>::THREADS, 1) project_kern
           if (tail) {
 #pragma unroll
             for (int u = 0; u < 4; ++u)
-              if (c0 + col + u >= ncols) v[u] = 0.f;
+              if (cw + u >= vc) v[u] = 0.f;
           }
-          uint32_t mb = max(max(__float_as_uint(v[0]) & 0x7fffffffu, __float_as_uint(v[1]) & 0x7fffffffu),
-                            max(__float_as_uint(v[2]) & 0x7fffffffu, __float_as_uint(v[3]) & 0x7fffffffu));
+          uint32_t mb = __vimax3_u32(__float_as_uint(v[0]) & 0x7fffffffu, __float_as_uint(v[1]) & 0x7fffffffu,
+                                     max(__float_as_uint(v[2]) & 0x7fffffffu, __float_as_uint(v[3]) & 0x7fffffffu));
           xb = max(xb, mb);
           // the row's 16 loads sit in one half-warp: max over that half
           static_assert(C::VPR == 16, "one row per half-warp");
           mb = __reduce_max_sync(lane < 16 ? 0x0000ffffu : 0xffff0000u, mb);
           const float sc = pow2_scale_bits(mb);
-          if ((f % C::VPR) == 0) scales[slot * 128 + row] = sc;  // FP16 path only
+          if (cw == 0) scales[slot * 128 + r0 + RSTEP * q] = sc;  // FP16 path only
           uint32_t h0, l0, h1, l1;
           split_h2(v[0] * sc, v[1] * sc, h0, l0);
           split_h2(v[2] * sc, v[3] * sc, h1, l1);
-          const uint32_t off = ptx::k_sw128_offset(row, col);
           asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a_hi + off), "r"(h0), "r"(h1) : "memory");
           asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a_lo + off), "r"(l0), "r"(l1) : "memory");
         } else if constexpr (XK == XK_BF16) {
           uint4 v = r[q];
-          if (tail && c0 + col + 8 > ncols) {
+          if (tail && cw + 8 > vc) {
             uint16_t* e = reinterpret_cast<uint16_t*>(&v);
 #pragma unroll
             for (int u = 0; u < 8; ++u)
-              if (c0 + col + u >= ncols) e[u] = 0;
+              if (cw + u >= vc) e[u] = 0;
           }
-          {
-            const uint32_t m2 = __vmaxu2(__vmaxu2(v.x & 0x7fff7fffu, v.y & 0x7fff7fffu),
-                                         __vmaxu2(v.z & 0x7fff7fffu, v.w & 0x7fff7fffu));
-            xb = max(xb, max(m2 >> 16, m2 & 0xffffu) << 16);  // BF16 bits widen to FP32 bits
-          }
-          asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a_hi + ptx::k_sw128_offset(row, col)),
-                       "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+          xb2 = __vmaxu2(xb2, __vmaxu2(__vmaxu2(v.x & 0x7fff7fffu, v.y & 0x7fff7fffu),
+                                       __vmaxu2(v.z & 0x7fff7fffu, v.w & 0x7fff7fffu)));
+          asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a_hi + off), "r"(v.x), "r"(v.y), "r"(v.z),
+                       "r"(v.w)
                        : "memory");
         } else {
           const __nv_fp8_e4m3* e8 = reinterpret_cast<const __nv_fp8_e4m3*>(&r[q]);
           uint32_t w[8];
 #pragma unroll
           for (int u = 0; u < 8; ++u) {
-            const float a = (!tail || c0 + col + 2 * u < ncols) ? float(e8[2 * u]) : 0.f;
-            const float b = (!tail || c0 + col + 2 * u + 1 < ncols) ? float(e8[2 * u + 1]) : 0.f;
+            const float a = (!tail || cw + 2 * u < vc) ? float(e8[2 * u]) : 0.f;
+            const float b = (!tail || cw + 2 * u + 1 < vc) ? float(e8[2 * u + 1]) : 0.f;
             xb = max(xb, max(__float_as_uint(a) & 0x7fffffffu, __float_as_uint(b) & 0x7fffffffu));
             __nv_bfloat162 h2 = __floats2bfloat162_rn(a, b);
             w[u] = *reinterpret_cast<uint32_t*>(&h2);
           }
-          asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a_hi + ptx::k_sw128_offset(row, col)),
-                       "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3])
+          // columns cw .. cw + 7 and cw + 8 .. cw + 15: the second half is the
+          // next 16-byte chunk of the row (cw is a multiple of 16)
+          asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a_hi + off), "r"(w[0]), "r"(w[1]),
+                       "r"(w[2]), "r"(w[3])
                        : "memory");
-          asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a_hi + ptx::k_sw128_offset(row, col + 8)),
-                       "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
+          asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a_hi + (off ^ 16u)), "r"(w[4]), "r"(w[5]),
+                       "r"(w[6]), "r"(w[7])
                        : "memory");
         }
       }
     };
+    // k-steps of this CTA over all its tiles
+    int64_t total = 0;
+    if (!p.units) {
+      const int64_t mine = tiles > blockIdx.x ? (tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+      total = mine * ksteps(tile_info(p, 0));
+    } else {
+      for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) total += ksteps(tile_info(p, t));
+    }
     // Two register buffers in ping-pong: the loads of k-step t + 1 are issued
     // before k-step t is converted and consumed one full iteration later (a
     // register copy out of a prefetch buffer would wait for them at once).
-    // The tile's fields are re-read from the parameters (or the table) when
-    // needed rather than held in registers across iterations.
-    int64_t tile = blockIdx.x;
-    int ks = 0, nks = 0;
     int64_t step = 0;
-    auto body = [&](const uint4 (&cur)[C::NV], uint4 (&nxt)[C::NV]) -> bool {
-      int64_t ntile = tile;
-      int nks_next = ks + 1;
-      int nks_n = nks;
-      if (nks_next >= nks) {
-        nks_next = 0;
-        ntile += gridDim.x;
-      }
-      const bool more = ntile < tiles;
-      if (more) {
-        const TileInfo tn = tile_info(p, ntile);
-        if (ntile != tile) nks_n = ksteps(tn);
-        load(tn, nks_next, nxt);
-      }
-      const int s = (int)(step % STAGES);
-      const uint32_t ph = (uint32_t)((step / STAGES) & 1);
+    uint32_t s = 0, ph = 0;
+    int slot = 0;
+    auto body = [&](const uint4 (&cur)[C::NV], int cvc, uint4 (&nxt)[C::NV], int& nvc) -> bool {
+      if (step + 1 < total) issue(nxt, nvc);
       if (!ptx::mbar_wait(&empty[s], ph ^ 1u, kWaitNs)) {
         fail();
         return false;
       }
       if (aborted()) return false;
-      store(cur, sbase + s * C::STAGE_BYTES, (int)(step % C::RING), ks, tile_info(p, tile).n);
+      store(cur, sbase + s * C::STAGE_BYTES, slot, cvc);
       ptx::fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) ptx::mbar_arrive(&full[s]);
-      ++step;
-      if (!more) return false;
-      tile = ntile;
-      ks = nks_next;
-      nks = nks_n;
-      return true;
+      if (++s == (uint32_t)STAGES) {
+        s = 0;
+        ph ^= 1u;
+      }
+      if (++slot == C::RING) slot = 0;
+      return ++step < total;
     };
     uint4 ra[C::NV], rb[C::NV];
-    if (tile < tiles) {
-      const TileInfo t0 = tile_info(p, tile);
-      nks = ksteps(t0);
-      load(t0, ks, ra);
-      while (body(ra, rb) && body(rb, ra)) {
+    int va = 0, vb = 0;
+    if (total > 0) {
+      enter();
+      issue(ra, va);
+      while (body(ra, va, rb, vb) && body(rb, vb, ra, va)) {
       }
     }
+    xb = max(xb, max(xb2 >> 16, xb2 & 0xffffu) << 16);  // BF16 bits widen to FP32 bits
     if (p.xmax) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) xb = max(xb, __shfl_xor_sync(0xffffffffu, xb, o));
