@@ -220,13 +220,13 @@ def serve_bench(L, S, torch, local: int, seconds: float, load: float = 0.8, seed
                           "capacity_req_s": 1.0 / svc.mean()}}
 
 
-# DRAM bytes (read + write) per row of X of one launch, from one ncu capture at
-# 50,000 rows of the same workload (profiles/sketch_sparse4_fp32_50000x4096.md,
-# profiles/chain_kernel_fp32_50000x4096.md); traffic grows in proportion to the
-# rows.  Set an entry to None when its kernel changes until it is captured again.
+# DRAM bytes (read + write) per row of X of one launch, from one ncu capture
+# (--set full) at 50,000 rows of the same workload; traffic grows in
+# proportion to the rows.  Set an entry to None when its kernel changes, until
+# it is captured again.
 TRAFFIC_PER_ROW = {
-    "sketch": None,
-    "chain_main": (846.242048e6 + 24.446976e6) / 50000,
+    "sketch": (820.3392e6 + 8.600576e6) / 50000,
+    "chain_main": (844.953088e6 + 25.067264e6) / 50000,
 }
 
 

@@ -13,7 +13,8 @@
 // E_ij = (s_ij + lambda_j r_ij) / (lambda_j - lambda_i) for separated pairs,
 // r_ij / 2 inside clusters, and updates X <- X + X E; it converges
 // quadratically; the cluster test here is per pair, see refine_e_kernel).
-// H, the refinement and V = F^T W D^-1 are FP64 throughout.
+// H and the refinement are FP64; V = F^T W D^-1 is an FP64 product for an
+// FP64 V and an FP32 product of the FP64 factors for an FP32 V.
 #include "common.cuh"
 #include "kernels.h"
 
