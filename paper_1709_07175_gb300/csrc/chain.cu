@@ -22,8 +22,9 @@
 // zeros).  For BF16 X and for the Gram the B operand is loaded the same way
 // and the kernel has no converter warps; FP32 and E4M3 X are converted by
 // converter warps that load X rows with 16-byte global loads one step ahead
-// (two register buffers in ping-pong).  (Bulk L2 prefetches of the rows a few
-// steps ahead were measured on GB300 to slow this pass down by a third.)
+// (two register buffers in ping-pong).  (L2 prefetches of the rows a few steps
+// ahead were measured on GB300 to slow this pass down: bulk prefetches by a
+// third, per-thread line prefetches two steps ahead by 6 %.)
 //
 // Accumulation.  Measured on GB300, the FP32 accumulation of tcgen05.mma into
 // TMEM behaves like round-toward-zero (its error is biased and grows with the

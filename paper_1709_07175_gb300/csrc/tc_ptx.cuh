@@ -247,6 +247,11 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr, uint32_t lbo, uin
   return d;
 }
 
+// Hint: bring the 128-byte line holding `p` into L2 (no register result).
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // The descriptor of the same operand layout `bytes` further on: the start
 // address field holds address >> 4 (shared-memory addresses stay below 2^18,
 // so the field does not carry into the next one).

@@ -51,6 +51,7 @@ namespace lspca {
 namespace tcp {
 
 constexpr int BK = 64;
+constexpr int kPrefetchSteps = 2;  // L2 prefetch distance of the converters, in k-steps
 constexpr uint64_t kWaitNs = 2000000000ull;
 constexpr uint64_t kDrainNs = 100000000ull;
 
@@ -304,6 +305,13 @@ __global__ void __launch_bounds__(Cfg<XK, NT, EXACT_V>::THREADS, 1) project_kern
             dst[q] = make_uint4(0u, 0u, 0u, 0u);
           }
         }
+      }
+      // L2 prefetch of this thread's rows two k-steps ahead (one per 128-byte
+      // line; within the tile's rows, and short of a partial last k-step)
+      if (lk + kPrefetchSteps < lnk - (int)((ln & (BK - 1)) != 0) && ((cw * C::ES) & 127) == 0) {
+#pragma unroll
+        for (int q = 0; q < C::NV; ++q)
+          if (r0 + RSTEP * q < lrows) ptx::prefetch_l2(lp + kPrefetchSteps * BK * C::ES + q * lrs);
       }
       lp += BK * C::ES;
       if (++lk >= lnk) {
