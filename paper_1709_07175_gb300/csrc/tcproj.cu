@@ -632,6 +632,351 @@ __global__ void tile_v_kernel(const float* __restrict__ V, int64_t n, int k, int
   }
 }
 
+// ---------------------------------------------------------------------------
+// The sketch U = X Omega of FP32 X against the very sparse Omega (exact in one
+// BF16 piece), k <= 128, with the A operand in tensor memory.
+//
+// Same arithmetic as project_kernel's three-piece path (x = x0 + x1 + x2, each
+// an exact BF16 piece; three products per 16-column slice; segments of SEG
+// k-steps folded into a round-to-nearest FP32 sum), but the converter warps
+// write the pieces straight into TMEM with tcgen05.st and the MMA reads A from
+// there, so the pieces never pass through shared memory: the tensor core's
+// shared-memory reads (B only) no longer compete with converter stores.  The
+// running sum S moves to shared memory (row-private, padded rows), which frees
+// TMEM for a double-buffered accumulator plus the A stages.
+//
+// Thread mapping: converter warp w owns TMEM lane quarter w % 4 (tile rows
+// 32 (w % 4) .. + 31, one row per lane) and the 16 columns 16 (w / 4) .. + 15
+// of every 64-column k-step: two 32-byte loads of its row per k-step, one
+// 16-column MMA slice (8 TMEM columns) per piece.
+//
+// TMEM columns: [0, 2 NPAD) accumulators D0, D1; then A_STAGES stages of
+// 3 pieces x 32 columns.  Warps: 16 converters, 4 epilogue (one per lane
+// quarter), the MMA issuer (also allocates TMEM), a producer (bulk copy of
+// each k-step's Omega tile).  Waits are bounded as in project_kernel.
+namespace sk {
+constexpr int CW = 16, EW_N = 4, EPI0 = 16, MMA_W = 20, PROD_W = 21;
+constexpr int THREADS = 22 * 32;
+constexpr int SEG = 8;
+}  // namespace sk
+
+template <int NT>
+struct SkCfg {
+  static constexpr int NPAD = 64 * NT;
+  static constexpr uint32_t B_BYTES = BK * NPAD * 2;
+  static constexpr uint32_t SBO_B = NT * 1024;
+  static constexpr int B_STAGES = 6;
+  static constexpr uint32_t ACOL0 = 2 * NPAD;  // first A column
+  static constexpr int A_STAGES = (512 - 2 * NPAD) / 96 < 4 ? (512 - 2 * NPAD) / 96 : 4;
+  static constexpr int SST = NPAD + 4;  // floats per row of S (padding spreads the rows over the banks)
+  static constexpr size_t SMEM = 1024 + (size_t)B_STAGES * B_BYTES + (size_t)128 * SST * 4 + 512;
+  static_assert(ACOL0 + A_STAGES * 96 <= 512, "TMEM budget");
+  static_assert(A_STAGES >= 2, "A stages");
+};
+
+template <int NT>
+__global__ void __launch_bounds__(sk::THREADS, 1) sketch_tmem_kernel(Params p) {
+  using C = SkCfg<NT>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  float* Ssm = reinterpret_cast<float*>(smem + C::B_STAGES * C::B_BYTES);
+  uint64_t* fullA = reinterpret_cast<uint64_t*>(Ssm + 128 * C::SST);
+  uint64_t* emptyA = fullA + C::A_STAGES;
+  uint64_t* fullB = emptyA + C::A_STAGES;
+  uint64_t* emptyB = fullB + C::B_STAGES;
+  uint64_t* accf = emptyB + C::B_STAGES;  // [2]
+  uint64_t* acce = accf + 2;              // [2]
+  uint64_t* drain = acce + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t tiles = (p.m + 127) / 128;
+  const int nks = (int)((p.n + BK - 1) / BK);
+  if (tid == 0) {
+    for (int s = 0; s < C::A_STAGES; ++s) {
+      ptx::mbar_init(&fullA[s], sk::CW);
+      ptx::mbar_init(&emptyA[s], 1);
+    }
+    for (int s = 0; s < C::B_STAGES; ++s) {
+      ptx::mbar_init(&fullB[s], 1);
+      ptx::mbar_init(&emptyB[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      ptx::mbar_init(&accf[b], 1);
+      ptx::mbar_init(&acce[b], sk::EW_N);
+    }
+    ptx::mbar_init(drain, 1);
+    *abort_flag = 0;
+    ptx::fence_mbar_init();
+  }
+  if (warp == sk::MMA_W) ptx::tmem_alloc(tmem_slot, 512);
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t sbase = ptx::smem_u32(smem);
+  auto fail = [&]() {
+    atomicOr(p.status, ST_TIMEOUT);
+    atomicExch(abort_flag, 1);
+  };
+  auto aborted = [&]() { return *(volatile int*)abort_flag != 0; };
+  const int64_t my_tiles = tiles > blockIdx.x ? (tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int64_t total = my_tiles * nks;  // k-steps of this CTA
+
+  if (warp == sk::PROD_W) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      int64_t step = 0;
+      uint32_t s = 0, ph = 0;
+      int ks = 0;
+      for (; step < total; ++step) {
+        if (!ptx::mbar_wait(&emptyB[s], ph ^ 1u, kWaitNs)) {
+          fail();
+          break;
+        }
+        if (aborted()) break;
+        ptx::mbar_arrive_expect_tx(&fullB[s], C::B_BYTES);
+        ptx::bulk_g2s(sbase + s * C::B_BYTES, p.vt + (size_t)ks * 2 * C::B_BYTES, C::B_BYTES, &fullB[s]);
+        if (++ks == nks) ks = 0;
+        if (++s == (uint32_t)C::B_STAGES) {
+          s = 0;
+          ph ^= 1u;
+        }
+      }
+      // bounded wait for the copies of the last stages issued
+      for (int64_t w = step - 1; w >= 0 && w >= step - C::B_STAGES; --w)
+        ptx::mbar_wait(&fullB[w % C::B_STAGES], (uint32_t)((w / C::B_STAGES) & 1), kDrainNs);
+    }
+    __syncwarp();
+  } else if (warp < sk::CW) {
+    // ------------------------------------------------------------ converters
+    const int qd = warp & 3, j = warp >> 2;
+    const uint32_t lane_base = (uint32_t)(32 * qd) << 16;
+    const int r = 32 * qd + lane;  // row of the tile
+    const int64_t rb = p.ldx * 4;  // row bytes
+    uint32_t xb2 = 0u;
+    // load cursor: tile lt, k-step lk
+    int64_t lt = blockIdx.x;
+    int lk = 0;
+    auto issue = [&](float (&v)[16]) {
+      const int64_t row = lt * 128 + r;
+      const int64_t c = (int64_t)lk * BK + 16 * j;
+      const float* src = reinterpret_cast<const float*>((const uint8_t*)p.X + row * rb) + c;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (row < p.m && c + 8 * h < p.n) {
+          asm volatile("ld.global.nc.L1::no_allocate.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                       : "=f"(v[8 * h + 0]), "=f"(v[8 * h + 1]), "=f"(v[8 * h + 2]), "=f"(v[8 * h + 3]),
+                         "=f"(v[8 * h + 4]), "=f"(v[8 * h + 5]), "=f"(v[8 * h + 6]), "=f"(v[8 * h + 7])
+                       : "l"(src + 8 * h));
+          if (c + 8 * h + 8 > p.n) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+              if (c + 8 * h + u >= p.n) v[8 * h + u] = 0.f;
+          }
+        } else {
+#pragma unroll
+          for (int u = 0; u < 8; ++u) v[8 * h + u] = 0.f;
+        }
+      }
+      // L2 prefetch of the row's segment two k-steps ahead (one per 128-byte
+      // line: the warps with j even start a line)
+      if ((j & 1) == 0 && lk + kPrefetchSteps < nks - (int)((p.n & (BK - 1)) != 0) && row < p.m)
+        ptx::prefetch_l2(src + kPrefetchSteps * BK);
+      if (++lk == nks) {
+        lk = 0;
+        lt += gridDim.x;
+      }
+    };
+    int64_t step = 0;
+    uint32_t s = 0, ph = 0;
+    auto body = [&](const float (&cur)[16], float (&nxt)[16]) -> bool {
+      if (step + 1 < total) issue(nxt);
+      uint32_t p0[8], p1[8], p2[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) split_b3(cur[2 * u], cur[2 * u + 1], p0[u], p1[u], p2[u]);
+#pragma unroll
+      for (int u = 0; u < 8; u += 2) xb2 = __vmaxu2(xb2, __vmaxu2(p0[u] & 0x7fff7fffu, p0[u + 1] & 0x7fff7fffu));
+      if (!ptx::mbar_wait(&emptyA[s], ph ^ 1u, kWaitNs)) {
+        fail();
+        return false;
+      }
+      if (aborted()) return false;
+      ptx::tc_fence_after();
+      const uint32_t ta = tmem + lane_base + C::ACOL0 + s * 96 + 8 * j;
+      ptx::tmem_st8(ta, p0);
+      ptx::tmem_st8(ta + 32, p1);
+      ptx::tmem_st8(ta + 64, p2);
+      ptx::tmem_wait_st();
+      ptx::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive(&fullA[s]);
+      if (++s == (uint32_t)C::A_STAGES) {
+        s = 0;
+        ph ^= 1u;
+      }
+      return ++step < total;
+    };
+    float va[16], vb[16];
+    if (total > 0) {
+      issue(va);
+      while (body(va, vb) && body(vb, va)) {
+      }
+    }
+    uint32_t xb = max(xb2 >> 16, xb2 & 0xffffu) << 16;  // BF16 bits widen to FP32 bits
+    if (p.xmax) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) xb = max(xb, __shfl_xor_sync(0xffffffffu, xb, o));
+      if (lane == 0) {
+        if (xb >= 0x7f800000u) atomicOr(p.status, ST_NONFINITE);
+        else atomic_max_nonneg(p.xmax, __uint_as_float(xb));
+      }
+    }
+  } else if (warp == sk::MMA_W) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      constexpr uint32_t idesc = ptx::idesc_f16(1, 128, C::NPAD, 0, 1);
+      int64_t step = 0, seg = 0;
+      uint32_t sa = 0, pa = 0, sb = 0, pb = 0;
+      bool ok = true;
+      for (int64_t t = 0; t < my_tiles && ok; ++t) {
+        for (int ks = 0; ks < nks && ok; ++ks, ++step) {
+          const bool seg_start = (ks % sk::SEG) == 0;
+          const int ab = (int)(seg & 1);
+          if (seg_start) {
+            if (!ptx::mbar_wait(&acce[ab], (uint32_t)(((seg >> 1) & 1) ^ 1), kWaitNs)) {
+              fail();
+              ok = false;
+              break;
+            }
+            ptx::tc_fence_after();
+          }
+          if (!ptx::mbar_wait(&fullB[sb], pb, kWaitNs) || !ptx::mbar_wait(&fullA[sa], pa, kWaitNs) || aborted()) {
+            if (!aborted()) fail();
+            ok = false;
+            break;
+          }
+          ptx::tc_fence_after();
+          const uint32_t d = tmem + (uint32_t)(ab * C::NPAD);
+          const uint64_t bd0 = ptx::desc_sw128(sbase + sb * C::B_BYTES, 1024, C::SBO_B);
+          const uint32_t a0 = tmem + C::ACOL0 + sa * 96;
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            const uint64_t bd = ptx::desc_advance(bd0, kk * 2 * C::SBO_B);
+#pragma unroll
+            for (int pc = 0; pc < 3; ++pc)
+              ptx::mma_f16_ts(d, a0 + pc * 32 + kk * 8, bd, idesc, (seg_start && kk == 0 && pc == 0) ? 0u : 1u);
+          }
+          ptx::mma_commit(&emptyA[sa]);
+          ptx::mma_commit(&emptyB[sb]);
+          if (++sa == (uint32_t)C::A_STAGES) {
+            sa = 0;
+            pa ^= 1u;
+          }
+          if (++sb == (uint32_t)C::B_STAGES) {
+            sb = 0;
+            pb ^= 1u;
+          }
+          if ((ks % sk::SEG) == sk::SEG - 1 || ks == nks - 1) {
+            ptx::mma_commit(&accf[ab]);
+            ++seg;
+          }
+        }
+      }
+      ptx::mma_commit(drain);
+      if (!ptx::mbar_wait(drain, 0u, kWaitNs)) atomicOr(p.status, ST_TIMEOUT);
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int e = warp & 3;  // TMEM lane quarter (EPI0 is a multiple of 4)
+    const uint32_t lane_base = (uint32_t)(32 * e) << 16;
+    const int row = 32 * e + lane;
+    float* srow = Ssm + row * C::SST;
+    const int nseg = (nks + sk::SEG - 1) / sk::SEG;
+    uint32_t yb = 0u;
+    int64_t seg = 0;
+    bool ok = true;
+    for (int64_t t = 0; t < my_tiles && ok; ++t) {
+      const int64_t grow = (blockIdx.x + t * gridDim.x) * 128 + row;
+      for (int g = 0; g < nseg; ++g, ++seg) {
+        const int ab = (int)(seg & 1);
+        if (!ptx::mbar_wait(&accf[ab], (uint32_t)((seg >> 1) & 1), kWaitNs) || aborted()) {
+          if (!aborted()) fail();
+          ok = false;
+          break;
+        }
+        ptx::tc_fence_after();
+        const bool first = g == 0, last = g == nseg - 1;
+        const uint32_t abase = tmem + lane_base + (uint32_t)(ab * C::NPAD);
+#pragma unroll 1
+        for (int cc = 0; cc < C::NPAD; cc += 16) {
+          uint32_t a[16];
+          ptx::tmem_ld16_nowait(abase + (uint32_t)cc, a);
+          ptx::tmem_wait_ld(a);
+          float y[16];
+          if (first) {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) y[q] = __uint_as_float(a[q]);
+          } else {
+#pragma unroll
+            for (int q = 0; q < 16; q += 4) {
+              const float4 sv = *reinterpret_cast<const float4*>(srow + cc + q);
+              y[q] = sv.x + __uint_as_float(a[q]);
+              y[q + 1] = sv.y + __uint_as_float(a[q + 1]);
+              y[q + 2] = sv.z + __uint_as_float(a[q + 2]);
+              y[q + 3] = sv.w + __uint_as_float(a[q + 3]);
+            }
+          }
+          if (!last) {
+#pragma unroll
+            for (int q = 0; q < 16; q += 4)
+              *reinterpret_cast<float4*>(srow + cc + q) = make_float4(y[q], y[q + 1], y[q + 2], y[q + 3]);
+          } else if (grow < p.m) {
+            float* dst = p.Y + grow * p.k + cc;
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+              if (cc + q < p.k) yb = max(yb, __float_as_uint(y[q]) & 0x7fffffffu);
+            if (cc + 16 <= p.k && (p.k % 4) == 0) {
+#pragma unroll
+              for (int q = 0; q < 16; q += 4)
+                *reinterpret_cast<float4*>(dst + q) = make_float4(y[q], y[q + 1], y[q + 2], y[q + 3]);
+            } else {
+#pragma unroll
+              for (int q = 0; q < 16; ++q)
+                if (cc + q < p.k) dst[q] = y[q];
+            }
+          }
+        }
+        ptx::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(&acce[ab]);
+      }
+    }
+    if (p.ymax) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) yb = max(yb, __shfl_xor_sync(0xffffffffu, yb, o));
+      if (lane == 0 && yb < 0x7f800000u) atomic_max_nonneg(p.ymax, __uint_as_float(yb));
+    }
+  }
+  __syncthreads();
+  if (warp == sk::MMA_W) {
+    ptx::tc_fence_after();
+    ptx::tmem_dealloc(tmem, 512);
+  }
+}
+
+template <int NT>
+static void launch_sketch_tmem(Launcher& L, const Params& p) {
+  using C = SkCfg<NT>;
+  cudaFuncSetAttribute(sketch_tmem_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+  const int64_t tiles = (p.m + 127) / 128;
+  const int grid = (int)(tiles < L.num_sms ? (tiles > 0 ? tiles : 1) : L.num_sms);
+  sketch_tmem_kernel<NT><<<grid, sk::THREADS, C::SMEM, L.stream>>>(p);
+  L.count(1);
+}
+
 template <int XK, int NT, bool EXACT_V>
 static void launch_project(Launcher& L, const Params& p, int max_tiles) {
   using C = Cfg<XK, NT, EXACT_V>;
@@ -672,6 +1017,15 @@ void plan_tc_project(char* base, TcProjectWs& w, int xt, int64_t n, int k) {
 
 namespace tcp {
 static void launch_xt(Launcher& L, const Params& p, int xt, int nt, int max_tiles, bool exact_v) {
+  // FP32 X against an exact V (the sketch with the very sparse Omega), k <= 128,
+  // one matrix with 32-byte aligned rows and n a multiple of 8 (whole 32-byte
+  // loads): A in TMEM
+  if (exact_v && xt == LSPCA_F32 && nt <= 2 && !p.units && ((uintptr_t)p.X % 32) == 0 && (p.ldx % 8) == 0 &&
+      (p.n % 8) == 0) {
+    if (nt == 1) launch_sketch_tmem<1>(L, p);
+    else launch_sketch_tmem<2>(L, p);
+    return;
+  }
   if (exact_v) {
     if (xt == LSPCA_F32) launch_project_nt<XK_F32, true>(L, p, nt, max_tiles);
     else if (xt == LSPCA_BF16) launch_project_nt<XK_BF16, true>(L, p, nt, max_tiles);

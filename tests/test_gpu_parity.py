@@ -114,13 +114,18 @@ def test_sketch_sparse_fp32(ctx, data, wl):
 
 @pytest.mark.parametrize("dtype,m,n,ldx,k", [(torch.float32, 777, 1001, 1004, 64),
                                              (torch.float32, 300, 4096, 4096, 128),
+                                             (torch.float32, 1100, 1000, 1000, 64),
+                                             (torch.float32, 515, 2040, 2056, 100),
                                              (torch.bfloat16, 515, 1003, 1008, 100),
                                              (torch.bfloat16, 129, 2048, 2048, 128)])
 def test_sketch_sparse_strided_and_ragged(ctx, dtype, m, n, ldx, k):
     """Pass S of the very sparse Omega on FP32 / BF16 X with ragged row tiles,
     a ragged last column step (n not a multiple of the copy width, X rows
     padded to ldx) and k not a multiple of 16: the FP32 gather sum is within
-    the sequential-summation bound of the FP64 oracle."""
+    the sequential-summation bound of the FP64 oracle.  The FP32 cases with n
+    and ldx multiples of 8 run the kernel that keeps its A operand in tensor
+    memory (k = 64: one 64-column N tile; k = 100: two), the others the
+    shared-memory one."""
     w = S.WORKLOADS["fp32_sparse"].scaled(m=m, n=ldx, k=k)
     base = S.generate(w).to(dtype)
     X = base.cuda()[:, :n]  # row-strided view, ldx > n where the two differ
