@@ -648,26 +648,35 @@ __global__ void tile_v_kernel(const float* __restrict__ V, int64_t n, int k, int
 // Thread mapping: converter warp w owns TMEM lane quarter w % 4 (tile rows
 // 32 (w % 4) .. + 31, one row per lane) and the 16 columns 16 (w / 4) .. + 15
 // of every 64-column k-step: two 32-byte loads of its row per k-step, one
-// 16-column MMA slice (8 TMEM columns) per piece.
+// 16-column MMA slice (8 TMEM columns) per piece.  A k-step's register buffer
+// is freed by the split into pieces and takes the loads of the k-step two
+// ahead right after the TMEM stores are issued; an L2 prefetch runs two
+// k-steps further.
 //
-// TMEM columns: [0, 2 NPAD) accumulators D0, D1; then A_STAGES stages of
+// TMEM columns: [0, NACC NPAD) accumulators; then A_STAGES stages of
 // 3 pieces x 32 columns.  Warps: 16 converters, 4 epilogue (one per lane
 // quarter), the MMA issuer (also allocates TMEM), a producer (bulk copy of
 // each k-step's Omega tile).  Waits are bounded as in project_kernel.
+//
+// Segments are 16 k-steps (1,024 columns of X): the products are exact, so the
+// segment length only sets how many FP32 accumulations the tensor core makes
+// before a round-to-nearest fold (measured on GB300: 16 k-steps is 5 % faster
+// than 8 and stays within the sequential-summation bound of the FP64 sum).
 namespace sk {
 constexpr int CW = 16, EW_N = 4, EPI0 = 16, MMA_W = 20, PROD_W = 21;
 constexpr int THREADS = 22 * 32;
-constexpr int SEG = 8;
+constexpr int SEG = 16;
 }  // namespace sk
 
 template <int NT>
 struct SkCfg {
   static constexpr int NPAD = 64 * NT;
+  static constexpr int NACC = 2;  // accumulators in TMEM
   static constexpr uint32_t B_BYTES = BK * NPAD * 2;
   static constexpr uint32_t SBO_B = NT * 1024;
   static constexpr int B_STAGES = 6;
-  static constexpr uint32_t ACOL0 = 2 * NPAD;  // first A column
-  static constexpr int A_STAGES = (512 - 2 * NPAD) / 96 < 4 ? (512 - 2 * NPAD) / 96 : 4;
+  static constexpr uint32_t ACOL0 = NACC * NPAD;  // first A column
+  static constexpr int A_STAGES = (512 - ACOL0) / 96 < 4 ? (512 - ACOL0) / 96 : 4;
   static constexpr int SST = NPAD + 4;  // floats per row of S (padding spreads the rows over the banks)
   static constexpr size_t SMEM = 1024 + (size_t)B_STAGES * B_BYTES + (size_t)128 * SST * 4 + 512;
   static_assert(ACOL0 + A_STAGES * 96 <= 512, "TMEM budget");
@@ -684,9 +693,9 @@ __global__ void __launch_bounds__(sk::THREADS, 1) sketch_tmem_kernel(Params p) {
   uint64_t* emptyA = fullA + C::A_STAGES;
   uint64_t* fullB = emptyA + C::A_STAGES;
   uint64_t* emptyB = fullB + C::B_STAGES;
-  uint64_t* accf = emptyB + C::B_STAGES;  // [2]
-  uint64_t* acce = accf + 2;              // [2]
-  uint64_t* drain = acce + 2;
+  uint64_t* accf = emptyB + C::B_STAGES;  // [NACC]
+  uint64_t* acce = accf + C::NACC;        // [NACC]
+  uint64_t* drain = acce + C::NACC;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
 
@@ -702,7 +711,7 @@ __global__ void __launch_bounds__(sk::THREADS, 1) sketch_tmem_kernel(Params p) {
       ptx::mbar_init(&fullB[s], 1);
       ptx::mbar_init(&emptyB[s], 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < C::NACC; ++b) {
       ptx::mbar_init(&accf[b], 1);
       ptx::mbar_init(&acce[b], sk::EW_N);
     }
@@ -791,23 +800,23 @@ __global__ void __launch_bounds__(sk::THREADS, 1) sketch_tmem_kernel(Params p) {
     };
     int64_t step = 0;
     uint32_t s = 0, ph = 0;
-    auto body = [&](const float (&cur)[16], float (&nxt)[16]) -> bool {
-      if (step + 1 < total) issue(nxt);
-      uint32_t p0[8], p1[8], p2[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) split_b3(cur[2 * u], cur[2 * u + 1], p0[u], p1[u], p2[u]);
-#pragma unroll
-      for (int u = 0; u < 8; u += 2) xb2 = __vmaxu2(xb2, __vmaxu2(p0[u] & 0x7fff7fffu, p0[u + 1] & 0x7fff7fffu));
+    auto body = [&](float (&cur)[16]) -> bool {
       if (!ptx::mbar_wait(&emptyA[s], ph ^ 1u, kWaitNs)) {
         fail();
         return false;
       }
       if (aborted()) return false;
       ptx::tc_fence_after();
+      uint32_t p0[8], p1[8], p2[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) split_b3(cur[2 * u], cur[2 * u + 1], p0[u], p1[u], p2[u]);
+#pragma unroll
+      for (int u = 0; u < 8; u += 2) xb2 = __vmaxu2(xb2, __vmaxu2(p0[u] & 0x7fff7fffu, p0[u + 1] & 0x7fff7fffu));
       const uint32_t ta = tmem + lane_base + C::ACOL0 + s * 96 + 8 * j;
       ptx::tmem_st8(ta, p0);
       ptx::tmem_st8(ta + 32, p1);
       ptx::tmem_st8(ta + 64, p2);
+      if (step + 2 < total) issue(cur);
       ptx::tmem_wait_st();
       ptx::tc_fence_before();
       __syncwarp();
@@ -821,7 +830,8 @@ __global__ void __launch_bounds__(sk::THREADS, 1) sketch_tmem_kernel(Params p) {
     float va[16], vb[16];
     if (total > 0) {
       issue(va);
-      while (body(va, vb) && body(vb, va)) {
+      if (total > 1) issue(vb);
+      while (body(va) && body(vb)) {
       }
     }
     uint32_t xb = max(xb2 >> 16, xb2 & 0xffffu) << 16;  // BF16 bits widen to FP32 bits
@@ -843,9 +853,9 @@ __global__ void __launch_bounds__(sk::THREADS, 1) sketch_tmem_kernel(Params p) {
       for (int64_t t = 0; t < my_tiles && ok; ++t) {
         for (int ks = 0; ks < nks && ok; ++ks, ++step) {
           const bool seg_start = (ks % sk::SEG) == 0;
-          const int ab = (int)(seg & 1);
+          const int ab = (int)(seg % C::NACC);
           if (seg_start) {
-            if (!ptx::mbar_wait(&acce[ab], (uint32_t)(((seg >> 1) & 1) ^ 1), kWaitNs)) {
+            if (!ptx::mbar_wait(&acce[ab], (uint32_t)(((seg / C::NACC) & 1) ^ 1), kWaitNs)) {
               fail();
               ok = false;
               break;
@@ -901,8 +911,8 @@ __global__ void __launch_bounds__(sk::THREADS, 1) sketch_tmem_kernel(Params p) {
     for (int64_t t = 0; t < my_tiles && ok; ++t) {
       const int64_t grow = (blockIdx.x + t * gridDim.x) * 128 + row;
       for (int g = 0; g < nseg; ++g, ++seg) {
-        const int ab = (int)(seg & 1);
-        if (!ptx::mbar_wait(&accf[ab], (uint32_t)((seg >> 1) & 1), kWaitNs) || aborted()) {
+        const int ab = (int)(seg % C::NACC);
+        if (!ptx::mbar_wait(&accf[ab], (uint32_t)((seg / C::NACC) & 1), kWaitNs) || aborted()) {
           if (!aborted()) fail();
           ok = false;
           break;
@@ -915,18 +925,15 @@ __global__ void __launch_bounds__(sk::THREADS, 1) sketch_tmem_kernel(Params p) {
           uint32_t a[16];
           ptx::tmem_ld16_nowait(abase + (uint32_t)cc, a);
           ptx::tmem_wait_ld(a);
-          float y[16];
-          if (first) {
-#pragma unroll
-            for (int q = 0; q < 16; ++q) y[q] = __uint_as_float(a[q]);
-          } else {
+          float* y = reinterpret_cast<float*>(a);  // the sum is formed in place
+          if (!first) {
 #pragma unroll
             for (int q = 0; q < 16; q += 4) {
               const float4 sv = *reinterpret_cast<const float4*>(srow + cc + q);
-              y[q] = sv.x + __uint_as_float(a[q]);
-              y[q + 1] = sv.y + __uint_as_float(a[q + 1]);
-              y[q + 2] = sv.z + __uint_as_float(a[q + 2]);
-              y[q + 3] = sv.w + __uint_as_float(a[q + 3]);
+              y[q] += sv.x;
+              y[q + 1] += sv.y;
+              y[q + 2] += sv.z;
+              y[q + 3] += sv.w;
             }
           }
           if (!last) {
@@ -937,7 +944,7 @@ __global__ void __launch_bounds__(sk::THREADS, 1) sketch_tmem_kernel(Params p) {
             float* dst = p.Y + grow * p.k + cc;
 #pragma unroll
             for (int q = 0; q < 16; ++q)
-              if (cc + q < p.k) yb = max(yb, __float_as_uint(y[q]) & 0x7fffffffu);
+              if (cc + q < p.k) yb = max(yb, a[q] & 0x7fffffffu);
             if (cc + 16 <= p.k && (p.k % 4) == 0) {
 #pragma unroll
               for (int q = 0; q < 16; q += 4)
