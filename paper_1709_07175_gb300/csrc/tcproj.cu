@@ -633,14 +633,19 @@ __global__ void tile_v_kernel(const float* __restrict__ V, int64_t n, int k, int
 }
 
 // ---------------------------------------------------------------------------
-// The sketch U = X Omega of FP32 X against the very sparse Omega (exact in one
-// BF16 piece), k <= 128, with the A operand in tensor memory.
+// Y = X V for FP32 X and k <= 128 with the A operand in tensor memory: the
+// sketch U = X Omega against the very sparse Omega (PV = 1: Omega is exact in
+// one BF16 piece) and the reduction map Y = X V (PV = 3: V split exactly into
+// three BF16 pieces v = v0 + v1 + v2 by tile_v3_kernel).
 //
-// Same arithmetic as project_kernel's three-piece path (x = x0 + x1 + x2, each
-// an exact BF16 piece; three products per 16-column slice; segments of SEG
-// k-steps folded into a round-to-nearest FP32 sum), but the converter warps
-// write the pieces straight into TMEM with tcgen05.st and the MMA reads A from
-// there, so the pieces never pass through shared memory: the tensor core's
+// X is split into three exact BF16 pieces x = x0 + x1 + x2 as in
+// project_kernel's three-piece path.  PV = 1 takes the three products x_a v0;
+// PV = 3 takes the six products x_a v_b with a + b <= 2 (the three left out are
+// below 2^-24 |x| |v| together, under FP32 rounding of the product).  Every
+// product is exact; the tensor core accumulates segments of SEG k-steps,
+// folded into a round-to-nearest FP32 sum.  The converter warps write the
+// pieces straight into TMEM with tcgen05.st and the MMA reads A from there, so
+// the pieces never pass through shared memory: the tensor core's
 // shared-memory reads (B only) no longer compete with converter stores.  The
 // running sum S moves to shared memory (row-private, padded rows), which frees
 // TMEM for a double-buffered accumulator plus the A stages.
@@ -656,39 +661,62 @@ __global__ void tile_v_kernel(const float* __restrict__ V, int64_t n, int k, int
 // TMEM columns: [0, NACC NPAD) accumulators; then A_STAGES stages of
 // 3 pieces x 32 columns.  Warps: 16 converters, 4 epilogue (one per lane
 // quarter), the MMA issuer (also allocates TMEM), a producer (bulk copy of
-// each k-step's Omega tile).  Waits are bounded as in project_kernel.
+// each k-step's V tile, PV parts).  Waits are bounded as in project_kernel.
 //
-// Segments are 16 k-steps (1,024 columns of X): the products are exact, so the
-// segment length only sets how many FP32 accumulations the tensor core makes
-// before a round-to-nearest fold (measured on GB300: 16 k-steps is 5 % faster
-// than 8 and stays within the sequential-summation bound of the FP64 sum).
+// Segments.  The tensor core's FP32 accumulation truncates, so every
+// accumulating MMA that changes the sum costs up to an ulp of it.  PV = 1: 16
+// k-steps (1,024 columns of X) -- most products of the very sparse Omega are
+// zero and leave the sum unchanged; measured on GB300, 16 is 5 % faster than 8
+// and stays within the sequential-summation bound of the FP64 sum.  PV = 3: one
+// k-step, with the large product last (see prod_pieces): about four
+// full-size truncations per fold.
 namespace sk {
 constexpr int CW = 16, EW_N = 4, EPI0 = 16, MMA_W = 20, PROD_W = 21;
 constexpr int THREADS = 22 * 32;
-constexpr int SEG = 16;
 }  // namespace sk
 
-template <int NT>
+template <int NT, int PV>
 struct SkCfg {
+  static_assert(PV == 1 || PV == 3, "V pieces");
   static constexpr int NPAD = 64 * NT;
   static constexpr int NACC = 2;  // accumulators in TMEM
-  static constexpr uint32_t B_BYTES = BK * NPAD * 2;
+  static constexpr int SEG = PV == 1 ? 16 : 1;
+  static constexpr int NPROD = PV == 1 ? 3 : 6;
+  static constexpr uint32_t B_BYTES = BK * NPAD * 2;           // one part of a k-step's V tile
+  static constexpr uint32_t STAGE_B = PV * B_BYTES;             // the parts used
+  static constexpr uint32_t TILE_STRIDE = (PV == 1 ? 2 : 3) * B_BYTES;  // bytes per k-step in the tiles
   static constexpr uint32_t SBO_B = NT * 1024;
-  static constexpr int B_STAGES = 6;
+  static constexpr int B_STAGES = PV == 1 ? 6 : 3;
   static constexpr uint32_t ACOL0 = NACC * NPAD;  // first A column
   static constexpr int A_STAGES = (512 - ACOL0) / 96 < 4 ? (512 - ACOL0) / 96 : 4;
   static constexpr int SST = NPAD + 4;  // floats per row of S (padding spreads the rows over the banks)
-  static constexpr size_t SMEM = 1024 + (size_t)B_STAGES * B_BYTES + (size_t)128 * SST * 4 + 512;
+  static constexpr size_t SMEM = 1024 + (size_t)B_STAGES * STAGE_B + (size_t)128 * SST * 4 + 512;
   static_assert(ACOL0 + A_STAGES * 96 <= 512, "TMEM budget");
   static_assert(A_STAGES >= 2, "A stages");
+  static_assert(SMEM <= 227 * 1024, "shared memory");
 };
 
-template <int NT>
-__global__ void __launch_bounds__(sk::THREADS, 1) sketch_tmem_kernel(Params p) {
-  using C = SkCfg<NT>;
+// Pieces (a, b) of the products x_a v_b, in issue order: for PV = 3 the five
+// cross products first, smallest first, while the accumulator is small, and
+// x0 v0 last, so that only its four slices truncate at the full size of the
+// sum.
+__device__ __forceinline__ void prod_pieces(int q, int pv, int& a, int& b) {
+  if (pv == 1) {
+    a = q;
+    b = 0;
+  } else {
+    constexpr int A6[6] = {2, 1, 0, 1, 0, 0}, B6[6] = {0, 1, 2, 0, 1, 0};
+    a = A6[q];
+    b = B6[q];
+  }
+}
+
+template <int NT, int PV>
+__global__ void __launch_bounds__(sk::THREADS, 1) tmem_a_kernel(Params p) {
+  using C = SkCfg<NT, PV>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  float* Ssm = reinterpret_cast<float*>(smem + C::B_STAGES * C::B_BYTES);
+  float* Ssm = reinterpret_cast<float*>(smem + C::B_STAGES * C::STAGE_B);
   uint64_t* fullA = reinterpret_cast<uint64_t*>(Ssm + 128 * C::SST);
   uint64_t* emptyA = fullA + C::A_STAGES;
   uint64_t* fullB = emptyA + C::A_STAGES;
@@ -745,8 +773,8 @@ __global__ void __launch_bounds__(sk::THREADS, 1) sketch_tmem_kernel(Params p) {
           break;
         }
         if (aborted()) break;
-        ptx::mbar_arrive_expect_tx(&fullB[s], C::B_BYTES);
-        ptx::bulk_g2s(sbase + s * C::B_BYTES, p.vt + (size_t)ks * 2 * C::B_BYTES, C::B_BYTES, &fullB[s]);
+        ptx::mbar_arrive_expect_tx(&fullB[s], C::STAGE_B);
+        ptx::bulk_g2s(sbase + s * C::STAGE_B, p.vt + (size_t)ks * C::TILE_STRIDE, C::STAGE_B, &fullB[s]);
         if (++ks == nks) ks = 0;
         if (++s == (uint32_t)C::B_STAGES) {
           s = 0;
@@ -852,7 +880,7 @@ __global__ void __launch_bounds__(sk::THREADS, 1) sketch_tmem_kernel(Params p) {
       bool ok = true;
       for (int64_t t = 0; t < my_tiles && ok; ++t) {
         for (int ks = 0; ks < nks && ok; ++ks, ++step) {
-          const bool seg_start = (ks % sk::SEG) == 0;
+          const bool seg_start = (ks % C::SEG) == 0;
           const int ab = (int)(seg % C::NACC);
           if (seg_start) {
             if (!ptx::mbar_wait(&acce[ab], (uint32_t)(((seg / C::NACC) & 1) ^ 1), kWaitNs)) {
@@ -869,14 +897,17 @@ __global__ void __launch_bounds__(sk::THREADS, 1) sketch_tmem_kernel(Params p) {
           }
           ptx::tc_fence_after();
           const uint32_t d = tmem + (uint32_t)(ab * C::NPAD);
-          const uint64_t bd0 = ptx::desc_sw128(sbase + sb * C::B_BYTES, 1024, C::SBO_B);
+          const uint64_t bd0 = ptx::desc_sw128(sbase + sb * C::STAGE_B, 1024, C::SBO_B);
           const uint32_t a0 = tmem + C::ACOL0 + sa * 96;
 #pragma unroll
-          for (int kk = 0; kk < BK / 16; ++kk) {
-            const uint64_t bd = ptx::desc_advance(bd0, kk * 2 * C::SBO_B);
+          for (int q = 0; q < C::NPROD; ++q) {
+            int pa, pb;
+            prod_pieces(q, PV, pa, pb);
 #pragma unroll
-            for (int pc = 0; pc < 3; ++pc)
-              ptx::mma_f16_ts(d, a0 + pc * 32 + kk * 8, bd, idesc, (seg_start && kk == 0 && pc == 0) ? 0u : 1u);
+            for (int kk = 0; kk < BK / 16; ++kk)
+              ptx::mma_f16_ts(d, a0 + pa * 32 + kk * 8,
+                              ptx::desc_advance(bd0, kk * 2 * C::SBO_B + pb * C::B_BYTES), idesc,
+                              (seg_start && kk == 0 && q == 0) ? 0u : 1u);
           }
           ptx::mma_commit(&emptyA[sa]);
           ptx::mma_commit(&emptyB[sb]);
@@ -888,7 +919,7 @@ __global__ void __launch_bounds__(sk::THREADS, 1) sketch_tmem_kernel(Params p) {
             sb = 0;
             pb ^= 1u;
           }
-          if ((ks % sk::SEG) == sk::SEG - 1 || ks == nks - 1) {
+          if ((ks % C::SEG) == C::SEG - 1 || ks == nks - 1) {
             ptx::mma_commit(&accf[ab]);
             ++seg;
           }
@@ -904,7 +935,7 @@ __global__ void __launch_bounds__(sk::THREADS, 1) sketch_tmem_kernel(Params p) {
     const uint32_t lane_base = (uint32_t)(32 * e) << 16;
     const int row = 32 * e + lane;
     float* srow = Ssm + row * C::SST;
-    const int nseg = (nks + sk::SEG - 1) / sk::SEG;
+    const int nseg = (nks + C::SEG - 1) / C::SEG;
     uint32_t yb = 0u;
     int64_t seg = 0;
     bool ok = true;
@@ -921,14 +952,14 @@ __global__ void __launch_bounds__(sk::THREADS, 1) sketch_tmem_kernel(Params p) {
         const bool first = g == 0, last = g == nseg - 1;
         const uint32_t abase = tmem + lane_base + (uint32_t)(ab * C::NPAD);
 #pragma unroll 1
-        for (int cc = 0; cc < C::NPAD; cc += 16) {
-          uint32_t a[16];
-          ptx::tmem_ld16_nowait(abase + (uint32_t)cc, a);
+        for (int cc = 0; cc < C::NPAD; cc += 32) {
+          uint32_t a[32];
+          ptx::tmem_ld32_nowait(abase + (uint32_t)cc, a);
           ptx::tmem_wait_ld(a);
           float* y = reinterpret_cast<float*>(a);  // the sum is formed in place
           if (!first) {
 #pragma unroll
-            for (int q = 0; q < 16; q += 4) {
+            for (int q = 0; q < 32; q += 4) {
               const float4 sv = *reinterpret_cast<const float4*>(srow + cc + q);
               y[q] += sv.x;
               y[q + 1] += sv.y;
@@ -938,20 +969,20 @@ __global__ void __launch_bounds__(sk::THREADS, 1) sketch_tmem_kernel(Params p) {
           }
           if (!last) {
 #pragma unroll
-            for (int q = 0; q < 16; q += 4)
+            for (int q = 0; q < 32; q += 4)
               *reinterpret_cast<float4*>(srow + cc + q) = make_float4(y[q], y[q + 1], y[q + 2], y[q + 3]);
           } else if (grow < p.m) {
             float* dst = p.Y + grow * p.k + cc;
 #pragma unroll
-            for (int q = 0; q < 16; ++q)
+            for (int q = 0; q < 32; ++q)
               if (cc + q < p.k) yb = max(yb, a[q] & 0x7fffffffu);
-            if (cc + 16 <= p.k && (p.k % 4) == 0) {
+            if (cc + 32 <= p.k && (p.k % 4) == 0) {
 #pragma unroll
-              for (int q = 0; q < 16; q += 4)
+              for (int q = 0; q < 32; q += 4)
                 *reinterpret_cast<float4*>(dst + q) = make_float4(y[q], y[q + 1], y[q + 2], y[q + 3]);
             } else {
 #pragma unroll
-              for (int q = 0; q < 16; ++q)
+              for (int q = 0; q < 32; ++q)
                 if (cc + q < p.k) dst[q] = y[q];
             }
           }
@@ -974,14 +1005,47 @@ __global__ void __launch_bounds__(sk::THREADS, 1) sketch_tmem_kernel(Params p) {
   }
 }
 
-template <int NT>
-static void launch_sketch_tmem(Launcher& L, const Params& p) {
-  using C = SkCfg<NT>;
-  cudaFuncSetAttribute(sketch_tmem_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+template <int NT, int PV>
+static void launch_tmem_a(Launcher& L, const Params& p) {
+  using C = SkCfg<NT, PV>;
+  cudaFuncSetAttribute(tmem_a_kernel<NT, PV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
   const int64_t tiles = (p.m + 127) / 128;
   const int grid = (int)(tiles < L.num_sms ? (tiles > 0 ? tiles : 1) : L.num_sms);
-  sketch_tmem_kernel<NT><<<grid, sk::THREADS, C::SMEM, L.stream>>>(p);
+  tmem_a_kernel<NT, PV><<<grid, sk::THREADS, C::SMEM, L.stream>>>(p);
   L.count(1);
+}
+
+// Whether the tensor-memory kernel takes this FP32 X: one matrix, k <= 128,
+// 32-byte aligned rows and n a multiple of 8 (whole 32-byte loads).
+static bool tmem_a_ok(const Params& p, int nt) {
+  return nt <= 2 && !p.units && ((uintptr_t)p.X % 32) == 0 && (p.ldx % 8) == 0 && (p.n % 8) == 0;
+}
+
+// V (n x k FP32) -> per k-step tiles [v0 | v1 | v2] of three exact BF16
+// pieces (v = v0 + v1 + v2: the top 8 significand bits, then the top 8 of the
+// exact remainder, then the rest), in the MN-major SW128 layout of
+// tile_v_kernel, zero padded to NPAD columns and to whole k-steps.
+__global__ void tile_v3_kernel(const float* __restrict__ V, int64_t n, int k, int npad, uint8_t* __restrict__ out) {
+  const int nt = npad / 64;
+  const int nks = (int)((n + BK - 1) / BK);
+  const uint32_t sbo = nt * 1024;
+  const size_t part = (size_t)BK * npad * 2;
+  const int64_t total = (int64_t)nks * BK * npad;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e % npad);
+    const int64_t j = e / npad;  // global row of V
+    const int ks = (int)(j / BK), kr = (int)(j % BK);
+    const float v = (j < n && c < k) ? V[j * k + c] : 0.f;
+    const uint32_t b0 = __float_as_uint(v) & 0xffff0000u;
+    const float r = v - __uint_as_float(b0);
+    const uint32_t b1 = __float_as_uint(r) & 0xffff0000u;
+    const float r2 = r - __uint_as_float(b1);
+    uint8_t* base = out + (size_t)ks * 3 * part;
+    const uint32_t off = ptx::mn_sw128_offset(kr, c, sbo);
+    *reinterpret_cast<uint16_t*>(base + off) = (uint16_t)(b0 >> 16);
+    *reinterpret_cast<uint16_t*>(base + part + off) = (uint16_t)(b1 >> 16);
+    *reinterpret_cast<uint16_t*>(base + 2 * part + off) = (uint16_t)(__float_as_uint(r2) >> 16);
+  }
 }
 
 template <int XK, int NT, bool EXACT_V>
@@ -1016,7 +1080,7 @@ void plan_tc_project(char* base, TcProjectWs& w, int xt, int64_t n, int k) {
     off += b;
     return r;
   };
-  w.vhi = take((size_t)nks * 2 * tcp::BK * npad * 2);
+  w.vhi = take((size_t)nks * 3 * tcp::BK * npad * 2);  // two-part tiles, or three for the FP32 TMEM path
   w.vlo = take(256);  // scalars: [0] max|V|, [1] t
   w.bytes = off + 256;
   (void)xt;
@@ -1024,13 +1088,10 @@ void plan_tc_project(char* base, TcProjectWs& w, int xt, int64_t n, int k) {
 
 namespace tcp {
 static void launch_xt(Launcher& L, const Params& p, int xt, int nt, int max_tiles, bool exact_v) {
-  // FP32 X against an exact V (the sketch with the very sparse Omega), k <= 128,
-  // one matrix with 32-byte aligned rows and n a multiple of 8 (whole 32-byte
-  // loads): A in TMEM
-  if (exact_v && xt == LSPCA_F32 && nt <= 2 && !p.units && ((uintptr_t)p.X % 32) == 0 && (p.ldx % 8) == 0 &&
-      (p.n % 8) == 0) {
-    if (nt == 1) launch_sketch_tmem<1>(L, p);
-    else launch_sketch_tmem<2>(L, p);
+  // FP32 X against an exact V (the sketch with the very sparse Omega): A in TMEM
+  if (exact_v && xt == LSPCA_F32 && tmem_a_ok(p, nt)) {
+    if (nt == 1) launch_tmem_a<1, 1>(L, p);
+    else launch_tmem_a<2, 1>(L, p);
     return;
   }
   if (exact_v) {
@@ -1049,6 +1110,31 @@ void tc_project(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_
                 TcProjectWs& w, float* Y, int* status, bool exact_v, float* xmax, float* ymax) {
   const int npad = (k + 63) / 64 * 64;
   float* scal = (float*)w.vlo;
+  {
+    // FP32 X against a general V, k <= 128: V in three exact BF16 pieces, A in TMEM
+    tcp::Params p{};
+    p.X = X;
+    p.ldx = ldx;
+    p.m = m;
+    p.n = n;
+    p.k = k;
+    p.vt = (const uint8_t*)w.vhi;
+    p.Y = Y;
+    p.status = status;
+    p.xmax = xmax;
+    p.ymax = ymax;
+    if (xt == LSPCA_F32 && !exact_v && tcp::tmem_a_ok(p, npad / 64)) {
+      const int64_t nks = (n + tcp::BK - 1) / tcp::BK;
+      const int64_t total = nks * tcp::BK * npad;
+      int blocks = (int)((total + 255) / 256);
+      if (blocks > 16 * L.num_sms) blocks = 16 * L.num_sms;
+      tcp::tile_v3_kernel<<<blocks, 256, 0, L.stream>>>(V, n, k, npad, (uint8_t*)w.vhi);
+      L.count(1);
+      if (npad == 64) tcp::launch_tmem_a<1, 3>(L, p);
+      else tcp::launch_tmem_a<2, 3>(L, p);
+      return;
+    }
+  }
   const bool f16 = xt == LSPCA_F32 && !exact_v;  // FP32 X against an exact V takes BF16 tiles
   cudaMemsetAsync(scal, 0, 8, L.stream);
   if (f16) launch_scan_x(L, V, LSPCA_F32, n, k, k, scal, status);

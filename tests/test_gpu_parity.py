@@ -400,11 +400,14 @@ def test_alg4_slicing_invariance(ctx, data):
 # ------------------------------------------------------------------ tensor-core projection, all X types
 
 @pytest.mark.parametrize("dtype,k,m,n", [("f32", 20, 1000, 500), ("f32", 128, 3001, 4096), ("f32", 200, 777, 1000),
+                                         ("f32", 64, 1100, 1000), ("f32", 100, 515, 2040),
                                          ("bf16", 64, 2049, 1024), ("bf16", 256, 513, 2048),
                                          ("e4m3", 256, 1500, 4096), ("e4m3", 128, 4001, 1040)])
 def test_project_tensor_core_paths(ctx, dtype, k, m, n):
     """Y = X V against the FP64 product of the same stored values (relative Frobenius):
-    FP32 X split-FP16 (per-row scales) 2e-6; BF16 / E4M3 X with split-BF16 V 1e-5."""
+    FP32 X 2e-6 (k <= 128 with n a multiple of 8: X and V in three exact BF16
+    pieces each, six products, A in tensor memory; otherwise split-FP16 with
+    per-row scales); BF16 / E4M3 X with split-BF16 V 1e-5."""
     if dtype == "e4m3":
         w = S.WORKLOADS["e4m3_binary"].scaled(m=m, n=n, k=k)
     elif dtype == "bf16":
