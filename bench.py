@@ -439,7 +439,7 @@ def run_gpu(args):
             "project": {"ms_per_call": proj_ms, "samples_per_s": w.m / (proj_ms / 1e3),
                         "achieved_gbs": (x_bytes + u_bytes) / (proj_ms / 1e3) / 1e9,
                         "frac": (x_bytes + u_bytes) / (proj_ms / 1e3) / 1e9 / peak,
-                        "bytes_per_call": x_bytes + u_bytes, "kernel": "tcproj project_kernel (FP32 X, k=128)"},
+                        "bytes_per_call": x_bytes + u_bytes, "kernel": "tmem_a_kernel (FP32 X and V in three exact BF16 pieces, k=128)"},
             "e2e": {"value": w.m * ws / (e2e_ms / 1e3), "unit": "samples/s",
                     "h2d_bytes_per_step": x_bytes, "d2h_bytes_per_step": w.n * w.k * 4 + w.k * 8,
                     "ms_per_step": e2e_ms, "api": "lspca_fit_host (pinned host X, row slices overlapped)",
