@@ -596,8 +596,242 @@ __global__ void __launch_bounds__(kSeedThreads, 1) eig_seed_kernel(const double*
 
 size_t eig_seed_smem(int k) { return k <= 128 ? ((size_t)128 * k + (size_t)2 * k * k) * sizeof(float) : 0; }
 
-void launch_eig_seed(Launcher& L, const double* H, int k, float* gA, float* gZ, float* gQ, double* Xout,
+// ---------------------------------------------------------------------------
+// The same seed for k <= 128 in four launches, so that the steps that are
+// independent across eigenvalues or columns run on many SMs instead of one:
+//   seed_tri_kernel   (one CTA)        scale, load, steps 1 and the Gershgorin
+//                                      interval; reflectors and T to global;
+//   seed_bisect_kernel (k / 4 CTAs)    step 2, one warp per eigenvalue, 32
+//                                      interior points per round (6 rounds,
+//                                      33^6 >= 2^30: the resolution of 30
+//                                      halvings);
+//   seed_vec_kernel   (one CTA)        step 3, as in eig_seed_kernel;
+//   seed_back_kernel  (k / 8 CTAs)     step 4, one warp per column of Z: the
+//                                      reflectors applied one at a time with a
+//                                      warp reduction each, no block barrier.
+// Scratch `tri` (floats): d [0, k), e [k, 2k), e^2 [2k, 3k), beta [3k, 4k),
+// eigenvalues of T [4k, 5k), then gl, gu, ||T||, pivmin, 1 / scale (as two
+// floats: the FP64 max |H_ii| split hi + lo).  gA: reflector j in row j
+// (k x k, zero outside rows j+1 .. k-1); gZ: eigenvectors of T (k x k, column
+// i = vector i).
+
+__global__ void __launch_bounds__(kSeedThreads, 1) seed_tri_kernel(const double* __restrict__ H, int k, float* gV,
+                                                                float* tri, double* scal) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ float dv[256], ev[256], betav[256], wl[256];
+  __shared__ float gpart[kSeedThreads];
+  __shared__ __align__(16) float vperm[128], wperm[128];
+  __shared__ float rowbuf[128], vfl[128];
+  __shared__ double hmax_s;
+  __shared__ double hmx[kSeedThreads / 32];
+  __shared__ double redd[32];
+  float* A = reinterpret_cast<float*>(smem_raw);  // 128 x k: scaled H, then the reflectors (permuted rows)
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kSeedThreads / 32;
+  {
+    double mx = 0.0;
+    for (int i = tid; i < k; i += kSeedThreads) mx = fmax(mx, fabs(H[(int64_t)i * k + i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) hmx[warp] = mx;
+    __syncthreads();
+    if (tid == 0) {
+      double m2 = 0.0;
+      for (int i = 0; i < nw; ++i) m2 = fmax(m2, hmx[i]);
+      hmax_s = m2 > 0.0 ? m2 : 1.0;
+    }
+  }
+  __syncthreads();
+  const double sc = 1.0 / hmax_s;
+  double hf = 0.0;
+#pragma unroll 8
+  for (int e = tid; e < k * k; e += kSeedThreads) {
+    const double h = H[e];
+    hf += h * h;
+    A[e] = (float)(h * sc);
+  }
+  hf = warp_sum(hf);
+  if (lane == 0) redd[warp] = hf;
+  __syncthreads();
+  if (tid == 0) {
+    double sum = 0.0;
+    for (int i = 0; i < nw; ++i) sum += redd[i];
+    scal[1] = sqrt(sum);
+  }
+  __syncthreads();
+  tridiag_regs(A, k, A, dv, ev, betav, rowbuf, vfl, wl, vperm, wperm, gpart);
+  // reflectors to global in natural order, T and its Gershgorin interval
+  for (int e = tid; e < k * k; e += kSeedThreads) {
+    const int j = e / k, r = e % k;
+    gV[e] = A[j * 128 + perm_idx(r)];
+  }
+  for (int i = tid; i < k; i += kSeedThreads) {
+    tri[i] = dv[i];
+    tri[k + i] = ev[i];
+    tri[2 * k + i] = (i + 1 < k) ? ev[i] * ev[i] : 0.f;
+    tri[3 * k + i] = betav[i];
+  }
+  if (tid == 0) {
+    float gl = 1e30f, gu = -1e30f, tn = 0.f;
+    for (int i = 0; i < k; ++i) {
+      const float off = (i > 0 ? fabsf(ev[i - 1]) : 0.f) + (i + 1 < k ? fabsf(ev[i]) : 0.f);
+      gl = fminf(gl, dv[i] - off);
+      gu = fmaxf(gu, dv[i] + off);
+      tn = fmaxf(tn, fabsf(dv[i]) + off);
+    }
+    const float pad = 2.f * 1.2e-7f * tn + 1e-30f;
+    float* c = tri + 5 * k;
+    c[0] = gl - pad;
+    c[1] = gu + pad;
+    c[2] = tn;
+    c[3] = fmaxf(1e-30f, 1.2e-7f * 1e-6f * tn);  // pivmin
+    const float hi = (float)hmax_s;
+    c[4] = hi;
+    c[5] = (float)(hmax_s - (double)hi);
+  }
+}
+
+// One warp per eigenvalue idx (ascending): Sturm counts at 32 interior points
+// of the bracket per round.
+__global__ void __launch_bounds__(128) seed_bisect_kernel(int k, float* tri) {
+  __shared__ float d[128], e2[128];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    d[i] = tri[i];
+    e2[i] = tri[2 * k + i];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int idx = blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (idx >= k) return;
+  const float* c = tri + 5 * k;
+  const float pivmin = c[3];
+  float lo = c[0], hi = c[1];
+#pragma unroll 1
+  for (int it = 0; it < 6; ++it) {
+    const float x = lo + (hi - lo) * (float)(lane + 1) / 33.f;
+    const bool above = sturm_count(d, e2, k, x, pivmin) > idx;
+    const unsigned ball = __ballot_sync(0xffffffffu, above);
+    const int first = ball ? __ffs((int)ball) - 1 : 32;  // first point with count > idx
+    const float nlo = first == 0 ? lo : lo + (hi - lo) * (float)first / 33.f;
+    const float nhi = first == 32 ? hi : lo + (hi - lo) * (float)(first + 1) / 33.f;
+    lo = nlo;
+    hi = nhi;
+  }
+  if (lane == 0) tri[4 * k + idx] = 0.5f * (lo + hi);
+}
+
+// Step 3 of eig_seed_kernel (clusters, inverse iteration, Gram-Schmidt inside
+// clusters) for k <= 128: Z and the per-cluster scratch in shared memory.
+__global__ void __launch_bounds__(128, 1) seed_vec_kernel(int k, const float* __restrict__ tri, float* gZ,
+                                                        int32_t* nclusters) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ float dv[128], ev[128], lamv[128];
+  __shared__ int clstart[130];
+  float* Z = reinterpret_cast<float*>(smem_raw);  // k x k, column i = eigenvector i
+  float* Qs = Z + k * k;                          // one row per cluster
+  const int tid = threadIdx.x;
+  for (int i = tid; i < k; i += blockDim.x) {
+    dv[i] = tri[i];
+    ev[i] = tri[k + i];
+    lamv[i] = tri[4 * k + i];
+  }
+  __syncthreads();
+  const float tnorm = tri[5 * k + 2], pivmin = tri[5 * k + 3];
+  if (tid == 0) {
+    int nc = 0;
+    for (int i = 0; i < k; ++i)
+      if (i == 0 || lamv[i] - lamv[i - 1] > 1e-5f * tnorm) clstart[nc++] = i;
+    clstart[nc] = k;
+    clstart[129] = nc;
+    *nclusters = nc;
+  }
+  __syncthreads();
+  const int ncl = clstart[129];
+  for (int cl = tid; cl < ncl; cl += blockDim.x) {
+    const int i0 = clstart[cl], i1 = clstart[cl + 1];
+    float* q = Qs + cl;
+    for (int i = i0; i < i1; ++i) {
+      for (int r = 0; r < k; ++r) Z[r * k + i] = 1.f + 0.5f * __sinf(0.7f * (float)(r + 3 * i) + 0.3f);
+      const float lam = lamv[i];
+      for (int rep = 0; rep < 2; ++rep) {
+        inv_iter(dv, ev, k, lam, pivmin, Z + i, q, k, k);
+        for (int pj = (i - 32 > i0 ? i - 32 : i0); pj < i; ++pj) {
+          float dot = 0.f;
+          for (int r = 0; r < k; ++r) dot = fmaf(Z[r * k + pj], Z[r * k + i], dot);
+          float nrm = 0.f;
+          for (int r = 0; r < k; ++r) {
+            Z[r * k + i] -= dot * Z[r * k + pj];
+            nrm = fmaf(Z[r * k + i], Z[r * k + i], nrm);
+          }
+          const float inv = nrm > 0.f ? rsqrtf(nrm) : 1.f;
+          for (int r = 0; r < k; ++r) Z[r * k + i] *= inv;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < k * k; e += blockDim.x) gZ[e] = Z[e];
+}
+
+// Step 4, one warp per column c of Z: z <- H_0 H_1 ... H_{k-3} z, lane l
+// holding rows l, l + 32, l + 64, l + 96; eigenvalues scaled back into lam.
+__global__ void __launch_bounds__(256) seed_back_kernel(int k, const float* __restrict__ gV,
+                                                      const float* __restrict__ gZ, const float* __restrict__ tri,
+                                                      double* __restrict__ Xout, double* __restrict__ lam_out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* Vs = reinterpret_cast<float*>(smem_raw);  // k x k reflectors
+  __shared__ float beta[128];
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) Vs[e] = gV[e];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) beta[i] = tri[3 * k + i];
+  __syncthreads();
+  const double hmax = (double)tri[5 * k + 4] + (double)tri[5 * k + 5];
+  if (blockIdx.x == 0)
+    for (int i = threadIdx.x; i < k; i += blockDim.x) lam_out[i] = (double)tri[4 * k + i] * hmax;
+  const int lane = threadIdx.x & 31;
+  const int c = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (c >= k) return;
+  float z[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const int r = lane + 32 * t;
+    z[t] = r < k ? gZ[r * k + c] : 0.f;
+  }
+  for (int j = k - 3; j >= 0; --j) {
+    const float b = beta[j];
+    if (b == 0.f) continue;  // uniform across the warp
+    float v[4], dot = 0.f;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int r = lane + 32 * t;
+      v[t] = r < k ? Vs[j * k + r] : 0.f;
+      dot = fmaf(v[t], z[t], dot);
+    }
+    const float w = b * warp_sumf(dot);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) z[t] = fmaf(-w, v[t], z[t]);
+  }
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const int r = lane + 32 * t;
+    if (r < k) Xout[r * k + c] = (double)z[t];
+  }
+}
+
+void launch_eig_seed(Launcher& L, const double* H, int k, float* gA, float* gZ, float* gQ, float* tri, double* Xout,
                      double* lam, double* scal, int32_t* nclusters) {
+  if (k <= 128) {
+    const size_t s1 = (size_t)128 * k * sizeof(float);
+    cudaFuncSetAttribute(seed_tri_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1);
+    seed_tri_kernel<<<1, kSeedThreads, s1, L.stream>>>(H, k, gA, tri, scal);
+    seed_bisect_kernel<<<(k + 3) / 4, 128, 0, L.stream>>>(k, tri);
+    const size_t s3 = (size_t)2 * k * k * sizeof(float);
+    cudaFuncSetAttribute(seed_vec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s3);
+    seed_vec_kernel<<<1, 128, s3, L.stream>>>(k, tri, gZ, nclusters);
+    const size_t s4 = (size_t)k * k * sizeof(float);
+    cudaFuncSetAttribute(seed_back_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s4);
+    seed_back_kernel<<<(k + 7) / 8, 256, s4, L.stream>>>(k, gA, gZ, tri, Xout, lam);
+    L.count(4);
+    return;
+  }
   const size_t shm = eig_seed_smem(k);
   cudaFuncSetAttribute(eig_seed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
   eig_seed_kernel<<<1, kSeedThreads, shm, L.stream>>>(H, k, gA, gZ, gQ, Xout, lam, scal, nclusters);

@@ -64,12 +64,13 @@ struct SmallWs {
   double* scal;    // 8 scalars, sigma copy (k), sqrt(S_rr) (k), order (k int32)
   double* Vd;      // n x k
   int32_t* sweeps; // 1: eigenvalue clusters found by the FP32 seed
+  float* tri;      // seed scratch (k <= 128): d, e, e^2, beta, eigenvalues of T (k each), 8 scalars
   int h_splits;
 };
 size_t small_ws_bytes(int k, int64_t n, int* h_splits);
 // FP32 eigen seed of H (k x k FP64): eigenvectors -> Xout (k x k FP64, columns),
 // eigenvalues -> lam (ascending), scal[1] = ||H||_F.
-void launch_eig_seed(Launcher& L, const double* H, int k, float* gA, float* gZ, float* gQ, double* Xout,
+void launch_eig_seed(Launcher& L, const double* H, int k, float* gA, float* gZ, float* gQ, float* tri, double* Xout,
                      double* lam, double* scal, int32_t* nclusters);
 void carve_small_ws(SmallWs& w, void* base, int k, int64_t n);
 void launch_decompose(Launcher& L, SmallWs& w, const double* F, int k, int64_t n, int64_t m, bool v_f64, void* V,

@@ -38,7 +38,8 @@ size_t small_ws_bytes(int k, int64_t n, int* h_splits) {
   b += (size_t)k * 8 + 64 + (size_t)k * 24;  // lam, scal (+ src, sd)
   b += (size_t)n * k * 8;               // Vd
   b += 64;                              // sweeps
-  return b + 16 * 256;                  // alignment slack
+  b += (size_t)k * 4 * 5 + 64;          // seed scratch: d, e, e^2, beta, eigenvalues of T, scalars
+  return b + 17 * 256;                  // alignment slack
 }
 
 static char* align256(char* p) { return (char*)(((uintptr_t)p + 255) & ~(uintptr_t)255); }
@@ -65,6 +66,7 @@ void carve_small_ws(SmallWs& w, void* base, int k, int64_t n) {
   w.scal = (double*)take(64 + (size_t)k * 24);
   w.Vd = (double*)take((size_t)n * k * 8);
   w.sweeps = (int32_t*)take(64);
+  w.tri = (float*)take((size_t)k * 4 * 5 + 64);
 }
 
 // Block-wide FP64 sum (blockDim.x multiple of 32, <= 1024).
@@ -310,7 +312,7 @@ void launch_decompose(Launcher& L, SmallWs& w, const double* F, int k, int64_t n
   }
   launch_reduce_splits(L, w.Hpart, w.h_splits, kk, kk, w.H);
   // FP32 seed (tridiagonalisation + bisection + inverse iteration)
-  launch_eig_seed(L, w.H, k, w.h32, w.w32, w.q32, w.Xa, w.lam, w.scal, w.sweeps);
+  launch_eig_seed(L, w.H, k, w.h32, w.w32, w.q32, w.tri, w.Xa, w.lam, w.scal, w.sweeps);
   // FP64 refinement
   double* X = w.Xa;
   double* Xn = w.Xb;
