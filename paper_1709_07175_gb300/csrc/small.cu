@@ -21,8 +21,6 @@
 namespace lspca {
 
 constexpr int kRefineIters = 2;
-constexpr int kJacobiMaxSweeps = 16;
-constexpr int kJacobiThreads = 1024;
 
 size_t small_ws_bytes(int k, int64_t n, int* h_splits) {
   int hs = (int)((n + 511) / 512);
@@ -99,29 +97,25 @@ __global__ void rayleigh_kernel(const double* __restrict__ Rm, const double* __r
 // per-pair test replaces the method's global cluster threshold, which
 // (evaluated with Frobenius norms) would leave close but well-coupled pairs
 // unresolved; the iteration still converges quadratically for resolved pairs.
+// The Rayleigh quotients lambda are formed here from the diagonals of S and
+// Rm (as rayleigh_kernel does), so the step needs no separate launch for them.
 __global__ void refine_e_kernel(const double* __restrict__ Rm, const double* __restrict__ S,
-                                const double* __restrict__ lam, const double* __restrict__ scal, int k,
-                                double* __restrict__ E) {
+                                const double* __restrict__ scal, int k, double* __restrict__ E) {
   const int i = blockIdx.x;
   const double noise = 64.0 * 0x1p-52 * scal[1];
-  const double li = lam[i];
+  const double li = S[(int64_t)i * k + i] / Rm[(int64_t)i * k + i];
   for (int j = threadIdx.x; j < k; j += blockDim.x) {
     const int64_t e = (int64_t)i * k + j;
     const double r = (i == j ? 1.0 : 0.0) - Rm[e];
     double v = 0.5 * r;
     if (i != j) {
-      const double gap = lam[j] - li;
-      const double num = S[e] + lam[j] * r;
+      const double lj = S[(int64_t)j * k + j] / Rm[(int64_t)j * k + j];
+      const double gap = lj - li;
+      const double num = S[e] + lj * r;
       if (fabs(gap) > noise && fabs(num) <= 0.5 * fabs(gap)) v = num / gap;
     }
     E[e] = v;
   }
-}
-
-// C = A + A E (k x k, FP64), one thread per output.
-__global__ void add_ae_kernel(const double* __restrict__ A, const double* __restrict__ AE, int k, double* __restrict__ C) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < k * k) C[e] = A[e] + AE[e];
 }
 
 // Sort eigenpairs by descending lambda (stable) and apply the rank rule; write
@@ -135,49 +129,58 @@ __global__ void add_ae_kernel(const double* __restrict__ A, const double* __rest
 // exactly diagonalising W this is the paper's D^-1.
 __global__ void sort_rank_kernel(const double* __restrict__ lam, const double* __restrict__ S, int k, int64_t m,
                                  int64_t n, double* __restrict__ sigma, int32_t* rank, double* scal) {
-  __shared__ int dest[256];
+  __shared__ double key[256];
   __shared__ int src[256];
-  __shared__ double lmax_s;
-  __shared__ int rank_s;
+  __shared__ double wmax[32];
   int32_t* src_g = reinterpret_cast<int32_t*>(scal + 8 + 2 * k);
   double* sd_g = scal + 8 + k;
   const int tid = threadIdx.x;
-  // total order: NaN keys rank as -inf, ties by index, so dest is a permutation
-  auto key = [&](int i) { const double v = lam[i]; return isnan(v) ? -INFINITY : v; };
-  for (int r = tid; r < k; r += blockDim.x) src[r] = r;
-  __syncthreads();
+  // total order: NaN keys rank as -inf, ties by index, so the positions form a permutation
+  double mx = 0.0;
   for (int i = tid; i < k; i += blockDim.x) {
-    const double li = key(i);
+    const double v = lam[i];
+    key[i] = isnan(v) ? -INFINITY : v;
+    mx = fmax(mx, key[i]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((tid & 31) == 0) wmax[tid >> 5] = mx;
+  __syncthreads();
+  double lmax = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) lmax = fmax(lmax, wmax[w]);
+  for (int i = tid; i < k; i += blockDim.x) {
+    const double li = key[i];
     int pos = 0;
     for (int j = 0; j < k; ++j) {
-      const double lj = key(j);
+      const double lj = key[j];
       pos += (lj > li) || (lj == li && j < i);
     }
-    dest[i] = pos;
     src[pos] = i;
   }
   __syncthreads();
-  if (tid == 0) {
-    double mx = 0.0;
-    for (int i = 0; i < k; ++i) mx = fmax(mx, key(i));
-    lmax_s = mx;
-    rank_s = 0;
-  }
-  __syncthreads();
-  const double tol = (double)(m > n ? m : n) * 0x1p-52 * lmax_s;
+  const double tol = (double)(m > n ? m : n) * 0x1p-52 * lmax;
+  int kept = 0;
   for (int r = tid; r < k; r += blockDim.x) {
     const int i = src[r];
-    const bool keep = lam[i] > tol && lmax_s > 0.0;  // false for NaN
+    const bool keep = lam[i] > tol && lmax > 0.0;  // false for NaN
     if (sigma) sigma[r] = keep ? sqrt(lam[i]) : 0.0;
     scal[8 + r] = keep ? sqrt(lam[i]) : 0.0;
     const double sii = S[(int64_t)i * k + i];
     sd_g[r] = (keep && sii > 0.0) ? sqrt(sii) : 0.0;
     src_g[r] = i;
-    if (keep) atomicAdd(&rank_s, 1);
+    kept += keep;
   }
+  __shared__ int wsum[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) kept += __shfl_xor_sync(0xffffffffu, kept, o);
+  if ((tid & 31) == 0) wsum[tid >> 5] = kept;
   __syncthreads();
-  if (tid == 0 && rank) *rank = rank_s;
-  if (tid == 0) scal[0] = (double)rank_s;
+  if (tid == 0) {
+    int rk = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) rk += wsum[w];
+    if (rank) *rank = rk;
+    scal[0] = (double)rk;
+  }
 }
 
 // Row a of Ws (column-permuted eigenvectors) and of Tinv, the first-order
@@ -248,32 +251,44 @@ __global__ void finalize_v_kernel(const double* __restrict__ Vd, int64_t n, int 
 // are small enough to spread even a 128 x 128 product over all SMs.  sym:
 // C is symmetric (op(B) = op(A)^T); only tiles with blockIdx.x <= blockIdx.y
 // run and each also writes its mirror.
+struct DgemmArgs {
+  int64_t M, N, K;
+  const double* A;
+  int64_t lda;
+  int at;
+  const double* B;
+  int64_t ldb;
+  int bt;
+  double* C;
+  int64_t ldc;
+  int64_t c_split_stride, kchunk;
+  int sym;
+  const double* Cin;  // nullable: C = Cin + op(A) op(B)
+};
+
 template <int TM, int TN, int KS>
-__global__ void __launch_bounds__(TM* TN) dgemm_tile_kernel(int64_t M, int64_t N, int64_t K, const double* __restrict__ A,
-                                                           int64_t lda, int at, const double* __restrict__ B,
-                                                           int64_t ldb, int bt, double* __restrict__ C, int64_t ldc,
-                                                           int64_t c_split_stride, int64_t kchunk, int sym) {
-  if (sym && blockIdx.x > blockIdx.y) return;
+__device__ __forceinline__ void dgemm_tile_body(const DgemmArgs& g, int z) {
+  if (g.sym && blockIdx.x > blockIdx.y) return;
   __shared__ double As[TM][KS + 1];
   __shared__ double Bs[TN][KS + 1];
   const int tid = threadIdx.x;
   const int r = tid / TN, c = tid % TN;
   const int64_t i0 = (int64_t)blockIdx.x * TM, j0 = (int64_t)blockIdx.y * TN;
-  const int64_t kb = (int64_t)blockIdx.z * kchunk;
-  const int64_t ke = min(K, kb + kchunk);
+  const int64_t kb = (int64_t)z * g.kchunk;
+  const int64_t ke = min(g.K, kb + g.kchunk);
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
   for (int64_t k0 = kb; k0 < ke; k0 += KS) {
     for (int e = tid; e < TM * KS; e += TM * TN) {
       int rr, q;
-      if (at) { q = e / TM; rr = e % TM; } else { rr = e / KS; q = e % KS; }
+      if (g.at) { q = e / TM; rr = e % TM; } else { rr = e / KS; q = e % KS; }
       const int64_t gi = i0 + rr, gq = k0 + q;
-      As[rr][q] = (gi < M && gq < ke) ? (at ? A[gq * lda + gi] : A[gi * lda + gq]) : 0.0;
+      As[rr][q] = (gi < g.M && gq < ke) ? (g.at ? g.A[gq * g.lda + gi] : g.A[gi * g.lda + gq]) : 0.0;
     }
     for (int e = tid; e < TN * KS; e += TM * TN) {
       int cc, q;
-      if (bt) { cc = e / KS; q = e % KS; } else { q = e / TN; cc = e % TN; }
+      if (g.bt) { cc = e / KS; q = e % KS; } else { q = e / TN; cc = e % TN; }
       const int64_t gj = j0 + cc, gq = k0 + q;
-      Bs[cc][q] = (gj < N && gq < ke) ? (bt ? B[gj * ldb + gq] : B[gq * ldb + gj]) : 0.0;
+      Bs[cc][q] = (gj < g.N && gq < ke) ? (g.bt ? g.B[gj * g.ldb + gq] : g.B[gq * g.ldb + gj]) : 0.0;
     }
     __syncthreads();
 #pragma unroll 4
@@ -283,20 +298,60 @@ __global__ void __launch_bounds__(TM* TN) dgemm_tile_kernel(int64_t M, int64_t N
     }
     __syncthreads();
   }
-  const double v = (acc[0] + acc[1]) + (acc[2] + acc[3]);
-  double* Cs = C + (int64_t)blockIdx.z * c_split_stride;
+  double v = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+  double* Cs = g.C + (int64_t)z * g.c_split_stride;
   const int64_t gi = i0 + r, gj = j0 + c;
-  if (gi < M && gj < N) {
-    Cs[gi * ldc + gj] = v;
-    if (sym && blockIdx.x != blockIdx.y) Cs[gj * ldc + gi] = v;
+  if (gi < g.M && gj < g.N) {
+    if (g.Cin) v += g.Cin[gi * g.ldc + gj];
+    Cs[gi * g.ldc + gj] = v;
+    if (g.sym && blockIdx.x != blockIdx.y) Cs[gj * g.ldc + gi] = v;
   }
 }
 
+// blockIdx.z: the K split.
+template <int TM, int TN, int KS>
+__global__ void __launch_bounds__(TM* TN) dgemm_tile_kernel(const DgemmArgs g) {
+  dgemm_tile_body<TM, TN, KS>(g, blockIdx.z);
+}
+
+// Two independent products in one launch (blockIdx.z selects), K unsplit.
+template <int TM, int TN, int KS>
+__global__ void __launch_bounds__(TM* TN) dgemm_pair_kernel(const DgemmArgs g0, const DgemmArgs g1) {
+  dgemm_tile_body<TM, TN, KS>(blockIdx.z == 0 ? g0 : g1, 0);
+}
+
+static DgemmArgs dargs(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda, bool at, const double* B,
+                       int64_t ldb, bool bt, double* C, int64_t ldc, const double* Cin = nullptr) {
+  DgemmArgs g{};
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.A = A;
+  g.lda = lda;
+  g.at = at ? 1 : 0;
+  g.B = B;
+  g.ldb = ldb;
+  g.bt = bt ? 1 : 0;
+  g.C = C;
+  g.ldc = ldc;
+  g.c_split_stride = 0;
+  g.kchunk = K;
+  g.sym = 0;
+  g.Cin = Cin;
+  return g;
+}
+
+// Both products are M x N.
+static void dgemm2(Launcher& L, const DgemmArgs& g0, const DgemmArgs& g1) {
+  dim3 grid((unsigned)((g0.M + 7) / 8), (unsigned)((g0.N + 7) / 8), 2);
+  dgemm_pair_kernel<8, 8, 64><<<grid, 64, 0, L.stream>>>(g0, g1);
+  L.count(1);
+}
+
 static void dgemm(Launcher& L, int64_t M, int64_t N, int64_t K, const double* A, int64_t lda, bool at, const double* B,
-                  int64_t ldb, bool bt, double* C, int64_t ldc) {
+                  int64_t ldb, bool bt, double* C, int64_t ldc, const double* Cin = nullptr) {
   dim3 grid((unsigned)((M + 7) / 8), (unsigned)((N + 7) / 8), 1);
-  dgemm_tile_kernel<8, 8, 64><<<grid, 64, 0, L.stream>>>(M, N, K, A, lda, at ? 1 : 0, B, ldb, bt ? 1 : 0, C, ldc, 0,
-                                                          K, 0);
+  dgemm_tile_kernel<8, 8, 64><<<grid, 64, 0, L.stream>>>(dargs(M, N, K, A, lda, at, B, ldb, bt, C, ldc, Cin));
   L.count(1);
 }
 
@@ -307,7 +362,11 @@ void launch_decompose(Launcher& L, SmallWs& w, const double* F, int k, int64_t n
   {
     const int64_t kchunk = ((n + w.h_splits - 1) / w.h_splits + 63) / 64 * 64;
     dim3 grid((unsigned)((k + 15) / 16), (unsigned)((k + 15) / 16), (unsigned)w.h_splits);
-    dgemm_tile_kernel<16, 16, 64><<<grid, 256, 0, L.stream>>>(k, k, n, F, n, 0, F, n, 1, w.Hpart, k, kk, kchunk, 1);
+    DgemmArgs g = dargs(k, k, n, F, n, false, F, n, true, w.Hpart, k);
+    g.c_split_stride = kk;
+    g.kchunk = kchunk;
+    g.sym = 1;
+    dgemm_tile_kernel<16, 16, 64><<<grid, 256, 0, L.stream>>>(g);
     L.count(1);
   }
   launch_reduce_splits(L, w.Hpart, w.h_splits, kk, kk, w.H);
@@ -317,16 +376,17 @@ void launch_decompose(Launcher& L, SmallWs& w, const double* F, int k, int64_t n
   double* X = w.Xa;
   double* Xn = w.Xb;
   for (int it = 0; it <= kRefineIters; ++it) {
-    dgemm(L, k, k, k, X, k, true, X, k, false, w.Rm, k);    // X^T X
-    dgemm(L, k, k, k, w.H, k, false, X, k, false, w.T, k);  // H X
-    dgemm(L, k, k, k, X, k, true, w.T, k, false, w.S, k);   // X^T H X
-    rayleigh_kernel<<<1, 256, 0, L.stream>>>(w.Rm, w.S, k, w.lam);
+    dgemm2(L, dargs(k, k, k, X, k, true, X, k, false, w.Rm, k),    // X^T X
+           dargs(k, k, k, w.H, k, false, X, k, false, w.T, k));  // H X
+    dgemm(L, k, k, k, X, k, true, w.T, k, false, w.S, k);          // X^T H X
+    if (it == kRefineIters) {  // last pass only refreshes lambda and S
+      rayleigh_kernel<<<1, 256, 0, L.stream>>>(w.Rm, w.S, k, w.lam);
+      L.count(1);
+      break;
+    }
+    refine_e_kernel<<<k, 128, 0, L.stream>>>(w.Rm, w.S, w.scal, k, w.E);
     L.count(1);
-    if (it == kRefineIters) break;  // last pass only refreshes lambda and S
-    refine_e_kernel<<<k, 128, 0, L.stream>>>(w.Rm, w.S, w.lam, w.scal, k, w.E);
-    dgemm(L, k, k, k, X, k, false, w.E, k, false, w.T, k);  // X E
-    add_ae_kernel<<<(int)((kk + 255) / 256), 256, 0, L.stream>>>(X, w.T, k, Xn);
-    L.count(2);
+    dgemm(L, k, k, k, X, k, false, w.E, k, false, Xn, k, X);  // X + X E
     double* t = X;
     X = Xn;
     Xn = t;
