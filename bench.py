@@ -225,7 +225,7 @@ def serve_bench(L, S, torch, local: int, seconds: float, load: float = 0.8, seed
 # proportion to the rows.  Set an entry to None when its kernel changes, until
 # it is captured again.
 TRAFFIC_PER_ROW = {
-    "sketch": (822.42432e6 + 23.196416e6) / 50000,
+    "sketch": (822.426624e6 + 23.101952e6) / 50000,
     "chain_main": (844.953088e6 + 25.067264e6) / 50000,
 }
 
