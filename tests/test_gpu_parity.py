@@ -116,6 +116,8 @@ def test_sketch_sparse_fp32(ctx, data, wl):
                                              (torch.float32, 300, 4096, 4096, 128),
                                              (torch.float32, 1100, 1000, 1000, 64),
                                              (torch.float32, 515, 2040, 2056, 100),
+                                             (torch.float32, 1, 1000, 1000, 64),
+                                             (torch.float32, 100, 4096, 4096, 128),
                                              (torch.bfloat16, 515, 1003, 1008, 100),
                                              (torch.bfloat16, 129, 2048, 2048, 128)])
 def test_sketch_sparse_strided_and_ragged(ctx, dtype, m, n, ldx, k):
@@ -400,7 +402,8 @@ def test_alg4_slicing_invariance(ctx, data):
 # ------------------------------------------------------------------ tensor-core projection, all X types
 
 @pytest.mark.parametrize("dtype,k,m,n", [("f32", 20, 1000, 500), ("f32", 128, 3001, 4096), ("f32", 200, 777, 1000),
-                                         ("f32", 64, 1100, 1000), ("f32", 100, 515, 2040),
+                                         ("f32", 64, 1100, 1000), ("f32", 100, 515, 2040), ("f32", 128, 1, 1000),
+                                         ("f32", 64, 77, 4096),
                                          ("bf16", 64, 2049, 1024), ("bf16", 256, 513, 2048),
                                          ("e4m3", 256, 1500, 4096), ("e4m3", 128, 4001, 1040)])
 def test_project_tensor_core_paths(ctx, dtype, k, m, n):
