@@ -255,6 +255,27 @@ def test_fit_fp32_parity(ctx, data, wl):
     assert np.max(np.abs(r.sigma.cpu().numpy() - fit["sigma"]) / fit["sigma"]) < 1e-5
 
 
+def test_fit_fp32_gaussian_parity(ctx):
+    """FP32 X with the Gaussian Omega: the sketch takes Omega in three exact
+    BF16 pieces (six products, A in tensor memory).  U within 2e-6 of the FP64
+    product of the same stored values (relative Frobenius); the fit's Y within
+    1e-5 of the oracle's (Procrustes-aligned) and sigma within 1e-5."""
+    w = S.WORKLOADS["fp32_sparse"].scaled(m=3001, n=1024, k=64)
+    X = S.generate(w)
+    Xd = X.double().numpy()
+    Om = P.omega_gaussian(7, w.n, w.k)  # FP64 draws rounded to FP32, as the library stores them
+    om = L.omega("gaussian", 7)
+    U = ctx.sketch(X.cuda(), w.k, om).double().cpu().numpy()
+    Uref = Xd @ Om
+    assert np.linalg.norm(U - Uref) / np.linalg.norm(Uref) < 2e-6
+    r = ctx.fit(X.cuda(), w.k, om)
+    assert r.status == L.OK
+    fit = O.lspca_fit(Xd, Om)
+    Y = ctx.project(X.cuda(), r.V).double().cpu().numpy()
+    assert M.procrustes_rel(Y, O.project(Xd, fit["V"])) < 1e-5
+    assert np.max(np.abs(r.sigma.cpu().numpy() - fit["sigma"]) / fit["sigma"]) < 1e-5
+
+
 def test_fit_is_deterministic(ctx, data):
     w, X, Xd, Om, fit = _get(data, C2S)
     Xg = X.cuda()
