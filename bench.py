@@ -94,6 +94,27 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows), "power_w_max": max(pw) if pw else None}
 
 
+def cpu_model() -> str:
+    """The host CPU as /proc/cpuinfo names it (model name on x86; implementer
+    and part numbers on Arm), else the platform's machine string."""
+    import platform
+    try:
+        info = open("/proc/cpuinfo").read().splitlines()
+    except OSError:
+        return platform.machine()
+    for line in info:
+        if line.lower().startswith("model name"):
+            return line.split(":", 1)[1].strip()
+    fields = {}
+    for line in info:
+        if ":" in line:
+            key, val = (t.strip() for t in line.split(":", 1))
+            fields.setdefault(key, val)
+    if "CPU part" in fields:
+        return f"{platform.machine()} implementer {fields.get('CPU implementer', '?')} part {fields['CPU part']}"
+    return platform.machine()
+
+
 def cpu_baseline(rows: int, reps_seconds: float = 10.0) -> dict:
     """The FP64 oracle as it stands, on a bounded sample of the workload."""
     import numpy as np
@@ -116,16 +137,17 @@ def cpu_baseline(rows: int, reps_seconds: float = 10.0) -> dict:
     return {"value": rows * reps / dt, "unit": "samples/s", "cores": cores, "kind": "oracle",
             "sample": f"{rows} rows x {w.n} of the {WORKLOAD} workload (same recipe), k={w.k}, "
                       f"{reps} fit(s) in {dt:.1f} s; FP64 numpy, BLAS threads = host default",
-            "np": np.__version__}
+            "cpu": cpu_model(), "np": np.__version__}
 
 
-def serve_bench(L, S, torch, local: int, seconds: float, load: float = 0.8, seed: int = 5) -> dict:
+def serve_bench(L, S, torch, local: int, seconds: float, loads=(0.5, 0.8, 0.95), seed: int = 5) -> dict:
     """Continuous-batching serving run shaped like the serving workload: three
     resident V (n = 4096, k in {64, 128, 256}) fitted from BF16 low-rank data,
     Poisson arrivals of projection requests (log-uniform 1..65,536 BF16 rows)
     mixed 9:1 with fit requests (m log-uniform 1e4..5e5, n = 4096, k = 128,
-    Gaussian Omega), offered at `load` times the measured unbatched capacity.
-    Latency = completion - arrival on the host clock."""
+    Gaussian Omega), offered at each of `loads` times the measured unbatched
+    capacity (the same requests and seed at every load).  Latency = completion
+    - arrival on the host clock.  The top-level fields are those of load 0.8."""
     import math
     import numpy as np
     dev = torch.device(f"cuda:{local}")
@@ -143,6 +165,7 @@ def serve_bench(L, S, torch, local: int, seconds: float, load: float = 0.8, seed
     frow = np.floor(np.exp(rng.uniform(math.log(1e4), math.log(5e5), nreq))).astype(np.int64)
     pk = rng.choice([64, 128, 256], nreq)
     poff = rng.integers(0, 500_000 - 65_536, nreq)
+    gaps = rng.exponential(1.0, nreq)  # unit-rate Poisson gaps, scaled per load
     om = L.omega("gaussian", 0)
 
     def direct(i):
@@ -162,16 +185,6 @@ def serve_bench(L, S, torch, local: int, seconds: float, load: float = 0.8, seed
         direct(i)
         torch.cuda.synchronize()
         svc[i] = time.perf_counter() - t0
-    rate = load / svc.mean()
-    arrivals = np.cumsum(rng.exponential(1.0 / rate, nreq))
-    # baseline latency: one FIFO server with those service times
-    done_b = np.zeros(nreq)
-    tfree = 0.0
-    for i in range(nreq):
-        start = max(arrivals[i], tfree)
-        tfree = start + svc[i]
-        done_b[i] = tfree
-    lat_b = (done_b - arrivals) * 1e3
 
     srv = L.Server(local, 24 << 30, 64)
     vid = {k: srv.register_v(V) for k, V in Vs.items()}
@@ -181,43 +194,61 @@ def serve_bench(L, S, torch, local: int, seconds: float, load: float = 0.8, seed
         srv.wait(r)
         srv.release(r)
     torch.cuda.synchronize()
-    t_start = time.perf_counter()
-    deadline = t_start + seconds
-    nxt = 0
-    live = {}
-    lat = []
-    rows_done = 0
-    while (nxt < nreq or live) and time.perf_counter() < deadline + 30:
-        now = time.perf_counter() - t_start
-        while nxt < nreq and arrivals[nxt] <= now:
-            if kinds[nxt]:
-                req, V, sig = srv.submit_fit(pool[: frow[nxt]], 128, om)
-                rows = int(frow[nxt])
-            else:
-                req, Y = srv.submit_project(vid[int(pk[nxt])], pool[poff[nxt]: poff[nxt] + prow[nxt]])
-                rows = int(prow[nxt])
-            live[req] = (arrivals[nxt], rows)
-            nxt += 1
-        srv.step()
-        for req in list(live):
-            if srv.done(req):
-                arr, rows = live.pop(req)
-                lat.append((time.perf_counter() - t_start - arr) * 1e3)
-                rows_done += rows
-                srv.release(req)
-        if not live and nxt < nreq:
-            time.sleep(max(0.0, min(1e-3, arrivals[nxt] - (time.perf_counter() - t_start))))
-    wall = time.perf_counter() - t_start
-    torch.cuda.synchronize()
+
+    def run_load(load):
+        rate = load / svc.mean()
+        arrivals = np.cumsum(gaps / rate)
+        # baseline latency: one FIFO server with the measured service times
+        done_b = np.zeros(nreq)
+        tfree = 0.0
+        for i in range(nreq):
+            start = max(arrivals[i], tfree)
+            tfree = start + svc[i]
+            done_b[i] = tfree
+        lat_b = (done_b - arrivals) * 1e3
+        t_start = time.perf_counter()
+        deadline = t_start + seconds
+        nxt = 0
+        live = {}
+        lat = []
+        rows_done = 0
+        while (nxt < nreq or live) and time.perf_counter() < deadline + 30:
+            now = time.perf_counter() - t_start
+            while nxt < nreq and arrivals[nxt] <= now:
+                if kinds[nxt]:
+                    req, V, sig = srv.submit_fit(pool[: frow[nxt]], 128, om)
+                    rows = int(frow[nxt])
+                else:
+                    req, Y = srv.submit_project(vid[int(pk[nxt])], pool[poff[nxt]: poff[nxt] + prow[nxt]])
+                    rows = int(prow[nxt])
+                live[req] = (arrivals[nxt], rows)
+                nxt += 1
+            srv.step()
+            for req in list(live):
+                if srv.done(req):
+                    arr, rows = live.pop(req)
+                    lat.append((time.perf_counter() - t_start - arr) * 1e3)
+                    rows_done += rows
+                    srv.release(req)
+            if not live and nxt < nreq:
+                time.sleep(max(0.0, min(1e-3, arrivals[nxt] - (time.perf_counter() - t_start))))
+        wall = time.perf_counter() - t_start
+        torch.cuda.synchronize()
+        lat = np.array(lat)
+        return {"load": load, "requests": int(len(lat)), "mix": "9:1 projections:fits",
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "throughput_req_s": len(lat) / wall, "rows_per_s": rows_done / wall,
+                "unbatched": {"p50_ms": float(np.percentile(lat_b, 50)), "p99_ms": float(np.percentile(lat_b, 99)),
+                              "capacity_req_s": 1.0 / svc.mean()}}
+
+    runs = [run_load(ld) for ld in loads]
     srv.close()
     ctx.close()
     del pool
-    lat = np.array(lat)
-    return {"load": load, "requests": int(len(lat)), "mix": "9:1 projections:fits",
-            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "throughput_req_s": len(lat) / wall, "rows_per_s": rows_done / wall,
-            "unbatched": {"p50_ms": float(np.percentile(lat_b, 50)), "p99_ms": float(np.percentile(lat_b, 99)),
-                          "capacity_req_s": 1.0 / svc.mean()}}
+    main = next((r for r in runs if abs(r["load"] - 0.8) < 1e-9), runs[0])
+    out = dict(main)
+    out["loads"] = runs
+    return out
 
 
 # DRAM bytes (read + write) per row of X of one launch, from one ncu capture
@@ -332,6 +363,28 @@ def run_gpu(args):
     ms_step = ms / args.steps
     value = w.m * ws * args.steps / (ms / 1e3)
 
+    # ---- the same fit with the optional Gram G = U^T U (Lemma 1 / Prop. 1) on
+    G = torch.empty(w.k, w.k, dtype=torch.float64, device=X.device)
+
+    def step_gram():
+        rc = L.lspca_fit(ctx.handle, X, w.k, om, L.WANT_GRAM, V, sigma, G, rk, stream)
+        if rc != L.OK:
+            raise L.LspcaError(rc, "lspca_fit")
+
+    for _ in range(2):
+        step_gram()
+    torch.cuda.synchronize()
+    g0 = torch.cuda.Event(enable_timing=True)
+    g1 = torch.cuda.Event(enable_timing=True)
+    ngr = max(3, min(args.steps, 10))
+    g0.record(stream)
+    for _ in range(ngr):
+        step_gram()
+    g1.record(stream)
+    torch.cuda.synchronize()
+    gram_ms = g0.elapsed_time(g1) / ngr
+    del G
+
     # ---- SPCA comparison path (same workload, same launch configuration)
     for _ in range(2):
         step(L.spca_fit)
@@ -436,6 +489,8 @@ def run_gpu(args):
             "spca": {"ms_per_step": spca_ms, "samples_per_s": w.m * ws / (spca_ms / 1e3),
                      "lazy_speedup": spca_ms / ms_step},
             "passes_ms": per,
+            "gram": {"ms_per_step_on": gram_ms, "ms_per_step_off": ms_step,
+                     "note": "the same fit with the optional G = U^T U output (LSPCA_WANT_GRAM) on and off"},
             "project": {"ms_per_call": proj_ms, "samples_per_s": w.m / (proj_ms / 1e3),
                         "achieved_gbs": (x_bytes + u_bytes) / (proj_ms / 1e3) / 1e9,
                         "frac": (x_bytes + u_bytes) / (proj_ms / 1e3) / 1e9 / peak,

@@ -137,6 +137,26 @@ int lspca_fit(lspca_ctx* ctx, const void* X, int32_t xt, int64_t m, int64_t n, i
               int32_t k, lspca_omega om, uint32_t flags, void* V, double* sigma, double* gram,
               int32_t* rank, void* stream, lspca_report* rep);
 
+/* Lazy SPCA fit with oversampling, l >= k (Sec. I-B: l = k + p with a small
+ * oversampling parameter p; the Corollary of Sec. II bounds the error of the
+ * l-dimensional approximation): the fit of lspca_fit with an l-column Omega
+ * (its first k columns are the k-column Omega of the same seed), then the
+ * truncation of the SVD of F = U^T X to its top k.  V receives the first k
+ * columns (descending sigma, sign rule as lspca_fit), sigma the first k
+ * values, rank min(rank of the l-column fit, k).  The span of the top-k
+ * truncation depends on l and, unlike the full l-dimensional span (Prop. 2),
+ * differs from SPCA's in general.
+ * l             k <= l <= min(m, n, 256); l = k is lspca_fit.
+ * Other arguments: as lspca_fit, with V n x k; flags must not hold
+ * LSPCA_WANT_GRAM.  The n x l intermediate V and the l values of sigma live in
+ * a context-owned buffer, grown on demand (a device synchronisation) and freed
+ * by lspca_destroy.
+ * Errors: as lspca_fit; LSPCA_ERR_INVALID also for l < k or LSPCA_WANT_GRAM;
+ * with rep, LSPCA_WARN_RANK_DEFICIENT only when the rank is below k.        */
+int lspca_fit_oversampled(lspca_ctx* ctx, const void* X, int32_t xt, int64_t m, int64_t n, int64_t ldx,
+                          int32_t k, int32_t l, lspca_omega om, uint32_t flags, void* V, double* sigma,
+                          int32_t* rank, void* stream, lspca_report* rep);
+
 /* SPCA fit, the comparison path: Algorithm 1 in its streaming form,
  * Algorithm 3 (table of Sec. III; Eq. "approx_svd"): U = X Omega; R from a
  * tall-skinny Householder QR of U (row blocks, then a reduction tree of the

@@ -8,8 +8,9 @@ eigensolver and the Householder QR are written out so that independent
 library routines can pin them in the tests.
 
 Notation follows the paper: X is m x n with samples as rows (Sec. I-A), Omega
-is n x l with l = k (no oversampling, as in Experiment 1), U = X Omega is
-m x k, F = U^T X is k x n, V is n x k, the reduction is Y = X V (m x k).
+is n x l with l = k (no oversampling, as in Experiment 1; lspca_fit_oversampled
+takes l > k and keeps the top k), U = X Omega is m x l, F = U^T X is l x n,
+V is n x k, the reduction is Y = X V (m x k).
 X is never centred (Sec. I-B, "uncentered" PCA).
 
 Readings where the paper is silent (shared with the GPU library):
@@ -270,6 +271,16 @@ def lspca_fit(X: np.ndarray, Omega: np.ndarray, route: str = "eig") -> dict:
     dec = decompose_eig if route == "eig" else decompose_svd
     V, sigma, rank = dec(F, m, n)
     return {"V": V, "sigma": sigma, "rank": rank, "U": U, "F": F, "G": gram(U)}
+
+
+def lspca_fit_oversampled(X: np.ndarray, Omega: np.ndarray, k: int, route: str = "eig") -> dict:
+    """Lazy SPCA with oversampling (Sec. I-B: l = k + p columns of Omega, a
+    small oversampling parameter p): the fit of Algorithm 2 with the n x l
+    Omega, then the truncated SVD of F = U^T X kept to its top k singular
+    triplets (V's first k columns, sigma's first k values; rank capped at k).
+    Returns V (n x k), sigma (k), rank and the l-column fit under "full"."""
+    full = lspca_fit(X, Omega, route)
+    return {"V": full["V"][:, :k], "sigma": full["sigma"][:k], "rank": min(full["rank"], k), "full": full}
 
 
 def spca_fit(X: np.ndarray, Omega: np.ndarray, route: str = "svd") -> dict:

@@ -26,6 +26,9 @@ struct lspca_ctx {
   cudaStream_t cstream = nullptr;
   cudaEvent_t copied[2] = {};
   cudaEvent_t consumed[2] = {};
+  // oversampled fits: the n x l V, the l sigma and the rank of the l-column fit
+  void* aux = nullptr;
+  size_t aux_size = 0;
   // profiling ring: 5 events per call
   bool profiling = false;
   std::vector<cudaEvent_t> pev;
@@ -357,6 +360,7 @@ int lspca_destroy(lspca_ctx* ctx) {
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
   if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->aux) cudaFree(ctx->aux);
   if (ctx->d_status) cudaFree(ctx->d_status);
   for (auto& e : ctx->ev)
     if (e) cudaEventDestroy(e);
@@ -378,6 +382,54 @@ int lspca_fit(lspca_ctx* ctx, const void* X, int32_t xt, int64_t m, int64_t n, i
 int spca_fit(lspca_ctx* ctx, const void* X, int32_t xt, int64_t m, int64_t n, int64_t ldx, int32_t k, lspca_omega om,
              uint32_t flags, void* V, double* sigma, double* gram, int32_t* rank, void* stream, lspca_report* rep) {
   return fit_impl(ctx, X, xt, m, n, ldx, k, om, flags, V, sigma, gram, rank, stream, rep, true);
+}
+
+namespace {
+__global__ void rank_min_kernel(const int32_t* rl, int32_t k, int32_t* rank) { *rank = *rl < k ? *rl : k; }
+}  // namespace
+
+int lspca_fit_oversampled(lspca_ctx* ctx, const void* X, int32_t xt, int64_t m, int64_t n, int64_t ldx, int32_t k,
+                          int32_t l, lspca_omega om, uint32_t flags, void* V, double* sigma, int32_t* rank,
+                          void* stream, lspca_report* rep) {
+  if (!ctx || !V || !sigma || k < 1 || l < k || (flags & LSPCA_WANT_GRAM)) return LSPCA_ERR_INVALID;
+  if (l == k) return lspca_fit(ctx, X, xt, m, n, ldx, k, om, flags, V, sigma, nullptr, rank, stream, rep);
+  if (xt < LSPCA_F64 || xt > LSPCA_E4M3 || n < 1) return LSPCA_ERR_INVALID;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return LSPCA_ERR_CUDA;
+  const size_t vel = xt == LSPCA_F64 ? 8 : 4;  // result type of V
+  const size_t vbytes = ((size_t)n * l * vel + 255) & ~(size_t)255;
+  const size_t need = vbytes + (size_t)l * 8 + 256;
+  if (ctx->aux_size < need) {
+    if (ctx->aux) {
+      cudaDeviceSynchronize();  // the buffer may still be read by queued work
+      cudaFree(ctx->aux);
+      ctx->aux = nullptr;
+      ctx->aux_size = 0;
+    }
+    if (cudaMalloc(&ctx->aux, need) != cudaSuccess) return LSPCA_ERR_NOMEM;
+    ctx->aux_size = need;
+  }
+  char* base = (char*)ctx->aux;
+  double* sl = reinterpret_cast<double*>(base + vbytes);
+  int32_t* rl = reinterpret_cast<int32_t*>(base + vbytes + (((size_t)l * 8 + 255) & ~(size_t)255));
+  int st = fit_impl(ctx, X, xt, m, n, ldx, l, om, flags, base, sl, nullptr, rl, stream, rep, false);
+  if (st != LSPCA_OK && st != LSPCA_WARN_RANK_DEFICIENT) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  // top k of the l sorted singular triplets: the first k columns of every row of V
+  if (cudaMemcpy2DAsync(V, (size_t)k * vel, base, (size_t)l * vel, (size_t)k * vel, (size_t)n,
+                        cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(sigma, sl, (size_t)k * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return LSPCA_ERR_CUDA;
+  if (rank) {
+    rank_min_kernel<<<1, 1, 0, s>>>(rl, k, rank);
+    ctx->launches += 1;
+  }
+  if (cudaGetLastError() != cudaSuccess) return LSPCA_ERR_CUDA;
+  if (rep) {
+    if (cudaStreamSynchronize(s) != cudaSuccess) return LSPCA_ERR_CUDA;
+    if (rep->rank > k) rep->rank = k;
+    if (st == LSPCA_WARN_RANK_DEFICIENT && rep->rank >= k) st = LSPCA_OK;
+  }
+  return st;
 }
 
 int lspca_fit_host(lspca_ctx* ctx, const void* Xh, int32_t xt, int64_t m, int64_t n, int64_t ldx, int32_t k,

@@ -65,6 +65,8 @@ _SIGS = {
                                 ctypes.POINTER(lspca_report)]),
     "lspca_fit_host": (ctypes.c_int, [_P, _P, _I32, _I64, _I64, _I64, _I32, lspca_omega, _U32, _I64, _P, _P, _P,
                                       _P, ctypes.POINTER(lspca_report)]),
+    "lspca_fit_oversampled": (ctypes.c_int, [_P, _P, _I32, _I64, _I64, _I64, _I32, _I32, lspca_omega, _U32, _P,
+                                             _P, _P, _P, ctypes.POINTER(lspca_report)]),
     "lspca_project": (ctypes.c_int, [_P, _P, _I32, _I64, _I64, _I64, _P, _I32, _P, _P]),
     "lspca_omega_materialize": (ctypes.c_int, [_P, lspca_omega, _I64, _I32, _I32, _P, _P]),
     "lspca_sketch": (ctypes.c_int, [_P, _P, _I32, _I64, _I64, _I64, _I32, lspca_omega, _U32, _P, _P]),
@@ -170,6 +172,13 @@ def lspca_fit(ctx, X, k, om, flags, V, sigma, gram=None, rank=None, stream=None,
     rp = ctypes.byref(report) if report is not None else None
     return load().lspca_fit(ctx, x, xt, m, n, ldx, k, om, flags, _ptr(V), _ptr(sigma), _ptr(gram), _ptr(rank),
                             _stream(stream), rp)
+
+
+def lspca_fit_oversampled(ctx, X, k, l, om, flags, V, sigma, rank=None, stream=None, report=None) -> int:
+    x, xt, m, n, ldx = _xargs(X)
+    rp = ctypes.byref(report) if report is not None else None
+    return load().lspca_fit_oversampled(ctx, x, xt, m, n, ldx, k, l, om, flags, _ptr(V), _ptr(sigma), _ptr(rank),
+                                        _stream(stream), rp)
 
 
 def spca_fit(ctx, X, k, om, flags, V, sigma, gram=None, rank=None, stream=None, report=None) -> int:
@@ -402,6 +411,18 @@ class Context:
 
     def fit(self, X, k, om, flags=0, report=True, stream=None) -> FitResult:
         return self._fit(lspca_fit, X, k, om, flags, report, stream)
+
+    def fit_oversampled(self, X, k, l, om, flags=0, report=True, stream=None) -> FitResult:
+        """Fit with an l-column Omega (l >= k), truncated to the top k."""
+        dev = X.device
+        rt = RESULT_DTYPE[DTYPE_CODES[X.dtype]]
+        V = torch.empty(X.shape[1], k, dtype=rt, device=dev)
+        sigma = torch.empty(k, dtype=torch.float64, device=dev)
+        rank = torch.empty(1, dtype=torch.int32, device=dev)
+        rep = lspca_report() if report else None
+        rc = lspca_fit_oversampled(self.handle, X, k, l, om, flags, V, sigma, rank, stream, rep)
+        _check(rc, "lspca_fit_oversampled", allow=(OK, WARN_RANK_DEFICIENT))
+        return FitResult(V, sigma, rank, None, rc, rep.as_dict() if rep is not None else None)
 
     def fit_host(self, Xh, k, om, slice_rows=0, report=True, stream=None) -> FitResult:
         """Fit a host-resident X (CPU tensor, pinned for overlapped copies) slice by slice."""

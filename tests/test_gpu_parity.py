@@ -276,6 +276,30 @@ def test_fit_fp32_gaussian_parity(ctx):
     assert np.max(np.abs(r.sigma.cpu().numpy() - fit["sigma"]) / fit["sigma"]) < 1e-5
 
 
+@pytest.mark.parametrize("kind", ["gaussian", "sparse"])
+def test_fit_oversampled_parity(ctx, kind):
+    """Oversampled fit (l = 44 > k = 32, FP32 X): the top k of the l-column fit.
+    Y within 1e-5 of the oracle's (Procrustes-aligned), sigma within 1e-5,
+    rank k; and l = k gives lspca_fit's result bit for bit."""
+    w = S.WORKLOADS["fp32_sparse"].scaled(m=3001, n=1024, k=32)
+    X = S.generate(w)
+    Xd = X.double().numpy()
+    l = 44
+    if kind == "gaussian":
+        Om, om = P.omega_gaussian(7, w.n, l), L.omega("gaussian", 7)
+    else:
+        Om, om = P.omega_sparse(7, w.n, l, w.p), L.omega("sparse", 7, w.p)
+    r = ctx.fit_oversampled(X.cuda(), w.k, l, om)
+    assert r.status == L.OK and int(r.rank.item()) == w.k and r.report["rank"] == w.k
+    fit = O.lspca_fit_oversampled(Xd, Om, w.k)
+    Y = ctx.project(X.cuda(), r.V).double().cpu().numpy()
+    assert M.procrustes_rel(Y, O.project(Xd, fit["V"])) < 1e-5
+    assert np.max(np.abs(r.sigma.cpu().numpy() - fit["sigma"]) / fit["sigma"]) < 1e-5
+    same = ctx.fit_oversampled(X.cuda(), w.k, w.k, om)
+    plain = ctx.fit(X.cuda(), w.k, om)
+    assert torch.equal(same.V, plain.V) and torch.equal(same.sigma, plain.sigma)
+
+
 def test_fit_is_deterministic(ctx, data):
     w, X, Xd, Om, fit = _get(data, C2S)
     Xg = X.cuda()

@@ -221,6 +221,69 @@ def test_rank_r_recovery():
         assert np.all(fit["V"][:, 5:] == 0)
 
 
+def _lazy_residual_norm(X, U):
+    """||X - U' U^T X||_2 with U' = U (U^T U)^-1 (Lemma 1), by library routines."""
+    R = X - U @ np.linalg.solve(U.T @ U, U.T @ X)
+    return np.linalg.norm(R, 2)
+
+
+def test_oversampled_corollary_bound():
+    """Corollary of Sec. II (Gaussian Omega, l >= k + 2): the mean over draws of
+    ||X - U' U^T X||_2 is at most [1 + 4 sqrt(l) / (l - k - 1) sqrt(min(m, n))]
+    sigma_{k+1}; and no draw beats sigma_{l+1}, the best rank-l error."""
+    rng = np.random.default_rng(21)
+    m, n, k, l = 300, 120, 6, 12
+    A, _ = np.linalg.qr(rng.standard_normal((m, 40)))
+    B, _ = np.linalg.qr(rng.standard_normal((n, 40)))
+    X = A @ np.diag(0.8 ** np.arange(40)) @ B.T + 1e-3 * rng.standard_normal((m, n))
+    sv = np.linalg.svd(X, compute_uv=False)
+    errs = []
+    for seed in range(8):
+        U = O.sketch(X, P.omega_gaussian(seed, n, l))
+        e = _lazy_residual_norm(X, U)
+        assert e >= sv[l] * (1 - 1e-10)
+        errs.append(e)
+    bound = (1 + 4 * np.sqrt(l) / (l - k - 1) * np.sqrt(min(m, n))) * sv[k]
+    assert np.mean(errs) <= bound
+    # oversampling helps: the mean error with l = k + 6 is below the one with l = k
+    errs_k = [_lazy_residual_norm(X, O.sketch(X, P.omega_gaussian(seed, n, k))) for seed in range(8)]
+    assert np.mean(errs) < np.mean(errs_k)
+
+
+def test_oversampled_fit_is_the_top_k_of_the_l_column_fit():
+    """l > k: V and sigma are the top k singular triplets of F = U^T X for the
+    l-column Omega (library SVD of F); the full l-dimensional spans of Lazy and
+    SPCA agree (Prop. 2 at l), while their top-k truncations differ in general;
+    with l = n, SPCA's top k is the data's own top-k right singular space."""
+    rng = np.random.default_rng(22)
+    m, n, k, l = 200, 40, 5, 9
+    X = rng.standard_normal((m, n)) @ np.diag(0.9 ** np.arange(n))
+    Om = P.omega_gaussian(3, n, l)
+    lz = O.lspca_fit_oversampled(X, Om, k)
+    assert lz["V"].shape == (n, k) and lz["sigma"].shape == (k,) and lz["rank"] == k
+    F = O.sketch(X, Om).T @ X
+    _, s_ref, vt = np.linalg.svd(F, full_matrices=False)
+    assert np.max(np.abs(lz["sigma"] - s_ref[:k]) / s_ref[:k]) < 1e-10
+    assert M.max_sine(vt[:k].T, lz["V"]) < 1e-9
+    sp = O.spca_fit(X, Om, route="svd")
+    assert M.max_sine(lz["full"]["V"], sp["V"]) < 1e-10
+    assert M.max_sine(lz["V"], sp["V"][:, :k]) > 1e-6
+    # l = n: span(U) = range(X); Q^T X has X's singular values
+    spn = O.spca_fit(X, P.omega_gaussian(4, n, n), route="svd")
+    _, s_x, vt_x = np.linalg.svd(X, full_matrices=False)
+    assert M.max_sine(vt_x[:k].T, spn["V"][:, :k]) < 1e-8
+    assert np.max(np.abs(spn["sigma"][:k] - s_x[:k]) / s_x[:k]) < 1e-10
+
+
+def test_oversampled_rank_r_recovery():
+    """Exactly rank-r X with r < k < l: rank r, and V's first r columns span range(B)."""
+    X, B = (t.numpy() for t in S.rank_r_exact(60, 40, 4, seed=5))
+    fit = O.lspca_fit_oversampled(X, P.omega_gaussian(11, 40, 10), 6)
+    assert fit["rank"] == 4
+    assert M.max_sine(B, fit["V"][:, :4]) < 1e-10
+    assert np.all(fit["V"][:, 4:] == 0) and np.all(fit["sigma"][4:] == 0)
+
+
 def test_closed_form_selector_omega():
     """Omega = [e_1 ... e_k]: U = X[:, :k] and F = X[:, :k]^T X."""
     rng = np.random.default_rng(5)
@@ -315,3 +378,11 @@ def test_pins_catch_planted_mistakes(monkeypatch):
     # (c) a dropped slice in Algorithm 4 breaks the Alg 2 = Alg 4 pin
     F4, _ = O.streaming_lazy(X[:1500], Om, [0, 1500])
     assert np.abs(F4 - O.chain(U, X)).max() > 1e-6
+    # (d) an oversampled fit that keeps the last k triplets instead of the top k
+    # fails the top-k pin (sigma against the library SVD of F)
+    rng = np.random.default_rng(22)
+    Xo = rng.standard_normal((200, 40)) @ np.diag(0.9 ** np.arange(40))
+    Omo = P.omega_gaussian(3, 40, 9)
+    full = O.lspca_fit(Xo, Omo)
+    s_ref = np.linalg.svd(O.sketch(Xo, Omo).T @ Xo, compute_uv=False)
+    assert np.max(np.abs(full["sigma"][-5:] - s_ref[:5]) / s_ref[:5]) > 1e-3
