@@ -137,6 +137,38 @@ int lspca_fit(lspca_ctx* ctx, const void* X, int32_t xt, int64_t m, int64_t n, i
               int32_t k, lspca_omega om, uint32_t flags, void* V, double* sigma, double* gram,
               int32_t* rank, void* stream, lspca_report* rep);
 
+/* Lazy SPCA fit of a sparse X given in CSR form (rows = samples), the format
+ * of the paper's experiments (sparse slices, Sec. IV; the cost of Algorithm 2
+ * is then proportional to nnz(X), Prop. 4): U = X Omega row by row (FP64
+ * accumulation of the gathered rows of the FP32 Omega; U stored in FP32),
+ * F = U^T X column by column over a stable CSC copy of X built on the device
+ * (every sum in a fixed order: two fits of the same input are bit-identical),
+ * then the k x k step of lspca_fit.
+ * row_ptr [dev]  m + 1 int64 offsets, row_ptr[0] = 0, nondecreasing,
+ *                row_ptr[m] = nnz.
+ * col_idx [dev]  nnz int32 column indices of the nonzeros (any order within
+ *                a row; duplicates are summed).
+ * val     [dev]  nnz FP32 values.
+ * n              columns, 1 <= n <= 2^31 - 1.
+ * k, om, V (FP32, n x k), sigma, rank, rep: as lspca_fit; flags must be 0.
+ * The workspace holds Omega (n x k FP32), U (m x k FP32), F, the CSC copy (8
+ * bytes per nonzero plus per-column counters of ceil(m / S) row blocks,
+ * S >= 256 rows chosen to keep them near 256 MB) and the k x k step's.
+ * Errors: as lspca_fit; with rep (or at lspca_sync_status) LSPCA_ERR_INVALID
+ * for a column index outside [0, n) and LSPCA_ERR_NUMERIC for NaN / Inf
+ * values.                                                                  */
+int lspca_fit_csr(lspca_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx, const float* val, int64_t m,
+                  int64_t n, int64_t nnz, int32_t k, lspca_omega om, uint32_t flags, float* V, double* sigma,
+                  int32_t* rank, void* stream, lspca_report* rep);
+
+/* The reduction map Y = X V (Sec. III-B.2) of a sparse X in CSR form (as
+ * lspca_fit_csr): Y[i, :] = sum over row i's nonzeros (j, x) of x V[j, :],
+ * FP64 accumulation, Y m x k FP32 row-major.  V [dev] n x k FP32 row-major.
+ * Errors: LSPCA_ERR_INVALID for bad arguments (column indices are checked on
+ * the device and reported by lspca_sync_status), LSPCA_ERR_CUDA.           */
+int lspca_project_csr(lspca_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx, const float* val, int64_t m,
+                      int64_t n, int64_t nnz, const float* V, int32_t k, float* Y, void* stream);
+
 /* Lazy SPCA fit with oversampling, l >= k (Sec. I-B: l = k + p with a small
  * oversampling parameter p; the Corollary of Sec. II bounds the error of the
  * l-dimensional approximation): the fit of lspca_fit with an l-column Omega

@@ -273,6 +273,20 @@ def lspca_fit(X: np.ndarray, Omega: np.ndarray, route: str = "eig") -> dict:
     return {"V": V, "sigma": sigma, "rank": rank, "U": U, "F": F, "G": gram(U)}
 
 
+def lspca_fit_sparse(Xs, Omega: np.ndarray, route: str = "eig") -> dict:
+    """Lazy SPCA (Algorithm 2) of a sparse X (a scipy.sparse matrix, rows =
+    samples): U = X Omega and F = U^T X by sparse-dense matrix products in
+    FP64, whose cost is proportional to nnz(X) (Prop. 4); then the same
+    truncated SVD of F.  Returns V^l, sigma~, rank, U, F."""
+    m, n = Xs.shape
+    Xs = Xs.astype(np.float64)
+    U = np.asarray(Xs @ np.asarray(Omega, np.float64))
+    F = np.asarray((Xs.T @ U).T)
+    dec = decompose_eig if route == "eig" else decompose_svd
+    V, sigma, rank = dec(F, m, n)
+    return {"V": V, "sigma": sigma, "rank": rank, "U": U, "F": F}
+
+
 def lspca_fit_oversampled(X: np.ndarray, Omega: np.ndarray, k: int, route: str = "eig") -> dict:
     """Lazy SPCA with oversampling (Sec. I-B: l = k + p columns of Omega, a
     small oversampling parameter p): the fit of Algorithm 2 with the n x l

@@ -2,6 +2,7 @@
 // the passes (declared in include/lspca.h).
 #include <chrono>
 #include <functional>
+#include <cstdint>
 #include <cstring>
 #include <vector>
 
@@ -388,6 +389,86 @@ namespace {
 __global__ void rank_min_kernel(const int32_t* rl, int32_t k, int32_t* rank) { *rank = *rl < k ? *rl : k; }
 }  // namespace
 
+int lspca_fit_csr(lspca_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx, const float* val, int64_t m,
+                  int64_t n, int64_t nnz, int32_t k, lspca_omega om, uint32_t flags, float* V, double* sigma,
+                  int32_t* rank, void* stream, lspca_report* rep) {
+  if (!ctx || !row_ptr || !V || !sigma || m < 1 || n < 1 || nnz < 0 || (nnz > 0 && (!col_idx || !val)))
+    return LSPCA_ERR_INVALID;
+  if (n > INT32_MAX || k < 1 || k > 256 || k > m || k > n || flags != 0) return LSPCA_ERR_INVALID;
+  int st;
+  if ((st = check_omega(om, LSPCA_F32))) return st;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return LSPCA_ERR_CUDA;
+  const auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t s = (cudaStream_t)stream;
+  Launcher L{s, &ctx->launches, ctx->num_sms};
+  float *omega = nullptr, *U = nullptr;
+  double* F = nullptr;
+  void *csc = nullptr, *small = nullptr;
+  auto plan = [&](Plan& P) {
+    omega = (float*)P.take((size_t)n * k * 4);
+    U = (float*)P.take((size_t)m * k * 4);
+    F = (double*)P.take((size_t)k * n * 8);
+    csc = P.take(csc_ws_bytes(m, n, nnz, k));
+    small = P.take(small_ws_bytes(k, n, nullptr));
+  };
+  Plan p0;
+  plan(p0);
+  if ((st = ensure_ws(ctx, p0.off + 4096, s))) return st;
+  Plan p1;
+  p1.base = (char*)ctx->ws;
+  plan(p1);
+  SmallWs sw;
+  carve_small_ws(sw, small, k, n);
+  if (rep) cudaEventRecord(ctx->ev[0], s);
+  // U = X Omega (rows), the CSC copy, F = U^T X (columns), the k x k step
+  launch_omega_dense(L, om, n, k, LSPCA_F32, omega, k, false, false);
+  launch_csr_rows(L, row_ptr, col_idx, val, m, n, nnz, omega, k, U, ctx->d_status);
+  if (rep) cudaEventRecord(ctx->ev[1], s);
+  CscView cv;
+  launch_csr_to_csc(L, row_ptr, col_idx, val, m, n, nnz, k, csc, &cv);
+  launch_csc_passf(L, cv, n, nnz, U, k, F);
+  if (rep) cudaEventRecord(ctx->ev[2], s);
+  int32_t* rk = rank ? rank : ctx->d_rank;
+  launch_decompose(L, sw, F, k, n, m, false, V, sigma, rk, ctx->d_status);
+  if (rep) cudaEventRecord(ctx->ev[4], s);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return LSPCA_ERR_CUDA;
+  if (!rep) return LSPCA_OK;
+  memset(rep, 0, sizeof(*rep));
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return LSPCA_ERR_CUDA;
+  rep->ms_sketch = ev_ms(ctx->ev[0], ctx->ev[1]);
+  rep->ms_chain = ev_ms(ctx->ev[1], ctx->ev[2]);
+  rep->ms_small = ev_ms(ctx->ev[2], ctx->ev[4]);
+  rep->bytes_x = (double)nnz * 8 + (double)(m + 1) * 8;
+  int32_t hr = 0, hst = 0, hsw = 0;
+  cudaMemcpy(&hr, rk, 4, cudaMemcpyDeviceToHost);
+  cudaMemcpy(&hst, ctx->d_status, 4, cudaMemcpyDeviceToHost);
+  cudaMemcpy(&hsw, sw.sweeps, 4, cudaMemcpyDeviceToHost);
+  cudaMemsetAsync(ctx->d_status, 0, 4, s);
+  cudaStreamSynchronize(s);
+  rep->rank = hr;
+  rep->device_status = hst;
+  rep->sweeps = hsw;
+  rep->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (hst & ST_BADINDEX) return LSPCA_ERR_INVALID;
+  if (hst & ST_NONFINITE) return LSPCA_ERR_NUMERIC;
+  if (hst & ST_TIMEOUT) return LSPCA_ERR_TIMEOUT;
+  if (hst & ST_NUMERIC) return LSPCA_ERR_NUMERIC;
+  if (hr < k) return LSPCA_WARN_RANK_DEFICIENT;
+  return LSPCA_OK;
+}
+
+int lspca_project_csr(lspca_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx, const float* val, int64_t m,
+                      int64_t n, int64_t nnz, const float* V, int32_t k, float* Y, void* stream) {
+  if (!ctx || !row_ptr || !V || !Y || m < 1 || n < 1 || n > INT32_MAX || nnz < 0 ||
+      (nnz > 0 && (!col_idx || !val)) || k < 1 || k > 256)
+    return LSPCA_ERR_INVALID;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return LSPCA_ERR_CUDA;
+  Launcher L{(cudaStream_t)stream, &ctx->launches, ctx->num_sms};
+  launch_csr_rows(L, row_ptr, col_idx, val, m, n, nnz, V, k, Y, ctx->d_status);
+  return cuda_status(cudaGetLastError());
+}
+
 int lspca_fit_oversampled(lspca_ctx* ctx, const void* X, int32_t xt, int64_t m, int64_t n, int64_t ldx, int32_t k,
                           int32_t l, lspca_omega om, uint32_t flags, void* V, double* sigma, int32_t* rank,
                           void* stream, lspca_report* rep) {
@@ -654,6 +735,7 @@ int lspca_sync_status(lspca_ctx* ctx, void* stream) {
   int32_t h = 0;
   if (cudaMemcpy(&h, ctx->d_status, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return LSPCA_ERR_CUDA;
   cudaMemset(ctx->d_status, 0, 4);
+  if (h & ST_BADINDEX) return LSPCA_ERR_INVALID;
   if (h & ST_NONFINITE) return LSPCA_ERR_NUMERIC;
   if (h & ST_TIMEOUT) return LSPCA_ERR_TIMEOUT;
   if (h & ST_NUMERIC) return LSPCA_ERR_NUMERIC;

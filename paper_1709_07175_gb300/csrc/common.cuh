@@ -16,6 +16,7 @@ enum : int {
   ST_NONFINITE = 1,   // NaN or Inf found in X
   ST_TIMEOUT = 2,     // a bounded wait gave up
   ST_NUMERIC = 4,     // eigensolver did not converge within its sweep limit
+  ST_BADINDEX = 8,    // a sparse X's column index outside [0, n)
 };
 
 // Element access: every X element type decodes exactly to float (F32/BF16/E4M3)

@@ -48,6 +48,29 @@ void launch_sketch_sparse(Launcher& L, const void* X, int xt, int64_t m, int64_t
 void launch_scan_x(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_t ldx, float* absmax, int* status);
 
 // ---- K3: the k x k step ---------------------------------------------------
+// ---- sparse X (CSR, rows = samples) ------------------------------------------
+// Y[i, :] = sum over row i's nonzeros (j, x) of x D[j, :] (D n x k FP32, FP64
+// accumulate, Y m x k FP32): the sketch with D = Omega, the reduction map with D = V.
+void launch_csr_rows(Launcher& L, const int64_t* row_ptr, const int32_t* col, const float* val, int64_t m, int64_t n,
+                     int64_t nnz, const float* D, int k, float* Y, int* status);
+// Stable CSR -> CSC (entries of a column in row order) in the workspace `ws`
+// of csc_ws_bytes bytes, which also holds pass F's segment partials.
+struct CscView {
+  int64_t* col_ptr;   // n + 1
+  int32_t* crow;      // nnz row indices
+  float* cval;        // nnz values
+  int64_t* segc;      // n: segments per column
+  int64_t* seg_ptr;   // n + 1
+  double* part;       // max_segments x k partials of F
+  int64_t max_segments;
+};
+int64_t csr_rows_per_block(int64_t m, int64_t n);
+size_t csc_ws_bytes(int64_t m, int64_t n, int64_t nnz, int k);
+void launch_csr_to_csc(Launcher& L, const int64_t* row_ptr, const int32_t* col, const float* val, int64_t m,
+                       int64_t n, int64_t nnz, int k, void* ws, CscView* out);
+// F[:, j] = sum over column j's entries (row order) of x U[i, :]; F k x n FP64.
+void launch_csc_passf(Launcher& L, const CscView& c, int64_t n, int64_t nnz, const float* U, int k, double* F);
+
 struct SmallWs {
   double* Hpart;   // splits x k x k
   double* H;       // k x k

@@ -67,6 +67,9 @@ _SIGS = {
                                       _P, ctypes.POINTER(lspca_report)]),
     "lspca_fit_oversampled": (ctypes.c_int, [_P, _P, _I32, _I64, _I64, _I64, _I32, _I32, lspca_omega, _U32, _P,
                                              _P, _P, _P, ctypes.POINTER(lspca_report)]),
+    "lspca_fit_csr": (ctypes.c_int, [_P, _P, _P, _P, _I64, _I64, _I64, _I32, lspca_omega, _U32, _P, _P, _P, _P,
+                                     ctypes.POINTER(lspca_report)]),
+    "lspca_project_csr": (ctypes.c_int, [_P, _P, _P, _P, _I64, _I64, _I64, _P, _I32, _P, _P]),
     "lspca_project": (ctypes.c_int, [_P, _P, _I32, _I64, _I64, _I64, _P, _I32, _P, _P]),
     "lspca_omega_materialize": (ctypes.c_int, [_P, lspca_omega, _I64, _I32, _I32, _P, _P]),
     "lspca_sketch": (ctypes.c_int, [_P, _P, _I32, _I64, _I64, _I64, _I32, lspca_omega, _U32, _P, _P]),
@@ -179,6 +182,26 @@ def lspca_fit_oversampled(ctx, X, k, l, om, flags, V, sigma, rank=None, stream=N
     rp = ctypes.byref(report) if report is not None else None
     return load().lspca_fit_oversampled(ctx, x, xt, m, n, ldx, k, l, om, flags, _ptr(V), _ptr(sigma), _ptr(rank),
                                         _stream(stream), rp)
+
+
+def _csr_args(row_ptr, col, val):
+    """Device CSR arrays (int64 row offsets, int32 columns, FP32 values) -> pointers, m, nnz."""
+    if row_ptr.dtype != torch.int64 or col.dtype != torch.int32 or val.dtype != torch.float32:
+        raise TypeError("CSR arrays must be int64 row offsets, int32 column indices and float32 values")
+    nnz = val.numel()
+    return _ptr(row_ptr), (_ptr(col) if nnz else None), (_ptr(val) if nnz else None), row_ptr.numel() - 1, nnz
+
+
+def lspca_fit_csr(ctx, row_ptr, col, val, n, k, om, flags, V, sigma, rank=None, stream=None, report=None) -> int:
+    rp_, cp, vp, m, nnz = _csr_args(row_ptr, col, val)
+    rp = ctypes.byref(report) if report is not None else None
+    return load().lspca_fit_csr(ctx, rp_, cp, vp, m, n, nnz, k, om, flags, _ptr(V), _ptr(sigma), _ptr(rank),
+                                _stream(stream), rp)
+
+
+def lspca_project_csr(ctx, row_ptr, col, val, n, V, k, Y, stream=None) -> int:
+    rp_, cp, vp, m, nnz = _csr_args(row_ptr, col, val)
+    return load().lspca_project_csr(ctx, rp_, cp, vp, m, n, nnz, _ptr(V), k, _ptr(Y), _stream(stream))
 
 
 def spca_fit(ctx, X, k, om, flags, V, sigma, gram=None, rank=None, stream=None, report=None) -> int:
@@ -423,6 +446,23 @@ class Context:
         rc = lspca_fit_oversampled(self.handle, X, k, l, om, flags, V, sigma, rank, stream, rep)
         _check(rc, "lspca_fit_oversampled", allow=(OK, WARN_RANK_DEFICIENT))
         return FitResult(V, sigma, rank, None, rc, rep.as_dict() if rep is not None else None)
+
+    def fit_csr(self, row_ptr, col, val, n, k, om, report=True, stream=None) -> FitResult:
+        """Fit a sparse X given by device CSR arrays (rows = samples)."""
+        dev = val.device
+        V = torch.empty(n, k, dtype=torch.float32, device=dev)
+        sigma = torch.empty(k, dtype=torch.float64, device=dev)
+        rank = torch.empty(1, dtype=torch.int32, device=dev)
+        rep = lspca_report() if report else None
+        rc = lspca_fit_csr(self.handle, row_ptr, col, val, n, k, om, 0, V, sigma, rank, stream, rep)
+        _check(rc, "lspca_fit_csr", allow=(OK, WARN_RANK_DEFICIENT))
+        return FitResult(V, sigma, rank, None, rc, rep.as_dict() if rep is not None else None)
+
+    def project_csr(self, row_ptr, col, val, n, V, stream=None):
+        k = V.shape[1]
+        Y = torch.empty(row_ptr.numel() - 1, k, dtype=torch.float32, device=V.device)
+        _check(lspca_project_csr(self.handle, row_ptr, col, val, n, V, k, Y, stream), "lspca_project_csr")
+        return Y
 
     def fit_host(self, Xh, k, om, slice_rows=0, report=True, stream=None) -> FitResult:
         """Fit a host-resident X (CPU tensor, pinned for overlapped copies) slice by slice."""

@@ -16,6 +16,12 @@ Workloads (the sigma index i runs 1..r):
 * ``e4m3_binary``  4,600,000 x 4,096 binary features, column rates
                    p_j ~ Beta(0.5, 9.5) (5 % mean density), stored FP8 E4M3,
                    k = 256, very sparse Omega p = 64.
+* ``sparse_tfidf`` (``sparse_csr``) 74,067 x 28,606 CSR at density 0.000513,
+                   the shape of Experiment 2's TF-IDF matrix: per-row counts
+                   Poisson(density n), columns drawn with Zipf-like weights
+                   (j + 10)^-0.9 (a few frequent terms, a long tail), values
+                   0.5 + |N(0, 1)| in FP32; k = 128, very sparse Omega with
+                   p = round(sqrt(n)) = 169.
 
 A and B are orthonormal (reduced QR of Gaussian draws, on the CPU in FP64 for
 every target device).  Rows of the noise are drawn in fixed chunks from
@@ -161,3 +167,33 @@ def serving_rows(seed: int, count: int, lo: int = 1, hi: int = 65536) -> np.ndar
     """Log-uniform request row counts in [lo, hi] (serving workload)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     return np.floor(np.exp(rng.uniform(math.log(lo), math.log(hi + 1), size=count))).astype(np.int64)
+
+
+SPARSE_TFIDF = {"m": 74_067, "n": 28_606, "density": 0.000513, "k": 128, "p": 169, "seed": 6, "omega_seed": 0}
+
+
+def sparse_csr(m: int, n: int, density: float, seed: int) -> tuple:
+    """Seeded sparse X in CSR form: (row_ptr int64 [m + 1], col int32 [nnz]
+    sorted within rows, val float32 [nnz]) as CPU tensors.  Row counts are
+    Poisson(density n) capped at n; the columns of a row are distinct, drawn
+    with weights (j + 10)^-0.9; values 0.5 + |N(0, 1)|."""
+    rng = np.random.default_rng(seed)
+    counts = np.minimum(rng.poisson(density * n, m), n).astype(np.int64)
+    w = (np.arange(n, dtype=np.float64) + 10.0) ** -0.9
+    cdf = np.cumsum(w / w.sum())
+    cols = []
+    for c in counts:
+        if c == 0:
+            cols.append(np.zeros(0, np.int32))
+            continue
+        picked = np.unique(np.searchsorted(cdf, rng.random(int(c) * 2 + 4)))
+        picked = picked[picked < n]
+        if picked.size < c:  # top up from the uniform tail so the row has c distinct columns
+            extra = rng.permutation(np.setdiff1d(np.arange(n), picked))[: int(c) - picked.size]
+            picked = np.union1d(picked, extra)
+        cols.append(np.sort(rng.permutation(picked)[: int(c)]).astype(np.int32))
+    row_ptr = np.zeros(m + 1, np.int64)
+    row_ptr[1:] = np.cumsum([c.size for c in cols])
+    col = np.concatenate(cols) if cols else np.zeros(0, np.int32)
+    val = (0.5 + np.abs(rng.standard_normal(col.size))).astype(np.float32)
+    return torch.from_numpy(row_ptr), torch.from_numpy(col), torch.from_numpy(val)

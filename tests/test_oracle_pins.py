@@ -386,3 +386,23 @@ def test_pins_catch_planted_mistakes(monkeypatch):
     full = O.lspca_fit(Xo, Omo)
     s_ref = np.linalg.svd(O.sketch(Xo, Omo).T @ Xo, compute_uv=False)
     assert np.max(np.abs(full["sigma"][-5:] - s_ref[:5]) / s_ref[:5]) > 1e-3
+
+
+def test_sparse_oracle_equals_dense_oracle():
+    """The sparse-input oracle (scipy sparse products) is the dense oracle on the
+    densified matrix: F to 1e-13, V and sigma to 1e-10.  The CSR generator's
+    output is valid CSR (offsets, sorted distinct columns per row)."""
+    sp = pytest.importorskip("scipy.sparse")
+    rp, c, v = S.sparse_csr(400, 300, 0.02, seed=1)
+    rp, c, v = rp.numpy(), c.numpy(), v.numpy()
+    assert rp[0] == 0 and np.all(np.diff(rp) >= 0) and rp[-1] == c.size == v.size
+    for i in range(400):
+        cols = c[rp[i]:rp[i + 1]]
+        assert np.all(np.diff(cols) > 0) and (cols.size == 0 or (cols[0] >= 0 and cols[-1] < 300))
+    Xs = sp.csr_matrix((v, c, rp), shape=(400, 300))
+    Om = P.omega_gaussian(2, 300, 16)
+    a = O.lspca_fit_sparse(Xs, Om)
+    b = O.lspca_fit(Xs.toarray(), Om)
+    assert np.max(np.abs(a["F"] - b["F"])) <= 1e-13 * np.max(np.abs(b["F"]))
+    assert np.max(np.abs(a["sigma"] - b["sigma"]) / b["sigma"]) < 1e-10
+    assert M.max_sine(a["V"], b["V"]) < 1e-10
