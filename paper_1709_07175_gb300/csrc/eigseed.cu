@@ -1,14 +1,11 @@
-// FP32 seed of the symmetric eigensolve of the k x k step (one CTA).
+// FP32 seed of the symmetric eigensolve of the k x k step.
 //
 // The FP64 refinement that follows (small.cu) needs eigenvectors accurate to
 // well under a radian per pair; a standard dense symmetric route gives them in
 // O(k^3) flops with O(k) synchronisations:
-//   1. Householder tridiagonalisation  H = Q T Q^T; the reflector of step j
-//      is kept in row j right of the diagonal (the trailing block is updated
-//      whole, so row j equals column j and is read contiguously);
-//   2. eigenvalues of T by multisection on Sturm counts: 4 threads per
-//      eigenvalue (2 for k > 128) split the bracket into 5 (3) parts per
-//      round, to the resolution of 30 halvings of the Gershgorin interval;
+//   1. Householder tridiagonalisation  H = Q T Q^T;
+//   2. eigenvalues of T by multisection on Sturm counts, to the resolution of
+//      30 halvings of the Gershgorin interval;
 //   3. eigenvectors of T by two steps of inverse iteration with an LDL^T solve
 //      of T - lambda I; eigenvalues closer than 1e-5 ||T|| form a cluster whose
 //      vectors are computed in order by one thread and Gram-Schmidt
@@ -17,10 +14,15 @@
 //      thresholds come out non-orthogonal by at most ~1e-2 here, well inside
 //      what the FP64 refinement corrects);
 //   4. back-transformation W = Q Z.
-// H is scaled by 1 / max|H_ii| first.  Matrices live in shared memory for
-// k <= 128 and in a global scratch otherwise.  Steps 1 and 4 map thread t to
-// (group t / kp, column t % kp), kp = 128 or 256, so consecutive lanes touch
-// consecutive addresses and every step needs at most four block barriers.
+// H is scaled by 1 / max|H_ii| first.
+//
+// k <= 128 runs as four launches (seed_*_kernel, below): the
+// tridiagonalisation in registers on one CTA, the multisection with one warp
+// per eigenvalue and the back-transformation with one warp per column on many
+// SMs, the inverse iteration on one CTA.  k > 128 runs in one CTA
+// (eig_seed_kernel) over a global scratch matrix: thread t maps to (group
+// t / 256, column t % 256), so consecutive lanes touch consecutive addresses
+// and every step needs at most four block barriers.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -76,11 +78,11 @@ __device__ __forceinline__ void inv_iter(const float* d, const float* e, int k, 
   for (int i = 0; i < k; ++i) z[i * zstride] *= inv;
 }
 
-// Register-resident forms of steps 1 and 4 for k <= 128: thread t owns the
-// entries (r, c) with c = t mod 128 and r = t / 128 + 4 i, i = 0..31, of the
-// matrix being reduced (step 1) or back-transformed (step 4).  Vectors indexed
-// by row are also kept "permuted", x[(r mod 4) * 32 + r / 4], so that a thread
-// reads the 32 entries of its rows with eight 16-byte broadcast loads.
+// Register-resident form of step 1 for k <= 128: thread t owns the entries
+// (r, c) with c = t mod 128 and r = t / 128 + 4 i, i = 0..31, of the matrix
+// being reduced.  Vectors indexed by row are also kept "permuted",
+// x[(r mod 4) * 32 + r / 4], so that a thread reads the 32 entries of its
+// rows with eight 16-byte broadcast loads.
 // Vectors are zero outside the active range, which makes every update a plain
 // multiply-add over all 32 rows (no predicates).
 __device__ __forceinline__ int perm_idx(int r) { return (r & 3) * 32 + (r >> 2); }
@@ -212,137 +214,17 @@ __device__ void tridiag_regs(const float* Asrc, int k, float* Vh, float* dv, flo
   __syncthreads();
 }
 
-// Step 4: Z <- H_0 H_1 ... H_{k-3} Z with the reflectors left in Vh by
-// tridiag_regs; Z (k x k, row-major, column i = eigenvector i of T) is read
-// from and written back to `Z`.  The reflectors are applied four at a time in
-// compact WY form: H_a H_{a+1} H_{a+2} H_{a+3} = I - V T V^T with V = [v_a ..
-// v_{a+3}] and T 4 x 4 upper triangular (T_ii = beta_i, T[0:i, i] = -beta_i
-// T[0:i, 0:i] V[:, 0:i]^T v_i), so Z <- Z - V (T (V^T Z)) costs two barriers
-// per four reflectors.  The T of every group is formed first, one warp per
-// group.  gp: 16 x 128 floats of partial sums; Tg: 16 floats per group.
-__device__ void backtransform_regs(float* Z, int k, const float* Vh, const float* betav, float* gp, float* Tg) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int tr = tid & 127, tg = tid >> 7;
-  const int nr = k > 2 ? k - 2 : 0;  // reflectors 0 .. nr - 1
-  const int ng = (nr + 3) / 4;
-  float z[32];
-#pragma unroll
-  for (int i = 0; i < 32; ++i) {
-    const int r = tg + 4 * i;
-    z[i] = (r < k && tr < k) ? Z[r * k + tr] : 0.f;
-  }
-  // T of each group: the six inner products v_l . v_i (l < i) by one warp
-  for (int g = warp; g < ng; g += kSeedThreads / 32) {
-    const int a = 4 * g;
-    float w[6];
-    int t = 0;
-#pragma unroll
-    for (int i = 1; i < 4; ++i)
-#pragma unroll
-      for (int l = 0; l < i; ++l) {
-        float d = 0.f;
-        if (a + i < nr) {
-#pragma unroll
-          for (int q = 0; q < 4; ++q) d = fmaf(Vh[(a + l) * 128 + lane + 32 * q], Vh[(a + i) * 128 + lane + 32 * q], d);
-        }
-        w[t++] = warp_sumf(d);
-      }
-    if (lane == 0) {
-      float T[4][4] = {};
-      t = 0;
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const float bi = (a + i < nr) ? betav[a + i] : 0.f;
-        float tmp[4] = {0.f, 0.f, 0.f, 0.f};
-        for (int l = 0; l < i; ++l) tmp[l] = -bi * w[t++];
-        for (int l = 0; l < i; ++l) {
-          float acc = 0.f;
-          for (int m = l; m < i; ++m) acc = fmaf(T[l][m], tmp[m], acc);
-          T[l][i] = acc;
-        }
-        T[i][i] = bi;
-      }
-      for (int i = 0; i < 16; ++i) Tg[g * 16 + i] = T[i / 4][i % 4];
-    }
-  }
-  __syncthreads();
-  for (int g = ng - 1; g >= 0; --g) {
-    const int a = 4 * g;
-    // partial inner products v_{a+i} . z over the thread's 32 rows
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      float s0 = 0.f, s1 = 0.f;
-      if (a + i < nr) {
-        const float4* vp = reinterpret_cast<const float4*>(Vh + (a + i) * 128 + tg * 32);
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const float4 v = vp[q];
-          s0 = fmaf(v.x, z[4 * q], s0);
-          s1 = fmaf(v.y, z[4 * q + 1], s1);
-          s0 = fmaf(v.z, z[4 * q + 2], s0);
-          s1 = fmaf(v.w, z[4 * q + 3], s1);
-        }
-      }
-      gp[(i * 4 + tg) * 128 + tr] = s0 + s1;
-    }
-    __syncthreads();
-    float S[4], u[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-      S[i] = gp[(i * 4) * 128 + tr] + gp[(i * 4 + 1) * 128 + tr] + gp[(i * 4 + 2) * 128 + tr] +
-             gp[(i * 4 + 3) * 128 + tr];
-    const float* T = Tg + g * 16;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      float acc = 0.f;
-#pragma unroll
-      for (int l = i; l < 4; ++l) acc = fmaf(T[i * 4 + l], S[l], acc);
-      u[i] = acc;
-    }
-    // z <- z - V u over the thread's rows
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      if (a + i < nr) {
-        const float4* vp = reinterpret_cast<const float4*>(Vh + (a + i) * 128 + tg * 32);
-        const float ui = u[i];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const float4 v = vp[q];
-          z[4 * q] -= v.x * ui;
-          z[4 * q + 1] -= v.y * ui;
-          z[4 * q + 2] -= v.z * ui;
-          z[4 * q + 3] -= v.w * ui;
-        }
-      }
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int i = 0; i < 32; ++i) {
-    const int r = tg + 4 * i;
-    if (r < k && tr < k) Z[r * k + tr] = z[i];
-  }
-  __syncthreads();
-}
-
 __global__ void __launch_bounds__(kSeedThreads, 1) eig_seed_kernel(const double* __restrict__ H, int k, float* gA,
                                                                 float* gZ, float* gQ, double* __restrict__ Xout,
                                                                 double* __restrict__ lam_out, double* scal,
                                                                 int32_t* nclusters) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ float dv[256], ev[256], e2v[256], betav[256], wl[256], pv_s[256], lamv[256], vv_s[256];
   __shared__ float gpart[kSeedThreads];
-  __shared__ __align__(16) float gp16[16 * 128];  // back-transformation partials
-  __shared__ float Tgrp[16 * 32];                  // compact-WY T of each group of four reflectors
   __shared__ float coef[4];
   __shared__ int clstart[257];
-  const bool sm = k <= 128;
-  // k <= 128: A (scaled H, then the reflectors, 128 k floats), Z, Qs in SMEM
-  float* A = sm ? reinterpret_cast<float*>(smem_raw) : gA;               // k x k row-major
-  float* Z = sm ? reinterpret_cast<float*>(smem_raw) + 128 * k : gZ;     // k x k, column j = eigenvector j
-  float* Qs = sm ? Z + k * k : gQ;  // inverse-iteration scratch, one row per cluster
-  __shared__ __align__(16) float vperm[128], wperm[128];
-  __shared__ float rowbuf[128], vfl[128];
+  float* A = gA;   // k x k row-major: scaled H, then the reflectors
+  float* Z = gZ;   // k x k, column j = eigenvector j
+  float* Qs = gQ;  // inverse-iteration scratch, one row per cluster
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kSeedThreads / 32;
 
   // scale and load; ||H||_F for the refinement's noise floor
@@ -383,103 +265,98 @@ __global__ void __launch_bounds__(kSeedThreads, 1) eig_seed_kernel(const double*
   }
   __syncthreads();
 
-  // ---- 1. tridiagonalisation: in registers for k <= 128 (tridiag_regs),
-  // else the form below over the SMEM/global matrix
-  const int kp = k <= 128 ? 128 : 256;  // padded width: thread t = (t / kp, t % kp)
-  const int GR = kSeedThreads / kp;      // 4 or 2 groups
+  // ---- 1. tridiagonalisation over the global scratch matrix
+  const int kp = 256;                // padded width: thread t = (t / kp, t % kp)
+  const int GR = kSeedThreads / kp;  // 2 groups
   const int tr = tid % kp, tg = tid / kp;
-  if (sm) {
-    tridiag_regs(A, k, A, dv, ev, betav, rowbuf, vfl, wl, vperm, wperm, gpart);
-  } else {
-    // Step j reflects the trailing block
-    // A' = A[j+1:, j+1:] with H = I - beta v v^T built from row j (equal to
-    // column j: the trailing block is kept whole and symmetric).  Four barriers
-    // per step:
-    //   a. warp 0: norm of row j right of the diagonal, alpha, beta, v (stored
-    //      back into row j for the back-transformation and into vv_s);
-    //   b. p = A' v: thread (g, r) sums a quarter (k <= 128) or half of the
-    //      terms of p_r, reading A'[l][r] = A'[r][l] along rows (consecutive
-    //      lanes, consecutive addresses);
-    //   c. warp 0: p = beta sum of the partials, K = beta p.v / 2, w = p - K v;
-    //   d. A' -= v w^T + w v^T, thread (g, c) over rows r = g mod GR.
-    for (int j = 0; j + 2 < k; ++j) {
-      const int n1 = k - j - 1;
-      float* rowj = A + j * k + (j + 1);  // row j right of the diagonal (length n1)
-      if (warp == 0) {
-        float sq = 0.f;
-        for (int r = 1 + lane; r < n1; r += 32) sq = fmaf(rowj[r], rowj[r], sq);
-        sq = warp_sumf(sq);
-        const float x0 = rowj[0];
-        const float nrm = sqrtf(x0 * x0 + sq);
-        float alpha = 0.f, beta = 0.f, v0 = x0;
-        if (nrm > 0.f) {
-          alpha = x0 >= 0.f ? -nrm : nrm;
-          v0 = x0 - alpha;
-          const float vv = v0 * v0 + sq;
-          beta = vv > 0.f ? 2.f / vv : 0.f;
-        }
-        for (int r = lane; r < n1; r += 32) vv_s[r] = r == 0 ? v0 : rowj[r];
-        __syncwarp();
-        if (lane == 0) {
-          dv[j] = A[j * k + j];
-          ev[j] = (nrm > 0.f) ? alpha : x0;
-          betav[j] = beta;
-          rowj[0] = v0;
-        }
+// Step j reflects the trailing block
+  // A' = A[j+1:, j+1:] with H = I - beta v v^T built from row j (equal to
+  // column j: the trailing block is kept whole and symmetric).  Four barriers
+  // per step:
+  //   a. warp 0: norm of row j right of the diagonal, alpha, beta, v (stored
+  //      back into row j for the back-transformation and into vv_s);
+  //   b. p = A' v: thread (g, r) sums a quarter (k <= 128) or half of the
+  //      terms of p_r, reading A'[l][r] = A'[r][l] along rows (consecutive
+  //      lanes, consecutive addresses);
+  //   c. warp 0: p = beta sum of the partials, K = beta p.v / 2, w = p - K v;
+  //   d. A' -= v w^T + w v^T, thread (g, c) over rows r = g mod GR.
+  for (int j = 0; j + 2 < k; ++j) {
+    const int n1 = k - j - 1;
+    float* rowj = A + j * k + (j + 1);  // row j right of the diagonal (length n1)
+    if (warp == 0) {
+      float sq = 0.f;
+      for (int r = 1 + lane; r < n1; r += 32) sq = fmaf(rowj[r], rowj[r], sq);
+      sq = warp_sumf(sq);
+      const float x0 = rowj[0];
+      const float nrm = sqrtf(x0 * x0 + sq);
+      float alpha = 0.f, beta = 0.f, v0 = x0;
+      if (nrm > 0.f) {
+        alpha = x0 >= 0.f ? -nrm : nrm;
+        v0 = x0 - alpha;
+        const float vv = v0 * v0 + sq;
+        beta = vv > 0.f ? 2.f / vv : 0.f;
       }
-      __syncthreads();
-      const float beta = betav[j];
-      if (beta == 0.f) continue;  // uniform: the block is already reduced here
-      const float* Ap = A + (j + 1) * k + (j + 1);
-      {
-        const int chunk = (n1 + GR - 1) / GR;
-        const int l0 = tg * chunk, l1 = min(n1, l0 + chunk);
-        float a0 = 0.f, a1 = 0.f;
-        if (tr < n1) {
-          int l = l0;
-          for (; l + 1 < l1; l += 2) {
-            a0 = fmaf(Ap[l * k + tr], vv_s[l], a0);
-            a1 = fmaf(Ap[(l + 1) * k + tr], vv_s[l + 1], a1);
-          }
-          if (l < l1) a0 = fmaf(Ap[l * k + tr], vv_s[l], a0);
-        }
-        gpart[tg * kp + tr] = a0 + a1;
+      for (int r = lane; r < n1; r += 32) vv_s[r] = r == 0 ? v0 : rowj[r];
+      __syncwarp();
+      if (lane == 0) {
+        dv[j] = A[j * k + j];
+        ev[j] = (nrm > 0.f) ? alpha : x0;
+        betav[j] = beta;
+        rowj[0] = v0;
       }
-      __syncthreads();
-      if (warp == 0) {
-        float pv = 0.f;
-        for (int r = lane; r < n1; r += 32) {
-          float s = 0.f;
-          for (int g = 0; g < GR; ++g) s += gpart[g * kp + r];
-          s *= beta;
-          pv_s[r] = s;
-          pv = fmaf(s, vv_s[r], pv);
-        }
-        pv = warp_sumf(pv);
-        const float K = 0.5f * beta * pv;
-        for (int r = lane; r < n1; r += 32) wl[r] = pv_s[r] - K * vv_s[r];
-      }
-      __syncthreads();
-      if (tr < n1) {
-        const float vc = vv_s[tr], wc = wl[tr];
-        for (int r = tg; r < n1; r += GR) {
-          float* a = A + (j + 1 + r) * k + (j + 1) + tr;
-          *a -= vv_s[r] * wc + wl[r] * vc;
-        }
-      }
-      __syncthreads();
     }
-    if (tid == 0) {
-      if (k >= 2) {
-        dv[k - 2] = A[(k - 2) * k + (k - 2)];
-        ev[k - 2] = A[(k - 1) * k + (k - 2)];
+    __syncthreads();
+    const float beta = betav[j];
+    if (beta == 0.f) continue;  // uniform: the block is already reduced here
+    const float* Ap = A + (j + 1) * k + (j + 1);
+    {
+      const int chunk = (n1 + GR - 1) / GR;
+      const int l0 = tg * chunk, l1 = min(n1, l0 + chunk);
+      float a0 = 0.f, a1 = 0.f;
+      if (tr < n1) {
+        int l = l0;
+        for (; l + 1 < l1; l += 2) {
+          a0 = fmaf(Ap[l * k + tr], vv_s[l], a0);
+          a1 = fmaf(Ap[(l + 1) * k + tr], vv_s[l + 1], a1);
+        }
+        if (l < l1) a0 = fmaf(Ap[l * k + tr], vv_s[l], a0);
       }
-      dv[k - 1] = A[(k - 1) * k + (k - 1)];
-      if (k >= 2) betav[k - 2] = 0.f;
-      betav[k - 1] = 0.f;
+      gpart[tg * kp + tr] = a0 + a1;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      float pv = 0.f;
+      for (int r = lane; r < n1; r += 32) {
+        float s = 0.f;
+        for (int g = 0; g < GR; ++g) s += gpart[g * kp + r];
+        s *= beta;
+        pv_s[r] = s;
+        pv = fmaf(s, vv_s[r], pv);
+      }
+      pv = warp_sumf(pv);
+      const float K = 0.5f * beta * pv;
+      for (int r = lane; r < n1; r += 32) wl[r] = pv_s[r] - K * vv_s[r];
+    }
+    __syncthreads();
+    if (tr < n1) {
+      const float vc = vv_s[tr], wc = wl[tr];
+      for (int r = tg; r < n1; r += GR) {
+        float* a = A + (j + 1 + r) * k + (j + 1) + tr;
+        *a -= vv_s[r] * wc + wl[r] * vc;
+      }
     }
     __syncthreads();
   }
+  if (tid == 0) {
+    if (k >= 2) {
+      dv[k - 2] = A[(k - 2) * k + (k - 2)];
+      ev[k - 2] = A[(k - 1) * k + (k - 2)];
+    }
+    dv[k - 1] = A[(k - 1) * k + (k - 1)];
+    if (k >= 2) betav[k - 2] = 0.f;
+    betav[k - 1] = 0.f;
+  }
+  __syncthreads();
   for (int i = tid; i < k; i += kSeedThreads) e2v[i] = (i + 1 < k) ? ev[i] * ev[i] : 0.f;
 
   // Gershgorin interval, ||T||, pivmin
@@ -568,33 +445,28 @@ __global__ void __launch_bounds__(kSeedThreads, 1) eig_seed_kernel(const double*
   //   1. partial of w_c = v^T Z[j+1:, c] over the rows r = g mod GR;
   //   2. w_c = beta (sum of the GR partials of column c), then
   //      Z[j+1+r][c] -= v_r w_c over the same rows.
-  if (sm) {
-    backtransform_regs(Z, k, A, betav, gp16, Tgrp);
-  } else {
-    for (int j = k - 3; j >= 0; --j) {
-      const float beta = betav[j];
-      if (beta == 0.f) continue;
-      const int n1 = k - j - 1;
-      const float* v = A + j * k + (j + 1);
-      float acc = 0.f;
-      if (tr < k)
-        for (int r = tg; r < n1; r += GR) acc = fmaf(v[r], Z[(j + 1 + r) * k + tr], acc);
-      gpart[tg * kp + tr] = acc;
-      __syncthreads();
-      if (tr < k) {
-        float wc = 0.f;
-        for (int g = 0; g < GR; ++g) wc += gpart[g * kp + tr];
-        wc *= beta;
-        for (int r = tg; r < n1; r += GR) Z[(j + 1 + r) * k + tr] -= v[r] * wc;
-      }
-      __syncthreads();
+for (int j = k - 3; j >= 0; --j) {
+    const float beta = betav[j];
+    if (beta == 0.f) continue;
+    const int n1 = k - j - 1;
+    const float* v = A + j * k + (j + 1);
+    float acc = 0.f;
+    if (tr < k)
+      for (int r = tg; r < n1; r += GR) acc = fmaf(v[r], Z[(j + 1 + r) * k + tr], acc);
+    gpart[tg * kp + tr] = acc;
+    __syncthreads();
+    if (tr < k) {
+      float wc = 0.f;
+      for (int g = 0; g < GR; ++g) wc += gpart[g * kp + tr];
+      wc *= beta;
+      for (int r = tg; r < n1; r += GR) Z[(j + 1 + r) * k + tr] -= v[r] * wc;
     }
+    __syncthreads();
   }
   for (int e = tid; e < k * k; e += kSeedThreads) Xout[e] = (double)Z[e];
   for (int i = tid; i < k; i += kSeedThreads) lam_out[i] = (double)lamv[i] * hmax_s;
 }
 
-size_t eig_seed_smem(int k) { return k <= 128 ? ((size_t)128 * k + (size_t)2 * k * k) * sizeof(float) : 0; }
 
 // ---------------------------------------------------------------------------
 // The same seed for k <= 128 in four launches, so that the steps that are
@@ -832,9 +704,7 @@ void launch_eig_seed(Launcher& L, const double* H, int k, float* gA, float* gZ, 
     L.count(4);
     return;
   }
-  const size_t shm = eig_seed_smem(k);
-  cudaFuncSetAttribute(eig_seed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-  eig_seed_kernel<<<1, kSeedThreads, shm, L.stream>>>(H, k, gA, gZ, gQ, Xout, lam, scal, nclusters);
+  eig_seed_kernel<<<1, kSeedThreads, 0, L.stream>>>(H, k, gA, gZ, gQ, Xout, lam, scal, nclusters);
   L.count(1);
 }
 
