@@ -139,8 +139,9 @@ int lspca_fit(lspca_ctx* ctx, const void* X, int32_t xt, int64_t m, int64_t n, i
 
 /* Lazy SPCA fit of a sparse X given in CSR form (rows = samples), the format
  * of the paper's experiments (sparse slices, Sec. IV; the cost of Algorithm 2
- * is then proportional to nnz(X), Prop. 4): U = X Omega row by row (FP64
- * accumulation of the gathered rows of the FP32 Omega; U stored in FP32),
+ * is then proportional to nnz(X), Prop. 4): U = X Omega row by row
+ * (compensated FP32 sums of the gathered rows of the FP32 Omega: exact
+ * products, Neumaier summation; U stored in FP32),
  * F = U^T X column by column over a stable CSC copy of X built on the device
  * (every sum in a fixed order: two fits of the same input are bit-identical),
  * then the k x k step of lspca_fit.
@@ -163,7 +164,7 @@ int lspca_fit_csr(lspca_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx
 
 /* The reduction map Y = X V (Sec. III-B.2) of a sparse X in CSR form (as
  * lspca_fit_csr): Y[i, :] = sum over row i's nonzeros (j, x) of x V[j, :],
- * FP64 accumulation, Y m x k FP32 row-major.  V [dev] n x k FP32 row-major.
+ * compensated FP32 sums, Y m x k FP32 row-major.  V [dev] n x k FP32 row-major.
  * Errors: LSPCA_ERR_INVALID for bad arguments (column indices are checked on
  * the device and reported by lspca_sync_status), LSPCA_ERR_CUDA.           */
 int lspca_project_csr(lspca_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx, const float* val, int64_t m,

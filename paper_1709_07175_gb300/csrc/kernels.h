@@ -49,8 +49,9 @@ void launch_scan_x(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int
 
 // ---- K3: the k x k step ---------------------------------------------------
 // ---- sparse X (CSR, rows = samples) ------------------------------------------
-// Y[i, :] = sum over row i's nonzeros (j, x) of x D[j, :] (D n x k FP32, FP64
-// accumulate, Y m x k FP32): the sketch with D = Omega, the reduction map with D = V.
+// Y[i, :] = sum over row i's nonzeros (j, x) of x D[j, :] (D n x k FP32,
+// compensated FP32 sums, Y m x k FP32): the sketch with D = Omega, the
+// reduction map with D = V.
 void launch_csr_rows(Launcher& L, const int64_t* row_ptr, const int32_t* col, const float* val, int64_t m, int64_t n,
                      int64_t nnz, const float* D, int k, float* Y, int* status);
 // Stable CSR -> CSC (entries of a column in row order) in the workspace `ws`

@@ -2,7 +2,8 @@
 // (F = U^T X, Algorithm 2 step 2) and the reduction map Y = X V for a data
 // matrix given by its nonzeros, the format of the paper's experiments (sparse
 // slices, Sec. IV).  The work is proportional to nnz(X) (Prop. 4's nnz(X) l
-// terms), so these kernels are plain SIMT gathers in FP64 accumulation:
+// terms), so these kernels are plain SIMT gathers with compensated FP32 dot
+// products (exact products, Neumaier sums: a few ulps, at FP32 rates):
 //
 //   rows:   Y[i, :] = sum over the nonzeros (j, x) of row i of x D[j, :]
 //           (D = Omega for the sketch, V for the reduction map), one warp per
@@ -29,11 +30,26 @@ namespace lspca {
 
 namespace {
 
+// Compensated FP32 dot product: the product x d is taken exactly as y + e
+// (y rounded, e = fma(x, d, -y) its error) and the sum by Neumaier's method,
+// s + c then carries the sum to a few ulps whatever the number of terms, at
+// FP32 rates (GB300 runs FP64 FMAs at 1/64 of the FP32 rate).  The rounded
+// product is formed on its own (no contraction into the sum), as the
+// compensation assumes.
+__device__ __forceinline__ void nsum_add(float& s, float& c, float x, float d) {
+  const float y = __fmul_rn(x, d);
+  const float e = fmaf(x, d, -y);
+  const float t = __fadd_rn(s, y);
+  const float r = fabsf(s) >= fabsf(y) ? __fadd_rn(__fsub_rn(s, t), y) : __fadd_rn(__fsub_rn(y, t), s);
+  c = __fadd_rn(c, __fadd_rn(r, e));
+  s = t;
+}
+
 // A row offset clamped to [0, nnz]: inconsistent offsets (flagged by the row
 // kernel) never take a kernel outside the arrays.
 __device__ __forceinline__ int64_t clamp_nnz(int64_t p, int64_t nnz) { return p < 0 ? 0 : (p > nnz ? nnz : p); }
 
-// Y[i, :] (+)= sum_p val[p] D[col[p], :]; FP64 accumulate, FP32 output.
+// Y[i, :] = sum_p val[p] D[col[p], :]; compensated FP32 sums, FP32 output.
 __global__ void __launch_bounds__(256) csr_rows_kernel(const int64_t* __restrict__ row_ptr,
                                                        const int32_t* __restrict__ col,
                                                        const float* __restrict__ val, int64_t m, int64_t n,
@@ -42,7 +58,7 @@ __global__ void __launch_bounds__(256) csr_rows_kernel(const int64_t* __restrict
   const int lane = threadIdx.x & 31;
   const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (i >= m) return;
-  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // columns lane + 32 t, k <= 256
+  float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0}, cmp[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // columns lane + 32 t, k <= 256
   const int64_t a = row_ptr[i], e = row_ptr[i + 1];
   int bad = (e < a || a < 0 || e > nnz || (i == 0 && a != 0) || (i == m - 1 && e != nnz)) ? ST_BADINDEX : 0;
   const int64_t p0 = clamp_nnz(a, nnz), p1 = clamp_nnz(e, nnz);
@@ -58,13 +74,13 @@ __global__ void __launch_bounds__(256) csr_rows_kernel(const int64_t* __restrict
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
       const int c = lane + 32 * t;
-      if (c < k) acc[t] = fma((double)x, (double)d[c], acc[t]);
+      if (c < k) nsum_add(acc[t], cmp[t], x, d[c]);
     }
   }
 #pragma unroll
   for (int t = 0; t < 8; ++t) {
     const int c = lane + 32 * t;
-    if (c < k) Y[i * k + c] = (float)acc[t];
+    if (c < k) Y[i * k + c] = __fadd_rn(acc[t], cmp[t]);
   }
   if (bad && lane == 0) atomicOr(status, bad);
 }
@@ -171,7 +187,8 @@ __global__ void seg_count_kernel(const int64_t* __restrict__ col_ptr, int64_t n,
 }
 
 // One warp per segment s of column j (seg_ptr[j] <= s < seg_ptr[j + 1]):
-// P[s, :] = sum over the segment's entries (row order) of x U[i, :], FP64.
+// P[s, :] = sum over the segment's entries (row order) of x U[i, :]
+// (compensated FP32 sum, written as the FP64 value s + c).
 __global__ void __launch_bounds__(256) passf_seg_kernel(const int64_t* __restrict__ col_ptr,
                                                         const int32_t* __restrict__ crow,
                                                         const float* __restrict__ cval, int64_t n, int64_t nnz,
@@ -189,11 +206,11 @@ __global__ void __launch_bounds__(256) passf_seg_kernel(const int64_t* __restric
   const int64_t j = lo;
   const int64_t p0 = col_ptr[j] + (s - seg_ptr[j]) * kSeg;
   const int64_t p1 = min(min(col_ptr[j + 1], p0 + kSeg), nnz);  // nnz: see csc_fill_kernel
-  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0}, cmp[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   int64_t p = p0;
   for (; p + 4 <= p1; p += 4) {  // four entries' loads in flight at once
     int64_t i[4];
-    double x[4];
+    float x[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       i[u] = crow[p + u];
@@ -205,23 +222,23 @@ __global__ void __launch_bounds__(256) passf_seg_kernel(const int64_t* __restric
 #pragma unroll
       for (int t = 0; t < 8; ++t) {
         const int c = lane + 32 * t;
-        if (c < k) acc[t] = fma(x[u], (double)r[c], acc[t]);
+        if (c < k) nsum_add(acc[t], cmp[t], x[u], r[c]);
       }
     }
   }
   for (; p < p1; ++p) {
     const float* r = U + (int64_t)crow[p] * k;
-    const double x = cval[p];
+    const float x = cval[p];
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
       const int c = lane + 32 * t;
-      if (c < k) acc[t] = fma(x, (double)r[c], acc[t]);
+      if (c < k) nsum_add(acc[t], cmp[t], x, r[c]);
     }
   }
 #pragma unroll
   for (int t = 0; t < 8; ++t) {
     const int c = lane + 32 * t;
-    if (c < k) P[s * k + c] = acc[t];
+    if (c < k) P[s * k + c] = (double)acc[t] + (double)cmp[t];
   }
 }
 
