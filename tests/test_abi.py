@@ -58,3 +58,23 @@ def test_library_targets_sm_103a(libpath):
     # the build passes exactly one -gencode for sm_103a
     from paper_1709_07175_gb300 import build
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_csr_binding_checks_array_types():
+    """The CSR entry points take int64 row offsets, int32 column indices and
+    FP32 values; the binding rejects other types before any library call, and
+    passes null column / value pointers for an X without nonzeros."""
+    import torch
+
+    from paper_1709_07175_gb300 import lspca as L
+    rp = torch.tensor([0, 1, 2], dtype=torch.int64)
+    col = torch.tensor([0, 1], dtype=torch.int32)
+    val = torch.tensor([1.0, 2.0], dtype=torch.float32)
+    for bad in ((rp.int(), col, val), (rp, col.long(), val), (rp, col, val.double())):
+        with pytest.raises(TypeError):
+            L._csr_args(*bad)
+    p_rp, p_col, p_val, m, nnz = L._csr_args(rp, col, val)
+    assert (m, nnz) == (2, 2) and p_col is not None and p_val is not None
+    empty = L._csr_args(torch.zeros(4, dtype=torch.int64), torch.zeros(0, dtype=torch.int32),
+                        torch.zeros(0, dtype=torch.float32))
+    assert empty[1] is None and empty[2] is None and empty[3:] == (3, 0)
