@@ -105,7 +105,15 @@ __global__ void csc_count_kernel(const unsigned long long* __restrict__ hist, in
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   unsigned long long s = 0;
-  for (int64_t b = 0; b < nblocks; ++b) s += hist[b * n + j];
+  int64_t b = 0;
+  for (; b + 8 <= nblocks; b += 8) {  // eight loads in flight, summed in order
+    unsigned long long c[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) c[u] = hist[(b + u) * n + j];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) s += c[u];
+  }
+  for (; b < nblocks; ++b) s += hist[b * n + j];
   cnt[j] = (int64_t)s;
 }
 
@@ -145,7 +153,18 @@ __global__ void csc_offsets_kernel(unsigned long long* hist, int64_t nblocks, in
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   unsigned long long run = (unsigned long long)col_ptr[j];
-  for (int64_t b = 0; b < nblocks; ++b) {
+  int64_t b = 0;
+  for (; b + 8 <= nblocks; b += 8) {  // eight loads in flight, the prefix in order
+    unsigned long long c[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) c[u] = hist[(b + u) * n + j];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      hist[(b + u) * n + j] = run;
+      run += c[u];
+    }
+  }
+  for (; b < nblocks; ++b) {
     const unsigned long long c = hist[b * n + j];
     hist[b * n + j] = run;
     run += c;
