@@ -4,14 +4,16 @@
  * Method: Wojnowicz, Nguyen, Li, Zhao, "Lazy stochastic principal component
  * analysis", arXiv 1709.07175.  Notation of the paper: X is m x n with the
  * samples as rows (Sec. I-A), Omega is n x l with l = k (no oversampling, as
- * in Experiment 1), U = X Omega (Eq. 1, c = 1), F = U^T X, V is n x k, and
- * the reduction is Y = X V (Sec. III-B.2, Eq. "dim_reduction_maps").
+ * in Experiment 1; lspca_fit_oversampled takes l > k), U = X Omega (Eq. 1,
+ * c = 1), F = U^T X, V is n x k, and the reduction is Y = X V (Sec. III-B.2,
+ * Eq. "dim_reduction_maps").
  *
  * Conventions for every entry point
  * ---------------------------------
- * - All matrices are row-major.  X has leading dimension ldx (elements,
- *   ldx >= n); ldx * sizeof(element) must be a multiple of 16 bytes and X
- *   16-byte aligned (pad rows otherwise).  V is n x k (ld k), Y is m x k
+ * - All matrices are row-major.  A dense X has leading dimension ldx
+ *   (elements, ldx >= n); ldx * sizeof(element) must be a multiple of 16
+ *   bytes and X 16-byte aligned (pad rows otherwise).  A sparse X is given in
+ *   CSR form (lspca_fit_csr).  V is n x k (ld k), Y is m x k
  *   (ld k), U is m x k (ld k), F is k x n (ld n), G is k x k (ld k).
  * - The "result type" of a path is FP64 when X is LSPCA_F64 and FP32
  *   otherwise; V, U and Y are stored in the result type.
