@@ -101,7 +101,7 @@ typedef struct {
   double bytes_x;         /* bytes of X read per pass                          */
   int32_t rank;           /* numerical rank (rank rule)                         */
   int32_t device_status;  /* status word read from the device                  */
-  int32_t sweeps;         /* eigenvalue clusters seen by the FP32 eigen seed    */
+  int32_t sweeps;         /* levels of the graded k x k eigensolve that ran (1-3) */
   int32_t reserved;
 } lspca_report;
 

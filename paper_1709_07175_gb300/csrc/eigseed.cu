@@ -1,42 +1,62 @@
-// FP32 seed of the symmetric eigensolve of the k x k step.
+// FP32 seed of the symmetric eigensolve of the k x k step (k <= 256), one
+// level of a graded solve.
 //
-// The FP64 refinement that follows (small.cu) needs eigenvectors accurate to
-// well under a radian per pair; a standard dense symmetric route gives them in
-// O(k^3) flops with O(k) synchronisations:
-//   1. Householder tridiagonalisation  H = Q T Q^T;
-//   2. eigenvalues of T by multisection on Sturm counts, to the resolution of
-//      30 halvings of the Gershgorin interval;
-//   3. eigenvectors of T by two steps of inverse iteration with an LDL^T solve
-//      of T - lambda I; eigenvalues closer than 1e-5 ||T|| form a cluster whose
-//      vectors are computed in order by one thread and Gram-Schmidt
-//      orthogonalised against (up to 32 of) the cluster's earlier vectors, as
-//      LAPACK's stein does (which uses 1e-3 ||T||: pairs between the two
-//      thresholds come out non-orthogonal by at most ~1e-2 here, well inside
-//      what the FP64 refinement corrects);
-//   4. back-transformation W = Q Z.
-// H is scaled by 1 / max|H_ii| first.
+// The eigen route of the table footnote (Sec. III) squares the singular
+// values of F = U^T X, so the eigenvalues of H = F F^T span the fourth power
+// of the spectrum of X: on uncentred binary features the first is 10^4 to
+// 10^5 times the rest, and a decaying spectrum puts most eigenvalues far
+// below FP32 resolution of the largest.  An FP32 seed of the whole H cannot
+// separate those.  The solve is therefore graded (small.cu drives it):
+//   level 0   seeds H;  eigenvalues below kTailTau times the largest form the
+//             "tail" and get only an orthonormal basis of their subspace;
+//   level l   after the FP64 refinement of level l - 1, seeds the leading
+//             block S[0:t, 0:t] of S = W^T H W over that tail (t columns,
+//             a prefix in ascending order), scaled by its own largest entry,
+//             so FP32 resolves the next four decades; its vectors rotate the
+//             tail columns of W.
+// Block sizes live on the device (lvl[l]), so the launch sequence is fixed
+// and a level whose block has fewer than two columns does nothing.
 //
-// k <= 128 runs as four launches (seed_*_kernel, below): the
-// tridiagonalisation in registers on one CTA, the multisection with one warp
-// per eigenvalue and the back-transformation with one warp per column on many
-// SMs, the inverse iteration on one CTA.  k > 128 runs in one CTA
-// (eig_seed_kernel) over a global scratch matrix: thread t maps to (group
-// t / 256, column t % 256), so consecutive lanes touch consecutive addresses
-// and every step needs at most four block barriers.
+// One level of the seed, on the s x s block (s <= 256), scaled by 1/max|M_ii|:
+//   1. seed_tri_kernel (one CTA): Householder tridiagonalisation M = Q T Q^T.
+//      Thread (g, c) owns column c and rows g + 4i; rows below 128 in
+//      registers, the rest in shared memory.  Every thread derives the
+//      reflector of step j from row j (published by its owners with per-warp
+//      partial norms), so a step needs three block barriers and no phase
+//      runs on a single warp.
+//   2. seed_bisect_kernel: one warp per eigenvalue, Sturm counts at 32
+//      interior points per round, 6 rounds (33^6 >= 2^30: the resolution of
+//      30 halvings of the Gershgorin interval).
+//   3. seed_ii_kernel: one thread per eigenvalue outside the tail, two steps
+//      of inverse iteration with an LDL^T solve of T - lambda I.
+//   4. seed_orth_kernel (one CTA): eigenvalues closer than kClusterTol ||T||
+//      form clusters; each cluster's vectors are replaced by an orthonormal
+//      basis of their span (Householder QR), and the tail gets an
+//      orthonormal basis of the complement of the other vectors (the
+//      trailing columns of the Q factor of their Householder QR).  The cost
+//      is one QR step per clustered vector, plus one per non-tail vector when
+//      there is a tail.
+//   5. seed_back_kernel: W = Q Z, one warp per column.
 #include "common.cuh"
 #include "kernels.h"
 
 namespace lspca {
 
-constexpr int kSeedThreads = 512;
+constexpr float kTailTau = 1e-4f;     // tail: eigenvalues below this times the largest of the level
+constexpr float kClusterTol = 1e-5f;  // cluster: consecutive eigenvalues closer than this times ||T||
+
+// Layout of `tri` (floats), for a k-wide workspace:
+//   d [0, k), e [k, 2k), e^2 [2k, 3k), beta [3k, 4k), eigenvalues of T
+//   (ascending) [4k, 5k), then gl, gu, ||T||, pivmin, max|M_ii| as hi + lo.
+__device__ __forceinline__ int level_size(const int32_t* lvl, int level, int k) { return level == 0 ? k : lvl[level]; }
 
 // Number of eigenvalues of T (d, e) smaller than x (Sturm count).
-__device__ __forceinline__ int sturm_count(const float* d, const float* e2, int k, float x, float pivmin) {
+__device__ __forceinline__ int sturm_count(const float* d, const float* e2, int s, float x, float pivmin) {
   int c = 0;
   float q = d[0] - x;
   if (fabsf(q) < pivmin) q = -pivmin;
   c += q < 0.f;
-  for (int i = 1; i < k; ++i) {
+  for (int i = 1; i < s; ++i) {
     q = d[i] - x - __fdividef(e2[i - 1], q);
     if (fabsf(q) < pivmin) q = -pivmin;
     c += q < 0.f;
@@ -44,543 +64,328 @@ __device__ __forceinline__ int sturm_count(const float* d, const float* e2, int 
   return c;
 }
 
-// One inverse-iteration solve (T - lam I) z <- z with the LDL^T factorisation
-// (no pivoting; tiny pivots replaced by -pivmin), then normalisation.
-// q is per-thread scratch of length k.
-__device__ __forceinline__ void inv_iter(const float* d, const float* e, int k, float lam, float pivmin, float* z, float* q,
-                         int zstride, int qstride) {
-  // factor: q_0 = d_0 - lam, q_i = d_i - lam - e_{i-1}^2 / q_{i-1}; L_i = e_{i-1} / q_{i-1}
-  float qi = d[0] - lam;
-  if (fabsf(qi) < pivmin) qi = -pivmin;
-  q[0] = qi;
-  for (int i = 1; i < k; ++i) {
-    qi = d[i] - lam - __fdividef(e[i - 1] * e[i - 1], qi);
-    if (fabsf(qi) < pivmin) qi = -pivmin;
-    q[i * qstride] = qi;
-  }
-  // forward: L y = z  (L unit lower bidiagonal, L_i = e_{i-1}/q_{i-1})
-  for (int i = 1; i < k; ++i) z[i * zstride] -= __fdividef(e[i - 1], q[(i - 1) * qstride]) * z[(i - 1) * zstride];
-  // diagonal and backward: D L^T x = y
-  z[(k - 1) * zstride] = __fdividef(z[(k - 1) * zstride], q[(k - 1) * qstride]);
-  for (int i = k - 2; i >= 0; --i) {
-    const float rq = __fdividef(1.f, q[i * qstride]);
-    z[i * zstride] = z[i * zstride] * rq - (e[i] * rq) * z[(i + 1) * zstride];
-  }
-  float nrm = 0.f;
-  for (int i = 0; i < k; ++i) nrm = fmaf(z[i * zstride], z[i * zstride], nrm);
-  if (!(nrm > 0.f) || !isfinite(nrm)) {
-    // overflow or a zero solve: fall back to a coordinate vector
-    for (int i = 0; i < k; ++i) z[i * zstride] = 0.f;
-    z[0] = 1.f;
-    return;
-  }
-  const float inv = rsqrtf(nrm);
-  for (int i = 0; i < k; ++i) z[i * zstride] *= inv;
-}
+// ---------------------------------------------------------------------------
+// 1. Tridiagonalisation.
+template <int NC>
+struct TriCfg {
+  static constexpr int THREADS = 4 * NC;
+  static constexpr int NR = NC / 4;              // rows per thread
+  static constexpr int NRR = NR < 32 ? NR : 32;  // of them in registers (rows < 128)
+  static constexpr int NRS = NR - NRR;           // in shared memory (rows 128 .. NC-1)
+  static constexpr int NW = THREADS / 32;
+  static constexpr int GW = NC / 32;             // warps per row group
+  // floats of dynamic shared memory
+  static constexpr int SMEM_FLOATS = NRS * 4 * NC   // rows >= 128
+                                     + 2 * NC       // row j, natural order (ping-pong)
+                                     + 2 * NC       // x of row j, permuted (ping-pong)
+                                     + NC           // w, permuted
+                                     + 4 * NC       // partial matrix-vector products
+                                     + NW           // partial v^T A v
+                                     + 2 * 8        // partial squared norms (ping-pong)
+                                     + 3 * NC;      // d, e, beta
+};
 
-// Register-resident form of step 1 for k <= 128: thread t owns the entries
-// (r, c) with c = t mod 128 and r = t / 128 + 4 i, i = 0..31, of the matrix
-// being reduced.  Vectors indexed by row are also kept "permuted",
-// x[(r mod 4) * 32 + r / 4], so that a thread reads the 32 entries of its
-// rows with eight 16-byte broadcast loads.
-// Vectors are zero outside the active range, which makes every update a plain
-// multiply-add over all 32 rows (no predicates).
-__device__ __forceinline__ int perm_idx(int r) { return (r & 3) * 32 + (r >> 2); }
+__device__ __forceinline__ int perm_of(int r, int nr) { return (r & 3) * nr + (r >> 2); }
 
-// Step 1: tridiagonalisation.  A (k x k, row-major, already scaled) is read
-// from `Asrc`; the reflectors are left in Vh (row j: permuted v_j) and d, e,
-// beta in dv, ev, betav.  Four barriers per reflector.
-__device__ void tridiag_regs(const float* Asrc, int k, float* Vh, float* dv, float* ev, float* betav, float* rowbuf,
-                             float* vfl, float* wl, float* vperm, float* wperm, float* gpart) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int tr = tid & 127, tg = tid >> 7;
-  float a[32];
-#pragma unroll
-  for (int i = 0; i < 32; ++i) {
-    const int r = tg + 4 * i;
-    a[i] = (r < k && tr < k) ? Asrc[r * k + tr] : 0.f;
-  }
-  if (tg == 0) rowbuf[tr] = a[0];  // row 0
-  __syncthreads();
-  for (int j = 0; j + 2 < k; ++j) {
-    // a. warp 0: reflector of row j (x = A[j][j+1..k-1])
-    if (warp == 0) {
-      float sq = 0.f;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int r = lane + 32 * q;
-        const float x = (r >= j + 2 && r < k) ? rowbuf[r] : 0.f;
-        sq = fmaf(x, x, sq);
-      }
-      sq = warp_sumf(sq);
-      const float x0 = rowbuf[j + 1];
-      const float nrm = sqrtf(x0 * x0 + sq);
-      float alpha = 0.f, beta = 0.f, v0 = x0;
-      if (nrm > 0.f) {
-        alpha = x0 >= 0.f ? -nrm : nrm;
-        v0 = x0 - alpha;
-        const float vv = v0 * v0 + sq;
-        beta = vv > 0.f ? 2.f / vv : 0.f;
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int r = lane + 32 * q;
-        const float v = r == j + 1 ? v0 : ((r > j + 1 && r < k) ? rowbuf[r] : 0.f);
-        vfl[r] = v;
-        vperm[perm_idx(r)] = v;
-        Vh[j * 128 + perm_idx(r)] = v;
-      }
-      if (lane == 0) {
-        dv[j] = rowbuf[j];
-        ev[j] = (nrm > 0.f) ? alpha : x0;
-        betav[j] = beta;
-      }
-    }
-    __syncthreads();
-    const float beta = betav[j];
-    // b. partial p_c = sum over the thread's rows of A[r][c] v_r
-    {
-      const float4* vp = reinterpret_cast<const float4*>(vperm + tg * 32);
-      float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const float4 v = vp[q];
-        s0 = fmaf(a[4 * q], v.x, s0);
-        s1 = fmaf(a[4 * q + 1], v.y, s1);
-        s0 = fmaf(a[4 * q + 2], v.z, s0);
-        s1 = fmaf(a[4 * q + 3], v.w, s1);
-      }
-      gpart[tg * 128 + tr] = s0 + s1;
-    }
-    __syncthreads();
-    // c. warp 0: p = beta A' v, K = beta p.v / 2, w = p - K v (zero outside rows j+1..k-1)
-    if (warp == 0) {
-      float pr[4], pv = 0.f;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int r = lane + 32 * q;
-        const bool act = r > j && r < k;
-        const float p = act ? beta * (gpart[r] + gpart[128 + r] + gpart[256 + r] + gpart[384 + r]) : 0.f;
-        pr[q] = p;
-        pv = fmaf(p, vfl[r], pv);
-      }
-      pv = warp_sumf(pv);
-      const float K = 0.5f * beta * pv;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int r = lane + 32 * q;
-        const float w = (r > j && r < k) ? pr[q] - K * vfl[r] : 0.f;
-        wl[r] = w;
-        wperm[perm_idx(r)] = w;
-      }
-    }
-    __syncthreads();
-    // d. A -= v w^T + w v^T; the owners of row j + 1 publish it for the next step
-    {
-      const float vc = vfl[tr], wc = wl[tr];
-      const float4* vp = reinterpret_cast<const float4*>(vperm + tg * 32);
-      const float4* wp = reinterpret_cast<const float4*>(wperm + tg * 32);
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const float4 v = vp[q], w = wp[q];
-        a[4 * q] -= v.x * wc + w.x * vc;
-        a[4 * q + 1] -= v.y * wc + w.y * vc;
-        a[4 * q + 2] -= v.z * wc + w.z * vc;
-        a[4 * q + 3] -= v.w * wc + w.w * vc;
-      }
-#pragma unroll
-      for (int i = 0; i < 32; ++i)
-        if (tg + 4 * i == j + 1) rowbuf[tr] = a[i];
-    }
-    __syncthreads();
-  }
-  // the last 2 x 2 block (rows k-2, k-1), or the whole matrix when k < 3
-#pragma unroll
-  for (int i = 0; i < 32; ++i) {
-    const int r = tg + 4 * i;
-    if (r == k - 2 && tr < k) gpart[tr] = a[i];
-    if (r == k - 1 && tr < k) gpart[128 + tr] = a[i];
-  }
-  __syncthreads();
-  if (tid == 0) {
-    if (k >= 2) {
-      dv[k - 2] = gpart[k - 2];
-      ev[k - 2] = gpart[128 + k - 2];
-      betav[k - 2] = 0.f;
-    }
-    dv[k - 1] = gpart[128 + k - 1];
-    betav[k - 1] = 0.f;
-  }
-  __syncthreads();
-}
+// Reflector j of the tridiagonalisation has entries in rows j+1 .. s-1; they
+// are stored packed, reflector after reflector.
+__device__ __forceinline__ int packed_off(int j, int s) { return j * (s - 1) - j * (j - 1) / 2; }
 
-__global__ void __launch_bounds__(kSeedThreads, 1) eig_seed_kernel(const double* __restrict__ H, int k, float* gA,
-                                                                float* gZ, float* gQ, double* __restrict__ Xout,
-                                                                double* __restrict__ lam_out, double* scal,
-                                                                int32_t* nclusters) {
-  __shared__ float dv[256], ev[256], e2v[256], betav[256], wl[256], pv_s[256], lamv[256], vv_s[256];
-  __shared__ float gpart[kSeedThreads];
-  __shared__ float coef[4];
-  __shared__ int clstart[257];
-  float* A = gA;   // k x k row-major: scaled H, then the reflectors
-  float* Z = gZ;   // k x k, column j = eigenvector j
-  float* Qs = gQ;  // inverse-iteration scratch, one row per cluster
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kSeedThreads / 32;
-
-  // scale and load; ||H||_F for the refinement's noise floor
+template <int NC>
+__global__ void __launch_bounds__(4 * NC, 1) seed_tri_kernel(const double* __restrict__ M, int k, int level,
+                                                            int32_t* lvl, float* __restrict__ gV,
+                                                            float* __restrict__ tri, double* scal) {
+  using C = TriCfg<NC>;
+  constexpr int NR = C::NR, NRR = C::NRR, NRS = C::NRS, GW = C::GW;
+  extern __shared__ __align__(16) float sm[];
+  float* As = sm;                           // (r - 128) * NC + c
+  float* rowb = As + NRS * 4 * NC;          // [2][NC]
+  float* rowp = rowb + 2 * NC;              // [2][NC] permuted, x_r = A[j][r] for r > j, else 0
+  float* wp = rowp + 2 * NC;                // [NC] permuted w
+  float* gpart = wp + NC;                   // [4][NC]
+  float* vavp = gpart + 4 * NC;             // [NW]
+  float* sqp = vavp + C::NW;                // [2][8]
+  float* dv = sqp + 16;                     // [NC]
+  float* ev = dv + NC;                      // [NC]
+  float* bv = ev + NC;                      // [NC]
+  __shared__ double red[32];
   __shared__ double hmax_s;
-  __shared__ double hmx[kSeedThreads / 32];
+
+  const int s = level_size(lvl, level, k);
+  if (level > 0 && s < 2) return;  // uniform: nothing to resolve at this level
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int c = tid % NC, g = tid / NC;
+  const int cw0 = (warp % GW) * 32;  // first column of this warp
+  if (level == 0 && tid < 3) lvl[1 + tid] = 0;
+
+  // scale by 1 / max |M_ii| over the block; ||H||_F at level 0 (refinement noise floor)
   {
     double mx = 0.0;
-    for (int i = tid; i < k; i += kSeedThreads) mx = fmax(mx, fabs(H[(int64_t)i * k + i]));
+    for (int i = tid; i < s; i += C::THREADS) mx = fmax(mx, fabs(M[(int64_t)i * k + i]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (lane == 0) hmx[warp] = mx;
+    if (lane == 0) red[warp] = mx;
     __syncthreads();
     if (tid == 0) {
       double m2 = 0.0;
-      for (int i = 0; i < nw; ++i) m2 = fmax(m2, hmx[i]);
+      for (int i = 0; i < C::NW; ++i) m2 = fmax(m2, red[i]);
       hmax_s = m2 > 0.0 ? m2 : 1.0;
     }
+    __syncthreads();
+    if (level == 0) {
+      double hf = 0.0;
+      for (int e = tid; e < s * s; e += C::THREADS) {
+        const double h = M[(int64_t)(e / s) * k + (e % s)];
+        hf += h * h;
+      }
+      hf = warp_sum(hf);
+      __syncthreads();
+      if (lane == 0) red[warp] = hf;
+      __syncthreads();
+      if (tid == 0) {
+        double sum = 0.0;
+        for (int i = 0; i < C::NW; ++i) sum += red[i];
+        scal[1] = sqrt(sum);
+      }
+    }
   }
-  __syncthreads();
   const double sc = 1.0 / hmax_s;
-  double hf = 0.0;
-#pragma unroll 8
-  for (int e = tid; e < k * k; e += kSeedThreads) {
-    const double h = H[e];
-    hf += h * h;
-    A[e] = (float)(h * sc);
+  float a[NRR];
+#pragma unroll
+  for (int i = 0; i < NRR; ++i) {
+    const int r = g + 4 * i;
+    a[i] = (r < s && c < s) ? (float)(M[(int64_t)r * k + c] * sc) : 0.f;
   }
-  hf = warp_sum(hf);
-  {
-    __shared__ double redd[32];
-    if (lane == 0) redd[warp] = hf;
-    __syncthreads();
+#pragma unroll 4
+  for (int i = NRR; i < NR; ++i) {
+    const int r = g + 4 * i;
+    As[(r - 128) * NC + c] = (r < s && c < s) ? (float)(M[(int64_t)r * k + c] * sc) : 0.f;
+  }
+  for (int e = tid; e < 2 * NC; e += C::THREADS) rowp[e] = 0.f;
+  // value of A[row][c] held by this thread (row owned by group g; dynamic row)
+  auto get_own = [&](int row) -> float {
+    const int i = row >> 2;
+    if (i >= NRR) return As[(row - 128) * NC + c];
+    float v = 0.f;
+#pragma unroll
+    for (int q = 0; q < NRR; ++q)
+      if (q == i) v = a[q];
+    return v;
+  };
+  // publish row `row` (owners: group row & 3) into ping-pong buffer b: natural
+  // order, the permuted x (entries right of row + 1... i.e. columns > row, as
+  // the next reflector's x), and per-warp partial norms of columns > row + 1
+  auto publish = [&](int row, int b, float val) {
+    rowb[b * NC + c] = val;
+    const float xv = (c > row && c < s) ? val : 0.f;
+    rowp[b * NC + perm_of(c, NR)] = xv;
+    float q = (c > row + 1 && c < s) ? val * val : 0.f;
+    q = warp_sumf(q);
+    if (lane == 0) sqp[b * 8 + (warp % GW)] = q;
+  };
+  __syncthreads();
+  if (g == 0) publish(0, 0, a[0]);
+  __syncthreads();
+
+  for (int j = 0; j + 2 < s; ++j) {
+    const int b = j & 1;
+    const float* rb = rowb + b * NC;
+    const float* rp = rowp + b * NC;
+    // ---- phase 1: reflector (every thread, same data), partial A' u.  The
+    // reflector is kept as a unit vector u = v / |v| (H = I - 2 u u^T), and the
+    // row is scaled by 1 / |v| as it is loaded, so no product of the step
+    // over- or underflows however small the row is; a row below 1e-18 of the
+    // scaled block is taken as reduced.
+    float sq = 0.f;
+#pragma unroll
+    for (int w = 0; w < GW; ++w) sq += sqp[b * 8 + w];
+    const float x0 = rb[j + 1];
+    const float nrm = sqrtf(x0 * x0 + sq);
+    float alpha = 0.f, invv = 0.f;
+    if (nrm > 1e-18f) {
+      alpha = x0 >= 0.f ? -nrm : nrm;
+      const float v0 = x0 - alpha;
+      invv = rsqrtf(v0 * v0 + sq);
+    }
+    const bool refl = invv > 0.f;
     if (tid == 0) {
-      double s = 0.0;
-      for (int i = 0; i < nw; ++i) s += redd[i];
-      scal[1] = sqrt(s);
+      dv[j] = rb[j];
+      ev[j] = refl ? alpha : x0;
+      bv[j] = refl ? 2.f : 0.f;
     }
-  }
-  __syncthreads();
-
-  // ---- 1. tridiagonalisation over the global scratch matrix
-  const int kp = 256;                // padded width: thread t = (t / kp, t % kp)
-  const int GR = kSeedThreads / kp;  // 2 groups
-  const int tr = tid % kp, tg = tid / kp;
-// Step j reflects the trailing block
-  // A' = A[j+1:, j+1:] with H = I - beta v v^T built from row j (equal to
-  // column j: the trailing block is kept whole and symmetric).  Four barriers
-  // per step:
-  //   a. warp 0: norm of row j right of the diagonal, alpha, beta, v (stored
-  //      back into row j for the back-transformation and into vv_s);
-  //   b. p = A' v: thread (g, r) sums a quarter (k <= 128) or half of the
-  //      terms of p_r, reading A'[l][r] = A'[r][l] along rows (consecutive
-  //      lanes, consecutive addresses);
-  //   c. warp 0: p = beta sum of the partials, K = beta p.v / 2, w = p - K v;
-  //   d. A' -= v w^T + w v^T, thread (g, c) over rows r = g mod GR.
-  for (int j = 0; j + 2 < k; ++j) {
-    const int n1 = k - j - 1;
-    float* rowj = A + j * k + (j + 1);  // row j right of the diagonal (length n1)
-    if (warp == 0) {
-      float sq = 0.f;
-      for (int r = 1 + lane; r < n1; r += 32) sq = fmaf(rowj[r], rowj[r], sq);
-      sq = warp_sumf(sq);
-      const float x0 = rowj[0];
-      const float nrm = sqrtf(x0 * x0 + sq);
-      float alpha = 0.f, beta = 0.f, v0 = x0;
-      if (nrm > 0.f) {
-        alpha = x0 >= 0.f ? -nrm : nrm;
-        v0 = x0 - alpha;
-        const float vv = v0 * v0 + sq;
-        beta = vv > 0.f ? 2.f / vv : 0.f;
-      }
-      for (int r = lane; r < n1; r += 32) vv_s[r] = r == 0 ? v0 : rowj[r];
-      __syncwarp();
-      if (lane == 0) {
-        dv[j] = A[j * k + j];
-        ev[j] = (nrm > 0.f) ? alpha : x0;
-        betav[j] = beta;
-        rowj[0] = v0;
-      }
+    const int own = (j + 1) & 3;
+    const bool wact = (cw0 + 31 > j) && (cw0 < s);  // warp holds an active column
+    // u_c of the own column: u = (x - alpha e_{j+1}) / |v|
+    const float uc = (c > j && c < s) ? (rb[c] - (c == j + 1 ? alpha : 0.f)) * invv : 0.f;
+    if (g == 0 && c > j && c < s) gV[packed_off(j, s) + (c - j - 1)] = uc;
+    if (!refl) {
+      // nothing to reduce: publish row j + 1 unchanged
+      __syncthreads();
+      if (g == own) publish(j + 1, b ^ 1, get_own(j + 1));
+      __syncthreads();
+      continue;
     }
-    __syncthreads();
-    const float beta = betav[j];
-    if (beta == 0.f) continue;  // uniform: the block is already reduced here
-    const float* Ap = A + (j + 1) * k + (j + 1);
-    {
-      const int chunk = (n1 + GR - 1) / GR;
-      const int l0 = tg * chunk, l1 = min(n1, l0 + chunk);
-      float a0 = 0.f, a1 = 0.f;
-      if (tr < n1) {
-        int l = l0;
-        for (; l + 1 < l1; l += 2) {
-          a0 = fmaf(Ap[l * k + tr], vv_s[l], a0);
-          a1 = fmaf(Ap[(l + 1) * k + tr], vv_s[l + 1], a1);
+    float pc = 0.f;
+    if (wact) {
+      // row groups of four (rows g + 4i .. g + 4i + 12) wholly at or above row
+      // j hold x = 0 and are skipped (uniform per warp)
+      const float4* xp = reinterpret_cast<const float4*>(rp + g * NR);
+      if (j < 127) {
+#pragma unroll
+        for (int i = 0; i < NRR; i += 4) {
+          if (g + 4 * (i + 3) <= j) continue;
+          const float4 x = xp[i / 4];
+          pc = fmaf(a[i], x.x, pc);
+          pc = fmaf(a[i + 1], x.y, pc);
+          pc = fmaf(a[i + 2], x.z, pc);
+          pc = fmaf(a[i + 3], x.w, pc);
         }
-        if (l < l1) a0 = fmaf(Ap[l * k + tr], vv_s[l], a0);
       }
-      gpart[tg * kp + tr] = a0 + a1;
+      const int is = j < 128 ? NRR : max(NRR, ((j - g) >> 2) & ~3);
+#pragma unroll 4
+      for (int i = is; i < NR; i += 4) {
+        const float4 x = xp[i / 4];
+        const float* ar = As + (g + 4 * i - 128) * NC + c;
+        pc = fmaf(ar[0], x.x, pc);
+        pc = fmaf(ar[4 * NC], x.y, pc);
+        pc = fmaf(ar[8 * NC], x.z, pc);
+        pc = fmaf(ar[12 * NC], x.w, pc);
+      }
+      if (g == own) pc = fmaf(-alpha, get_own(j + 1), pc);  // the -alpha e_{j+1} part of v
+      pc *= invv;                                            // A' u = A' v / |v|
+    }
+    gpart[g * NC + c] = pc;
+    {
+      float t = uc * pc;
+      t = warp_sumf(t);
+      if (lane == 0) vavp[warp] = t;
     }
     __syncthreads();
-    if (warp == 0) {
-      float pv = 0.f;
-      for (int r = lane; r < n1; r += 32) {
-        float s = 0.f;
-        for (int g = 0; g < GR; ++g) s += gpart[g * kp + r];
-        s *= beta;
-        pv_s[r] = s;
-        pv = fmaf(s, vv_s[r], pv);
-      }
-      pv = warp_sumf(pv);
-      const float K = 0.5f * beta * pv;
-      for (int r = lane; r < n1; r += 32) wl[r] = pv_s[r] - K * vv_s[r];
+    // ---- phase 2: q = A' u, p = 2 q, K = 2 u^T q, w = p - K u
+    float uau = 0.f;
+#pragma unroll
+    for (int w = 0; w < C::NW; w += 4) {
+      const float4 t = *reinterpret_cast<const float4*>(vavp + w);
+      uau += (t.x + t.y) + (t.z + t.w);
     }
+    const float K = 2.f * uau;
+    const float p = 2.f * ((gpart[c] + gpart[NC + c]) + (gpart[2 * NC + c] + gpart[3 * NC + c]));
+    const float wc = (c > j && c < s) ? p - K * uc : 0.f;
+    if (g == 0) wp[perm_of(c, NR)] = wc;
     __syncthreads();
-    if (tr < n1) {
-      const float vc = vv_s[tr], wc = wl[tr];
-      for (int r = tg; r < n1; r += GR) {
-        float* a = A + (j + 1 + r) * k + (j + 1) + tr;
-        *a -= vv_s[r] * wc + wl[r] * vc;
+    // ---- phase 3: A' -= u w^T + w u^T (rows through x / |v|, row j + 1
+    // corrected by alpha w / |v|), then the owners publish row j + 1
+    if (wact) {
+      const float4* xp = reinterpret_cast<const float4*>(rp + g * NR);
+      const float4* wq = reinterpret_cast<const float4*>(wp + g * NR);
+      const float wci = wc * invv;
+      if (j < 127) {
+#pragma unroll
+        for (int i = 0; i < NRR; i += 4) {
+          if (g + 4 * (i + 3) <= j) continue;
+          const float4 x = xp[i / 4], w = wq[i / 4];
+          a[i] -= fmaf(x.x, wci, w.x * uc);
+          a[i + 1] -= fmaf(x.y, wci, w.y * uc);
+          a[i + 2] -= fmaf(x.z, wci, w.z * uc);
+          a[i + 3] -= fmaf(x.w, wci, w.w * uc);
+        }
       }
+      const int is = j < 128 ? NRR : max(NRR, ((j - g) >> 2) & ~3);
+#pragma unroll 4
+      for (int i = is; i < NR; i += 4) {
+        const float4 x = xp[i / 4], w = wq[i / 4];
+        float* ar = As + (g + 4 * i - 128) * NC + c;
+        ar[0] -= fmaf(x.x, wci, w.x * uc);
+        ar[4 * NC] -= fmaf(x.y, wci, w.y * uc);
+        ar[8 * NC] -= fmaf(x.z, wci, w.z * uc);
+        ar[12 * NC] -= fmaf(x.w, wci, w.w * uc);
+      }
+    }
+    if (g == own) {
+      // row j + 1: add alpha w_c / |v| back (the row update above used x_{j+1}, not v_{j+1})
+      const int i1 = (j + 1) >> 2;
+      const float corr = alpha * invv * wc;
+      float val;
+      if (i1 >= NRR) {
+        float* ar = As + (j + 1 - 128) * NC + c;
+        if (wact) *ar += corr;
+        val = *ar;
+      } else {
+        val = 0.f;
+#pragma unroll
+        for (int q = 0; q < NRR; ++q)
+          if (q == i1) {
+            if (wact) a[q] += corr;
+            val = a[q];
+          }
+      }
+      publish(j + 1, b ^ 1, val);
     }
     __syncthreads();
   }
-  if (tid == 0) {
-    if (k >= 2) {
-      dv[k - 2] = A[(k - 2) * k + (k - 2)];
-      ev[k - 2] = A[(k - 1) * k + (k - 2)];
+  // the last 2 x 2 block (rows s-2, s-1), or the 1 x 1 matrix
+  if (s >= 2) {
+    const int bl = (s - 2) & 1;  // row s-2 was published last (row 0 when s == 2)
+    if (tid == 0) {
+      dv[s - 2] = rowb[bl * NC + s - 2];
+      ev[s - 2] = rowb[bl * NC + s - 1];
+      bv[s - 2] = 0.f;
+      bv[s - 1] = 0.f;
     }
-    dv[k - 1] = A[(k - 1) * k + (k - 1)];
-    if (k >= 2) betav[k - 2] = 0.f;
-    betav[k - 1] = 0.f;
+    if (g == ((s - 1) & 3) && c == s - 1) dv[s - 1] = get_own(s - 1);
+  } else if (tid == 0) {
+    dv[0] = a[0];
+    bv[0] = 0.f;
   }
   __syncthreads();
-  for (int i = tid; i < k; i += kSeedThreads) e2v[i] = (i + 1 < k) ? ev[i] * ev[i] : 0.f;
-
-  // Gershgorin interval, ||T||, pivmin
+  for (int i = tid; i < s; i += C::THREADS) {
+    tri[i] = dv[i];
+    tri[k + i] = (i + 1 < s) ? ev[i] : 0.f;
+    tri[2 * k + i] = (i + 1 < s) ? ev[i] * ev[i] : 0.f;
+    tri[3 * k + i] = bv[i];
+  }
   if (tid == 0) {
     float gl = 1e30f, gu = -1e30f, tn = 0.f;
-    for (int i = 0; i < k; ++i) {
-      const float off = (i > 0 ? fabsf(ev[i - 1]) : 0.f) + (i + 1 < k ? fabsf(ev[i]) : 0.f);
+    for (int i = 0; i < s; ++i) {
+      const float off = (i > 0 ? fabsf(ev[i - 1]) : 0.f) + (i + 1 < s ? fabsf(ev[i]) : 0.f);
       gl = fminf(gl, dv[i] - off);
       gu = fmaxf(gu, dv[i] + off);
       tn = fmaxf(tn, fabsf(dv[i]) + off);
     }
     const float pad = 2.f * 1.2e-7f * tn + 1e-30f;
-    coef[0] = gl - pad;
-    coef[1] = gu + pad;
-    coef[2] = tn;
-    coef[3] = fmaxf(1e-30f, 1.2e-7f * 1e-6f * tn);  // pivmin
+    float* cst = tri + 5 * k;
+    cst[0] = gl - pad;
+    cst[1] = gu + pad;
+    cst[2] = tn;
+    cst[3] = fmaxf(1e-30f, 1.2e-7f * 1e-6f * tn);  // pivmin
+    const float hi = (float)hmax_s;
+    cst[4] = hi;
+    cst[5] = (float)(hmax_s - (double)hi);
   }
-  __syncthreads();
-  const float tnorm = coef[2], pivmin = coef[3];
-
-  // ---- 2. eigenvalues by multisection: GR threads (lanes of one warp) per
-  // eigenvalue evaluate Sturm counts at GR interior points of the bracket,
-  // which shrinks by GR + 1 per round ((GR + 1)^rounds >= 2^30, the
-  // resolution of 30 halvings of the Gershgorin interval).
-  {
-    const int idx = tid / GR, q = tid % GR;
-    const int rounds = GR == 4 ? 13 : 19;
-    const float den = (float)(GR + 1);
-    float lo = coef[0], hi = coef[1];
-#pragma unroll 1
-    for (int it = 0; it < rounds; ++it) {
-      const float x = lo + (hi - lo) * (float)(q + 1) / den;
-      const bool above = idx < k && sturm_count(dv, e2v, k, x, pivmin) > idx;
-      const unsigned ball = __ballot_sync(0xffffffffu, above);
-      const unsigned grp = (ball >> ((lane / GR) * GR)) & ((1u << GR) - 1u);
-      const int first = grp ? __ffs((int)grp) - 1 : GR;  // first point with count > idx
-      const float nlo = first == 0 ? lo : lo + (hi - lo) * (float)first / den;
-      const float nhi = first == GR ? hi : lo + (hi - lo) * (float)(first + 1) / den;
-      lo = nlo;
-      hi = nhi;
-    }
-    if (q == 0 && idx < k) lamv[idx] = 0.5f * (lo + hi);
-  }
-  __syncthreads();
-
-  // ---- 3. eigenvectors of T: clusters of close eigenvalues, inverse iteration
-  if (tid == 0) {
-    int nc = 0;
-    for (int i = 0; i < k; ++i)
-      if (i == 0 || lamv[i] - lamv[i - 1] > 1e-5f * tnorm) clstart[nc++] = i;
-    clstart[nc] = k;
-    clstart[256] = nc;
-    *nclusters = nc;
-  }
-  __syncthreads();
-  const int ncl = clstart[256];
-  for (int cl = tid; cl < ncl; cl += kSeedThreads) {
-    const int i0 = clstart[cl], i1 = clstart[cl + 1];
-    float* q = Qs + cl;  // element i at q[i * k]: the threads of a warp (clusters) hit consecutive banks
-    for (int i = i0; i < i1; ++i) {
-      // deterministic start vector, then two solves with Gram-Schmidt against
-      // the cluster's earlier vectors after each
-      for (int r = 0; r < k; ++r) Z[r * k + i] = 1.f + 0.5f * __sinf(0.7f * (float)(r + 3 * i) + 0.3f);
-      const float lam = lamv[i];
-      for (int rep = 0; rep < 2; ++rep) {
-        inv_iter(dv, ev, k, lam, pivmin, Z + i, q, k, k);
-        for (int pj = (i - 32 > i0 ? i - 32 : i0); pj < i; ++pj) {
-          float dot = 0.f;
-          for (int r = 0; r < k; ++r) dot = fmaf(Z[r * k + pj], Z[r * k + i], dot);
-          float nrm = 0.f;
-          for (int r = 0; r < k; ++r) {
-            Z[r * k + i] -= dot * Z[r * k + pj];
-            nrm = fmaf(Z[r * k + i], Z[r * k + i], nrm);
-          }
-          const float inv = nrm > 0.f ? rsqrtf(nrm) : 1.f;
-          for (int r = 0; r < k; ++r) Z[r * k + i] *= inv;
-        }
-      }
-    }
-  }
-  __syncthreads();
-
-  // ---- 4. back-transformation Z <- H_0 H_1 ... H_{k-3} Z, last reflector
-  // first; v_j is row j of A right of the diagonal.  Thread (g, c), two
-  // barriers per reflector:
-  //   1. partial of w_c = v^T Z[j+1:, c] over the rows r = g mod GR;
-  //   2. w_c = beta (sum of the GR partials of column c), then
-  //      Z[j+1+r][c] -= v_r w_c over the same rows.
-for (int j = k - 3; j >= 0; --j) {
-    const float beta = betav[j];
-    if (beta == 0.f) continue;
-    const int n1 = k - j - 1;
-    const float* v = A + j * k + (j + 1);
-    float acc = 0.f;
-    if (tr < k)
-      for (int r = tg; r < n1; r += GR) acc = fmaf(v[r], Z[(j + 1 + r) * k + tr], acc);
-    gpart[tg * kp + tr] = acc;
-    __syncthreads();
-    if (tr < k) {
-      float wc = 0.f;
-      for (int g = 0; g < GR; ++g) wc += gpart[g * kp + tr];
-      wc *= beta;
-      for (int r = tg; r < n1; r += GR) Z[(j + 1 + r) * k + tr] -= v[r] * wc;
-    }
-    __syncthreads();
-  }
-  for (int e = tid; e < k * k; e += kSeedThreads) Xout[e] = (double)Z[e];
-  for (int i = tid; i < k; i += kSeedThreads) lam_out[i] = (double)lamv[i] * hmax_s;
 }
-
 
 // ---------------------------------------------------------------------------
-// The same seed for k <= 128 in four launches, so that the steps that are
-// independent across eigenvalues or columns run on many SMs instead of one:
-//   seed_tri_kernel   (one CTA)        scale, load, steps 1 and the Gershgorin
-//                                      interval; reflectors and T to global;
-//   seed_bisect_kernel (k / 4 CTAs)    step 2, one warp per eigenvalue, 32
-//                                      interior points per round (6 rounds,
-//                                      33^6 >= 2^30: the resolution of 30
-//                                      halvings);
-//   seed_vec_kernel   (one CTA)        step 3, as in eig_seed_kernel;
-//   seed_back_kernel  (k / 8 CTAs)     step 4, one warp per column of Z: the
-//                                      reflectors applied one at a time with a
-//                                      warp reduction each, no block barrier.
-// Scratch `tri` (floats): d [0, k), e [k, 2k), e^2 [2k, 3k), beta [3k, 4k),
-// eigenvalues of T [4k, 5k), then gl, gu, ||T||, pivmin, 1 / scale (as two
-// floats: the FP64 max |H_ii| split hi + lo).  gA: reflector j in row j
-// (k x k, zero outside rows j+1 .. k-1); gZ: eigenvectors of T (k x k, column
-// i = vector i).
-
-__global__ void __launch_bounds__(kSeedThreads, 1) seed_tri_kernel(const double* __restrict__ H, int k, float* gV,
-                                                                float* tri, double* scal) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ float dv[256], ev[256], betav[256], wl[256];
-  __shared__ float gpart[kSeedThreads];
-  __shared__ __align__(16) float vperm[128], wperm[128];
-  __shared__ float rowbuf[128], vfl[128];
-  __shared__ double hmax_s;
-  __shared__ double hmx[kSeedThreads / 32];
-  __shared__ double redd[32];
-  float* A = reinterpret_cast<float*>(smem_raw);  // 128 x k: scaled H, then the reflectors (permuted rows)
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kSeedThreads / 32;
-  {
-    double mx = 0.0;
-    for (int i = tid; i < k; i += kSeedThreads) mx = fmax(mx, fabs(H[(int64_t)i * k + i]));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (lane == 0) hmx[warp] = mx;
-    __syncthreads();
-    if (tid == 0) {
-      double m2 = 0.0;
-      for (int i = 0; i < nw; ++i) m2 = fmax(m2, hmx[i]);
-      hmax_s = m2 > 0.0 ? m2 : 1.0;
-    }
-  }
-  __syncthreads();
-  const double sc = 1.0 / hmax_s;
-  double hf = 0.0;
-#pragma unroll 8
-  for (int e = tid; e < k * k; e += kSeedThreads) {
-    const double h = H[e];
-    hf += h * h;
-    A[e] = (float)(h * sc);
-  }
-  hf = warp_sum(hf);
-  if (lane == 0) redd[warp] = hf;
-  __syncthreads();
-  if (tid == 0) {
-    double sum = 0.0;
-    for (int i = 0; i < nw; ++i) sum += redd[i];
-    scal[1] = sqrt(sum);
-  }
-  __syncthreads();
-  tridiag_regs(A, k, A, dv, ev, betav, rowbuf, vfl, wl, vperm, wperm, gpart);
-  // reflectors to global in natural order, T and its Gershgorin interval
-  for (int e = tid; e < k * k; e += kSeedThreads) {
-    const int j = e / k, r = e % k;
-    gV[e] = A[j * 128 + perm_idx(r)];
-  }
-  for (int i = tid; i < k; i += kSeedThreads) {
-    tri[i] = dv[i];
-    tri[k + i] = ev[i];
-    tri[2 * k + i] = (i + 1 < k) ? ev[i] * ev[i] : 0.f;
-    tri[3 * k + i] = betav[i];
-  }
-  if (tid == 0) {
-    float gl = 1e30f, gu = -1e30f, tn = 0.f;
-    for (int i = 0; i < k; ++i) {
-      const float off = (i > 0 ? fabsf(ev[i - 1]) : 0.f) + (i + 1 < k ? fabsf(ev[i]) : 0.f);
-      gl = fminf(gl, dv[i] - off);
-      gu = fmaxf(gu, dv[i] + off);
-      tn = fmaxf(tn, fabsf(dv[i]) + off);
-    }
-    const float pad = 2.f * 1.2e-7f * tn + 1e-30f;
-    float* c = tri + 5 * k;
-    c[0] = gl - pad;
-    c[1] = gu + pad;
-    c[2] = tn;
-    c[3] = fmaxf(1e-30f, 1.2e-7f * 1e-6f * tn);  // pivmin
-    const float hi = (float)hmax_s;
-    c[4] = hi;
-    c[5] = (float)(hmax_s - (double)hi);
-  }
-}
-
-// One warp per eigenvalue idx (ascending): Sturm counts at 32 interior points
-// of the bracket per round.
-__global__ void __launch_bounds__(128) seed_bisect_kernel(int k, float* tri) {
-  __shared__ float d[128], e2[128];
-  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+// 2. Eigenvalues of T, ascending: one warp per eigenvalue idx.
+__global__ void __launch_bounds__(128) seed_bisect_kernel(int k, int level, const int32_t* __restrict__ lvl,
+                                                          float* tri) {
+  const int s = level_size(lvl, level, k);
+  if (level > 0 && s < 2) return;
+  __shared__ float d[256], e2[256];
+  for (int i = threadIdx.x; i < s; i += blockDim.x) {
     d[i] = tri[i];
     e2[i] = tri[2 * k + i];
   }
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int idx = blockIdx.x * 4 + (threadIdx.x >> 5);
-  if (idx >= k) return;
-  const float* c = tri + 5 * k;
-  const float pivmin = c[3];
-  float lo = c[0], hi = c[1];
+  if (idx >= s) return;
+  const float* cst = tri + 5 * k;
+  const float pivmin = cst[3];
+  float lo = cst[0], hi = cst[1];
 #pragma unroll 1
   for (int it = 0; it < 6; ++it) {
     const float x = lo + (hi - lo) * (float)(lane + 1) / 33.f;
-    const bool above = sturm_count(d, e2, k, x, pivmin) > idx;
+    const bool above = sturm_count(d, e2, s, x, pivmin) > idx;
     const unsigned ball = __ballot_sync(0xffffffffu, above);
     const int first = ball ? __ffs((int)ball) - 1 : 32;  // first point with count > idx
     const float nlo = first == 0 ? lo : lo + (hi - lo) * (float)first / 33.f;
@@ -591,121 +396,311 @@ __global__ void __launch_bounds__(128) seed_bisect_kernel(int k, float* tri) {
   if (lane == 0) tri[4 * k + idx] = 0.5f * (lo + hi);
 }
 
-// Step 3 of eig_seed_kernel (clusters, inverse iteration, Gram-Schmidt inside
-// clusters) for k <= 128: Z and the per-cluster scratch in shared memory.
-__global__ void __launch_bounds__(128, 1) seed_vec_kernel(int k, const float* __restrict__ tri, float* gZ,
-                                                        int32_t* nclusters) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ float dv[128], ev[128], lamv[128];
-  __shared__ int clstart[130];
-  float* Z = reinterpret_cast<float*>(smem_raw);  // k x k, column i = eigenvector i
-  float* Qs = Z + k * k;                          // one row per cluster
-  const int tid = threadIdx.x;
-  for (int i = tid; i < k; i += blockDim.x) {
-    dv[i] = tri[i];
-    ev[i] = tri[k + i];
-    lamv[i] = tri[4 * k + i];
-  }
-  __syncthreads();
-  const float tnorm = tri[5 * k + 2], pivmin = tri[5 * k + 3];
-  if (tid == 0) {
-    int nc = 0;
-    for (int i = 0; i < k; ++i)
-      if (i == 0 || lamv[i] - lamv[i - 1] > 1e-5f * tnorm) clstart[nc++] = i;
-    clstart[nc] = k;
-    clstart[129] = nc;
-    *nclusters = nc;
-  }
-  __syncthreads();
-  const int ncl = clstart[129];
-  for (int cl = tid; cl < ncl; cl += blockDim.x) {
-    const int i0 = clstart[cl], i1 = clstart[cl + 1];
-    float* q = Qs + cl;
-    for (int i = i0; i < i1; ++i) {
-      for (int r = 0; r < k; ++r) Z[r * k + i] = 1.f + 0.5f * __sinf(0.7f * (float)(r + 3 * i) + 0.3f);
-      const float lam = lamv[i];
-      for (int rep = 0; rep < 2; ++rep) {
-        inv_iter(dv, ev, k, lam, pivmin, Z + i, q, k, k);
-        for (int pj = (i - 32 > i0 ? i - 32 : i0); pj < i; ++pj) {
-          float dot = 0.f;
-          for (int r = 0; r < k; ++r) dot = fmaf(Z[r * k + pj], Z[r * k + i], dot);
-          float nrm = 0.f;
-          for (int r = 0; r < k; ++r) {
-            Z[r * k + i] -= dot * Z[r * k + pj];
-            nrm = fmaf(Z[r * k + i], Z[r * k + i], nrm);
-          }
-          const float inv = nrm > 0.f ? rsqrtf(nrm) : 1.f;
-          for (int r = 0; r < k; ++r) Z[r * k + i] *= inv;
-        }
-      }
-    }
-  }
-  __syncthreads();
-  for (int e = tid; e < k * k; e += blockDim.x) gZ[e] = Z[e];
+// Tail size of a level: the eigenvalues below kTailTau times the largest (a
+// prefix of the ascending list); a tail of one is resolved like the others.
+__device__ __forceinline__ int tail_count(const float* lam, int s) {
+  const float lim = kTailTau * lam[s - 1];
+  int t = 0;
+  while (t < s && lam[t] < lim) ++t;
+  return t >= 2 ? t : 0;
 }
 
-// Step 4, one warp per column c of Z: z <- H_0 H_1 ... H_{k-3} z, lane l
-// holding rows l, l + 32, l + 64, l + 96; eigenvalues scaled back into lam.
-__global__ void __launch_bounds__(256) seed_back_kernel(int k, const float* __restrict__ gV,
-                                                      const float* __restrict__ gZ, const float* __restrict__ tri,
-                                                      double* __restrict__ Xout, double* __restrict__ lam_out) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* Vs = reinterpret_cast<float*>(smem_raw);  // k x k reflectors
-  __shared__ float beta[128];
-  for (int e = threadIdx.x; e < k * k; e += blockDim.x) Vs[e] = gV[e];
-  for (int i = threadIdx.x; i < k; i += blockDim.x) beta[i] = tri[3 * k + i];
+// ---------------------------------------------------------------------------
+// 3. Inverse iteration, one thread per eigenvalue outside the tail, 32 per
+// CTA; each thread's vector and pivots live in shared memory (row r of the
+// CTA's vectors at r * 33: conflict-free for the threads and for the
+// coalesced copy out).  Zc is column-major (vector i at Zc[i k ...]).
+constexpr int kIIThreads = 32;
+
+__global__ void __launch_bounds__(kIIThreads) seed_ii_kernel(int k, int level, const int32_t* __restrict__ lvl,
+                                                             const float* __restrict__ tri, float* __restrict__ Zc) {
+  const int s = level_size(lvl, level, k);
+  if (level > 0 && s < 2) return;
+  extern __shared__ float zsm[];
+  float* zs = zsm;              // s x 33
+  float* qs = zsm + 33 * 256;   // s x 33
+  __shared__ float d[256], e[256], lam[256];
+  const int lane = threadIdx.x;
+  for (int i = lane; i < s; i += kIIThreads) {
+    d[i] = tri[i];
+    e[i] = tri[k + i];
+    lam[i] = tri[4 * k + i];
+  }
+  __syncwarp();
+  const int tcount = tail_count(lam, s);
+  const int i0 = blockIdx.x * kIIThreads;
+  if (i0 + kIIThreads <= tcount || i0 >= s) return;  // uniform: no vector of this CTA is computed
+  const int i = i0 + lane;
+  const bool mine = i < s && i >= tcount;
+  const float pivmin = tri[5 * k + 3];
+  if (mine) {
+    const float mu = lam[i];
+    float* z = zs + lane;
+    float* q = qs + lane;
+    for (int r = 0; r < s; ++r) z[r * 33] = 1.f + 0.5f * __sinf(0.7f * (float)(r + 3 * i) + 0.3f);
+    for (int rep = 0; rep < 2; ++rep) {
+      // LDL^T of T - mu I (tiny pivots replaced by -pivmin) fused with the
+      // forward solve L y = z, then D L^T x = y and the normalisation
+      float qi = d[0] - mu;
+      if (fabsf(qi) < pivmin) qi = -pivmin;
+      q[0] = qi;
+      float y = z[0];
+      for (int r = 1; r < s; ++r) {
+        const float l = __fdividef(e[r - 1], qi);
+        qi = d[r] - mu - l * e[r - 1];
+        if (fabsf(qi) < pivmin) qi = -pivmin;
+        q[r * 33] = qi;
+        y = z[r * 33] - l * y;
+        z[r * 33] = y;
+      }
+      float x = __fdividef(y, qi);
+      z[(s - 1) * 33] = x;
+      float nrm = x * x;
+      for (int r = s - 2; r >= 0; --r) {
+        const float rq = __fdividef(1.f, q[r * 33]);
+        x = z[r * 33] * rq - (e[r] * rq) * x;
+        z[r * 33] = x;
+        nrm = fmaf(x, x, nrm);
+      }
+      if (!(nrm > 0.f) || !isfinite(nrm)) {  // overflow or a zero solve: a coordinate vector
+        for (int r = 0; r < s; ++r) z[r * 33] = r == i ? 1.f : 0.f;
+        break;
+      }
+      const float inv = rsqrtf(nrm);
+      for (int r = 0; r < s; ++r) z[r * 33] *= inv;
+    }
+  }
+  __syncwarp();
+  // copy the computed vectors out, one vector per pass, lanes along rows
+  for (int cc = 0; cc < kIIThreads; ++cc) {
+    const int ic = i0 + cc;
+    if (ic >= s || ic < tcount) continue;  // uniform
+    for (int r = lane; r < s; r += kIIThreads) Zc[(int64_t)ic * k + r] = zs[r * 33 + cc];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 4. Orthonormal bases for clusters and the tail (one CTA of kOrthThreads).
+constexpr int kOrthThreads = 1024;
+
+// Householder QR of the nc columns src[0..nc) (column-major, length s, ld k)
+// held in the working copy Wk (overwritten); reflector jj (rows jj..s-1) goes
+// to U[jj k ...], its beta to bet[jj].  Two block barriers per column.
+__device__ void hh_qr(float* Wk, int nc, int s, int k, float* U, float* bet) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int jj = 0; jj < nc; ++jj) {
+    float* col = Wk + (int64_t)jj * k;
+    if (warp == 0) {
+      float sq = 0.f;
+      for (int r = jj + 1 + lane; r < s; r += 32) sq = fmaf(col[r], col[r], sq);
+      sq = warp_sumf(sq);
+      const float x0 = col[jj];
+      const float nrm = sqrtf(x0 * x0 + sq);
+      float alpha = 0.f, beta = 0.f, u0 = x0;
+      if (nrm > 1e-18f) {  // below that the column is taken as zero (no reflection)
+        alpha = x0 >= 0.f ? -nrm : nrm;
+        u0 = x0 - alpha;
+        beta = 2.f / (u0 * u0 + sq);
+      }
+      float* u = U + (int64_t)jj * k;
+      for (int r = lane; r < s; r += 32) u[r] = r < jj ? 0.f : (r == jj ? u0 : col[r]);
+      if (lane == 0) bet[jj] = beta;
+    }
+    __syncthreads();
+    const float beta = bet[jj];
+    const float* u = U + (int64_t)jj * k;
+    for (int cc = jj + 1 + warp; cc < nc; cc += nw) {
+      float* z = Wk + (int64_t)cc * k;
+      float dot = 0.f;
+      for (int r = jj + lane; r < s; r += 32) dot = fmaf(u[r], z[r], dot);
+      dot = beta * warp_sumf(dot);
+      for (int r = jj + lane; r < s; r += 32) z[r] = fmaf(-dot, u[r], z[r]);
+    }
+    __syncthreads();
+  }
+}
+
+// Column m of Q = H_0 H_1 ... H_{nc-1} (the reflectors of hh_qr) into dst
+// (length s), one warp; lane holds rows lane + 32 t.
+__device__ void hh_form_col(const float* U, const float* bet, int nc, int s, int k, int m, float* dst) {
+  const int lane = threadIdx.x & 31;
+  float y[8];
+#pragma unroll
+  for (int t = 0; t < 8; ++t) y[t] = (lane + 32 * t == m) ? 1.f : 0.f;
+  for (int jj = nc - 1; jj >= 0; --jj) {
+    const float beta = bet[jj];
+    if (beta == 0.f) continue;
+    const float* u = U + (int64_t)jj * k;
+    float uv[8], dot = 0.f;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int r = lane + 32 * t;
+      uv[t] = r < s ? u[r] : 0.f;
+      dot = fmaf(uv[t], y[t], dot);
+    }
+    dot = beta * warp_sumf(dot);
+#pragma unroll
+    for (int t = 0; t < 8; ++t) y[t] = fmaf(-dot, uv[t], y[t]);
+  }
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    const int r = lane + 32 * t;
+    if (r < s) dst[r] = y[t];
+  }
+}
+
+__global__ void __launch_bounds__(kOrthThreads, 1) seed_orth_kernel(int k, int level, int32_t* lvl,
+                                                                   const float* __restrict__ tri, float* Zc,
+                                                                   float* U, float* Wk, int32_t* stats,
+                                                                   int32_t* cid) {
+  const int s = level_size(lvl, level, k);
+  if (level > 0 && s < 2) return;
+  __shared__ float lam[256];
+  __shared__ float bet[256];
+  __shared__ int cstart[257];
+  __shared__ int ncl_s;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  for (int i = tid; i < s; i += blockDim.x) lam[i] = tri[4 * k + i];
+  __syncthreads();
+  const int t = tail_count(lam, s);
+  const float tol = kClusterTol * tri[5 * k + 2];
+  if (tid == 0) {
+    int nc = 0;
+    for (int i = t; i < s; ++i)
+      if (i == t || lam[i] - lam[i - 1] > tol) cstart[nc++] = i;
+    cstart[nc] = s;
+    ncl_s = nc;
+    if (level + 1 < kSeedLevels) lvl[level + 1] = t;
+    if (stats) *stats = level + 1;  // levels that ran
+  }
+  __syncthreads();
+  const int ncl = ncl_s;
+  // cluster ids of the block's columns: the tail is one cluster of the level
+  for (int cl = 0; cl < ncl; ++cl)
+    for (int i = cstart[cl] + tid; i < cstart[cl + 1]; i += blockDim.x) cid[i] = level * 1024 + cl;
+  for (int i = tid; i < t; i += blockDim.x) cid[i] = level * 1024 + 1023;
+  // clusters: Zc columns [i0, i1) <- orthonormal basis of their span.  The
+  // vectors of a tight cluster come out of inverse iteration nearly parallel,
+  // so their QR would bring rounding noise in from every direction: each is
+  // first projected (twice) against the level's singleton vectors, which
+  // span the rest of the block far more accurately.
+  for (int cl = 0; cl < ncl; ++cl) {
+    const int i0 = cstart[cl], i1 = cstart[cl + 1];
+    const int nc = i1 - i0;
+    if (nc < 2) continue;  // uniform
+    for (int e = tid; e < nc * k; e += blockDim.x) Wk[e] = Zc[(int64_t)i0 * k + e];
+    __syncthreads();
+    for (int m = warp; m < nc; m += nw) {
+      float* y = Wk + (int64_t)m * k;
+      for (int pass = 0; pass < 2; ++pass)
+        for (int sg = 0; sg < ncl; ++sg) {
+          if (cstart[sg + 1] - cstart[sg] != 1) continue;  // singletons only
+          const float* z = Zc + (int64_t)cstart[sg] * k;
+          float dot = 0.f;
+          for (int r = lane; r < s; r += 32) dot = fmaf(z[r], y[r], dot);
+          dot = warp_sumf(dot);
+          for (int r = lane; r < s; r += 32) y[r] = fmaf(-dot, z[r], y[r]);
+        }
+    }
+    __syncthreads();
+    hh_qr(Wk, nc, s, k, U, bet);
+    for (int m = warp; m < nc; m += nw) hh_form_col(U, bet, nc, s, k, m, Zc + (int64_t)(i0 + m) * k);
+    __syncthreads();
+  }
+  // tail: Zc columns [0, t) <- orthonormal basis of the complement of columns [t, s)
+  if (t > 0) {
+    const int r = s - t;
+    for (int e = tid; e < r * k; e += blockDim.x) Wk[e] = Zc[(int64_t)t * k + e];
+    __syncthreads();
+    hh_qr(Wk, r, s, k, U, bet);
+    for (int m = warp; m < t; m += nw) hh_form_col(U, bet, r, s, k, r + m, Zc + (int64_t)m * k);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 5. Back-transformation W = Q Z, one warp per column c of the k-wide output;
+// the CTA stages the packed reflectors in shared memory.  Level 0: Xout = W
+// (FP64 k x k, row-major) and lam_out = eigenvalues scaled back.  Level > 0:
+// Xout = blockdiag(W, I_{k-s}).
+constexpr int kBackWarps = 8;
+
+__global__ void __launch_bounds__(kBackWarps * 32) seed_back_kernel(int k, int level, const int32_t* __restrict__ lvl,
+                                                                    const float* __restrict__ gV,
+                                                                    const float* __restrict__ Zc,
+                                                                    const float* __restrict__ tri,
+                                                                    double* __restrict__ Xout,
+                                                                    double* __restrict__ lam_out) {
+  const int s = level_size(lvl, level, k);
+  if (level > 0 && s < 2) return;
+  extern __shared__ __align__(16) float P[];  // packed reflectors
+  __shared__ float bet[256];
+  const int np = s >= 3 ? packed_off(s - 2, s) : 0;  // entries of reflectors 0 .. s-3
+  for (int e = threadIdx.x; e < np; e += blockDim.x) P[e] = gV[e];
+  for (int j = threadIdx.x; j < s; j += blockDim.x) bet[j] = tri[3 * k + j];
   __syncthreads();
   const double hmax = (double)tri[5 * k + 4] + (double)tri[5 * k + 5];
-  if (blockIdx.x == 0)
-    for (int i = threadIdx.x; i < k; i += blockDim.x) lam_out[i] = (double)tri[4 * k + i] * hmax;
+  if (level == 0 && blockIdx.x == 0)
+    for (int i = threadIdx.x; i < s; i += blockDim.x) lam_out[i] = (double)tri[4 * k + i] * hmax;
   const int lane = threadIdx.x & 31;
-  const int c = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int c = blockIdx.x * kBackWarps + (threadIdx.x >> 5);
   if (c >= k) return;
-  float z[4];
-#pragma unroll
-  for (int t = 0; t < 4; ++t) {
-    const int r = lane + 32 * t;
-    z[t] = r < k ? gZ[r * k + c] : 0.f;
+  if (c >= s) {  // identity outside the block (level > 0 only: s == k at level 0)
+    for (int r = lane; r < k; r += 32) Xout[(int64_t)r * k + c] = r == c ? 1.0 : 0.0;
+    return;
   }
-  for (int j = k - 3; j >= 0; --j) {
-    const float b = beta[j];
-    if (b == 0.f) continue;  // uniform across the warp
-    float v[4], dot = 0.f;
+  float z[8];
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
+  for (int t = 0; t < 8; ++t) {
+    const int r = lane + 32 * t;
+    z[t] = r < s ? Zc[(int64_t)c * k + r] : 0.f;
+  }
+  for (int j = s - 3; j >= 0; --j) {
+    const float b = bet[j];
+    if (b == 0.f) continue;  // uniform across the warp
+    const float* v = P + packed_off(j, s) - (j + 1);  // v[r], r in (j, s)
+    float vv[8], dot = 0.f;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
       const int r = lane + 32 * t;
-      v[t] = r < k ? Vs[j * k + r] : 0.f;
-      dot = fmaf(v[t], z[t], dot);
+      vv[t] = (r > j && r < s) ? v[r] : 0.f;
+      dot = fmaf(vv[t], z[t], dot);
     }
     const float w = b * warp_sumf(dot);
 #pragma unroll
-    for (int t = 0; t < 4; ++t) z[t] = fmaf(-w, v[t], z[t]);
+    for (int t = 0; t < 8; ++t) z[t] = fmaf(-w, vv[t], z[t]);
   }
 #pragma unroll
-  for (int t = 0; t < 4; ++t) {
+  for (int t = 0; t < 8; ++t) {
     const int r = lane + 32 * t;
-    if (r < k) Xout[r * k + c] = (double)z[t];
+    if (r < k) Xout[(int64_t)r * k + c] = r < s ? (double)z[t] : 0.0;
   }
 }
 
-void launch_eig_seed(Launcher& L, const double* H, int k, float* gA, float* gZ, float* gQ, float* tri, double* Xout,
-                     double* lam, double* scal, int32_t* nclusters) {
-  if (k <= 128) {
-    const size_t s1 = (size_t)128 * k * sizeof(float);
-    cudaFuncSetAttribute(seed_tri_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1);
-    seed_tri_kernel<<<1, kSeedThreads, s1, L.stream>>>(H, k, gA, tri, scal);
-    seed_bisect_kernel<<<(k + 3) / 4, 128, 0, L.stream>>>(k, tri);
-    const size_t s3 = (size_t)2 * k * k * sizeof(float);
-    cudaFuncSetAttribute(seed_vec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s3);
-    seed_vec_kernel<<<1, 128, s3, L.stream>>>(k, tri, gZ, nclusters);
-    const size_t s4 = (size_t)k * k * sizeof(float);
-    cudaFuncSetAttribute(seed_back_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s4);
-    seed_back_kernel<<<(k + 7) / 8, 256, s4, L.stream>>>(k, gA, gZ, tri, Xout, lam);
-    L.count(4);
-    return;
-  }
-  eig_seed_kernel<<<1, kSeedThreads, 0, L.stream>>>(H, k, gA, gZ, gQ, Xout, lam, scal, nclusters);
-  L.count(1);
+template <int NC>
+static void launch_tri(Launcher& L, const double* M, int k, int level, int32_t* lvl, float* gV, float* tri,
+                       double* scal) {
+  const size_t smem = (size_t)TriCfg<NC>::SMEM_FLOATS * sizeof(float);
+  cudaFuncSetAttribute(seed_tri_kernel<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  seed_tri_kernel<NC><<<1, TriCfg<NC>::THREADS, smem, L.stream>>>(M, k, level, lvl, gV, tri, scal);
+}
+
+void launch_seed_level(Launcher& L, const double* M, int k, int level, int32_t* lvl, float* gV, float* Zc, float* U,
+                       float* Wk, float* tri, double* Xout, double* lam, double* scal, int32_t* stats,
+                       int32_t* cid) {
+  if (k <= 128)
+    launch_tri<128>(L, M, k, level, lvl, gV, tri, scal);
+  else
+    launch_tri<256>(L, M, k, level, lvl, gV, tri, scal);
+  seed_bisect_kernel<<<(k + 3) / 4, 128, 0, L.stream>>>(k, level, lvl, tri);
+  const size_t sii = (size_t)2 * 33 * 256 * sizeof(float);
+  cudaFuncSetAttribute(seed_ii_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sii);
+  seed_ii_kernel<<<(k + kIIThreads - 1) / kIIThreads, kIIThreads, sii, L.stream>>>(k, level, lvl, tri, Zc);
+  seed_orth_kernel<<<1, kOrthThreads, 0, L.stream>>>(k, level, lvl, tri, Zc, U, Wk, stats, cid);
+  const size_t sback = (size_t)((k * (k - 1)) / 2 + 4) * sizeof(float);
+  cudaFuncSetAttribute(seed_back_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sback);
+  seed_back_kernel<<<(k + kBackWarps - 1) / kBackWarps, kBackWarps * 32, sback, L.stream>>>(k, level, lvl, gV, Zc,
+                                                                                            tri, Xout, lam);
+  L.count(5);
 }
 
 }  // namespace lspca

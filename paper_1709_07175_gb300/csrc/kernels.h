@@ -75,9 +75,10 @@ void launch_csc_passf(Launcher& L, const CscView& c, int64_t n, int64_t nnz, con
 struct SmallWs {
   double* Hpart;   // splits x k x k
   double* H;       // k x k
-  float* h32;      // k x k (seed scratch when k > 128)
-  float* w32;      // k x k (seed scratch when k > 128)
-  float* q32;      // k x k (inverse-iteration scratch)
+  float* h32;      // k x k: the seed's tridiagonalisation reflectors
+  float* w32;      // k x k: the seed's eigenvectors of T (column-major)
+  float* q32;      // k x k: inverse-iteration pivots, then Householder vectors
+  float* p32;      // k x k: working copy of the seed's Householder QR
   double* Xa;      // k x k
   double* Xb;      // k x k
   double* Rm;      // k x k
@@ -87,15 +88,24 @@ struct SmallWs {
   double* lam;     // k
   double* scal;    // 8 scalars, sigma copy (k), sqrt(S_rr) (k), order (k int32)
   double* Vd;      // n x k
-  int32_t* sweeps; // 1: eigenvalue clusters found by the FP32 seed
-  float* tri;      // seed scratch (k <= 128): d, e, e^2, beta, eigenvalues of T (k each), 8 scalars
+  int32_t* sweeps; // 1: levels of the graded eigen seed that ran
+  int32_t* lvl;    // kSeedLevels + 1: block size of each seed level
+  int32_t* cid;    // k: seed cluster of each eigenvector column (level * 1024 + cluster)
+  float* tri;      // seed scratch: d, e, e^2, beta, eigenvalues of T (k each), 8 scalars
   int h_splits;
 };
+// Levels of the graded eigensolve of the k x k step (eigseed.cu).
+constexpr int kSeedLevels = 3;
 size_t small_ws_bytes(int k, int64_t n, int* h_splits);
-// FP32 eigen seed of H (k x k FP64): eigenvectors -> Xout (k x k FP64, columns),
-// eigenvalues -> lam (ascending), scal[1] = ||H||_F.
-void launch_eig_seed(Launcher& L, const double* H, int k, float* gA, float* gZ, float* gQ, float* tri, double* Xout,
-                     double* lam, double* scal, int32_t* nclusters);
+// One level of the FP32 eigen seed (eigseed.cu).  Level 0 seeds M = H
+// (k x k FP64) and writes its eigenvectors to Xout; level l > 0 seeds the
+// leading lvl[l] x lvl[l] block of M (ld k) and writes blockdiag(W, I) to
+// Xout.  lvl[l + 1] receives the size of the level's unresolved tail.
+// cid[i] (i < the level's block size) receives the seed cluster of column i:
+// columns with equal ids were not resolved from one another by the seed.
+void launch_seed_level(Launcher& L, const double* M, int k, int level, int32_t* lvl, float* gV, float* Zc, float* U,
+                       float* Wk, float* tri, double* Xout, double* lam, double* scal, int32_t* stats,
+                       int32_t* cid);
 void carve_small_ws(SmallWs& w, void* base, int k, int64_t n);
 void launch_decompose(Launcher& L, SmallWs& w, const double* F, int k, int64_t n, int64_t m, bool v_f64, void* V,
                       double* sigma, int32_t* rank, int* status);

@@ -5,9 +5,11 @@
 // column dropped, sigma_i = 0).
 //
 // GB300 executes FP64 at a small fraction of its FP32 rate, so the eigensolve
-// is split into an FP32 seed on one CTA (tridiagonalisation, bisection and
-// inverse iteration, eigseed.cu) and FP64 iterative refinement of the whole
-// eigenvector matrix built from k x k FP64 products spread over many CTAs (Ogita & Aishima, "Iterative refinement for symmetric
+// is split into an FP32 seed (tridiagonalisation, bisection, inverse
+// iteration, eigseed.cu) and FP64 iterative refinement of the whole
+// eigenvector matrix built from k x k FP64 products spread over many CTAs;
+// the seed runs in up to kSeedLevels levels, each on the tail block the
+// level before left unresolved (Ogita & Aishima, "Iterative refinement for symmetric
 // eigenvalue decomposition", Japan J. Indust. Appl. Math. 35, 2018: one step
 // forms R = I - X^T X, S = X^T H X, lambda_i = s_ii / (1 - r_ii),
 // E_ij = (s_ij + lambda_j r_ij) / (lambda_j - lambda_i) for separated pairs,
@@ -31,13 +33,15 @@ size_t small_ws_bytes(int k, int64_t n, int* h_splits) {
   size_t b = 0;
   b += (size_t)hs * kk * 8;            // Hpart
   b += kk * 8;                          // H
-  b += kk * 4 * 3;                      // seed scratch: A, Z, inverse-iteration q
+  b += kk * 4 * 4;                      // seed scratch: reflectors, Z, pivots / Householder vectors, QR copy
   b += kk * 8 * 6;                      // Xa Xb Rm T S E
   b += (size_t)k * 8 + 64 + (size_t)k * 24;  // lam, scal (+ src, sd)
   b += (size_t)n * k * 8;               // Vd
   b += 64;                              // sweeps
+  b += 64;                              // seed level sizes
+  b += (size_t)k * 4;                   // seed cluster ids
   b += (size_t)k * 4 * 5 + 64;          // seed scratch: d, e, e^2, beta, eigenvalues of T, scalars
-  return b + 17 * 256;                  // alignment slack
+  return b + 20 * 256;                  // alignment slack
 }
 
 static char* align256(char* p) { return (char*)(((uintptr_t)p + 255) & ~(uintptr_t)255); }
@@ -54,6 +58,7 @@ void carve_small_ws(SmallWs& w, void* base, int k, int64_t n) {
   w.h32 = (float*)take(kk * 4);
   w.w32 = (float*)take(kk * 4);
   w.q32 = (float*)take(kk * 4);
+  w.p32 = (float*)take(kk * 4);
   w.Xa = (double*)take(kk * 8);
   w.Xb = (double*)take(kk * 8);
   w.Rm = (double*)take(kk * 8);
@@ -64,6 +69,8 @@ void carve_small_ws(SmallWs& w, void* base, int k, int64_t n) {
   w.scal = (double*)take(64 + (size_t)k * 24);
   w.Vd = (double*)take((size_t)n * k * 8);
   w.sweeps = (int32_t*)take(64);
+  w.lvl = (int32_t*)take(64);
+  w.cid = (int32_t*)take((size_t)k * 4);
   w.tri = (float*)take((size_t)k * 4 * 5 + 64);
 }
 
@@ -84,35 +91,207 @@ __device__ double block_sum(double v, double* red) {
 }
 
 // lambda_i = S_ii / (X^T X)_ii (Rayleigh quotients of the current vectors).
-__global__ void rayleigh_kernel(const double* __restrict__ Rm, const double* __restrict__ S, int k, double* lam) {
+// act (nullable): the seed level's block size; below 2 the level is idle and
+// the kernel leaves its outputs as they are.
+__global__ void rayleigh_kernel(const double* __restrict__ Rm, const double* __restrict__ S, int k, double* lam,
+                                const int32_t* act) {
+  if (act && *act < 2) return;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x)
     lam[i] = S[(int64_t)i * k + i] / Rm[(int64_t)i * k + i];
 }
 
-// One refinement step's correction E, row i per block (R = I - Rm).  A pair
-// (i, j) takes the first-order correction (s_ij + lambda_j r_ij) /
-// (lambda_j - lambda_i) when that is a small rotation (|E_ij| <= 1/2) and the
-// gap is above FP64 noise of H (64 eps ||H||_F, scal[1] = ||H||_F); otherwise
-// it is treated as a cluster and only re-orthogonalised (r_ij / 2).  The
-// per-pair test replaces the method's global cluster threshold, which
-// (evaluated with Frobenius norms) would leave close but well-coupled pairs
-// unresolved; the iteration still converges quadratically for resolved pairs.
-// The Rayleigh quotients lambda are formed here from the diagonals of S and
-// Rm (as rayleigh_kernel does), so the step needs no separate launch for them.
+// Clusters the refinement resolves by Rayleigh-Ritz: runs of equal cid of 2
+// to kRRMax columns that are not a level's tail (cid % 1024 == 1023).
+constexpr int kRRMax = 16;
+
+// Size of the cid run that holds column i when it is such a cluster (first
+// column -> *first), else 0.
+__device__ __forceinline__ int rr_cluster(const int32_t* __restrict__ cid, int k, int i, int* first) {
+  const int id = cid[i];
+  if ((id & 1023) == 1023) return 0;
+  int a = i, b = i + 1;
+  while (a > 0 && cid[a - 1] == id && i - a < kRRMax) --a;
+  while (b < k && cid[b] == id && b - i <= kRRMax) ++b;
+  const int sc = b - a;
+  *first = a;
+  return (sc >= 2 && sc <= kRRMax) ? sc : 0;
+}
+
+// Rayleigh-Ritz inside each small seed cluster: the eigenvectors Z of the
+// cluster's block of S (symmetrised, FP64 cyclic Jacobi, one warp) are
+// written to Zr[C, C] (cluster_rotate_kernel applies them).  The FP32 seed
+// cannot order vectors whose eigenvalues are closer than its resolution; in
+// FP64 they may well be distinct.
+__global__ void __launch_bounds__(32) cluster_rr_kernel(const double* __restrict__ S, const int32_t* __restrict__ cid,
+                                                        int k, double* __restrict__ Zr, const int32_t* act) {
+  if (act && *act < 2) return;
+  const int c = blockIdx.x, lane = threadIdx.x;
+  int i0 = 0;
+  const int sc = rr_cluster(cid, k, c, &i0);
+  if (sc == 0 || i0 != c) return;  // one warp per cluster: its first column
+  __shared__ double A[kRRMax][kRRMax + 1], Z[kRRMax][kRRMax + 1];
+  __shared__ double cs[3];
+  for (int e = lane; e < sc * sc; e += 32) {
+    const int a = e / sc, b = e % sc;
+    A[a][b] = 0.5 * (S[(int64_t)(i0 + a) * k + i0 + b] + S[(int64_t)(i0 + b) * k + i0 + a]);
+    Z[a][b] = a == b ? 1.0 : 0.0;
+  }
+  __syncwarp();
+  for (int sweep = 0; sweep < 12; ++sweep) {
+    double off = 0.0, dia = 0.0;
+    for (int e = lane; e < sc * sc; e += 32) {
+      const int a = e / sc, b = e % sc;
+      if (a != b) off += A[a][b] * A[a][b];
+      else dia += A[a][b] * A[a][b];
+    }
+    off = warp_sum(off);
+    dia = warp_sum(dia);
+    if (!(off > 1e-30 * dia)) break;  // uniform
+    for (int p = 0; p < sc - 1; ++p)
+      for (int q = p + 1; q < sc; ++q) {
+        if (lane == 0) {
+          const double apq = A[p][q];
+          double cc = 1.0, ss = 0.0, tt = 0.0;
+          if (fabs(apq) > 1e-300) {
+            const double th = (A[q][q] - A[p][p]) / (2.0 * apq);
+            tt = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+            cc = 1.0 / sqrt(tt * tt + 1.0);
+            ss = tt * cc;
+          }
+          cs[0] = cc;
+          cs[1] = ss;
+          cs[2] = tt;
+        }
+        __syncwarp();
+        const double cc = cs[0], ss = cs[1], tt = cs[2];
+        if (ss != 0.0) {
+          const int r = lane;
+          double arp = 0.0, arq = 0.0, zrp = 0.0, zrq = 0.0;
+          if (r < sc) {
+            arp = A[r][p];
+            arq = A[r][q];
+            zrp = Z[r][p];
+            zrq = Z[r][q];
+          }
+          const double app = A[p][p], aqq = A[q][q], apq = A[p][q];
+          __syncwarp();
+          if (r < sc) {
+            if (r != p && r != q) {
+              const double np = cc * arp - ss * arq, nq = ss * arp + cc * arq;
+              A[r][p] = np;
+              A[p][r] = np;
+              A[r][q] = nq;
+              A[q][r] = nq;
+            }
+            Z[r][p] = cc * zrp - ss * zrq;
+            Z[r][q] = ss * zrp + cc * zrq;
+          }
+          if (lane == 0) {
+            A[p][p] = app - tt * apq;
+            A[q][q] = aqq + tt * apq;
+            A[p][q] = 0.0;
+            A[q][p] = 0.0;
+          }
+        }
+        __syncwarp();
+      }
+  }
+  for (int e = lane; e < sc * sc; e += 32) {
+    const int a = e / sc, b = e % sc;
+    Zr[(int64_t)(i0 + a) * k + i0 + b] = Z[a][b];
+  }
+}
+
+// Columns of each small seed cluster of X rotated in place by the cluster's
+// Rayleigh-Ritz vectors: X[:, C] <- X[:, C] Zr[C, C], one CTA per row of X.
+// It follows the first-order step X + X E, which leaves the cluster's span
+// decoupled from the other columns; a rotation inside that span keeps it so.
+// blockIdx.y selects the matrix: X, then (nullable) A1, A2.
+__global__ void cluster_rotate_kernel(double* __restrict__ X, double* __restrict__ A1, double* __restrict__ A2,
+                                      const int32_t* __restrict__ cid, const double* __restrict__ Zr, int k,
+                                      const int32_t* act) {
+  if (act && *act < 2) return;
+  double* M = blockIdx.y == 0 ? X : (blockIdx.y == 1 ? A1 : A2);
+  if (!M) return;
+  const int r = blockIdx.x;
+  for (int c = threadIdx.x; c < k; c += blockDim.x) {
+    int i0 = 0;
+    const int sc = rr_cluster(cid, k, c, &i0);
+    if (sc == 0 || i0 != c) continue;
+    double x[kRRMax], y[kRRMax];
+    for (int a = 0; a < sc; ++a) x[a] = M[(int64_t)r * k + i0 + a];
+    for (int b = 0; b < sc; ++b) {
+      double t = 0.0;
+      for (int a = 0; a < sc; ++a) t = fma(x[a], Zr[(int64_t)(i0 + a) * k + i0 + b], t);
+      y[b] = t;
+    }
+    for (int b = 0; b < sc; ++b) M[(int64_t)r * k + i0 + b] = y[b];
+  }
+}
+
+// Rows of each small cluster of A1 and A2 rotated in place: A[C, :] <-
+// Zr[C, C]^T A[C, :], one CTA per column (with the column rotation above:
+// A <- B^T A B for the block-diagonal B of the clusters' Rayleigh-Ritz vectors).
+__global__ void cluster_rotate_rows_kernel(double* __restrict__ A1, double* __restrict__ A2,
+                                           const int32_t* __restrict__ cid, const double* __restrict__ Zr, int k,
+                                           const int32_t* act) {
+  if (act && *act < 2) return;
+  double* M = blockIdx.y == 0 ? A1 : A2;
+  const int col = blockIdx.x;
+  for (int c = threadIdx.x; c < k; c += blockDim.x) {
+    int i0 = 0;
+    const int sc = rr_cluster(cid, k, c, &i0);
+    if (sc == 0 || i0 != c) continue;
+    double x[kRRMax], y[kRRMax];
+    for (int a = 0; a < sc; ++a) x[a] = M[(int64_t)(i0 + a) * k + col];
+    for (int b = 0; b < sc; ++b) {
+      double t = 0.0;
+      for (int a = 0; a < sc; ++a) t = fma(Zr[(int64_t)(i0 + a) * k + i0 + b], x[a], t);
+      y[b] = t;
+    }
+    for (int b = 0; b < sc; ++b) M[(int64_t)(i0 + b) * k + col] = y[b];
+  }
+}
+
+// One refinement step's correction E, row i per block (R = I - Rm).  Pairs
+// inside a level's unresolved tail, or inside a seed cluster of at most kRRMax
+// columns, are only re-orthogonalised (r_ij / 2): the next level resolves the
+// tail, and the Rayleigh-Ritz rotation (cluster_rr_kernel,
+// cluster_rotate_kernel) the small cluster.  Any other pair -- also inside a
+// larger seed cluster, where the gap must also exceed 1e-12 ||H||_F -- takes
+// the first-order correction
+// (s_ij + lambda_j r_ij) / (lambda_j - lambda_i) when that is a small
+// rotation (|E_ij| <= 1/2) and the gap is above FP64 noise of H
+// (64 eps ||H||_F, scal[1] = ||H||_F); otherwise it too is only
+// re-orthogonalised.  The per-pair test replaces the method's global cluster
+// threshold, which (evaluated with Frobenius norms) would leave close but
+// well-coupled pairs unresolved; the iteration still converges quadratically
+// for resolved pairs.  The Rayleigh quotients lambda are formed here from the
+// diagonals of S and Rm (as rayleigh_kernel does), so the step needs no
+// separate launch for them.
 __global__ void refine_e_kernel(const double* __restrict__ Rm, const double* __restrict__ S,
-                                const double* __restrict__ scal, int k, double* __restrict__ E) {
+                                const double* __restrict__ scal, const int32_t* __restrict__ cid, int k,
+                                double* __restrict__ E, const int32_t* act) {
+  if (act && *act < 2) return;
   const int i = blockIdx.x;
   const double noise = 64.0 * 0x1p-52 * scal[1];
   const double li = S[(int64_t)i * k + i] / Rm[(int64_t)i * k + i];
+  const int ci = cid[i];
+  int i0 = 0;
+  // pairs held apart from the first-order step: a level's tail, a small cluster
+  const bool held = (ci & 1023) == 1023 || rr_cluster(cid, k, i, &i0) != 0;
+  // inside a larger cluster, a pair closer than this is degenerate in FP64
+  const double degen = 1e-12 * scal[1];
   for (int j = threadIdx.x; j < k; j += blockDim.x) {
     const int64_t e = (int64_t)i * k + j;
     const double r = (i == j ? 1.0 : 0.0) - Rm[e];
     double v = 0.5 * r;
-    if (i != j) {
+    const bool same = cid[j] == ci;
+    if (i != j && !(held && same)) {
       const double lj = S[(int64_t)j * k + j] / Rm[(int64_t)j * k + j];
       const double gap = lj - li;
       const double num = S[e] + lj * r;
-      if (fabs(gap) > noise && fabs(num) <= 0.5 * fabs(gap)) v = num / gap;
+      if (fabs(gap) > (same ? degen : noise) && fabs(num) <= 0.5 * fabs(gap)) v = num / gap;
     }
     E[e] = v;
   }
@@ -250,7 +429,9 @@ __global__ void finalize_v_kernel(const double* __restrict__ Vd, int64_t n, int 
 // shared memory.  GB300 issues few FP64 FMAs per SM per clock, so the tiles
 // are small enough to spread even a 128 x 128 product over all SMs.  sym:
 // C is symmetric (op(B) = op(A)^T); only tiles with blockIdx.x <= blockIdx.y
-// run and each also writes its mirror.
+// run and each also writes its mirror.  act (nullable): a seed level's block
+// size on the device; below 2 the product is skipped and C = dflt when dflt is
+// given (else C is left as it is).
 struct DgemmArgs {
   int64_t M, N, K;
   const double* A;
@@ -264,11 +445,20 @@ struct DgemmArgs {
   int64_t c_split_stride, kchunk;
   int sym;
   const double* Cin;  // nullable: C = Cin + op(A) op(B)
+  const int32_t* act;
+  const double* dflt;
 };
 
 template <int TM, int TN, int KS>
 __device__ __forceinline__ void dgemm_tile_body(const DgemmArgs& g, int z) {
   if (g.sym && blockIdx.x > blockIdx.y) return;
+  if (g.act && *g.act < 2) {
+    if (g.dflt && z == 0) {
+      const int64_t gi = (int64_t)blockIdx.x * TM + threadIdx.x / TN, gj = (int64_t)blockIdx.y * TN + threadIdx.x % TN;
+      if (gi < g.M && gj < g.N) g.C[gi * g.ldc + gj] = g.dflt[gi * g.ldc + gj];
+    }
+    return;
+  }
   __shared__ double As[TM][KS + 1];
   __shared__ double Bs[TN][KS + 1];
   const int tid = threadIdx.x;
@@ -321,7 +511,8 @@ __global__ void __launch_bounds__(TM* TN) dgemm_pair_kernel(const DgemmArgs g0, 
 }
 
 static DgemmArgs dargs(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda, bool at, const double* B,
-                       int64_t ldb, bool bt, double* C, int64_t ldc, const double* Cin = nullptr) {
+                       int64_t ldb, bool bt, double* C, int64_t ldc, const double* Cin = nullptr,
+                       const int32_t* act = nullptr, const double* dflt = nullptr) {
   DgemmArgs g{};
   g.M = M;
   g.N = N;
@@ -338,6 +529,8 @@ static DgemmArgs dargs(int64_t M, int64_t N, int64_t K, const double* A, int64_t
   g.kchunk = K;
   g.sym = 0;
   g.Cin = Cin;
+  g.act = act;
+  g.dflt = dflt;
   return g;
 }
 
@@ -349,10 +542,18 @@ static void dgemm2(Launcher& L, const DgemmArgs& g0, const DgemmArgs& g1) {
 }
 
 static void dgemm(Launcher& L, int64_t M, int64_t N, int64_t K, const double* A, int64_t lda, bool at, const double* B,
-                  int64_t ldb, bool bt, double* C, int64_t ldc, const double* Cin = nullptr) {
+                  int64_t ldb, bool bt, double* C, int64_t ldc, const double* Cin = nullptr,
+                  const int32_t* act = nullptr, const double* dflt = nullptr, bool sym = false) {
   dim3 grid((unsigned)((M + 7) / 8), (unsigned)((N + 7) / 8), 1);
-  dgemm_tile_kernel<8, 8, 64><<<grid, 64, 0, L.stream>>>(dargs(M, N, K, A, lda, at, B, ldb, bt, C, ldc, Cin));
+  DgemmArgs g = dargs(M, N, K, A, lda, at, B, ldb, bt, C, ldc, Cin, act, dflt);
+  g.sym = sym ? 1 : 0;
+  dgemm_tile_kernel<8, 8, 64><<<grid, 64, 0, L.stream>>>(g);
   L.count(1);
+}
+
+static DgemmArgs sym_args(DgemmArgs g) {
+  g.sym = 1;
+  return g;
 }
 
 void launch_decompose(Launcher& L, SmallWs& w, const double* F, int k, int64_t n, int64_t m, bool v_f64, void* V,
@@ -370,26 +571,51 @@ void launch_decompose(Launcher& L, SmallWs& w, const double* F, int k, int64_t n
     L.count(1);
   }
   launch_reduce_splits(L, w.Hpart, w.h_splits, kk, kk, w.H);
-  // FP32 seed (tridiagonalisation + bisection + inverse iteration)
-  launch_eig_seed(L, w.H, k, w.h32, w.w32, w.q32, w.tri, w.Xa, w.lam, w.scal, w.sweeps);
-  // FP64 refinement
+  // Graded eigensolve: level 0 seeds H; each later level seeds the tail block
+  // of S = X^T H X left unresolved by the level before, and rotates those
+  // columns of X; every level ends with the FP64 refinement.
   double* X = w.Xa;
   double* Xn = w.Xb;
-  for (int it = 0; it <= kRefineIters; ++it) {
-    dgemm2(L, dargs(k, k, k, X, k, true, X, k, false, w.Rm, k),    // X^T X
-           dargs(k, k, k, w.H, k, false, X, k, false, w.T, k));  // H X
-    dgemm(L, k, k, k, X, k, true, w.T, k, false, w.S, k);          // X^T H X
-    if (it == kRefineIters) {  // last pass only refreshes lambda and S
-      rayleigh_kernel<<<1, 256, 0, L.stream>>>(w.Rm, w.S, k, w.lam);
-      L.count(1);
-      break;
+  for (int level = 0; level < kSeedLevels; ++level) {
+    const int32_t* act = level == 0 ? nullptr : w.lvl + level;
+    if (level == 0) {
+      launch_seed_level(L, w.H, k, 0, w.lvl, w.h32, w.w32, w.q32, w.p32, w.tri, X, w.lam, w.scal, w.sweeps,
+                        w.cid);
+    } else {
+      launch_seed_level(L, w.S, k, level, w.lvl, w.h32, w.w32, w.q32, w.p32, w.tri, w.E, w.lam, w.scal, w.sweeps,
+                        w.cid);
+      dgemm(L, k, k, k, X, k, false, w.E, k, false, Xn, k, nullptr, act, X);  // X blockdiag(W, I)
+      double* t = X;
+      X = Xn;
+      Xn = t;
     }
-    refine_e_kernel<<<k, 128, 0, L.stream>>>(w.Rm, w.S, w.scal, k, w.E);
-    L.count(1);
-    dgemm(L, k, k, k, X, k, false, w.E, k, false, Xn, k, X);  // X + X E
-    double* t = X;
-    X = Xn;
-    Xn = t;
+    // FP64 refinement
+    for (int it = 0; it <= kRefineIters; ++it) {
+      dgemm2(L, sym_args(dargs(k, k, k, X, k, true, X, k, false, w.Rm, k, nullptr, act)),  // X^T X
+             dargs(k, k, k, w.H, k, false, X, k, false, w.T, k, nullptr, act));            // H X
+      // X^T (H X): symmetric up to rounding; the upper triangle is mirrored
+      dgemm(L, k, k, k, X, k, true, w.T, k, false, w.S, k, nullptr, act, nullptr, true);
+      if (it == kRefineIters) {
+        // last pass: a final Rayleigh-Ritz rotation of the small clusters,
+        // applied to X, S and X^T X alike (B^T S B), then lambda
+        cluster_rr_kernel<<<k, 32, 0, L.stream>>>(w.S, w.cid, k, w.T, act);
+        cluster_rotate_kernel<<<dim3(k, 3), 64, 0, L.stream>>>(X, w.S, w.Rm, w.cid, w.T, k, act);
+        cluster_rotate_rows_kernel<<<dim3(k, 2), 64, 0, L.stream>>>(w.S, w.Rm, w.cid, w.T, k, act);
+        rayleigh_kernel<<<1, 256, 0, L.stream>>>(w.Rm, w.S, k, w.lam, act);
+        L.count(4);
+        break;
+      }
+      // T (H X) is free once S is formed: it holds the clusters' Rayleigh-Ritz vectors
+      cluster_rr_kernel<<<k, 32, 0, L.stream>>>(w.S, w.cid, k, w.T, act);
+      refine_e_kernel<<<k, 128, 0, L.stream>>>(w.Rm, w.S, w.scal, w.cid, k, w.E, act);
+      L.count(2);
+      dgemm(L, k, k, k, X, k, false, w.E, k, false, Xn, k, X, act, X);  // X + X E
+      cluster_rotate_kernel<<<dim3(k, 1), 64, 0, L.stream>>>(Xn, nullptr, nullptr, w.cid, w.T, k, act);
+      L.count(1);
+      double* t = X;
+      X = Xn;
+      Xn = t;
+    }
   }
   // order, rank rule, Ws and Tinv (S of the final X is in w.S)
   sort_rank_kernel<<<1, 256, 0, L.stream>>>(w.lam, w.S, k, m, n, sigma, rank, w.scal);
