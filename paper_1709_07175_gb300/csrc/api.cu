@@ -114,10 +114,25 @@ struct SketchBufs {
   int32_t* off = nullptr;
   void* omega = nullptr;  // dense Omega (n x k, result type) for the SIMT / tensor-core paths
   TcProjectWs pw;         // tensor-core path: pre-split tiles of Omega
+  void* bsws = nullptr;   // E4M3 X, plain SIMT path: Omega's rows for the gather
+  void* f8ws = nullptr;   // E4M3 X on the FP8 tensor cores (shared with pass F)
 };
 
-void plan_sketch(Plan& P, SketchBufs& b, int xt, int64_t n, int k, const lspca_omega& om, bool tc) {
-  if (tc) {
+// FP8 E4M3 X (binary features; the very sparse Omega is required): the FP8
+// tensor-core sketch and pass F (f8.cu); under LSPCA_FORCE_SIMT the sketch is
+// the gather over the nonzeros of X (bsketch.cu).
+bool use_f8(int xt, uint32_t flags) {
+  return xt == LSPCA_E4M3 && !(flags & LSPCA_FORCE_SIMT) && tc_available();
+}
+bool use_bsketch(int xt, uint32_t flags) { return xt == LSPCA_E4M3 && !use_f8(xt, flags); }
+
+void plan_sketch(Plan& P, SketchBufs& b, int xt, int64_t n, int k, const lspca_omega& om, bool tc, uint32_t flags,
+                 int64_t m, int num_sms) {
+  if (use_f8(xt, flags)) {
+    b.f8ws = P.take(f8_ws_bytes(m, n, k, num_sms));
+  } else if (use_bsketch(xt, flags)) {
+    b.bsws = P.take(bsketch_ws_bytes(n, k));
+  } else if (tc) {
     b.omega = P.take((size_t)n * k * 4);
     char* base = P.base ? P.base + ((P.off + 255) & ~(size_t)255) : nullptr;
     plan_tc_project(base, b.pw, xt, n, k);
@@ -136,6 +151,18 @@ using Mark = std::function<void(int)>;
 
 void run_sketch(lspca_ctx* ctx, Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_t ldx, int k,
                 const lspca_omega& om, bool tc, SketchBufs& b, void* U, const Mark& mark) {
+  if (b.f8ws) {
+    mark(1);
+    launch_f8_sketch(L, X, m, n, ldx, k, om, b.f8ws, (float*)U, ctx->d_absmax + 1, ctx->d_status);
+    mark(2);
+    return;
+  }
+  if (b.bsws) {
+    mark(1);
+    launch_bsketch(L, X, m, n, ldx, k, om, b.bsws, (float*)U, ctx->d_absmax + 1, ctx->d_status);
+    mark(2);
+    return;
+  }
   if (tc) {
     // dense Omega (BF16-rounded for BF16 X, exact +-1/0 for the very sparse kind)
     // through the tensor-core reduction-map kernel: U = X Omega; the kernel also
@@ -169,6 +196,7 @@ struct ChainBufs {
   double* Gpart = nullptr;
   int f_splits = 1, g_splits = 1;
   TcChainWs tcw;
+  void* f8ws = nullptr;  // E4M3 X: the FP8 pass F (the BF16 one runs only when U is not exact in E4M3)
 };
 
 int simt_splits(int64_t rows, int64_t cols, int64_t K, int num_sms) {
@@ -197,10 +225,16 @@ void plan_chain(Plan& P, ChainBufs& b, int xt, int64_t m, int64_t n, int k, bool
 int run_chain(lspca_ctx* ctx, Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_t ldx, const void* U,
               int k, bool tc, ChainBufs& b, double* F, double* G, const Mark& mark) {
   if (tc) {
-    if (!tc_chain_main(L, X, xt, m, n, ldx, (const float*)U, k, b.tcw, ctx->d_absmax, ctx->d_status, G != nullptr))
+    const int* gate = nullptr;
+    if (b.f8ws) {
+      if (!launch_f8_chain(L, X, m, n, ldx, k, b.f8ws, F, ctx->d_status)) return LSPCA_ERR_CUDA;
+      gate = f8_inexact_flag(b.f8ws, m, n, k, ctx->num_sms);
+    }
+    if (!tc_chain_main(L, X, xt, m, n, ldx, (const float*)U, k, b.tcw, ctx->d_absmax, ctx->d_status, G != nullptr,
+                       gate))
       return LSPCA_ERR_CUDA;
     mark(3);
-    tc_chain_reduce(L, n, k, b.tcw, F, G);
+    tc_chain_reduce(L, n, k, b.tcw, F, G, false, gate);
     mark(4);
     return LSPCA_OK;
   }
@@ -255,7 +289,8 @@ int fit_impl(lspca_ctx* ctx, const void* X, int32_t xt, int64_t m, int64_t n, in
   double *F = nullptr, *G = nullptr, *R = nullptr;
   auto plan = [&](Plan& P) {
     U = P.take((size_t)m * k * asz);
-    plan_sketch(P, sb, xt, n, k, om, tc_s);
+    plan_sketch(P, sb, xt, n, k, om, tc_s, flags, m, ctx->num_sms);
+    cb.f8ws = sb.f8ws;
     F = (double*)P.take((size_t)k * n * 8);
     G = (double*)P.take((size_t)k * k * 8);
     plan_chain(P, cb, xt, m, n, k, want_g, tc_f, ctx->num_sms);
@@ -674,11 +709,11 @@ int lspca_sketch(lspca_ctx* ctx, const void* X, int32_t xt, int64_t m, int64_t n
   const bool tc = use_tc_sketch(xt, om, flags);
   SketchBufs sb;
   Plan p0;
-  plan_sketch(p0, sb, xt, n, k, om, tc);
+  plan_sketch(p0, sb, xt, n, k, om, tc, flags, m, ctx->num_sms);
   if ((st = ensure_ws(ctx, p0.off + 4096, s))) return st;
   Plan p1;
   p1.base = (char*)ctx->ws;
-  plan_sketch(p1, sb, xt, n, k, om, tc);
+  plan_sketch(p1, sb, xt, n, k, om, tc, flags, m, ctx->num_sms);
   cudaMemsetAsync(ctx->d_absmax, 0, 2 * sizeof(float), s);
   run_sketch(ctx, L, X, xt, m, n, ldx, k, om, tc, sb, U, [](int) {});
   return cuda_status(cudaGetLastError());
@@ -694,13 +729,20 @@ int lspca_chain(lspca_ctx* ctx, const void* X, int32_t xt, int64_t m, int64_t n,
   cudaStream_t s = (cudaStream_t)stream;
   Launcher L{s, &ctx->launches, ctx->num_sms};
   const bool tc = use_tc_chain(xt, flags, k) && aligned16(U);
+  const bool f8 = tc && use_f8(xt, flags);
   ChainBufs cb;
+  auto plan = [&](Plan& P) {
+    plan_chain(P, cb, xt, m, n, k, G != nullptr, tc, ctx->num_sms);
+    if (f8) cb.f8ws = P.take(f8_ws_bytes(m, n, k, ctx->num_sms));
+  };
   Plan p0;
-  plan_chain(p0, cb, xt, m, n, k, G != nullptr, tc, ctx->num_sms);
+  plan(p0);
   if ((st = ensure_ws(ctx, p0.off + 4096, s))) return st;
   Plan p1;
   p1.base = (char*)ctx->ws;
-  plan_chain(p1, cb, xt, m, n, k, G != nullptr, tc, ctx->num_sms);
+  plan(p1);
+  // the FP8 pass F reads U as E4M3 bytes (exact, or flagged and left to the BF16 pass F)
+  if (f8) launch_f8_u8(L, (const float*)U, m, k, cb.f8ws, n);
   if (tc) {
     // the split-FP16 path scales by powers of two derived from max|X| and max|U|
     cudaMemsetAsync(ctx->d_absmax, 0, 2 * sizeof(float), s);

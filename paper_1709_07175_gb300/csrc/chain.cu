@@ -111,6 +111,7 @@ struct Params {
   const float* amax_b;  // max|B source| (FP32 X and Gram scales)
   const float* amax_u;  // max|U|
   int* status;
+  const int* gate;      // nullable: the pass runs only when *gate != 0
 };
 
 // Power-of-two scale s with |v s| < 2^14 for |v| <= amax (1 for amax 0 / non-finite).
@@ -163,7 +164,9 @@ __device__ __forceinline__ uint4 ldg16(const void* p) {
 // U s (s = pow2_scale(max|U|)) or BF16 pairs of U.
 template <bool F16>
 __global__ void split_u_kernel(const float* __restrict__ U, int64_t m, int k, int64_t ku,
-                               const float* __restrict__ amax, uint16_t* __restrict__ hi, uint16_t* __restrict__ lo) {
+                               const float* __restrict__ amax, uint16_t* __restrict__ hi, uint16_t* __restrict__ lo,
+                               const int* gate) {
+  if (gate && *gate == 0) return;
   const float s = F16 ? pow2_scale(*amax) : 1.f;
   const int k4 = k / 4;
   const int64_t total = m * k4;
@@ -190,6 +193,7 @@ __global__ void __launch_bounds__(Cfg<MODE, MH, NACC>::THREADS, 1)
                  const __grid_constant__ CUtensorMap tm_bhi, const __grid_constant__ CUtensorMap tm_blo, Params p) {
   using C = Cfg<MODE, MH, NACC>;
   constexpr int STAGES = C::STAGES;
+  if (p.gate && *p.gate == 0) return;  // uniform: another pass produces F
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* tfull = reinterpret_cast<uint64_t*>(smem + STAGES * C::STAGE_BYTES);
@@ -632,7 +636,7 @@ void plan_tc_chain(char* base, TcChainWs& w, int xt, int64_t m, int64_t n, int k
 }
 
 bool tc_chain_main(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_t ldx, const float* U, int k,
-                   TcChainWs& w, const float* absmax, int* status, bool want_g) {
+                   TcChainWs& w, const float* absmax, int* status, bool want_g, const int* gate) {
   const int BN = pf::tile_cols(k);
   const bool f16 = xt == LSPCA_F32;
   const int threads = 256;
@@ -641,10 +645,10 @@ bool tc_chain_main(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int
   if (blocks > 8 * L.num_sms) blocks = 8 * L.num_sms;
   if (f16)
     pf::split_u_kernel<true><<<blocks, threads, 0, L.stream>>>(U, m, k, w.ku, absmax + 1, (uint16_t*)w.uhi,
-                                                                (uint16_t*)w.ulo);
+                                                                (uint16_t*)w.ulo, gate);
   else
     pf::split_u_kernel<false><<<blocks, threads, 0, L.stream>>>(U, m, k, w.ku, absmax + 1, (uint16_t*)w.uhi,
-                                                                 (uint16_t*)w.ulo);
+                                                                 (uint16_t*)w.ulo, gate);
   L.count(1);
   const CUtensorMapDataType adt = f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   CUtensorMap ahi, alo, bhi, blo;
@@ -670,6 +674,7 @@ bool tc_chain_main(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int
   p.amax_b = absmax;
   p.amax_u = absmax + 1;
   p.status = status;
+  p.gate = gate;
   bool ok;
   if (xt == LSPCA_F32) ok = pf::launch_k<pf::M_F32>(L, k, ahi, alo, bhi, blo, p);
   else if (xt == LSPCA_BF16) ok = pf::launch_k<pf::M_BF16>(L, k, ahi, alo, bhi, blo, p);
@@ -680,7 +685,7 @@ bool tc_chain_main(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int
     CUtensorMap ghi = ahi, glo = alo;
     if (xt != LSPCA_F32) {
       pf::split_u_kernel<true><<<blocks, threads, 0, L.stream>>>(U, m, k, w.ku, absmax + 1, (uint16_t*)w.ghi,
-                                                                  (uint16_t*)w.glo);
+                                                                  (uint16_t*)w.glo, nullptr);
       L.count(1);
       if (!make_tmap_2d_sw128(&ghi, w.ghi, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, (uint64_t)m, (uint64_t)k,
                               (uint64_t)w.ku * 2, pf::BK, 64) ||
@@ -689,6 +694,7 @@ bool tc_chain_main(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int
         return false;
     }
     pf::Params g = p;
+    g.gate = nullptr;
     g.X = nullptr;
     g.nb = k;
     g.tiles = (k + BN - 1) / BN;

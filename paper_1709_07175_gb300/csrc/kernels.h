@@ -44,6 +44,27 @@ size_t sketch_off_bytes(int64_t n, int k);
 void launch_sketch_sparse(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_t ldx, int k,
                           const int32_t* col_ptr, const int32_t* entries, int32_t* off, void* U, int64_t ldu,
                           float* absmax, int* status);
+// U = X Omega for FP8 E4M3 X and the very sparse Omega, as a gather over the
+// nonzeros of X (bsketch.cu); ws holds Omega's rows (bsketch_ws_bytes).  U is
+// m x k FP32; *umax |= max|U|; NaN in X sets ST_NONFINITE.
+size_t bsketch_ws_bytes(int64_t n, int k);
+void launch_bsketch(Launcher& L, const void* X, int64_t m, int64_t n, int64_t ldx, int k, const lspca_omega& om,
+                    void* ws, float* U, float* umax, int* status);
+// FP8 tensor-core passes for E4M3 X with the very sparse Omega (f8.cu).  One
+// workspace (f8_ws_bytes) serves both: the sketch writes U (FP32, nullable)
+// and its E4M3 copy plus a flag raised when some U is not exactly an E4M3
+// value; pass F (launch_f8_chain: F = U^T X, k x n FP64) then reads the E4M3
+// copy, or does nothing when the flag is raised (f8_inexact_flag: the gate of
+// the BF16 pass F that runs instead).  launch_f8_u8 makes the copy of a
+// caller-supplied U.  The launchers return false when a tensor map cannot be
+// built.
+size_t f8_ws_bytes(int64_t m, int64_t n, int k, int num_sms);
+int* f8_inexact_flag(void* ws, int64_t m, int64_t n, int k, int num_sms);
+bool launch_f8_sketch(Launcher& L, const void* X, int64_t m, int64_t n, int64_t ldx, int k, const lspca_omega& om,
+                      void* ws, float* U, float* umax, int* status);
+void launch_f8_u8(Launcher& L, const float* U, int64_t m, int k, void* ws, int64_t n);
+bool launch_f8_chain(Launcher& L, const void* X, int64_t m, int64_t n, int64_t ldx, int k, void* ws, double* F,
+                     int* status);
 // Scan X for NaN/Inf and its largest magnitude (dense-Omega paths).
 void launch_scan_x(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_t ldx, float* absmax, int* status);
 

@@ -476,7 +476,8 @@ __global__ void __launch_bounds__(THREADS, 1) chain_kernel(Params p) {
 // carrying the rounding error of every addition (GB300 issues few FP64 adds);
 // sum + error is the partials' sum to ~2^-48 relative to their magnitudes.
 __global__ void reduce_f32_parts_kernel(const float* __restrict__ part, int chunks, int64_t count,
-                                        double* __restrict__ out, int accumulate) {
+                                        double* __restrict__ out, int accumulate, const int* gate) {
+  if (gate && *gate == 0) return;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
     float s = 0.f, c = 0.f;
     for (int q = 0; q < chunks; ++q) {
@@ -590,19 +591,20 @@ void tc_chain_inline_main(Launcher& L, const void* X, int xt, int64_t m, int64_t
   }
 }
 
-void tc_chain_reduce(Launcher& L, int64_t n, int k, TcChainWs& w, double* F, double* G, bool accumulate) {
+void tc_chain_reduce(Launcher& L, int64_t n, int k, TcChainWs& w, double* F, double* G, bool accumulate,
+                     const int* gate) {
   const int threads = 256;
   int64_t cnt = (int64_t)k * n;
   int blocks = (int)((cnt + threads - 1) / threads);
   if (blocks > 8 * L.num_sms) blocks = 8 * L.num_sms;
   tcc::reduce_f32_parts_kernel<<<blocks, threads, 0, L.stream>>>((const float*)w.Fpart, w.chunks, cnt, F,
-                                                                 accumulate ? 1 : 0);
+                                                                 accumulate ? 1 : 0, gate);
   L.count(1);
   if (G && w.Gpart) {
     cnt = (int64_t)k * k;
     blocks = (int)((cnt + threads - 1) / threads);
     tcc::reduce_f32_parts_kernel<<<blocks, threads, 0, L.stream>>>((const float*)w.Gpart, w.gchunks, cnt, G,
-                                                                   accumulate ? 1 : 0);
+                                                                   accumulate ? 1 : 0, nullptr);
     L.count(1);
   }
 }

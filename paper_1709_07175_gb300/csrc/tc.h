@@ -30,15 +30,17 @@ struct TcChainWs {
 void plan_tc_chain(char* base, TcChainWs& w, int xt, int64_t m, int64_t n, int k, bool want_g, int num_sms);
 // absmax[0] = max|X|, absmax[1] = max|U| on the device (FP32 / Gram scales).
 // Returns false when a tensor map cannot be built or the kernel cannot be configured.
+// gate (nullable): F's kernels do nothing unless *gate != 0 (the Gram always runs).
 bool tc_chain_main(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_t ldx, const float* U, int k,
-                   TcChainWs& w, const float* absmax, int* status, bool want_g);
+                   TcChainWs& w, const float* absmax, int* status, bool want_g, const int* gate = nullptr);
 // Pass F with U split inside the kernel (tc.cu): its workspace is the partials
 // only, which a fixed-size scratch array can hold for any m.
 void plan_tc_chain_inline(char* base, TcChainWs& w, int xt, int64_t m, int64_t n, int k, bool want_g, int num_sms);
 void tc_chain_inline_main(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_t ldx, const float* U,
                           int k, TcChainWs& w, const float* absmax, int* status, bool want_g);
 // F (k x n FP64) = sum of the chunk partials, or F += that sum with accumulate (Algorithm 4's F += U_s^T X_s).
-void tc_chain_reduce(Launcher& L, int64_t n, int k, TcChainWs& w, double* F, double* G, bool accumulate = false);
+void tc_chain_reduce(Launcher& L, int64_t n, int k, TcChainWs& w, double* F, double* G, bool accumulate = false,
+                     const int* gate = nullptr);
 
 // Y = X V on tensor cores (FP32, BF16 or E4M3 X; V and Y FP32, k <= 256).  With V = a
 // dense Omega the same kernel computes the sketch U = X Omega (pass S).
