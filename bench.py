@@ -1,9 +1,22 @@
-"""Benchmark: Lazy SPCA fit throughput on one GB300 (and N replicas under torchrun).
+"""Benchmark: Lazy SPCA on one GB300 (and N GPUs under torchrun).
 
-Workload (one step = one whole Lazy SPCA fit, every pass of the hot path):
-fp32_sparse -- X of 200,000 x 4,096 FP32 (sigma_i = 1/i over rank 512 plus
-N(0, 1e-3^2) noise), k = 128, very sparse Omega with p = 64.  X (3.28 GB)
-is larger than L2, so no flush is needed between steps.
+Headline workload (one step = one whole Lazy SPCA fit plus the reduction map
+of every row, the paper-scale form of the path): e4m3_binary -- X of
+4,600,000 x 4,096 binary features in FP8 E4M3 (column rates p_j ~ Beta(0.5,
+9.5), 5 % density; Experiment 1's mostly-binary design matrix, synthetic),
+k = 256, very sparse Omega with p = 64.  X (18.8 GB) is larger than L2, so no
+flush is needed between steps.  The same JSON line carries, as extra keys, the
+precision form (bf16_dense, 1,000,000 x 8,192 BF16, Gaussian Omega, k = 256),
+the FP32 form (fp32_sparse, 200,000 x 4,096, k = 128) with the SPCA
+comparison path and the Gram on and off, the k x k step on flat and steep
+spectra, the TF-IDF-shaped sparse fit and the serving run.
+
+With --gpus N > 1 the step is one fit whose rows are sharded over the N ranks
+(each rank holds a 4.6 M-row block of its own, so the work per GPU is fixed:
+weak scaling): per rank the sketch and pass F, one exchange of the k x n FP64
+partials of F over NCCL (gathered and summed in rank order by the library),
+the k x k step replicated, the reduction map of the rank's own rows.  Run
+without torchrun, --gpus N starts the N ranks itself.
 
 Prints ONE JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
 on a bounded sample of the same workload instead.
@@ -23,15 +36,18 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Lazy SPCA fit samples/s & HBM-roofline frac vs SPCA on GB300; serve p50/p99 ms"
-WORKLOAD = "fp32_sparse"
+WORKLOAD = "e4m3_binary"
 
 
 def _peaks():
+    """Measured HBM copy bandwidth (GB/s) and BF16 dense TFLOP/s (burst,
+    sustained), else the documented fallback figures."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         d = json.load(open(p))
-        return d.get("hbm_gbs", 6800.0), "measured"
-    return 6800.0, "fallback"
+        return {"hbm": d.get("hbm_gbs", 6800.0), "bf16": d.get("bf16_tflops", 1900.0),
+                "bf16_sustained": d.get("bf16_tflops_sustained", 1700.0), "kind": "measured"}
+    return {"hbm": 6800.0, "bf16": 1900.0, "bf16_sustained": 1700.0, "kind": "fallback"}
 
 
 def _dist():
@@ -115,28 +131,41 @@ def cpu_model() -> str:
     return platform.machine()
 
 
+def _oracle_step(O, X, Om):
+    """One oracle step of the headline workload: the FP64 fit and the
+    reduction map of the same rows."""
+    fit = O.lspca_fit(X, Om, route="eig")
+    return O.project(X, fit["V"])
+
+
+def _oracle_sample(rows: int):
+    from oracle import philox as P
+    from paper_1709_07175_gb300 import synthetic as S
+    w = S.WORKLOADS[WORKLOAD].scaled(m=rows)
+    X = S.generate(w).float().double().numpy()
+    Om = P.omega_sparse(w.omega_seed, w.n, w.k, w.p)
+    return w, X, Om
+
+
 def cpu_baseline(rows: int, reps_seconds: float = 10.0) -> dict:
     """The FP64 oracle as it stands, on a bounded sample of the workload."""
     import numpy as np
 
     from oracle import lspca as O
-    from oracle import philox as P
-    from paper_1709_07175_gb300 import synthetic as S
-    w = S.WORKLOADS[WORKLOAD].scaled(m=rows)
-    X = S.generate(w).double().numpy()
-    Om = P.omega_sparse(w.omega_seed, w.n, w.k, w.p)
+    w, X, Om = _oracle_sample(rows)
     t0 = time.perf_counter()
     reps = 0
     while True:
-        O.lspca_fit(X, Om, route="eig")
+        _oracle_step(O, X, Om)
         reps += 1
         if time.perf_counter() - t0 >= reps_seconds:
             break
     dt = time.perf_counter() - t0
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     return {"value": rows * reps / dt, "unit": "samples/s", "cores": cores, "kind": "oracle",
-            "sample": f"{rows} rows x {w.n} of the {WORKLOAD} workload (same recipe), k={w.k}, "
-                      f"{reps} fit(s) in {dt:.1f} s; FP64 numpy, BLAS threads = host default",
+            "sample": f"{rows} rows x {w.n} of the {WORKLOAD} workload (same recipe), k={w.k}: "
+                      f"{reps} oracle fit(s) plus reduction map of the sample in {dt:.1f} s; FP64 numpy, "
+                      f"BLAS threads = host default",
             "cpu": cpu_model(), "np": np.__version__}
 
 
@@ -252,44 +281,334 @@ def serve_bench(L, S, torch, local: int, seconds: float, loads=(0.5, 0.8, 0.95),
 
 
 # DRAM bytes (read + write) per row of X of one launch, from one ncu capture
-# (--set full) at 50,000 rows of the same workload; traffic grows in
-# proportion to the rows.  Set an entry to None when its kernel changes, until
-# it is captured again.
+# of the same kernel on a smaller case of the same workload (traffic grows in
+# proportion to the rows).  None until captured, and reset to None whenever
+# the kernel changes.
 TRAFFIC_PER_ROW = {
-    "sketch": (822.426624e6 + 23.101952e6) / 50000,
-    "chain_main": (844.953088e6 + 25.067264e6) / 50000,
+    ("e4m3_binary", "sketch"): None,
+    ("e4m3_binary", "chain_main"): None,
+    ("e4m3_binary", "project"): None,
 }
 
 
+def roofline(kernel, ms, bytes_, flops, peak_tflops, pk, m, workload, traffic_key=None):
+    """Roofline of one kernel: bound by HBM (bytes / copy bandwidth) or by the
+    tensor pipe (flops / peak), whichever is slower; achieved = algorithmic
+    work / measured time."""
+    t_hbm = bytes_ / (pk["hbm"] * 1e9)
+    t_ten = flops / (peak_tflops * 1e12) if flops else 0.0
+    sec = ms / 1e3
+    tr = TRAFFIC_PER_ROW.get((workload, traffic_key or kernel))
+    if t_ten > t_hbm:
+        ach = flops / sec / 1e12
+        out = {"bound": "tensor", "achieved": ach, "peak": peak_tflops, "unit": "TFLOP/s", "frac": ach / peak_tflops}
+    else:
+        ach = bytes_ / sec / 1e9
+        out = {"bound": "hbm", "achieved": ach, "peak": pk["hbm"], "unit": "GB/s", "frac": ach / pk["hbm"]}
+    out.update({"kernel": kernel, "ms_per_launch": ms, "bytes_per_launch": bytes_, "flops_per_launch": flops,
+                "traffic": (tr * m if tr else None), "peak_kind": pk["kind"]})
+    return out
+
+
+
+
 def run_reference(args):
+    """The reference arm: the FP64 oracle (the paper ships no program) on the
+    host cores, each step one oracle fit plus reduction map of a bounded
+    sample of the headline workload."""
     ws, rank, _ = _dist()
     if rank != 0:
         return
     from oracle import lspca as O
-    from oracle import philox as P
-    from paper_1709_07175_gb300 import synthetic as S
     rows = args.ref_rows
-    w = S.WORKLOADS[WORKLOAD].scaled(m=rows)
-    X = S.generate(w).double().numpy()
-    Om = P.omega_sparse(w.omega_seed, w.n, w.k, w.p)
+    w, X, Om = _oracle_sample(rows)
     for _ in range(args.warmup):
-        O.lspca_fit(X, Om, route="eig")
+        _oracle_step(O, X, Om)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        O.lspca_fit(X, Om, route="eig")
+        _oracle_step(O, X, Om)
     dt = time.perf_counter() - t0
     val = rows * args.steps / dt
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    full = S.WORKLOADS[WORKLOAD]
+    full = S_workload(WORKLOAD)
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "samples/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{WORKLOAD} {full.m}x{full.n} k={full.k} very sparse p={full.p}",
+            "config": {"workload": f"{WORKLOAD} {full.m}x{full.n} k={full.k} very sparse p={full.p}, "
+                                   f"fit + reduction map of all rows",
                        "m": full.m, "n": full.n, "k": full.k},
             "cpu_baseline": {"value": val, "unit": "samples/s", "cores": cores, "kind": "oracle",
-                             "sample": f"each step: one oracle fit of {rows} rows x {w.n} (same recipe)"},
+                             "sample": f"each step: one oracle fit plus reduction map of {rows} rows x {w.n} "
+                                       f"(same recipe)"},
             "e2e": {"value": val, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def S_workload(name):
+    from paper_1709_07175_gb300 import synthetic as S
+    return S.WORKLOADS[name]
+
+
+PASS_NAMES = ["omega", "sketch", "chain_main", "chain_reduce", "qr", "small", "total"]
+
+
+def _events(torch, n):
+    return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+
+
+def measure_headline(L, S, torch, w, X, ctx, stream, args, dist, pk, ws):
+    """The headline step on this rank: the Lazy SPCA fit of X (one GPU) or of
+    the row-sharded matrix (N ranks), then the reduction map of the rank's
+    rows.  Returns the timing, per-kernel rooflines and launch counts."""
+    from paper_1709_07175_gb300 import shard
+    dev = X.device
+    om = L.omega("sparse", w.omega_seed, w.p)
+    V = torch.empty(w.n, w.k, dtype=torch.float32, device=dev)
+    sigma = torch.empty(w.k, dtype=torch.float64, device=dev)
+    rk = torch.empty(1, dtype=torch.int32, device=dev)
+    Y = torch.empty(w.m, w.k, dtype=torch.float32, device=dev)
+    steps = max(args.steps, 1)
+    pe = _events(torch, 2 * steps)
+
+    def step(i=None):
+        if ws == 1:
+            rc = L.lspca_fit(ctx.handle, X, w.k, om, 0, V, sigma, None, rk, stream)
+            if rc != L.OK:
+                raise L.LspcaError(rc, "lspca_fit")
+        else:
+            V2, s2, r2, _, _ = shard.sharded_fit(ctx, X, w.m * ws, w.k, om)
+            V.copy_(V2)
+            sigma.copy_(s2)
+            rk.copy_(r2)
+        if i is not None:
+            pe[2 * i].record(stream)
+        rc = L.lspca_project(ctx.handle, X, V, w.k, Y, stream)
+        if rc != L.OK:
+            raise L.LspcaError(rc, "lspca_project")
+        if i is not None:
+            pe[2 * i + 1].record(stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    L.lspca_profile(ctx.handle, True)
+    launches0 = ctx.launch_count()
+    clocks = Clocks(dev.index or 0)
+    clocks.start()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = _events(torch, 2)
+    e0.record(stream)
+    for i in range(steps):
+        step(i)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    launches = ctx.launch_count() - launches0
+    pass_ms, calls = L.lspca_profile_read(ctx.handle)
+    L.lspca_profile(ctx.handle, False)
+    proj_ms = sum(pe[2 * i].elapsed_time(pe[2 * i + 1]) for i in range(steps)) / steps
+    ms = shard.max_over_ranks(ms, dev)
+    out = {"ms": ms / steps, "launches": launches // steps, "clocks": clk, "project_ms": proj_ms,
+           "rank": int(rk.item()), "sigma_1": float(sigma[0].item())}
+    if ws == 1 and calls:
+        per = {nm: pass_ms[i] / calls for i, nm in enumerate(PASS_NAMES)}
+        per["project"] = proj_ms
+        out["passes_ms"] = per
+        m, n, k = w.m, w.n, w.k
+        f8 = 2.0 * pk["bf16_sustained"]  # FP8 dense peak: the measured BF16 peak x the nominal ratio 2
+        kern = {
+            "sketch": roofline("sketch", per["sketch"], m * (n + k), 2.0 * m * n * k, f8, pk, m, w.name),
+            "chain_main": roofline("chain_main", per["chain_main"], m * (n + k), 2.0 * m * n * k, f8, pk, m, w.name),
+            "project": roofline("project", proj_ms, m * (n + 4 * k), 4.0 * m * n * k, pk["bf16_sustained"], pk, m,
+                                w.name),
+        }
+        out["kernels"] = kern
+        dom = max(("sketch", "chain_main", "project", "small"), key=lambda nm: per[nm])
+        out["dominant"] = dom
+        out["roofline"] = kern.get(dom, kern["project"])
+    del Y
+    return out, V, sigma
+
+
+def _time(torch, stream, fn, reps):
+    fn()
+    torch.cuda.synchronize()
+    a, b = _events(torch, 2)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def _sine(torch, A, B):
+    """Largest principal-angle sine between span(A) and span(B) (orthonormal
+    columns), ||B - A (A^T B)||_2 in FP64."""
+    A = A.double()
+    B = B.double()
+    return float(torch.linalg.matrix_norm(B - A @ (A.T @ B), ord=2).item())
+
+
+def measure_spca(L, torch, w, X, ctx, stream, om, V_lazy, ms_lazy, reps):
+    """The SPCA comparison path (Alg. 1/3: TSQR R, F = R^-T U^T X) on the same
+    X, with the agreement of its span with Lazy SPCA's (Prop. 2)."""
+    V = torch.empty(w.n, w.k, dtype=torch.float32, device=X.device)
+    sig = torch.empty(w.k, dtype=torch.float64, device=X.device)
+    rk = torch.empty(1, dtype=torch.int32, device=X.device)
+
+    def fn():
+        rc = L.spca_fit(ctx.handle, X, w.k, om, 0, V, sig, None, rk, stream)
+        if rc != L.OK:
+            raise L.LspcaError(rc, "spca_fit")
+    ms = _time(torch, stream, fn, reps)
+    return {"ms_per_fit": ms, "lazy_fit_ms": ms_lazy, "lazy_speedup": ms / ms_lazy,
+            "sine_spca_vs_lazy": _sine(torch, V, V_lazy),
+            "note": "sine: largest principal-angle sine between span(V^s) and span(V^l), equal spans by Prop. 2"}
+
+
+def measure_form(L, S, torch, name, stream, local, pk, reps, m=None, spca=False, gram=False):
+    """Fit and reduction map of another workload (same process, one GPU)."""
+    w = S.WORKLOADS[name]
+    if m:
+        w = w.scaled(m=m)
+    dev = torch.device(f"cuda:{local}")
+    X = S.generate(w, device=dev)
+    torch.cuda.synchronize()
+    ctx = L.Context(local)
+    om = L.omega(w.omega, w.omega_seed, w.p)
+    V = torch.empty(w.n, w.k, dtype=torch.float32, device=dev)
+    sig = torch.empty(w.k, dtype=torch.float64, device=dev)
+    rk = torch.empty(1, dtype=torch.int32, device=dev)
+    Y = torch.empty(w.m, w.k, dtype=torch.float32, device=dev)
+
+    def fit(flags=0, G=None):
+        rc = L.lspca_fit(ctx.handle, X, w.k, om, flags, V, sig, G, rk, stream)
+        if rc != L.OK:
+            raise L.LspcaError(rc, "lspca_fit")
+
+    def proj():
+        rc = L.lspca_project(ctx.handle, X, V, w.k, Y, stream)
+        if rc != L.OK:
+            raise L.LspcaError(rc, "lspca_project")
+    fit()
+    fit_ms = _time(torch, stream, fit, reps)
+    L.lspca_profile(ctx.handle, True)
+    fit()
+    pass_ms, calls = L.lspca_profile_read(ctx.handle)
+    L.lspca_profile(ctx.handle, False)
+    per = {nm: pass_ms[i] / max(calls, 1) for i, nm in enumerate(PASS_NAMES)}
+    proj_ms = _time(torch, stream, proj, reps)
+    esz = X.element_size()
+    xb = w.m * w.n * esz
+    out = {"workload": f"{name} {w.m}x{w.n} {w.dtype} k={w.k} {w.omega} omega" + (f" p={w.p}" if w.p else ""),
+           "fit_ms": fit_ms, "fit_samples_per_s": w.m / (fit_ms / 1e3), "passes_ms": per,
+           "project_ms": proj_ms, "project_samples_per_s": w.m / (proj_ms / 1e3),
+           "fit_x_pass_roofline_frac": (xb / (pk["hbm"] * 1e9)) / (fit_ms / 1e3)}
+    if name == "bf16_dense":
+        # BF16 X: sketch one exact product, pass F two (U split into a BF16 pair), projection two (V pair)
+        bf = pk["bf16_sustained"]
+        out["kernels"] = {
+            "sketch": roofline("sketch", per["sketch"], w.m * (w.n * 2 + w.k * 4), 2.0 * w.m * w.n * w.k, bf, pk,
+                               w.m, name),
+            "chain_main": roofline("chain_main", per["chain_main"], w.m * (w.n * 2 + w.k * 4),
+                                   4.0 * w.m * w.n * w.k, bf, pk, w.m, name),
+            "project": roofline("project", proj_ms, w.m * (w.n * 2 + w.k * 4), 4.0 * w.m * w.n * w.k, bf, pk, w.m,
+                                name)}
+    if name == "fp32_sparse":
+        out["kernels"] = {
+            "sketch": roofline("sketch", per["sketch"], w.m * (w.n + w.k) * 4, 0, 1.0, pk, w.m, name),
+            "chain_main": roofline("chain_main", per["chain_main"], w.m * (w.n + w.k) * 4, 0, 1.0, pk, w.m, name),
+            "project": roofline("project", proj_ms, w.m * (w.n + w.k) * 4, 0, 1.0, pk, w.m, name)}
+    if gram:
+        G = torch.empty(w.k, w.k, dtype=torch.float64, device=dev)
+        out["gram"] = {"ms_per_fit_on": _time(torch, stream, lambda: fit(L.WANT_GRAM, G), reps),
+                       "ms_per_fit_off": fit_ms,
+                       "note": "the same fit with the optional G = U^T U output (LSPCA_WANT_GRAM) on and off"}
+    if spca:
+        out["spca"] = measure_spca(L, torch, w, X, ctx, stream, om, V, fit_ms, reps)
+    ctx.close()
+    del X, Y
+    torch.cuda.empty_cache()
+    return out
+
+
+def measure_kxk(L, torch, local, stream, reps=5):
+    """The k x k step alone (lspca_decompose, n = 4,096, FP32 V) on a flat
+    spectrum (sigma_i(F) = i^-0.2) and a steep one (sigma_i(F) = 2^-i)."""
+    import numpy as np
+    ctx = L.Context(local)
+    out = {}
+    for k in (128, 256):
+        n = 4096
+        rng = np.random.default_rng(k)
+        Q, _ = np.linalg.qr(rng.standard_normal((n, k)))
+        P, _ = np.linalg.qr(rng.standard_normal((k, k)))
+        i = np.arange(1, k + 1, dtype=np.float64)
+        for spec, s in (("flat", i ** -0.2), ("steep", 2.0 ** -i)):
+            F = torch.from_numpy((P * s) @ Q.T).to(f"cuda:{local}").contiguous()
+            out[f"k{k}_{spec}_ms"] = _time(torch, stream, lambda: ctx.decompose(F, 200000, torch.float32), reps)
+    ctx.close()
+    return out
+
+
+def measure_sparse(L, S, torch, local, stream):
+    """A sparse X in CSR form, the shape of the paper's TF-IDF experiment."""
+    sw_ = S.SPARSE_TFIDF
+    dev = torch.device(f"cuda:{local}")
+    rp_, c_, v_ = (t.to(dev) for t in S.sparse_csr(sw_["m"], sw_["n"], sw_["density"], sw_["seed"]))
+    om_s = L.omega("sparse", sw_["omega_seed"], sw_["p"])
+    ctx = L.Context(local)
+    ms = _time(torch, stream, lambda: ctx.fit_csr(rp_, c_, v_, sw_["n"], sw_["k"], om_s, report=False,
+                                                  stream=stream), 5)
+    ctx.close()
+    return {"workload": f"CSR {sw_['m']}x{sw_['n']} density {sw_['density']} nnz {v_.numel()} "
+                        f"k={sw_['k']} very sparse p={sw_['p']}",
+            "ms_per_fit": ms, "samples_per_s": sw_["m"] / (ms / 1e3), "nnz_per_s": v_.numel() / (ms / 1e3),
+            "api": "lspca_fit_csr"}
+
+
+def measure_e2e(L, torch, w, X, ctx, stream, reps):
+    """The headline step end to end through the public API with host buffers:
+    X copied from pinned host memory, the fit and the reduction map of every
+    row, then V, sigma and Y copied back."""
+    dev = X.device
+    Xh = torch.empty(X.shape, dtype=X.dtype, pin_memory=True)
+    Xh.copy_(X)
+    om = L.omega("sparse", w.omega_seed, w.p)
+    V = torch.empty(w.n, w.k, dtype=torch.float32, device=dev)
+    sig = torch.empty(w.k, dtype=torch.float64, device=dev)
+    rk = torch.empty(1, dtype=torch.int32, device=dev)
+    Y = torch.empty(w.m, w.k, dtype=torch.float32, device=dev)
+    Vh = torch.empty(V.shape, dtype=V.dtype, pin_memory=True)
+    sh = torch.empty(sig.shape, dtype=sig.dtype, pin_memory=True)
+    Yh = torch.empty(Y.shape, dtype=Y.dtype, pin_memory=True)
+
+    def step():
+        X.copy_(Xh, non_blocking=True)
+        rc = L.lspca_fit(ctx.handle, X, w.k, om, 0, V, sig, None, rk, stream)
+        if rc != L.OK:
+            raise L.LspcaError(rc, "lspca_fit")
+        rc = L.lspca_project(ctx.handle, X, V, w.k, Y, stream)
+        if rc != L.OK:
+            raise L.LspcaError(rc, "lspca_project")
+        Vh.copy_(V, non_blocking=True)
+        sh.copy_(sig, non_blocking=True)
+        Yh.copy_(Y, non_blocking=True)
+    h2d_ms = _time(torch, stream, lambda: X.copy_(Xh, non_blocking=True), 1)
+    ms = _time(torch, stream, step, reps)
+    xb = Xh.numel() * Xh.element_size()
+    out = {"value": w.m / (ms / 1e3), "unit": "samples/s", "h2d_bytes_per_step": xb,
+           "d2h_bytes_per_step": Vh.numel() * 4 + sh.numel() * 8 + Yh.numel() * 4, "ms_per_step": ms,
+           "api": "lspca_fit + lspca_project, X from pinned host memory, V / sigma / Y back to pinned host memory",
+           "h2d_copy_ms": h2d_ms, "h2d_copy_gbs": xb / (h2d_ms / 1e3) / 1e9}
+    del Xh, Yh, Y
+    return out
 
 
 def run_gpu(args):
@@ -297,6 +616,7 @@ def run_gpu(args):
 
     from paper_1709_07175_gb300 import build as B
     from paper_1709_07175_gb300 import lspca as L
+    from paper_1709_07175_gb300 import shard
     from paper_1709_07175_gb300 import synthetic as S
 
     ws, rank, local = _dist()
@@ -307,257 +627,97 @@ def run_gpu(args):
         import torch.distributed as dist_mod
         dist_mod.init_process_group("nccl")
         dist = dist_mod
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
+    pk = _peaks()
+    stream = torch.cuda.current_stream()
     w = S.WORKLOADS[WORKLOAD]
     if args.m:
         w = w.scaled(m=args.m)
-    # weak scaling: each rank fits its own independent problem (different data seed)
     from dataclasses import replace
-    w = replace(w, data_seed=w.data_seed + 1000 * rank)
+    w = replace(w, data_seed=w.data_seed + 1000 * rank)  # each rank its own block of rows
     X = S.generate(w, device=f"cuda:{local}")
     torch.cuda.synchronize()
     ctx = L.Context(local)
-    om = L.omega("sparse", w.omega_seed, w.p)
-    stream = torch.cuda.current_stream()
-    V = torch.empty(w.n, w.k, dtype=torch.float32, device=X.device)
-    sigma = torch.empty(w.k, dtype=torch.float64, device=X.device)
-    rk = torch.empty(1, dtype=torch.int32, device=X.device)
-
-    def step(fn=L.lspca_fit):
-        rc = fn(ctx.handle, X, w.k, om, 0, V, sigma, None, rk, stream)
-        if rc != L.OK:
-            raise L.LspcaError(rc, fn.__name__)
-
-    for _ in range(max(args.warmup, 3)):
-        step()
-    torch.cuda.synchronize()
-
-    # ---- timed region: device-resident inputs
-    L.lspca_profile(ctx.handle, True)
-    launches0 = ctx.launch_count()
-    clocks = Clocks(local)
-    clocks.start()
-    barrier()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    launches = ctx.launch_count() - launches0
-    pass_ms, calls = L.lspca_profile_read(ctx.handle)
-    L.lspca_profile(ctx.handle, False)
-    if dist is not None:
-        t = torch.tensor([ms], device=X.device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    ms_step = ms / args.steps
-    value = w.m * ws * args.steps / (ms / 1e3)
-
-    # ---- the same fit with the optional Gram G = U^T U (Lemma 1 / Prop. 1) on
-    G = torch.empty(w.k, w.k, dtype=torch.float64, device=X.device)
-
-    def step_gram():
-        rc = L.lspca_fit(ctx.handle, X, w.k, om, L.WANT_GRAM, V, sigma, G, rk, stream)
-        if rc != L.OK:
-            raise L.LspcaError(rc, "lspca_fit")
-
-    for _ in range(2):
-        step_gram()
-    torch.cuda.synchronize()
-    g0 = torch.cuda.Event(enable_timing=True)
-    g1 = torch.cuda.Event(enable_timing=True)
-    ngr = max(3, min(args.steps, 10))
-    g0.record(stream)
-    for _ in range(ngr):
-        step_gram()
-    g1.record(stream)
-    torch.cuda.synchronize()
-    gram_ms = g0.elapsed_time(g1) / ngr
-    del G
-
-    # ---- SPCA comparison path (same workload, same launch configuration)
-    for _ in range(2):
-        step(L.spca_fit)
-    torch.cuda.synchronize()
-    s0 = torch.cuda.Event(enable_timing=True)
-    s1 = torch.cuda.Event(enable_timing=True)
-    nsp = max(3, min(args.steps, 10))
-    s0.record(stream)
-    for _ in range(nsp):
-        step(L.spca_fit)
-    s1.record(stream)
-    torch.cuda.synchronize()
-    spca_ms = s0.elapsed_time(s1) / nsp
-
-    # ---- the reduction map Y = X V (Sec. III-B.2) of the fitted V over the same X
-    Y = torch.empty(w.m, w.k, dtype=torch.float32, device=X.device)
-
-    def proj():
-        rc = L.lspca_project(ctx.handle, X, V, w.k, Y, stream)
-        if rc != L.OK:
-            raise L.LspcaError(rc, "lspca_project")
-
-    for _ in range(3):
-        proj()
-    torch.cuda.synchronize()
-    p0 = torch.cuda.Event(enable_timing=True)
-    p1 = torch.cuda.Event(enable_timing=True)
-    npj = max(3, min(args.steps, 10))
-    p0.record(stream)
-    for _ in range(npj):
-        proj()
-    p1.record(stream)
-    torch.cuda.synchronize()
-    proj_ms = p0.elapsed_time(p1) / npj
-    del Y
-
-    # ---- a sparse X in CSR form, the shape of the paper's TF-IDF experiment
-    sparse = None
-    if rank == 0:
-        try:
-            sw_ = S.SPARSE_TFIDF
-            rp_, c_, v_ = (t.to(X.device) for t in S.sparse_csr(sw_["m"], sw_["n"], sw_["density"], sw_["seed"]))
-            om_s = L.omega("sparse", sw_["omega_seed"], sw_["p"])
-            for _ in range(2):
-                ctx.fit_csr(rp_, c_, v_, sw_["n"], sw_["k"], om_s, report=False)
-            torch.cuda.synchronize()
-            q0 = torch.cuda.Event(enable_timing=True)
-            q1 = torch.cuda.Event(enable_timing=True)
-            q0.record(stream)
-            for _ in range(5):
-                ctx.fit_csr(rp_, c_, v_, sw_["n"], sw_["k"], om_s, report=False, stream=stream)
-            q1.record(stream)
-            torch.cuda.synchronize()
-            sms = q0.elapsed_time(q1) / 5
-            sparse = {"workload": f"CSR {sw_['m']}x{sw_['n']} density {sw_['density']} nnz {v_.numel()} "
-                                  f"k={sw_['k']} very sparse p={sw_['p']}",
-                      "ms_per_fit": sms, "samples_per_s": sw_["m"] / (sms / 1e3),
-                      "nnz_per_s": v_.numel() / (sms / 1e3), "api": "lspca_fit_csr"}
-            del rp_, c_, v_
-        except Exception as e:  # the fit line above stands on its own
-            sparse = {"error": f"{type(e).__name__}: {e}"}
-
-    # ---- end to end through the public API: a host-resident (pinned) X, fitted
-    # by lspca_fit_host (row slices copied to the device while the previous
-    # slice is computed, Algorithm 4), V and sigma copied back
-    Xh = torch.empty(X.shape, dtype=X.dtype, pin_memory=True)
-    Xh.copy_(X)
-    Vh = torch.empty(V.shape, dtype=V.dtype, pin_memory=True)
-    sh = torch.empty(sigma.shape, dtype=sigma.dtype, pin_memory=True)
-    ne2e = max(3, min(args.steps, 5))
-
-    def e2e_step():
-        rc = L.lspca_fit_host(ctx.handle, Xh, w.k, om, 0, 0, V, sigma, rk, stream)
-        if rc != L.OK:
-            raise L.LspcaError(rc, "lspca_fit_host")
-        Vh.copy_(V, non_blocking=True)
-        sh.copy_(sigma, non_blocking=True)
-
-    # the host -> device copy floor of this node: one plain copy of the same bytes
-    X.copy_(Xh, non_blocking=True)
-    torch.cuda.synchronize()
-    c0 = torch.cuda.Event(enable_timing=True)
-    c1 = torch.cuda.Event(enable_timing=True)
-    c0.record(stream)
-    X.copy_(Xh, non_blocking=True)
-    c1.record(stream)
-    torch.cuda.synchronize()
-    h2d_ms = c0.elapsed_time(c1)
-
-    e2e_step()
-    torch.cuda.synchronize()
-    barrier()
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
-    t0.record(stream)
-    for _ in range(ne2e):
-        e2e_step()
-    t1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = t0.elapsed_time(t1) / ne2e
-    if dist is not None:
-        t = torch.tensor([e2e_ms], device=X.device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-
-    # ---- roofline of the dominant kernel
-    names = ["omega", "sketch", "chain_main", "chain_reduce", "qr", "small", "total"]
-    per = {nm: pass_ms[i] / max(calls, 1) for i, nm in enumerate(names)}
-    x_bytes = w.m * w.n * 4
-    u_bytes = w.m * w.k * 4
-    alg = {"sketch": x_bytes + u_bytes, "chain_main": x_bytes + u_bytes}
-    dom = max(alg, key=lambda nm: per[nm])
-    peak, peak_kind = _peaks()
-    achieved = alg[dom] / (per[dom] / 1e3) / 1e9
-    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "peak_kind": peak_kind,
-            "traffic": (TRAFFIC_PER_ROW[dom] * w.m if TRAFFIC_PER_ROW.get(dom) else None),
-            "bytes_per_launch": alg[dom], "ms_per_launch": per[dom]}
-
+    head, V, sigma = measure_headline(L, S, torch, w, X, ctx, stream, args, dist, pk, ws)
+    value = w.m * ws / (head["ms"] / 1e3)
     line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"{WORKLOAD} {w.m}x{w.n} k={w.k} very sparse p={w.p}", "m": w.m, "n": w.n,
-                       "k": w.k, "x_bytes": x_bytes, "l2": "inputs larger than L2 (no flush)"},
-            "roofline": roof,
-            "fit_roofline_frac": {"lazy": (x_bytes / (peak * 1e9)) / (ms_step / 1e3),
-                                  "spca": (x_bytes / (peak * 1e9)) / (spca_ms / 1e3)},
-            "spca": {"ms_per_step": spca_ms, "samples_per_s": w.m * ws / (spca_ms / 1e3),
-                     "lazy_speedup": spca_ms / ms_step},
-            "passes_ms": per,
-            "gram": {"ms_per_step_on": gram_ms, "ms_per_step_off": ms_step,
-                     "note": "the same fit with the optional G = U^T U output (LSPCA_WANT_GRAM) on and off"},
-            "project": {"ms_per_call": proj_ms, "samples_per_s": w.m / (proj_ms / 1e3),
-                        "achieved_gbs": (x_bytes + u_bytes) / (proj_ms / 1e3) / 1e9,
-                        "frac": (x_bytes + u_bytes) / (proj_ms / 1e3) / 1e9 / peak,
-                        "bytes_per_call": x_bytes + u_bytes, "kernel": "tmem_a_kernel (FP32 X and V in three exact BF16 pieces, k=128)"},
-            "e2e": {"value": w.m * ws / (e2e_ms / 1e3), "unit": "samples/s",
-                    "h2d_bytes_per_step": x_bytes, "d2h_bytes_per_step": w.n * w.k * 4 + w.k * 8,
-                    "ms_per_step": e2e_ms, "api": "lspca_fit_host (pinned host X, row slices overlapped)",
-                    "h2d_copy_ms": h2d_ms, "h2d_copy_gbs": x_bytes / (h2d_ms / 1e3) / 1e9},
-            "sparse": sparse,
-            "gpu_launches": launches,
-            "clocks": clk}
-    if rank == 0 and args.serve_seconds > 0:
-        del Xh
-        X = None
+            "warmup": args.warmup, "ms_per_step": head["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "e4m3", "data": "synthetic",
+            "config": {"workload": f"{WORKLOAD} {w.m}x{w.n} k={w.k} very sparse p={w.p}: fit + reduction map of "
+                                   f"all rows" + (f", rows sharded over {ws} ranks (one NCCL exchange of F)"
+                                                  if ws > 1 else ""),
+                       "m": w.m * ws, "n": w.n, "k": w.k, "x_bytes": w.m * w.n * ws,
+                       "l2": "inputs larger than L2 (no flush)"},
+            "roofline": head.get("roofline"), "kernels": head.get("kernels"), "passes_ms": head.get("passes_ms"),
+            "dominant_kernel": head.get("dominant"), "project_ms": head["project_ms"],
+            "gpu_launches": head["launches"], "clocks": head["clocks"], "fit_rank": head["rank"]}
+    if rank == 0 and ws == 1:
+        if not args.quick:
+            om = L.omega("sparse", w.omega_seed, w.p)
+            lazy_ms = head["passes_ms"]["total"]
+            line["spca"] = measure_spca(L, torch, w, X, ctx, stream, om, V, lazy_ms, 3)
+            line["e2e"] = measure_e2e(L, torch, w, X, ctx, stream, 3)
+        ctx.close()
+        del X, V, sigma
         torch.cuda.empty_cache()
-        try:
-            line["serve"] = serve_bench(L, S, torch, local, args.serve_seconds)
-        except Exception as e:  # the fit line above stands on its own
-            line["serve"] = {"error": f"{type(e).__name__}: {e}"}
-    if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.cpu_rows, args.cpu_seconds)
+        if not args.quick:
+            for key, name, m, extra in (("bf16_dense", "bf16_dense", None, {}),
+                                        ("fp32_sparse", "fp32_sparse", None, {"spca": True, "gram": True})):
+                try:
+                    line[key] = measure_form(L, S, torch, name, stream, local, pk, 5, m=m, **extra)
+                except Exception as e:  # the headline line stands on its own
+                    line[key] = {"error": f"{type(e).__name__}: {e}"}
+            line["kxk"] = measure_kxk(L, torch, local, stream)
+            try:
+                line["sparse"] = measure_sparse(L, S, torch, local, stream)
+            except Exception as e:
+                line["sparse"] = {"error": f"{type(e).__name__}: {e}"}
+            if args.serve_seconds > 0:
+                try:
+                    line["serve"] = serve_bench(L, S, torch, local, args.serve_seconds)
+                except Exception as e:
+                    line["serve"] = {"error": f"{type(e).__name__}: {e}"}
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(args.cpu_rows, args.cpu_seconds)
+    else:
+        ctx.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
-    ctx.close()
     if dist is not None:
         dist.destroy_process_group()
 
 
-def main():
+
+
+def launch_ranks(n: int, argv: list) -> int:
+    """Start n ranks of this script on this node (torch.distributed.run, one
+    process per GPU, rendezvous on 127.0.0.1) and return their exit status."""
+    import socket
+    sk = socket.socket()
+    sk.bind(("127.0.0.1", 0))
+    port = sk.getsockname()[1]
+    sk.close()
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}",
+           "--master-addr=127.0.0.1", f"--master-port={port}", os.path.abspath(__file__), *argv]
+    return subprocess.call(cmd)
+
+
+def main(argv=None):
+    argv = sys.argv[1:] if argv is None else argv
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--m", type=int, default=0, help="override the row count (smaller runs)")
-    ap.add_argument("--cpu-rows", type=int, default=50_000)
+    ap.add_argument("--m", type=int, default=0, help="override the rows per rank (smaller runs)")
+    ap.add_argument("--cpu-rows", type=int, default=20_000)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--ref-rows", type=int, default=20_000)
+    ap.add_argument("--ref-rows", type=int, default=2_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="the headline line only (no extra keys)")
     ap.add_argument("--serve-seconds", type=float, default=5.0, help="serving run length (0 = skip)")
-    args = ap.parse_args()
+    args = ap.parse_args(argv)
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        sys.exit(launch_ranks(args.gpus, argv))
     if args.impl == "reference":
         run_reference(args)
     else:

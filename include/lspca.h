@@ -59,7 +59,7 @@ typedef enum {
 /* Element type of X (and the arithmetic the passes run in). */
 typedef enum {
   LSPCA_F64 = 0,   /* FP64 SIMT throughout                                          */
-  LSPCA_F32 = 1,   /* FP32 X; U in FP32; F on tensor cores with split-FP16 products */
+  LSPCA_F32 = 1,   /* FP32 X; U in FP32; tensor-core products of exact 16-bit pieces */
   LSPCA_BF16 = 2,  /* BF16 X; BF16 tensor cores, split-BF16 U for F                 */
   LSPCA_E4M3 = 3   /* FP8 E4M3 X (binary features); needs very sparse Omega         */
 } lspca_dtype;
@@ -228,8 +228,10 @@ int lspca_fit_host(lspca_ctx* ctx, const void* Xh, int32_t xt, int64_t m, int64_
 
 /* Reduction map pi(x) = V^T x for every row: Y = X V (Sec. III-B.2).
  * X [dev] m x n (xt, ldx); V [dev] n x k and Y [dev] m x k (output), both
- * in the result type.  F32 X runs split-FP16 tensor-core products (X and V
- * split into hi + lo parts), BF16/E4M3 X split-BF16 V, F64 X FP64 SIMT.
+ * in the result type.  F32 X, k <= 128: X and V each split into three exact
+ * BF16 pieces (x = x0 + x1 + x2), the six products x_a v_b with a + b <= 2;
+ * F32 X, k > 128: FP16 pairs (hi + lo, power-of-two scales), three products;
+ * BF16/E4M3 X: V split into a BF16 pair, two products; F64 X: FP64 SIMT.
  * 1 <= k <= 256.
  * Errors: LSPCA_ERR_INVALID, LSPCA_ERR_NOMEM, LSPCA_ERR_CUDA.               */
 int lspca_project(lspca_ctx* ctx, const void* X, int32_t xt, int64_t m, int64_t n, int64_t ldx,
@@ -267,12 +269,15 @@ int lspca_decompose(lspca_ctx* ctx, const double* F, int32_t k, int64_t n, int64
  * callers that may not allocate device memory, e.g. code running inside a
  * framework that owns all GPU memory through its own pool, or loops that
  * cannot afford the device synchronisation cudaMalloc/cudaFree imply).
- * Computes F = U^T X exactly as lspca_chain's tensor-core path (FP32 X:
- * split-FP16 products; BF16 X: split-BF16 U), without a context.
+ * Computes F = U^T X with the same split-product arithmetic as lspca_chain's
+ * tensor-core path (FP32 X: FP16 pairs; BF16 X: U as a BF16 pair) but in its
+ * own kernel and chunking, so the two agree within pass F's tolerance, not
+ * bit for bit; no context is needed.
  * X [dev] m x n, xt LSPCA_F32 or LSPCA_BF16; U [dev] m x k FP32 (ld k);
  * 4 <= k <= 256, k a multiple of 4; F [dev] k x n FP64 output;
  * status [dev] int32 output (nullable): zeroed, then the device status bits
- * (2 = a bounded wait inside the kernel gave up); stream as elsewhere.
+ * (1 = NaN or Inf in X, 2 = a bounded wait inside the kernel gave up);
+ * stream as elsewhere.
  * Scratch: a 16 MiB device array inside the library, held by every GPU that
  * loads the library until the process exits; k * n * 4 bytes of it must hold
  * one chunk's partial sums (k * n <= 4,194,240), else LSPCA_ERR_NOMEM.  The
@@ -326,6 +331,30 @@ int lspca_srv_poll(lspca_srv* srv, int64_t req, int32_t* done);
 int lspca_srv_wait(lspca_srv* srv, int64_t req, int32_t timeout_ms);
 int lspca_srv_release(lspca_srv* srv, int64_t req);
 int64_t lspca_srv_launch_count(lspca_srv* srv);
+
+/* Fixed-order sum of gathered partials, the exchange of a row-sharded fit
+ * (Algorithm 4's F = sum_s U_s^T X_s with the slices spread over ranks, and
+ * likewise G = sum_s U_s^T U_s): out[e] = (((p_0[e] + p_1[e]) + p_2[e]) + ...)
+ * in FP64, p_q[e] = parts[q * count + e].  Every rank that calls it on the
+ * same gathered parts holds the same bits, whatever order the collective used.
+ * parts [dev] nparts x count FP64; out [dev] count FP64 (may not overlap parts).
+ * Errors: LSPCA_ERR_INVALID (NULL pointers, nparts < 1, count < 0),
+ * LSPCA_ERR_CUDA.                                                          */
+int lspca_sum_partials(lspca_ctx* ctx, const double* parts, int32_t nparts, int64_t count, double* out,
+                       void* stream);
+
+/* The failure path of the device waits, run on purpose: one CTA waits, with
+ * the time-limited mbarrier wait every tensor-core pipeline uses, on a barrier
+ * that no thread arrives at.  After limit_ns nanoseconds (%globaltimer) the
+ * wait gives up, sets the timeout bit of the context's status word and raises
+ * the CTA's abort flag; the CTA's other warps leave their polling loops and
+ * the kernel ends normally, as a pipeline's roles do.  The next
+ * lspca_sync_status returns LSPCA_ERR_TIMEOUT and the context stays usable.
+ * Not in the paper: it tests the library's error handling.
+ * waited_ns [dev, nullable] int64 output: how long the wait lasted.
+ * Errors: LSPCA_ERR_INVALID (NULL ctx, limit_ns outside [1e3, 2e9]),
+ * LSPCA_ERR_CUDA.                                                          */
+int lspca_wait_probe(lspca_ctx* ctx, int64_t limit_ns, int64_t* waited_ns, void* stream);
 
 /* Synchronise `stream`, return and clear the device status word:
  * LSPCA_OK, LSPCA_ERR_NUMERIC or LSPCA_ERR_TIMEOUT.                         */

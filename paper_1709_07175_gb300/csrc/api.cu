@@ -719,6 +719,16 @@ int lspca_sketch(lspca_ctx* ctx, const void* X, int32_t xt, int64_t m, int64_t n
   return cuda_status(cudaGetLastError());
 }
 
+int lspca_sum_partials(lspca_ctx* ctx, const double* parts, int32_t nparts, int64_t count, double* out,
+                       void* stream) {
+  if (!ctx || !parts || !out || nparts < 1 || count < 0) return LSPCA_ERR_INVALID;
+  if (count == 0) return LSPCA_OK;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return LSPCA_ERR_CUDA;
+  Launcher L{(cudaStream_t)stream, &ctx->launches, ctx->num_sms};
+  launch_reduce_splits(L, parts, nparts, count, count, out);
+  return cuda_status(cudaGetLastError());
+}
+
 int lspca_chain(lspca_ctx* ctx, const void* X, int32_t xt, int64_t m, int64_t n, int64_t ldx, const void* U, int32_t k,
                 uint32_t flags, double* F, double* G, void* stream) {
   if (!ctx) return LSPCA_ERR_INVALID;
@@ -766,6 +776,14 @@ int lspca_decompose(lspca_ctx* ctx, const double* F, int32_t k, int64_t n, int64
   SmallWs sw;
   carve_small_ws(sw, ctx->ws, k, n);
   launch_decompose(L, sw, F, k, n, m, vt == LSPCA_F64, V, sigma, rank ? rank : ctx->d_rank, ctx->d_status);
+  return cuda_status(cudaGetLastError());
+}
+
+int lspca_wait_probe(lspca_ctx* ctx, int64_t limit_ns, int64_t* waited_ns, void* stream) {
+  if (!ctx || limit_ns < 1000 || limit_ns > 2000000000ll) return LSPCA_ERR_INVALID;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return LSPCA_ERR_CUDA;
+  Launcher L{(cudaStream_t)stream, &ctx->launches, ctx->num_sms};
+  launch_wait_probe(L, (uint64_t)limit_ns, ctx->d_status, waited_ns);
   return cuda_status(cudaGetLastError());
 }
 

@@ -138,4 +138,7 @@ void launch_tsqr(Launcher& L, const void* U, bool u_f64, int64_t m, int k, void*
 // F <- R^-T F in place (F k x n FP64).
 void launch_trsm_rt(Launcher& L, const double* R, int k, double* F, int64_t n);
 
+// The bounded-wait failure path on a barrier that never completes (waitprobe.cu).
+void launch_wait_probe(Launcher& L, uint64_t limit_ns, int* status, int64_t* waited_ns);
+
 }  // namespace lspca

@@ -38,7 +38,6 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_addr[kMaxDevices] = {};
 int g_sms[kMaxDevices] = {};
-int64_t g_launches = 0;
 
 // Device address of the scratch array on the current device (set up once).
 int scratch_address(int dev, void** out, int* sms) {
@@ -85,7 +84,8 @@ extern "C" int lspca_chain_noalloc(const void* X, int32_t xt, int64_t m, int64_t
   int st = scratch_address(dev, &base, &sms);
   if (st) return st;
   cudaStream_t s = (cudaStream_t)stream;
-  Launcher L{s, &g_launches, sms};
+  int64_t launches = 0;  // per call: nothing reads it, and calls may come from several threads
+  Launcher L{s, &launches, sms};
 
   float* absmax = reinterpret_cast<float*>(base);
   int* dstatus = status ? reinterpret_cast<int*>(status) : reinterpret_cast<int*>((char*)base + 64);
@@ -107,10 +107,9 @@ extern "C" int lspca_chain_noalloc(const void* X, int32_t xt, int64_t m, int64_t
 
   if (cudaMemsetAsync(base, 0, 64, s) != cudaSuccess) return LSPCA_ERR_CUDA;
   if (cudaMemsetAsync(dstatus, 0, sizeof(int), s) != cudaSuccess) return LSPCA_ERR_CUDA;
-  if (xt == LSPCA_F32) {
-    launch_scan_x(L, X, xt, m, n, ldx, absmax, dstatus);
-    launch_scan_x(L, U, LSPCA_F32, m, k, k, absmax + 1, dstatus);
-  }
+  // max|X| (the FP16 scale for FP32 X) and the non-finite check of X, as lspca_chain does
+  launch_scan_x(L, X, xt, m, n, ldx, absmax, dstatus);
+  if (xt == LSPCA_F32) launch_scan_x(L, U, LSPCA_F32, m, k, k, absmax + 1, dstatus);
   tc_chain_inline_main(L, X, xt, m, n, ldx, U, k, w, absmax, dstatus, false);
   tc_chain_reduce(L, n, k, w, F, nullptr);
   return cudaGetLastError() == cudaSuccess ? LSPCA_OK : LSPCA_ERR_CUDA;

@@ -79,6 +79,8 @@ _SIGS = {
     "lspca_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "lspca_launch_count": (ctypes.c_int64, [_P]),
     "lspca_chain_noalloc": (ctypes.c_int, [_P, _I32, _I64, _I64, _I64, _P, _I32, _P, _P, _P]),
+    "lspca_sum_partials": (ctypes.c_int, [_P, _P, _I32, _I64, _P, _P]),
+    "lspca_wait_probe": (ctypes.c_int, [_P, _I64, _P, _P]),
     "lspca_srv_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, _SZ, _I32]),
     "lspca_srv_destroy": (ctypes.c_int, [_P]),
     "lspca_srv_register_v": (ctypes.c_int, [_P, _P, _I64, _I32, ctypes.POINTER(_I32)]),
@@ -233,6 +235,16 @@ def lspca_chain(ctx, X, U, k, flags, F, G=None, stream=None) -> int:
 def lspca_chain_noalloc(X, U, k, F, status=None, stream=None) -> int:
     x, xt, m, n, ldx = _xargs(X)
     return load().lspca_chain_noalloc(x, xt, m, n, ldx, _ptr(U), k, _ptr(F), _ptr(status), _stream(stream))
+
+
+def lspca_sum_partials(ctx, parts, out, stream=None) -> int:
+    """parts: (nparts, ...) FP64 CUDA tensor; out: FP64 CUDA tensor of one part's shape."""
+    return load().lspca_sum_partials(ctx, _ptr(parts), parts.shape[0], out.numel(), _ptr(out), _stream(stream))
+
+
+def lspca_wait_probe(ctx, limit_ns, waited_ns=None, stream=None) -> int:
+    """waited_ns: optional int64 CUDA tensor of one element."""
+    return load().lspca_wait_probe(ctx, int(limit_ns), _ptr(waited_ns), _stream(stream))
 
 
 def lspca_decompose(ctx, F, k, n, m, vt, V, sigma, rank=None, stream=None) -> int:

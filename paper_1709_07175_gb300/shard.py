@@ -34,12 +34,13 @@ def ordered_sum(parts: list[torch.Tensor]) -> torch.Tensor:
     return acc
 
 
-def reduce_partials(F: torch.Tensor, G: torch.Tensor | None = None, group=None) -> tuple:
+def reduce_partials(F: torch.Tensor, G: torch.Tensor | None = None, group=None, ctx=None) -> tuple:
     """Sum the per-rank partials F (k x n) and G (k x k) over the process group.
 
-    All-gathers the FP64 partials and adds them in rank order (``ordered_sum``),
-    so every rank ends with the same bits.  Without an initialised process
-    group this is the identity.
+    All-gathers the FP64 partials and adds them in rank order -- on CUDA
+    tensors in the library (lspca_sum_partials, with ``ctx``), on host tensors
+    with ``ordered_sum`` -- so every rank ends with the same bits.  Without an
+    initialised process group this is the identity.
     """
     import torch.distributed as dist
 
@@ -56,7 +57,18 @@ def reduce_partials(F: torch.Tensor, G: torch.Tensor | None = None, group=None) 
         t64 = t.to(torch.float64).contiguous()
         parts = [torch.empty_like(t64) for _ in range(ws)]
         dist.all_gather(parts, t64, group=group)
-        outs.append(ordered_sum(parts))
+        if t64.is_cuda:
+            gathered = torch.stack(parts)
+            if ctx is None:
+                raise ValueError("a CUDA exchange needs the library context")
+            from . import lspca as L
+            out = torch.empty_like(t64)
+            rc = L.lspca_sum_partials(ctx.handle, gathered, out)
+            if rc != L.OK:
+                raise L.LspcaError(rc, "lspca_sum_partials")
+            outs.append(out)
+        else:
+            outs.append(ordered_sum(parts))
     return outs[0], outs[1]
 
 
@@ -93,6 +105,6 @@ def sharded_fit(ctx, X_local: torch.Tensor, m_total: int, k: int, om, want_gram:
         Gs.append(G)
     F = ordered_sum(Fs)
     G = ordered_sum(Gs) if want_gram else None
-    F, G = reduce_partials(F, G, group)
+    F, G = reduce_partials(F, G, group, ctx)
     V, sigma, rank = ctx.decompose(F, m_total, vt=vt)
     return V, sigma, rank, F, G

@@ -24,7 +24,8 @@ Workloads (the sigma index i runs 1..r):
                    p = round(sqrt(n)) = 169.
 
 A and B are orthonormal (reduced QR of Gaussian draws, on the CPU in FP64 for
-every target device).  Rows of the noise are drawn in fixed chunks from
+every target device, except the left factor of more than 250,000 rows on a
+CUDA device: drawn and QR-factored there in FP32).  Rows of the noise are drawn in fixed chunks from
 per-chunk generators on the target device.
 """
 from __future__ import annotations
@@ -99,6 +100,10 @@ def _orthonormal(rows: int, r: int, gen: torch.Generator) -> torch.Tensor:
     return q
 
 
+# Above this many rows, a CUDA target draws the left factor A on the device.
+DEVICE_FACTOR_ROWS = 250_000
+
+
 def lowrank_plus_noise(w: Workload, device="cpu", chunk_rows: int = 65536,
                        out: torch.Tensor | None = None) -> torch.Tensor:
     """X = A diag(sigma) B^T + noise, rounded once to the storage dtype.
@@ -112,8 +117,17 @@ def lowrank_plus_noise(w: Workload, device="cpu", chunk_rows: int = 65536,
     work = torch.float64 if dev.type == "cpu" else torch.float32
     gen = torch.Generator()
     gen.manual_seed(int(w.data_seed) * 1_000_003 + 17)
-    A = _orthonormal(w.m, w.r, gen).to(device=dev, dtype=work)
-    B = _orthonormal(w.n, w.r, gen).to(device=dev, dtype=work)
+    if dev.type == "cuda" and w.m > DEVICE_FACTOR_ROWS:
+        # a CPU QR of an m x r FP64 factor takes minutes at this size: the left
+        # factor is drawn and orthonormalised on the device instead (FP32 QR;
+        # the same distribution, other draws than the CPU path's)
+        B = _orthonormal(w.n, w.r, gen).to(device=dev, dtype=work)
+        gd = torch.Generator(device=dev)
+        gd.manual_seed(int(w.data_seed) * 1_000_003 + 29)
+        A, _ = torch.linalg.qr(torch.randn(w.m, w.r, generator=gd, dtype=torch.float32, device=dev), mode="reduced")
+    else:
+        A = _orthonormal(w.m, w.r, gen).to(device=dev, dtype=work)
+        B = _orthonormal(w.n, w.r, gen).to(device=dev, dtype=work)
     sig = torch.as_tensor(w.sigmas(), dtype=work, device=dev)
     BS = (B * sig).T.contiguous()  # r x n
     X = out if out is not None else torch.empty(w.m, w.n, dtype=TORCH_DTYPES[w.dtype], device=dev)

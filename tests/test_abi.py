@@ -78,3 +78,13 @@ def test_csr_binding_checks_array_types():
     empty = L._csr_args(torch.zeros(4, dtype=torch.int64), torch.zeros(0, dtype=torch.int32),
                         torch.zeros(0, dtype=torch.float32))
     assert empty[1] is None and empty[2] is None and empty[3:] == (3, 0)
+
+
+def test_argument_checks_run_before_any_device_call(libpath):
+    """Entry points reject bad arguments with LSPCA_ERR_INVALID before touching
+    a device, so these calls are safe without a GPU."""
+    from paper_1709_07175_gb300 import lspca as L
+    lib = L.load(libpath)
+    assert lib.lspca_sum_partials(None, None, 2, 10, None, None) == L.ERR_INVALID
+    assert lib.lspca_wait_probe(None, 1000000, None, None) == L.ERR_INVALID
+    assert lib.lspca_chain_noalloc(None, L.LSPCA_F32, 10, 10, 10, None, 64, None, None, None) == L.ERR_INVALID

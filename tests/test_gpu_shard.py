@@ -54,3 +54,18 @@ def test_virtual_shards_match_oracle_and_unsharded(ctx, wname, m, n, k, shards, 
     assert M.max_sine(full.V.double().cpu().numpy(), V.double().cpu().numpy()) < 10 * tol
     s1, s2 = sig.cpu().numpy(), full.sigma.cpu().numpy()
     assert np.max(np.abs(s1 - s2) / s2) < tol
+
+
+@pytest.mark.parametrize("nparts,count", [(1, 7), (3, 20 * 500), (8, 256 * 4096 + 13)])
+def test_sum_partials_fixed_order(ctx, nparts, count):
+    """The library's exchange sum adds the gathered parts in rank order."""
+    g = torch.Generator().manual_seed(11 + nparts)
+    parts = torch.randn((nparts, count), generator=g, dtype=torch.float64) * torch.logspace(
+        0, 12, nparts, dtype=torch.float64)[:, None]
+    ref = parts[0].clone()
+    for q in range(1, nparts):
+        ref = ref + parts[q]
+    out = torch.empty(count, dtype=torch.float64, device="cuda")
+    assert L.lspca_sum_partials(ctx.handle, parts.cuda(), out) == L.OK
+    torch.cuda.synchronize()
+    assert torch.equal(out.cpu(), ref)

@@ -34,10 +34,15 @@ def ctx():
     c.close()
 
 
-@pytest.mark.parametrize("m,n,k", [(3001, 4096, 128), (20000, 1000, 64), (60000, 4096, 128)])
-def test_noalloc_chain_matches_regular_path(ctx, m, n, k):
+# FP32 and BF16 X, one and two M halves (k <= 128 and k = 256); (60000, 2048,
+# 256) plans 38 chunks of 2 MiB partials, more than the array holds, so the
+# chunk count is capped (7 chunks of 8,576 rows).
+@pytest.mark.parametrize("dt", [torch.float32, torch.bfloat16])
+@pytest.mark.parametrize("m,n,k", [(3001, 4096, 128), (20000, 1000, 64), (60000, 4096, 128),
+                                   (3001, 2048, 256), (60000, 2048, 256)])
+def test_noalloc_chain_matches_regular_path(ctx, dt, m, n, k):
     w = S.WORKLOADS["fp32_sparse"].scaled(m=m, n=n, k=k)
-    X = S.generate(w).cuda()
+    X = S.generate(w).cuda().to(dt)
     U = ctx.sketch(X, k, L.omega("sparse", 0, 64))
     F_ref, _ = ctx.chain(X, U)
     outs = []
@@ -65,3 +70,16 @@ def test_noalloc_rejects_oversized_and_bad_arguments(ctx):
     U2 = torch.zeros(64, 6, dtype=torch.float32, device="cuda")
     F2 = torch.empty(6, 32, dtype=torch.float64, device="cuda")
     assert L.lspca_chain_noalloc(X2, U2, 6, F2) == L.ERR_INVALID  # k not a multiple of 4
+
+
+@pytest.mark.parametrize("dt", [torch.float32, torch.bfloat16])
+def test_noalloc_flags_non_finite_x(ctx, dt):
+    """Status bit 1: a NaN in X is reported for FP32 and BF16 X alike."""
+    X = torch.ones(4000, 512, dtype=dt, device="cuda")
+    X[1234, 77] = float("nan")
+    U = torch.ones(4000, 64, dtype=torch.float32, device="cuda")
+    F = torch.empty(64, 512, dtype=torch.float64, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    assert L.lspca_chain_noalloc(X, U, 64, F, st) == L.OK
+    torch.cuda.synchronize()
+    assert int(st.item()) & 1
