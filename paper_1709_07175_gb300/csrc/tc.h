@@ -80,6 +80,14 @@ void tc_project_pretiled(Launcher& L, const void* X, int xt, int64_t m, int64_t 
 // One persistent launch over *d_count (<= max_tiles) table entries.
 void tc_project_batch(Launcher& L, int xt, int k, const TcProjUnit* d_units, const int* d_count, int max_tiles,
                       int* status);
+// Y = X V for BF16 or E4M3 X with X fed by TMA (xproj.cu).  vtiles: V split
+// and tiled by tile_v_kernel (BF16 X: BF16 pair, or the exact hi piece with
+// exact_v; E4M3 X: FP16 pair of V t with t at *vscale).  check_y: a non-finite
+// Y sets ST_NONFINITE.  False (nothing launched) when X's alignment or pitch
+// does not allow the tensor map.
+bool tc_xproj_ok(const void* X, int xt, int64_t ldx, bool exact_v);
+bool tc_xproj(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_t ldx, const void* vtiles,
+              const float* vscale, int k, bool exact_v, float* Y, int* status, float* ymax, bool check_y);
 void tc_project(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_t ldx, const float* V, int k,
                 TcProjectWs& w, float* Y, int* status, bool exact_v = false, float* xmax = nullptr,
                 float* ymax = nullptr);

@@ -1110,6 +1110,19 @@ void tc_project(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_
                 TcProjectWs& w, float* Y, int* status, bool exact_v, float* xmax, float* ymax) {
   const int npad = (k + 63) / 64 * 64;
   float* scal = (float*)w.vlo;
+  if (tc_xproj_ok(X, xt, ldx, exact_v)) {
+    // BF16 / E4M3 X: the TMA-fed kernel; E4M3 takes V as an FP16 pair of V t
+    const bool f16 = xt == LSPCA_E4M3;
+    cudaMemsetAsync(scal, 0, 8, L.stream);
+    if (f16) launch_scan_x(L, V, LSPCA_F32, n, k, k, scal, status);
+    const int64_t nks = (n + tcp::BK - 1) / tcp::BK;
+    const int64_t total = nks * tcp::BK * npad;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 16 * L.num_sms) blocks = 16 * L.num_sms;
+    tcp::tile_v_kernel<<<blocks, 256, 0, L.stream>>>(V, n, k, npad, f16 ? 1 : 0, scal, scal + 1, (uint8_t*)w.vhi);
+    L.count(1);
+    if (tc_xproj(L, X, xt, m, n, ldx, w.vhi, scal + 1, k, exact_v, Y, status, ymax, xmax != nullptr)) return;
+  }
   {
     // FP32 X against a general V, k <= 128: V in three exact BF16 pieces, A in TMEM
     tcp::Params p{};

@@ -450,12 +450,18 @@ def test_alg4_slicing_invariance(ctx, data):
                                          ("f32", 64, 1100, 1000), ("f32", 100, 515, 2040), ("f32", 128, 1, 1000),
                                          ("f32", 64, 77, 4096),
                                          ("bf16", 64, 2049, 1024), ("bf16", 256, 513, 2048),
-                                         ("e4m3", 256, 1500, 4096), ("e4m3", 128, 4001, 1040)])
+                                         ("bf16", 192, 1000, 1984), ("bf16", 1, 129, 512), ("bf16", 33, 1, 576),
+                                         ("bf16", 128, 300, 1000),
+                                         ("e4m3", 256, 1500, 4096), ("e4m3", 128, 4001, 1040),
+                                         ("e4m3", 64, 700, 960), ("e4m3", 200, 257, 2112), ("e4m3", 17, 1, 64),
+                                         ("e4m3", 96, 333, 1008)])
 def test_project_tensor_core_paths(ctx, dtype, k, m, n):
     """Y = X V against the FP64 product of the same stored values (relative Frobenius):
     FP32 X 2e-6 (k <= 128 with n a multiple of 8: X and V in three exact BF16
     pieces each, six products, A in tensor memory; otherwise split-FP16 with
-    per-row scales); BF16 / E4M3 X with split-BF16 V 1e-5."""
+    per-row scales); BF16 X with split-BF16 V 1e-5; E4M3 X (its pitch a
+    multiple of 16 bytes by the library's contract) widened exactly to FP16
+    against V as an FP16 pair of 22 bits, 2e-6."""
     if dtype == "e4m3":
         w = S.WORKLOADS["e4m3_binary"].scaled(m=m, n=n, k=k)
     elif dtype == "bf16":
@@ -469,7 +475,9 @@ def test_project_tensor_core_paths(ctx, dtype, k, m, n):
     Y = ctx.project(X.cuda(), V32.cuda()).double().cpu().numpy()
     Yref = X.double().numpy() @ V32.double().numpy()
     err = np.linalg.norm(Y - Yref) / np.linalg.norm(Yref)
-    assert err < (2e-6 if dtype == "f32" else 1e-5), err
+    tol = 1e-5 if dtype == "bf16" else 2e-6
+    print(f"project {dtype} k={k} m={m} n={n}: rel err {err:.2e}")
+    assert err < tol, err
 
 
 # ------------------------------------------------------------------ BF16 and FP8 (binary) workloads
