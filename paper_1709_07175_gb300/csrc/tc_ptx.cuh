@@ -96,6 +96,32 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
       : "memory");
 }
 
+// Bulk copy global -> shared multicast to the CTAs of the cluster in
+// cta_mask: the data lands at offset dst, and complete_tx is counted on the
+// mbarrier at offset bar, in each of those CTAs (dst, bar: this CTA's shared
+// addresses, the same offsets everywhere).
+__device__ __forceinline__ void bulk_g2s_mc(uint32_t dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                            uint16_t cta_mask) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1], %2, [%3], "
+      "%4;" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "h"(cta_mask)
+      : "memory");
+}
+
+// This CTA's rank in its cluster.
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+// All threads of all CTAs of the cluster (release / acquire at cluster scope).
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 // Tiled tensor copy global -> shared of one box of a 2-D tensor map at
 // (x = innermost coordinate, y), completion counted in bytes on `bar`.  x times
 // the element size must be a multiple of 16 bytes.
@@ -154,6 +180,16 @@ __device__ __forceinline__ void mma_f16_ts(uint32_t d_tmem, uint32_t a_tmem, uin
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
+}
+
+// Arrive once on the mbarrier at offset `bar` in each CTA of cta_mask when
+// all previously issued tcgen05.mma of this thread complete.
+__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t cta_mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"(cta_mask)
+      : "memory");
 }
 
 // 32 consecutive 32-bit TMEM columns of this thread's lane (32x32b shape, x32).
@@ -257,6 +293,17 @@ __device__ __forceinline__ void tmem_st16_nowait(uint32_t taddr, uint32_t (&r)[1
 }
 __device__ __forceinline__ void tmem_wait_st(uint32_t (&r)[16]) {
   asm volatile("tcgen05.wait::st.sync.aligned;" : LSPCA_R16(r)::"memory");
+}
+
+// Store 16 TMEM columns from r[0..15] without waiting (r must stay unchanged
+// until a tcgen05.wait::st).
+__device__ __forceinline__ void tmem_st16_from(uint32_t taddr, const uint32_t* r) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%16], "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15};" ::"r"(r[0]),
+      "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]), "r"(r[10]),
+      "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(taddr)
+      : "memory");
 }
 
 // 8 consecutive 32-bit TMEM columns of this thread's lane (32x32b shape, x8).

@@ -28,8 +28,16 @@
 // writing S as the rows of Y after the last segment.  For NPAD <= 128 two
 // accumulators alternate, so the tensor core runs on while a fold is read.
 //
+// CTA pairs.  The kernel runs in clusters of two CTAs on neighbouring SMs
+// that take consecutive row tiles and share every V stage: each CTA fetches
+// half of the stage and multicasts it into both (cp.async.bulk
+// .multicast::cluster), and each MMA thread signals the stage free in both
+// CTAs (tcgen05.commit .multicast::cluster), so every SM pulls half as much V
+// out of L2 and its TMA unit issues half the copies.  Both CTAs walk K in the
+// same order, rotated per pair.
+//
 // Roles (one persistent CTA per SM):
-//   warps 0..CW-1       converters (E4M3 only, CW = 4);
+//   warps 0..CW-1       converters (E4M3 only, CW = 2);
 //   warps CW..CW+7      epilogue: two per TMEM lane quarter (the quarter is
 //                       the warp index mod 4), each folding half the columns;
 //   warp  CW+8          TMEM allocation and the thread that issues tcgen05.mma;
@@ -75,9 +83,16 @@ struct Cfg {
   static constexpr int NPAD = 64 * NT;
   static constexpr int PB = EXACT_V ? 1 : 2;                 // V pieces
   static constexpr uint32_t B_BYTES = BK * NPAD * 2;         // one piece of one k-step
-  static constexpr uint32_t B_STAGE = PB * B_BYTES;
   static constexpr uint32_t SBO_B = NT * 1024;
-  static constexpr int CW = E4M3 ? 4 : 0;                    // converter warps
+  // V arrives in stages of B_SUB K-slices (16 K-rows each) of every piece, at
+  // least 32 KB a stage: small stages keep more of V in flight per byte of ring
+  static constexpr uint32_t SLICE = 2 * SBO_B;               // one K-slice of one piece
+  static constexpr int B_SUB0 = (int)(32768 / (PB * SLICE));
+  static constexpr int B_SUB = B_SUB0 < 1 ? 1 : (B_SUB0 > 4 ? 4 : B_SUB0);
+  static constexpr int SUBS = (BK / 16) / B_SUB;              // V stages per k-step
+  static constexpr uint32_t B_PART = B_SUB * SLICE;           // one piece of one stage
+  static constexpr uint32_t B_STAGE = PB * B_PART;
+  static constexpr int CW = E4M3 ? 2 : 0;                    // converter warps
   static constexpr int EPI0 = CW;
   static constexpr int EW = 8;                               // epilogue warps
   static constexpr int MMA_W = CW + EW;
@@ -86,15 +101,20 @@ struct Cfg {
   // rings: E4M3 raw boxes (two k-steps each), A tiles and V tiles (one k-step each)
   static constexpr int R_STAGES = E4M3 ? 2 : 0;
   static constexpr int A_STAGES = E4M3 ? 3 : 4;
+  static constexpr int CWX = CW > 0 ? CW : 1;               // divisors for the converter code,
+  static constexpr int RSX = R_STAGES > 0 ? R_STAGES : 1;   // which BF16 instances never run
   static constexpr uint32_t FIXED = R_STAGES * RAW_BYTES + A_STAGES * A_BYTES;
   static constexpr int B_STAGES_FIT = (int)((kSmemBudget - FIXED) / B_STAGE);
-  static constexpr int B_STAGES = B_STAGES_FIT > 4 ? 4 : B_STAGES_FIT;
+  static constexpr int B_STAGES = B_STAGES_FIT > 8 ? 8 : B_STAGES_FIT;
   static constexpr int NACC = NPAD <= 128 ? 2 : 1;
   static constexpr uint32_t S_COL = NACC * NPAD;
   static constexpr uint32_t TMEM_COLS = S_COL + NPAD <= 256 ? 256 : 512;
   static constexpr int WCOLS = NPAD / 2;                     // columns folded per epilogue warp
+  static constexpr int NCH = WCOLS / 32;
   static constexpr size_t SMEM = 1024 + (size_t)FIXED + (size_t)B_STAGES * B_STAGE + 512;
   static_assert(B_STAGES >= 2, "shared-memory budget");
+  static_assert(R_STAGES <= 4 && A_STAGES <= 4 && B_STAGES <= 8, "barrier slots");
+  static_assert(SUBS * B_SUB == BK / 16, "V stages tile the k-step");
   static_assert(S_COL + NPAD <= 512, "TMEM budget");
   static_assert(WCOLS % 32 == 0, "fold chunks of 32 columns");
 };
@@ -115,16 +135,28 @@ __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volati
   return __all_sync(0xffffffffu, ok);
 }
 
+// The X box (and its V tiles) that tile t takes j-th: every tile walks K in
+// its own rotation, so the CTAs, which hold consecutive tiles, read different
+// V tiles at any moment instead of all loading the same one from the same
+// L2 slices.  A row's result depends only on its tile.
+__device__ __forceinline__ int box_rotation(int64_t t, int nboxes) { return (int)(t % nboxes); }
+__device__ __forceinline__ int rotated_box(int rot, int j, int nboxes) {
+  const int b = j + rot;
+  return b >= nboxes ? b - nboxes : b;
+}
+
 // Four E4M3 bytes (K order, low byte first) -> two words of FP16 pairs, exact.
 __device__ __forceinline__ void e4m3x4_to_f16(uint32_t w, uint32_t& lo, uint32_t& hi) {
-  const __half2_raw a = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w & 0xffffu), __NV_E4M3);
-  const __half2_raw b = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w >> 16), __NV_E4M3);
-  lo = (uint32_t)a.x | ((uint32_t)a.y << 16);
-  hi = (uint32_t)b.x | ((uint32_t)b.y << 16);
+  asm("{\n\t.reg .b16 l, h;\n\t"
+      "mov.b32 {l, h}, %2;\n\t"
+      "cvt.rn.f16x2.e4m3x2 %0, l;\n\t"
+      "cvt.rn.f16x2.e4m3x2 %1, h;\n\t}"
+      : "=r"(lo), "=r"(hi)
+      : "r"(w));
 }
 
 template <bool E4M3, int NT, bool EXACT_V>
-__global__ void __launch_bounds__(Cfg<E4M3, NT, EXACT_V>::THREADS, 1)
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Cfg<E4M3, NT, EXACT_V>::THREADS, 1)
     xproj_kernel(const __grid_constant__ CUtensorMap tmx, Params p) {
   using C = Cfg<E4M3, NT, EXACT_V>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -134,12 +166,12 @@ __global__ void __launch_bounds__(Cfg<E4M3, NT, EXACT_V>::THREADS, 1)
   uint8_t* btile = atile + C::A_STAGES * A_BYTES;                // [B_STAGES][B_STAGE]
   uint64_t* bars = (uint64_t*)(btile + (size_t)C::B_STAGES * C::B_STAGE);
   uint64_t* rfull = bars;
-  uint64_t* rempty = rfull + 2;
-  uint64_t* afull = rempty + 2;
+  uint64_t* rempty = rfull + 4;
+  uint64_t* afull = rempty + 4;
   uint64_t* aempty = afull + 4;
   uint64_t* bfull = aempty + 4;
-  uint64_t* bempty = bfull + 4;
-  uint64_t* accf = bempty + 4;  // [NACC]
+  uint64_t* bempty = bfull + 8;
+  uint64_t* accf = bempty + 8;  // [NACC]
   uint64_t* acce = accf + 2;    // [NACC]
   uint64_t* drain = acce + 2;
   uint32_t* tslot = (uint32_t*)(drain + 1);
@@ -159,7 +191,7 @@ __global__ void __launch_bounds__(Cfg<E4M3, NT, EXACT_V>::THREADS, 1)
     }
     for (int s = 0; s < C::B_STAGES; ++s) {
       ptx::mbar_init(&bfull[s], 1);
-      ptx::mbar_init(&bempty[s], 1);
+      ptx::mbar_init(&bempty[s], 2);  // both CTAs of the pair have consumed the stage
     }
     for (int b = 0; b < C::NACC; ++b) {
       ptx::mbar_init(&accf[b], 1);
@@ -174,6 +206,13 @@ __global__ void __launch_bounds__(Cfg<E4M3, NT, EXACT_V>::THREADS, 1)
   __syncthreads();
   ptx::tc_fence_after();
   const uint32_t tmem = *tslot;
+  // the pair's barriers exist before either CTA multicasts into the other
+  ptx::cluster_sync();
+  // A CTA pair takes tiles t0 and t0 + 1 (t0 even); both run the same number
+  // of pair steps (a tile past the end is a phantom: TMA fills zeros, nothing
+  // is written) and walk K in the pair's rotation.
+  const int crank = (int)ptx::cluster_ctarank();
+  const int64_t t0_first = (int64_t)blockIdx.x - crank;
 
   if (warp == C::PROD_W) {
     // ------------------------------------------------------------ producer
@@ -186,46 +225,78 @@ __global__ void __launch_bounds__(Cfg<E4M3, NT, EXACT_V>::THREADS, 1)
       uint64_t* xf = E4M3 ? rfull : afull;
       uint64_t* xe = E4M3 ? rempty : aempty;
       uint8_t* xr = E4M3 ? raw : atile;
-      const int64_t mine = p.tiles > blockIdx.x ? (p.tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-      const int64_t xtot = mine * nboxes, btot = mine * nks;
-      int64_t xi = 0, bi = 0;
-      uint64_t t0 = ptx::globaltimer();
+      const int64_t mine = p.tiles > t0_first ? (p.tiles - 1 - t0_first) / gridDim.x + 1 : 0;
+      const int64_t xtot = mine * nboxes, btot = mine * nks * C::SUBS;
+      // cursors kept incrementally (no divisions in the issue loop)
+      int64_t xi = 0, bi = 0, xpair = t0_first, bpair = t0_first;
+      int xj = 0, xs = 0, bj = 0, bh = 0, bsub = 0, bs = 0;
+      int xrot = box_rotation(xpair >> 1, nboxes), brot = xrot;
+      uint32_t xph = 0, bph = 0;
+      uint64_t t0 = 0;  // start of the current run of polls without progress
       while (xi < xtot || bi < btot) {
         bool prog = false;
-        if (xi < xtot) {
-          const int s = (int)(xi % XS);
-          if (ptx::mbar_test_wait(&xe[s], (uint32_t)((xi / XS) & 1) ^ 1u)) {
-            const int64_t t = blockIdx.x + (xi / nboxes) * gridDim.x;
-            const int j = (int)(xi % nboxes);
-            ptx::mbar_arrive_expect_tx(&xf[s], XB);
-            ptx::tma_load_2d(ptx::smem_u32(xr + (size_t)s * XB), &tmx, j * (E4M3 ? 128 : BK), (int)(t * 128),
-                             &xf[s]);
-            ++xi;
-            prog = true;
+        if (xi < xtot && ptx::mbar_test_wait(&xe[xs], xph ^ 1u)) {
+          ptx::mbar_arrive_expect_tx(&xf[xs], XB);
+          const int xb = rotated_box(xrot, xj, nboxes);
+          ptx::tma_load_2d(ptx::smem_u32(xr + (size_t)xs * XB), &tmx, xb * (E4M3 ? 128 : BK),
+                           (int)((xpair + crank) * 128), &xf[xs]);
+          ++xi;
+          if (++xj == nboxes) {
+            xj = 0;
+            xpair += gridDim.x;
+            xrot = box_rotation(xpair >> 1, nboxes);
           }
+          if (++xs == XS) {
+            xs = 0;
+            xph ^= 1u;
+          }
+          prog = true;
         }
-        if (bi < btot) {
-          const int s = (int)(bi % C::B_STAGES);
-          if (ptx::mbar_test_wait(&bempty[s], (uint32_t)((bi / C::B_STAGES) & 1) ^ 1u)) {
-            const int ks = (int)(bi % nks);
-            ptx::mbar_arrive_expect_tx(&bfull[s], C::B_STAGE);
-            ptx::bulk_g2s(ptx::smem_u32(btile + (size_t)s * C::B_STAGE), p.vt + (size_t)ks * 2 * C::B_BYTES,
-                          C::B_STAGE, &bfull[s]);
-            ++bi;
-            prog = true;
+        if (bi < btot && ptx::mbar_test_wait(&bempty[bs], bph ^ 1u)) {
+          const int bb = rotated_box(brot, bj, nboxes);
+          const int bks = E4M3 ? 2 * bb + bh : bb;
+          // this CTA fetches its half of the stage (piece crank, or half the
+          // single piece) into both CTAs of the pair
+          constexpr uint32_t HALF = C::PB == 2 ? C::B_PART : C::B_PART / 2;
+          const uint8_t* src = p.vt + (size_t)bks * 2 * C::B_BYTES + (size_t)bsub * C::B_PART +
+                               (C::PB == 2 ? (size_t)crank * C::B_BYTES : (size_t)crank * HALF);
+          const uint32_t dst = ptx::smem_u32(btile + (size_t)bs * C::B_STAGE) + (uint32_t)crank * HALF;
+          ptx::mbar_arrive_expect_tx(&bfull[bs], C::B_STAGE);
+          ptx::bulk_g2s_mc(dst, src, HALF, &bfull[bs], (uint16_t)0x3);
+          ++bi;
+          if (++bsub == C::SUBS) {
+            bsub = 0;
+            // next k-step: the box's second half (E4M3, if it exists), else the next box
+            if (E4M3 && bh == 0 && 2 * bb + 1 < nks) {
+              bh = 1;
+            } else {
+              bh = 0;
+              if (++bj == nboxes) {
+                bj = 0;
+                bpair += gridDim.x;
+                brot = box_rotation(bpair >> 1, nboxes);
+              }
+            }
           }
+          if (++bs == C::B_STAGES) {
+            bs = 0;
+            bph ^= 1u;
+          }
+          prog = true;
         }
         if (prog) {
-          t0 = ptx::globaltimer();
-        } else {
-          if (*abort) break;
-          if (ptx::globaltimer() - t0 > kWaitNs) {
-            *abort = 1;
-            atomicOr(p.status, ST_TIMEOUT);
-            break;
-          }
-          __nanosleep(32);
+          t0 = 0;
+          continue;
         }
+        if (*abort) break;
+        const uint64_t now = ptx::globaltimer();
+        if (t0 == 0) t0 = now;
+        if (now - t0 > kWaitNs) {
+          *abort = 1;
+          atomicOr(p.status, ST_TIMEOUT);
+          break;
+        }
+        __nanosleep(20);
       }
       if (*abort) {  // copies in flight land before the CTA leaves
         for (int64_t q = xi - XS; q < xi; ++q)
@@ -239,20 +310,22 @@ __global__ void __launch_bounds__(Cfg<E4M3, NT, EXACT_V>::THREADS, 1)
     // ------------------------------------------------------------ converters
     // Half h of a box (K bytes 64h .. 64h + 63) becomes the FP16 A tile of
     // k-step 2j + h.  Thread (warp w, lane l) converts, in pass i, the 16-byte
-    // chunk c = 4h + (l & 3) of row r = 32 i + 8 w + (l >> 2) into the FP16
+    // chunk c = 4h + (l & 3) of row r = 8 CW i + 8 w + (l >> 2) into the FP16
     // chunks 2(l & 3) and 2(l & 3) + 1 of the tile.
     const int cq = lane & 3;
     int64_t ri = 0, ai = 0;
     bool ok = true;
-    for (int64_t t = blockIdx.x; t < p.tiles && ok; t += gridDim.x) {
+    for (int64_t t0 = t0_first; t0 < p.tiles && ok; t0 += gridDim.x) {
+      const int rot = box_rotation(t0 >> 1, nboxes);
       for (int j = 0; j < nboxes && ok; ++j, ++ri) {
-        const int rs = (int)(ri % C::R_STAGES);
-        if (!warp_wait(&rfull[rs], (uint32_t)((ri / C::R_STAGES) & 1), abort, p.status)) {
+        const int rs = (int)(ri % C::RSX);
+        if (!warp_wait(&rfull[rs], (uint32_t)((ri / C::RSX) & 1), abort, p.status)) {
           ok = false;
           break;
         }
         const uint32_t src = ptx::smem_u32(raw + (size_t)rs * RAW_BYTES);
-        for (int h = 0; h < 2 && 2 * j + h < nks; ++h, ++ai) {
+        const int jb = rotated_box(rot, j, nboxes);
+        for (int h = 0; h < 2 && 2 * jb + h < nks; ++h, ++ai) {
           const int as = (int)(ai % C::A_STAGES);
           if (!warp_wait(&aempty[as], (uint32_t)((ai / C::A_STAGES) & 1) ^ 1u, abort, p.status)) {
             ok = false;
@@ -261,8 +334,8 @@ __global__ void __launch_bounds__(Cfg<E4M3, NT, EXACT_V>::THREADS, 1)
           const uint32_t dst = ptx::smem_u32(atile + (size_t)as * A_BYTES);
           const uint32_t c = (uint32_t)(4 * h + cq), c0 = (uint32_t)(2 * cq);
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int r = 32 * i + 8 * warp + (lane >> 2);
+          for (int i = 0; i < 128 / (8 * C::CWX); ++i) {
+            const int r = 8 * C::CWX * i + 8 * warp + (lane >> 2);
             const uint32_t sw = (uint32_t)(r & 7);
             uint32_t w0, w1, w2, w3;
             asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
@@ -293,49 +366,62 @@ __global__ void __launch_bounds__(Cfg<E4M3, NT, EXACT_V>::THREADS, 1)
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       constexpr uint32_t idesc = ptx::idesc_f16(E4M3 ? 0 : 1, 128, C::NPAD, 0, 1);
-      int64_t ai = 0, bi = 0, seg = 0;
+      // ring cursors kept incrementally: stage index and phase parity
+      int as = 0, bs = 0, ab = 0;
+      uint32_t aph = 0, bph = 0, accph = 0;
       bool ok = true;
-      for (int64_t t = blockIdx.x; t < p.tiles && ok; t += gridDim.x) {
+      for (int64_t t0 = t0_first; t0 < p.tiles && ok; t0 += gridDim.x) {
         for (int ks = 0; ks < nks && ok; ++ks) {
           const bool seg_start = (ks % SEG) == 0;
-          const int ab = (int)(seg % C::NACC);
           if (seg_start) {
             // the epilogue has read the segment that last used accumulator ab
-            if (!wait_or_abort(&acce[ab], (uint32_t)(((seg / C::NACC) & 1) ^ 1), abort, p.status)) {
+            if (!wait_or_abort(&acce[ab], accph ^ 1u, abort, p.status)) {
               ok = false;
               break;
             }
             ptx::tc_fence_after();
           }
-          const int as = (int)(ai % C::A_STAGES), bs = (int)(bi % C::B_STAGES);
-          if (!wait_or_abort(&afull[as], (uint32_t)((ai / C::A_STAGES) & 1), abort, p.status)) {
-            ok = false;
-            break;
-          }
-          if (!wait_or_abort(&bfull[bs], (uint32_t)((bi / C::B_STAGES) & 1), abort, p.status)) {
+          if (!wait_or_abort(&afull[as], aph, abort, p.status)) {
             ok = false;
             break;
           }
           ptx::tc_fence_after();
           const uint32_t a0 = ptx::smem_u32(atile + (size_t)as * A_BYTES);
-          const uint32_t b0 = ptx::smem_u32(btile + (size_t)bs * C::B_STAGE);
           const uint32_t d = tmem + (uint32_t)(ab * C::NPAD);
           const uint64_t ad0 = ptx::desc_sw128(a0, 16, 1024);
-          const uint64_t bd0 = ptx::desc_sw128(b0, 1024, C::SBO_B);
+          for (int sub = 0; sub < C::SUBS && ok; ++sub) {
+            if (!wait_or_abort(&bfull[bs], bph, abort, p.status)) {
+              ok = false;
+              break;
+            }
+            ptx::tc_fence_after();
+            const uint64_t bd0 = ptx::desc_sw128(ptx::smem_u32(btile + (size_t)bs * C::B_STAGE), 1024, C::SBO_B);
 #pragma unroll
-          for (int kk = 0; kk < BK / 16; ++kk) {
-            const uint64_t ad = ptx::desc_advance(ad0, kk * 32);
-            const uint64_t bd = ptx::desc_advance(bd0, kk * 2 * C::SBO_B);
-            ptx::mma_f16(d, ad, bd, idesc, (seg_start && kk == 0) ? 0u : 1u);
-            if (!EXACT_V) ptx::mma_f16(d, ad, ptx::desc_advance(bd, C::B_BYTES), idesc, 1u);
+            for (int q = 0; q < C::B_SUB; ++q) {
+              const int kk = sub * C::B_SUB + q;
+              const uint64_t ad = ptx::desc_advance(ad0, kk * 32);
+              const uint64_t bd = ptx::desc_advance(bd0, q * C::SLICE);
+              ptx::mma_f16(d, ad, bd, idesc, (seg_start && kk == 0) ? 0u : 1u);
+              if (!EXACT_V) ptx::mma_f16(d, ad, ptx::desc_advance(bd, C::B_PART), idesc, 1u);
+            }
+            ptx::mma_commit_mc(&bempty[bs], (uint16_t)0x3);  // the stage is free in both CTAs
+            if (++bs == C::B_STAGES) {
+              bs = 0;
+              bph ^= 1u;
+            }
           }
-          ptx::mma_commit(&bempty[bs]);
+          if (!ok) break;
           ptx::mma_commit(&aempty[as]);
-          ++bi;
-          ++ai;
+          if (++as == C::A_STAGES) {
+            as = 0;
+            aph ^= 1u;
+          }
           if ((ks % SEG) == SEG - 1 || ks == nks - 1) {
             ptx::mma_commit(&accf[ab]);
-            ++seg;
+            if (++ab == C::NACC) {
+              ab = 0;
+              accph ^= 1u;
+            }
           }
         }
       }
@@ -353,8 +439,8 @@ __global__ void __launch_bounds__(Cfg<E4M3, NT, EXACT_V>::THREADS, 1)
     const int nseg = (nks + SEG - 1) / SEG;
     int64_t seg = 0;
     bool ok = true;
-    for (int64_t t = blockIdx.x; t < p.tiles && ok; t += gridDim.x) {
-      const int64_t grow = t * 128 + 32 * e + lane;
+    for (int64_t t0 = t0_first; t0 < p.tiles && ok; t0 += gridDim.x) {
+      const int64_t grow = (t0 + crank) * 128 + 32 * e + lane;
       for (int g = 0; g < nseg; ++g, ++seg) {
         const int ab = (int)(seg % C::NACC);
         if (!warp_wait(&accf[ab], (uint32_t)((seg / C::NACC) & 1), abort, p.status)) {
@@ -365,43 +451,60 @@ __global__ void __launch_bounds__(Cfg<E4M3, NT, EXACT_V>::THREADS, 1)
         const bool first = g == 0, last = g == nseg - 1;
         const uint32_t abase = tmem + lane_base + (uint32_t)(ab * C::NPAD);
         const uint32_t sbase = tmem + lane_base + C::S_COL;
-#pragma unroll 1
-        for (int cc = ehalf * C::WCOLS; cc < (ehalf + 1) * C::WCOLS; cc += 32) {
-          uint32_t a[32], s[32];
-          ptx::tmem_ld32_nowait(abase + (uint32_t)cc, a);
-          if (!first) ptx::tmem_ld32_nowait(sbase + (uint32_t)cc, s);
-          ptx::tmem_wait_ld(a);
-          if (first) {
+        // The warp's whole share of the segment comes into registers at once
+        // (one wait), and the accumulator goes back to the tensor core before
+        // S is touched: S is updated while the next segment accumulates.
+        const int col0 = ehalf * C::WCOLS;
+        uint32_t a[C::NCH][32];
 #pragma unroll
-            for (int q = 0; q < 32; ++q) s[q] = __float_as_uint(__uint_as_float(a[q]) * us);
-          } else {
-            ptx::tmem_regs_ready(s);
+        for (int c = 0; c < C::NCH; ++c) ptx::tmem_ld32_nowait(abase + (uint32_t)(col0 + 32 * c), a[c]);
+        ptx::tmem_wait_ld(a[0]);
 #pragma unroll
-            for (int q = 0; q < 32; ++q) s[q] = __float_as_uint(fmaf(__uint_as_float(a[q]), us, __uint_as_float(s[q])));
-          }
-          if (!last) {
-            ptx::tmem_st32_nowait(sbase + (uint32_t)cc, s);
-            ptx::tmem_wait_st(s);
-          } else if (grow < p.m) {
-            float* dst = p.Y + grow * p.k + cc;
-#pragma unroll
-            for (int q = 0; q < 32; ++q)
-              if (cc + q < p.k) yb = max(yb, s[q] & 0x7fffffffu);
-            if (cc + 32 <= p.k && (p.k % 4) == 0) {
-#pragma unroll
-              for (int q = 0; q < 32; q += 4)
-                *reinterpret_cast<float4*>(dst + q) = make_float4(__uint_as_float(s[q]), __uint_as_float(s[q + 1]),
-                                                                  __uint_as_float(s[q + 2]), __uint_as_float(s[q + 3]));
-            } else {
-#pragma unroll
-              for (int q = 0; q < 32; ++q)
-                if (cc + q < p.k) dst[q] = __uint_as_float(s[q]);
-            }
-          }
-        }
+        for (int c = 1; c < C::NCH; ++c) ptx::tmem_regs_ready(a[c]);
         ptx::tc_fence_before();
         __syncwarp();
         if (lane == 0) ptx::mbar_arrive(&acce[ab]);
+        // S (+)= A / t in place in a[], 16 columns at a time; the stores of S
+        // run from a[], which nothing overwrites before the next segment
+#pragma unroll
+        for (int c = 0; c < C::NCH; ++c) {
+#pragma unroll
+          for (int hh = 0; hh < 2; ++hh) {
+            const int cc = col0 + 32 * c + 16 * hh;
+            uint32_t* ah = &a[c][16 * hh];
+            if (first) {
+#pragma unroll
+              for (int q = 0; q < 16; ++q) ah[q] = __float_as_uint(__uint_as_float(ah[q]) * us);
+            } else {
+              uint32_t sv[16];
+              ptx::tmem_ld16_nowait(sbase + (uint32_t)cc, sv);
+              ptx::tmem_wait_ld(sv);
+#pragma unroll
+              for (int q = 0; q < 16; ++q)
+                ah[q] = __float_as_uint(fmaf(__uint_as_float(ah[q]), us, __uint_as_float(sv[q])));
+            }
+            if (!last) {
+              ptx::tmem_st16_from(sbase + (uint32_t)cc, ah);
+            } else if (grow < p.m) {
+              float* dst = p.Y + grow * p.k + cc;
+#pragma unroll
+              for (int q = 0; q < 16; ++q)
+                if (cc + q < p.k) yb = max(yb, ah[q] & 0x7fffffffu);
+              if (cc + 16 <= p.k && (p.k % 4) == 0) {
+#pragma unroll
+                for (int q = 0; q < 16; q += 4)
+                  *reinterpret_cast<float4*>(dst + q) = make_float4(__uint_as_float(ah[q]), __uint_as_float(ah[q + 1]),
+                                                                    __uint_as_float(ah[q + 2]), __uint_as_float(ah[q + 3]));
+              } else {
+#pragma unroll
+                for (int q = 0; q < 16; ++q)
+                  if (cc + q < p.k) dst[q] = __uint_as_float(ah[q]);
+              }
+            }
+          }
+        }
+        // S stores land before a[] is reloaded (and before the next fold reads S)
+        ptx::tmem_wait_st();
       }
     }
 #pragma unroll
@@ -416,6 +519,9 @@ __global__ void __launch_bounds__(Cfg<E4M3, NT, EXACT_V>::THREADS, 1)
   }
   ptx::tc_fence_before();
   __syncthreads();
+  // neither CTA leaves while the other may still multicast into it or arrive
+  // on its barriers
+  ptx::cluster_sync();
   if (warp == C::MMA_W) {
     ptx::tc_fence_after();
     ptx::tmem_dealloc(tmem, C::TMEM_COLS);
@@ -428,7 +534,24 @@ bool launch_cfg(Launcher& L, const CUtensorMap& tm, const Params& p) {
   if (cudaFuncSetAttribute(xproj_kernel<E4M3, NT, EXACT_V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)C::SMEM) != cudaSuccess)
     return false;
-  const int grid = (int)(p.tiles < L.num_sms ? p.tiles : L.num_sms);
+  // CTA pairs (clusters of two): an even grid of at most the pairs that can
+  // be resident at once (a GPC with an odd number of free SMs leaves one out)
+  static int resident = -1;
+  if (resident < 0) {
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3((unsigned)(L.num_sms / 2 * 2));
+    lc.blockDim = dim3(C::THREADS);
+    lc.dynamicSmemBytes = C::SMEM;
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, xproj_kernel<E4M3, NT, EXACT_V>, &lc) != cudaSuccess || nc < 1) {
+      cudaGetLastError();
+      nc = L.num_sms / 2;
+    }
+    resident = nc < L.num_sms / 2 ? nc : L.num_sms / 2;
+  }
+  const int64_t pairs = (p.tiles + 1) / 2;
+  int grid = (int)(pairs < resident ? pairs : resident) * 2;
+  if (grid < 2) grid = 2;
   xproj_kernel<E4M3, NT, EXACT_V><<<grid, C::THREADS, C::SMEM, L.stream>>>(tm, p);
   L.count(1);
   return true;
