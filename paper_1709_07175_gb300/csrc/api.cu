@@ -149,11 +149,15 @@ void plan_sketch(Plan& P, SketchBufs& b, int xt, int64_t n, int k, const lspca_o
 
 using Mark = std::function<void(int)>;
 
+// need_u: the fit uses the FP32 U itself (SPCA's QR, the Gram); otherwise the
+// FP8 path writes only the E4M3 copy, and a gated second run writes U in the
+// rare case that copy is not exact (the BF16 pass F then takes over).
 void run_sketch(lspca_ctx* ctx, Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_t ldx, int k,
-                const lspca_omega& om, bool tc, SketchBufs& b, void* U, const Mark& mark) {
+                const lspca_omega& om, bool tc, SketchBufs& b, void* U, const Mark& mark, bool need_u = true) {
   if (b.f8ws) {
     mark(1);
-    launch_f8_sketch(L, X, m, n, ldx, k, om, b.f8ws, (float*)U, ctx->d_absmax + 1, ctx->d_status);
+    launch_f8_sketch(L, X, m, n, ldx, k, om, b.f8ws, need_u ? (float*)U : nullptr, ctx->d_absmax + 1, ctx->d_status);
+    if (!need_u) launch_f8_sketch(L, X, m, n, ldx, k, om, b.f8ws, (float*)U, ctx->d_absmax + 1, ctx->d_status, true);
     mark(2);
     return;
   }
@@ -318,7 +322,7 @@ int fit_impl(lspca_ctx* ctx, const void* X, int32_t xt, int64_t m, int64_t n, in
   };
   cudaMemsetAsync(ctx->d_absmax, 0, 2 * sizeof(float), s);
   mark(0);
-  run_sketch(ctx, L, X, xt, m, n, ldx, k, om, tc_s, sb, U, mark);
+  run_sketch(ctx, L, X, xt, m, n, ldx, k, om, tc_s, sb, U, mark, spca || want_g);
   if (tc_f && !tc_s && om.kind == LSPCA_OMEGA_GAUSSIAN)
     launch_scan_x(L, U, LSPCA_F32, m, k, k, ctx->d_absmax + 1, ctx->d_status);  // max|U| for the FP16 scales
   if ((st = run_chain(ctx, L, X, xt, m, n, ldx, U, k, tc_f, cb, F, want_g ? G : nullptr, mark))) return st;

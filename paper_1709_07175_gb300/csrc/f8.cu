@@ -118,6 +118,7 @@ struct SketchParams {
   float* umax;
   int* inexact;       // set when some U is not exactly an E4M3 value
   int* status;
+  const int* run_if;  // nullable: the kernel does nothing unless *run_if != 0
 };
 
 template <int NP>
@@ -135,6 +136,7 @@ __global__ void __launch_bounds__(kThreads, 1) f8_sketch_kernel(const __grid_con
                                                                 const __grid_constant__ CUtensorMap tmo,
                                                                 SketchParams p) {
   using C = SkCfg<NP>;
+  if (p.run_if && *p.run_if == 0) return;  // uniform: the gated second run is not needed
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = (uint64_t*)(smem + (size_t)C::STAGES * C::STAGE);
@@ -494,11 +496,11 @@ int* f8_inexact_flag(void* ws, int64_t m, int64_t n, int k, int num_sms) {
 }
 
 bool launch_f8_sketch(Launcher& L, const void* X, int64_t m, int64_t n, int64_t ldx, int k, const lspca_omega& om,
-                      void* ws, float* U, float* umax, int* status) {
+                      void* ws, float* U, float* umax, int* status, bool again) {
   F8Ws w = carve_f8(ws, m, n, k, L.num_sms);
   const int np = f8_np(k);
-  cudaMemsetAsync(w.inexact, 0, sizeof(int), L.stream);
-  {
+  if (!again) {
+    cudaMemsetAsync(w.inexact, 0, sizeof(int), L.stream);
     const int64_t total = n * (np / 4);
     f8::omega_t_e4m3_kernel<<<(unsigned)((total + 255) / 256), 256, 0, L.stream>>>(om, n, pitch16b(n), k, np,
                                                                                     w.omt);
@@ -509,7 +511,7 @@ bool launch_f8_sketch(Launcher& L, const void* X, int64_t m, int64_t n, int64_t 
       !make_tmap_2d_sw128(&tmo, w.omt, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, (uint64_t)np, (uint64_t)n,
                           (uint64_t)pitch16b(n), (uint32_t)np, 128))
     return false;
-  f8::SketchParams p{m, n, k, np, (m + 127) / 128, U, w.U8, umax, w.inexact, status};
+  f8::SketchParams p{m, n, k, np, (m + 127) / 128, U, w.U8, umax, w.inexact, status, again ? w.inexact : nullptr};
   const int64_t grid = p.tiles < L.num_sms ? p.tiles : L.num_sms;
   auto go = [&](auto kern, size_t smem) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

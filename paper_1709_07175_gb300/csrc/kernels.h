@@ -60,8 +60,11 @@ void launch_bsketch(Launcher& L, const void* X, int64_t m, int64_t n, int64_t ld
 // built.
 size_t f8_ws_bytes(int64_t m, int64_t n, int k, int num_sms);
 int* f8_inexact_flag(void* ws, int64_t m, int64_t n, int k, int num_sms);
+// U (FP32) is nullable: the E4M3 copy alone feeds the FP8 pass F.  again:
+// the run after one with U == nullptr, which writes U only if that run found U
+// not exact in E4M3 (the BF16 pass F then needs it); it does nothing otherwise.
 bool launch_f8_sketch(Launcher& L, const void* X, int64_t m, int64_t n, int64_t ldx, int k, const lspca_omega& om,
-                      void* ws, float* U, float* umax, int* status);
+                      void* ws, float* U, float* umax, int* status, bool again = false);
 void launch_f8_u8(Launcher& L, const float* U, int64_t m, int k, void* ws, int64_t n);
 bool launch_f8_chain(Launcher& L, const void* X, int64_t m, int64_t n, int64_t ldx, int k, void* ws, double* F,
                      int* status);

@@ -537,3 +537,28 @@ def test_fit_binary_e4m3_parity(ctx):
     e = _report_errors(Y, Yref, r.V.double().cpu().numpy(), fit["V"])
     print("e4m3_binary", e)
     assert e["procrustes"] < 1e-4
+
+
+def test_fit_e4m3_not_binary_takes_the_bf16_pass_f(ctx):
+    """E4M3 X with values other than 0 and 1: U is not exact in E4M3, so the
+    FP8 pass F stands down, a second (gated) sketch run writes U in FP32 and
+    the BF16 pass F computes F; the fit still matches the oracle."""
+    w = C4S
+    g = torch.Generator().manual_seed(17)
+    scale = torch.rand(w.m, w.n, generator=g) * 2.75 + 0.25
+    X = (S.generate(w).float() * scale).to(torch.float8_e4m3fn)
+    Xd = X.float().double().numpy()
+    Om = P.omega_sparse(w.omega_seed, w.n, w.k, w.p)
+    Uref = Xd @ Om
+    U8 = torch.from_numpy(Uref).float().to(torch.float8_e4m3fn).float().double().numpy()
+    assert not np.array_equal(U8, Uref)  # the case under test: U is not exact in E4M3
+    fit = O.lspca_fit(Xd, Om, route="eig")
+    Xg = X.cuda()
+    r = ctx.fit(Xg, w.k, _om(w))
+    assert ctx.sync_status() == L.OK
+    Y = ctx.project(Xg, r.V).double().cpu().numpy()
+    Yref = O.project(Xd, fit["V"])
+    e = _report_errors(Y, Yref, r.V.double().cpu().numpy(), fit["V"])
+    print("e4m3 not binary", e)
+    assert e["procrustes"] < 1e-4
+    assert np.max(np.abs(r.sigma.cpu().numpy() - fit["sigma"]) / fit["sigma"]) < 1e-4
