@@ -102,7 +102,7 @@ typedef struct {
   int32_t rank;           /* numerical rank (rank rule)                         */
   int32_t device_status;  /* status word read from the device                  */
   int32_t sweeps;         /* levels of the graded k x k eigensolve that ran (1-3) */
-  int32_t reserved;
+  int32_t qr_path;        /* SPCA's R: 1 CholeskyQR2, 2 Householder TSQR; 0 Lazy */
 } lspca_report;
 
 /* ------------------------------------------------------------------------- */
@@ -193,10 +193,17 @@ int lspca_fit_oversampled(lspca_ctx* ctx, const void* X, int32_t xt, int64_t m, 
                           int32_t* rank, void* stream, lspca_report* rep);
 
 /* SPCA fit, the comparison path: Algorithm 1 in its streaming form,
- * Algorithm 3 (table of Sec. III; Eq. "approx_svd"): U = X Omega; R from a
- * tall-skinny Householder QR of U (row blocks, then a reduction tree of the
- * stacked R factors: Algorithm 3's qr([R; U_s]) in parallel form);
- * F = R^-T U^T X (= Q^T X); truncated SVD of F by the same eigen route.
+ * Algorithm 3 (table of Sec. III; Eq. "approx_svd"): U = X Omega; R, the
+ * triangular factor of the QR of U (Q itself is never kept, as in
+ * Algorithm 3); F = R^-T U^T X (= Q^T X); truncated SVD of F by the same eigen
+ * route.  R comes from CholeskyQR2 for FP32 U on the tensor-core paths:
+ * R1 = chol(U^T U) from pass F's Gram, Q1 = U R1^-1 on the tensor cores,
+ * R2 = chol(Q1^T Q1), R = R2 R1.  When a Cholesky meets a pivot below 1e-6
+ * of its diagonal entry (U too close to rank deficient for the Gram's
+ * precision) the tall-skinny Householder QR runs instead (row blocks, then a
+ * reduction tree of the stacked R factors: Algorithm 3's qr([R; U_s]) in
+ * parallel form); FP64 U and the SIMT paths always take it.  The report's
+ * qr_path says which ran.
  * Arguments and errors as lspca_fit; sigma receives Sigma^s of Q^T X and
  * V receives V^s.  `gram` (with LSPCA_WANT_GRAM) receives U^T U.           */
 int spca_fit(lspca_ctx* ctx, const void* X, int32_t xt, int64_t m, int64_t n, int64_t ldx,

@@ -286,22 +286,44 @@ int fit_impl(lspca_ctx* ctx, const void* X, int32_t xt, int64_t m, int64_t n, in
   const bool tc_f = use_tc_chain(xt, flags, k);
   const size_t asz = acc_size(xt);
 
+  // SPCA's R: CholeskyQR2 from the Gram for FP32 U on the tensor-core paths
+  // (the Householder TSQR stands by, gated, for a Gram that is numerically
+  // singular); the Householder TSQR alone for FP64 U and the SIMT paths
+  const bool cq = spca && tc_f && xt != LSPCA_F64;
+  const bool need_g = want_g || cq;
+
   SketchBufs sb;
   ChainBufs cb;
   SmallWs sw;
   void *U = nullptr, *small = nullptr, *qrws = nullptr;
-  double *F = nullptr, *G = nullptr, *R = nullptr;
+  double *F = nullptr, *G = nullptr, *R = nullptr, *G2 = nullptr;
+  float *Q1 = nullptr, *R1 = nullptr, *Rinv = nullptr, *R2 = nullptr, *cqs = nullptr;
+  TcProjectWs pw2;
+  TcChainWs w2;
   auto plan = [&](Plan& P) {
     U = P.take((size_t)m * k * asz);
     plan_sketch(P, sb, xt, n, k, om, tc_s, flags, m, ctx->num_sms);
     cb.f8ws = sb.f8ws;
     F = (double*)P.take((size_t)k * n * 8);
     G = (double*)P.take((size_t)k * k * 8);
-    plan_chain(P, cb, xt, m, n, k, want_g, tc_f, ctx->num_sms);
+    plan_chain(P, cb, xt, m, n, k, need_g, tc_f, ctx->num_sms);
     small = P.take(small_ws_bytes(k, n, nullptr));
     if (spca) {
       qrws = P.take(tsqr_ws_bytes(m, k));
       R = (double*)P.take((size_t)k * k * 8);
+    }
+    if (cq) {
+      Q1 = (float*)P.take((size_t)m * k * 4);
+      R1 = (float*)P.take((size_t)k * k * 4);
+      Rinv = (float*)P.take((size_t)k * k * 4);
+      R2 = (float*)P.take((size_t)k * k * 4);
+      G2 = (double*)P.take((size_t)k * k * 8);
+      cqs = (float*)P.take(256);  // max|Q1| twice, the failure flag
+      plan_tc_project(P.base ? P.base + ((P.off + 255) & ~(size_t)255) : nullptr, pw2, LSPCA_F32, k, k);
+      P.take(pw2.bytes);
+      plan_tc_chain_inline(P.base ? P.base + ((P.off + 255) & ~(size_t)255) : nullptr, w2, LSPCA_F32, m, k, k, false,
+                           ctx->num_sms);
+      P.take(w2.bytes);
     }
   };
   Plan p0;
@@ -325,10 +347,25 @@ int fit_impl(lspca_ctx* ctx, const void* X, int32_t xt, int64_t m, int64_t n, in
   run_sketch(ctx, L, X, xt, m, n, ldx, k, om, tc_s, sb, U, mark, spca || want_g);
   if (tc_f && !tc_s && om.kind == LSPCA_OMEGA_GAUSSIAN)
     launch_scan_x(L, U, LSPCA_F32, m, k, k, ctx->d_absmax + 1, ctx->d_status);  // max|U| for the FP16 scales
-  if ((st = run_chain(ctx, L, X, xt, m, n, ldx, U, k, tc_f, cb, F, want_g ? G : nullptr, mark))) return st;
-  if (spca) {
+  if ((st = run_chain(ctx, L, X, xt, m, n, ldx, U, k, tc_f, cb, F, need_g ? G : nullptr, mark))) return st;
+  int* cq_fail = cq ? reinterpret_cast<int*>(cqs + 2) : nullptr;
+  if (cq) {
+    // R1 = chol(U^T U); Q1 = U R1^-1; R2 = chol(Q1^T Q1); R = R2 R1
+    cudaMemsetAsync(cqs, 0, 16, s);
+    launch_chol(L, G, k, R1, cq_fail);
+    launch_tri_inv(L, R1, k, Rinv, cq_fail);
+    tc_project(L, U, LSPCA_F32, m, k, k, Rinv, k, pw2, Q1, ctx->d_status);
+    launch_scan_x(L, Q1, LSPCA_F32, m, k, k, cqs, ctx->d_status);
+    cudaMemcpyAsync(cqs + 1, cqs, sizeof(float), cudaMemcpyDeviceToDevice, s);  // X = U = Q1: one scale
+    tc_chain_inline_main(L, Q1, LSPCA_F32, m, k, k, Q1, k, w2, cqs, ctx->d_status, false);
+    tc_chain_reduce(L, k, k, w2, G2, nullptr);
+    launch_chol(L, G2, k, R2, cq_fail);
+    launch_rmul(L, R2, R1, k, R, cq_fail);
+    launch_tsqr(L, U, false, m, k, qrws, R, cq_fail);  // runs only if a Cholesky broke down
+    launch_trsm_rt(L, R, k, F, n, false);
+  } else if (spca) {
     launch_tsqr(L, U, xt == LSPCA_F64, m, k, qrws, R);
-    launch_trsm_rt(L, R, k, F, n);
+    launch_trsm_rt(L, R, k, F, n, xt == LSPCA_F64);
   }
   mark(5);
   int32_t* rk = rank ? rank : ctx->d_rank;
@@ -355,6 +392,12 @@ int fit_impl(lspca_ctx* ctx, const void* X, int32_t xt, int64_t m, int64_t n, in
   rep->rank = hr;
   rep->device_status = hst;
   rep->sweeps = hsw;
+  rep->qr_path = 0;
+  if (spca) {
+    int32_t hf = 1;
+    if (cq) cudaMemcpy(&hf, cq_fail, 4, cudaMemcpyDeviceToHost);
+    rep->qr_path = hf ? 2 : 1;
+  }
   rep->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   if (hst & ST_NONFINITE) return LSPCA_ERR_NUMERIC;
   if (hst & ST_TIMEOUT) return LSPCA_ERR_TIMEOUT;

@@ -136,10 +136,22 @@ void launch_decompose(Launcher& L, SmallWs& w, const double* F, int k, int64_t n
 
 // ---- K4: TSQR (SPCA) ------------------------------------------------------
 size_t tsqr_ws_bytes(int64_t m, int k);
-// R (k x k FP64, upper triangular) of U (m x k, FP64 if u_f64 else FP32).
-void launch_tsqr(Launcher& L, const void* U, bool u_f64, int64_t m, int k, void* ws, double* R);
-// F <- R^-T F in place (F k x n FP64).
-void launch_trsm_rt(Launcher& L, const double* R, int k, double* F, int64_t n);
+// R (k x k FP64, upper triangular) of U (m x k, FP64 if u_f64 else FP32) by
+// Householder reflections.  run_if (nullable): every kernel does nothing
+// unless *run_if != 0 (the fallback of CholeskyQR2).
+void launch_tsqr(Launcher& L, const void* U, bool u_f64, int64_t m, int k, void* ws, double* R,
+                 const int* run_if = nullptr);
+// CholeskyQR2 pieces (cholqr.cu); each does nothing once *fail is set.
+// launch_chol: R (k x k FP32, upper) with G = R^T R, or *fail = 1 when a
+// pivot falls below its tolerance.  launch_tri_inv: Rinv = R^-1 (zeros once
+// *fail is set).  launch_rmul: R = R2 R1 in FP64.
+size_t cholqr_smem_bytes(int k);
+void launch_chol(Launcher& L, const double* G, int k, float* R, int* fail);
+void launch_tri_inv(Launcher& L, const float* R, int k, float* Rinv, const int* fail);
+void launch_rmul(Launcher& L, const float* R2, const float* R1, int k, double* R, const int* fail);
+// F <- R^-T F in place (F k x n FP64); pivots below 1e-10 (FP64 U) or 1e-4
+// (FP32 U) of the largest give zero rows.
+void launch_trsm_rt(Launcher& L, const double* R, int k, double* F, int64_t n, bool u_f64);
 
 // The bounded-wait failure path on a barrier that never completes (waitprobe.cu).
 void launch_wait_probe(Launcher& L, uint64_t limit_ns, int* status, int64_t* waited_ns);

@@ -39,7 +39,8 @@ template <typename Acc, typename SrcT>
 __global__ void __launch_bounds__(kQrThreads) qr_block_kernel(const SrcT* __restrict__ src, int64_t m, int k,
                                                               int rows_per_block, const double* __restrict__ rin,
                                                               int nin, double* __restrict__ rout, Acc* gwork,
-                                                              int use_smem) {
+                                                              int use_smem, const int* run_if) {
+  if (run_if && *(volatile const int*)run_if == 0) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ Acc beta_s, rjj_s;
   const int B = qr_rows(k);
@@ -63,11 +64,26 @@ __global__ void __launch_bounds__(kQrThreads) qr_block_kernel(const SrcT* __rest
   }
   __syncthreads();
 
+  // Rows a reflector touches.  A leaf block is dense: rows j .. B-1.  A tree
+  // node stacks two upper triangles, so reflector j has nonzeros only in row
+  // j and rows k .. k + j (the rows of the first triangle below j are still
+  // zero, those of the second below k + j too), and its update touches only
+  // those rows.  Lane l of a warp takes the l-th, (l+32)-th, ... of them.
+  const bool node = rin != nullptr;
+  auto row_at = [&](int j, int t) { return node ? (t == 0 ? j : k + t - 1) : j + t; };
+  auto row_count = [&](int j) { return node ? j + 2 : B - j; };
   for (int j = 0; j < k; ++j) {
     Acc* colj = Wm + (size_t)j * B;
+    const int nr = row_count(j);
     if (warp == 0) {
+      // the diagonal of the previous step lands now (the update there read
+      // v's leading entry from the same place), saving a barrier
+      if (lane == 0 && j > 0) Wm[(size_t)(j - 1) * B + (j - 1)] = rjj_s;
       Acc sq = Acc(0);
-      for (int r = j + 1 + lane; r < B; r += 32) sq += colj[r] * colj[r];
+      for (int t = 1 + lane; t < nr; t += 32) {
+        const Acc x = colj[row_at(j, t)];
+        sq += x * x;
+      }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
       if (lane == 0) {
@@ -88,20 +104,40 @@ __global__ void __launch_bounds__(kQrThreads) qr_block_kernel(const SrcT* __rest
     __syncthreads();
     const Acc beta = beta_s;
     if (beta != Acc(0)) {
-      for (int c = j + 1 + warp; c < k; c += nwarps) {
-        Acc* colc = Wm + (size_t)c * B;
-        Acc wsum = Acc(0);
-        for (int r = j + lane; r < B; r += 32) wsum += colj[r] * colc[r];
+      // trailing columns j+1 .. k-1, four at a time per warp (independent
+      // load / reduction / update chains)
+      for (int c0 = j + 1 + 4 * warp; c0 < k; c0 += 4 * nwarps) {
+        Acc* cc[4];
+        Acc ws[4];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
-        const Acc f = beta * wsum;
-        for (int r = j + lane; r < B; r += 32) colc[r] -= f * colj[r];
+        for (int q = 0; q < 4; ++q) {
+          cc[q] = Wm + (size_t)(c0 + q < k ? c0 + q : c0) * B;
+          ws[q] = Acc(0);
+        }
+        for (int t = lane; t < nr; t += 32) {
+          const int r = row_at(j, t);
+          const Acc v = colj[r];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) ws[q] += v * cc[q][r];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) ws[q] += __shfl_xor_sync(0xffffffffu, ws[q], o);
+        }
+        for (int t = lane; t < nr; t += 32) {
+          const int r = row_at(j, t);
+          const Acc v = colj[r];
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (c0 + q < k) cc[q][r] -= beta * ws[q] * v;
+        }
       }
     }
     __syncthreads();
-    if (tid == 0) colj[j] = rjj_s;
-    __syncthreads();
   }
+  if (tid == 0) Wm[(size_t)(k - 1) * B + (k - 1)] = rjj_s;
+  __syncthreads();
   double* R = rout + (size_t)b * k * k;
   for (int e = tid; e < k * k; e += kQrThreads) {
     const int i = e / k, c = e % k;
@@ -109,8 +145,13 @@ __global__ void __launch_bounds__(kQrThreads) qr_block_kernel(const SrcT* __rest
   }
 }
 
+__global__ void copy_r_kernel(const double* __restrict__ src, double* __restrict__ dst, int n, const int* run_if) {
+  if (run_if && *(volatile const int*)run_if == 0) return;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) dst[e] = src[e];
+}
+
 template <typename Acc, typename SrcT>
-static void tsqr_typed(Launcher& L, const SrcT* U, int64_t m, int k, void* ws, double* R) {
+static void tsqr_typed(Launcher& L, const SrcT* U, int64_t m, int k, void* ws, double* R, const int* run_if) {
   const int B = qr_rows(k);
   const int64_t nb0 = (m + B - 1) / B;
   char* p = (char*)ws;
@@ -124,7 +165,8 @@ static void tsqr_typed(Launcher& L, const SrcT* U, int64_t m, int k, void* ws, d
   for (int64_t b0 = 0; b0 < nb0; b0 += 4096) {
     const int nb = (int)((nb0 - b0) < 4096 ? (nb0 - b0) : 4096);
     qr_block_kernel<Acc, SrcT><<<nb, kQrThreads, shm, L.stream>>>(U + b0 * B * k, m - b0 * B, k, B, nullptr, 0,
-                                                                   ra + (size_t)b0 * k * k, gwork, smem ? 1 : 0);
+                                                                   ra + (size_t)b0 * k * k, gwork, smem ? 1 : 0,
+                                                                   run_if);
     L.count(1);
   }
   int64_t nin = nb0;
@@ -133,40 +175,48 @@ static void tsqr_typed(Launcher& L, const SrcT* U, int64_t m, int k, void* ws, d
   while (nin > 1) {
     const int64_t nout = (nin + 1) / 2;
     qr_block_kernel<Acc, SrcT><<<(int)nout, kQrThreads, shm, L.stream>>>(U, 0, k, B, cur, (int)nin, nxt, gwork,
-                                                                         smem ? 1 : 0);
+                                                                         smem ? 1 : 0, run_if);
     L.count(1);
     double* t = cur;
     cur = nxt;
     nxt = t;
     nin = nout;
   }
-  cudaMemcpyAsync(R, cur, (size_t)k * k * 8, cudaMemcpyDeviceToDevice, L.stream);
+  copy_r_kernel<<<(k * k + 255) / 256, 256, 0, L.stream>>>(cur, R, k * k, run_if);
+  L.count(1);
 }
 
-void launch_tsqr(Launcher& L, const void* U, bool u_f64, int64_t m, int k, void* ws, double* R) {
+void launch_tsqr(Launcher& L, const void* U, bool u_f64, int64_t m, int k, void* ws, double* R, const int* run_if) {
   if (u_f64)
-    tsqr_typed<double, double>(L, (const double*)U, m, k, ws, R);
+    tsqr_typed<double, double>(L, (const double*)U, m, k, ws, R, run_if);
   else
-    tsqr_typed<float, float>(L, (const float*)U, m, k, ws, R);
+    tsqr_typed<float, float>(L, (const float*)U, m, k, ws, R, run_if);
 }
 
 // F <- R^-T F: forward substitution on R^T (lower triangular), one thread per
 // column of F; R (k x k FP64) is read through the read-only cache, every lane
-// of a warp reading the same entry.
-__global__ void trsm_rt_kernel(const double* __restrict__ R, int k, double* __restrict__ F, int64_t n) {
+// of a warp reading the same entry.  A pivot below rtol times the largest
+// |R_ii| marks a direction U does not resolve (U rank deficient to working
+// precision): that row of the result is 0.  Dividing by such a pivot would
+// blow F's own rounding error (relative u) up to u / rtol, so rtol sits near
+// sqrt(u): 1e-4 for FP32 U, 1e-10 for FP64 U.
+__global__ void trsm_rt_kernel(const double* __restrict__ R, int k, double* __restrict__ F, int64_t n, double rtol) {
   const int64_t col = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (col >= n) return;
+  double dmax = 0.0;
+  for (int i = 0; i < k; ++i) dmax = fmax(dmax, fabs(__ldg(R + i * k + i)));
+  const double tol = rtol * dmax;
   for (int i = 0; i < k; ++i) {
     double s = F[(int64_t)i * n + col];
     for (int l = 0; l < i; ++l) s -= __ldg(R + l * k + i) * F[(int64_t)l * n + col];
     const double d = __ldg(R + i * k + i);
-    F[(int64_t)i * n + col] = d != 0.0 ? s / d : 0.0;
+    F[(int64_t)i * n + col] = fabs(d) > tol ? s / d : 0.0;
   }
 }
 
-void launch_trsm_rt(Launcher& L, const double* R, int k, double* F, int64_t n) {
+void launch_trsm_rt(Launcher& L, const double* R, int k, double* F, int64_t n, bool u_f64) {
   const int threads = 32;
-  trsm_rt_kernel<<<(int)((n + threads - 1) / threads), threads, 0, L.stream>>>(R, k, F, n);
+  trsm_rt_kernel<<<(int)((n + threads - 1) / threads), threads, 0, L.stream>>>(R, k, F, n, u_f64 ? 1e-10 : 1e-4);
   L.count(1);
 }
 

@@ -46,10 +46,10 @@ class lspca_report(ctypes.Structure):
     _fields_ = [("ms_total", ctypes.c_double), ("ms_sketch", ctypes.c_double), ("ms_chain", ctypes.c_double),
                 ("ms_small", ctypes.c_double), ("ms_qr", ctypes.c_double), ("bytes_x", ctypes.c_double),
                 ("rank", ctypes.c_int32), ("device_status", ctypes.c_int32), ("sweeps", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("qr_path", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 _lib = None

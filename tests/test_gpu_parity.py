@@ -353,6 +353,45 @@ def test_spca_fp32_parity(ctx, data):
     assert np.max(np.abs(r.sigma.cpu().numpy() - sp["sigma"]) / sp["sigma"]) < 1e-4
 
 
+@pytest.mark.parametrize("wl", [C2S, C2R])
+def test_spca_cholesky_qr2_agrees_with_householder_and_oracle(ctx, data, wl):
+    """SPCA's R by CholeskyQR2 (tensor-core path) and by the Householder TSQR
+    (the SIMT path, LSPCA_FORCE_SIMT): the same span (Prop. 2 holds for any
+    invertible R, and both equal Lazy SPCA's), singular values of Q^T X within
+    1e-4 of the oracle for both, and within 2e-5 of each other."""
+    w, X, Xd, Om, fit = _get(data, wl)
+    Xg = X.cuda()
+    sp = O.spca_fit(Xd, Om, route="eig")
+    cq = ctx.spca(Xg, w.k, _om(w))
+    hh = ctx.spca(Xg, w.k, _om(w), flags=L.FORCE_SIMT)
+    assert cq.report["qr_path"] == 1 and hh.report["qr_path"] == 2
+    s_cq, s_hh = cq.sigma.cpu().numpy(), hh.sigma.cpu().numpy()
+    e_cq = np.max(np.abs(s_cq - sp["sigma"]) / sp["sigma"])
+    e_hh = np.max(np.abs(s_hh - sp["sigma"]) / sp["sigma"])
+    print(f"SPCA sigma vs oracle: CholeskyQR2 {e_cq:.2e}, Householder {e_hh:.2e}")
+    assert e_cq < 1e-4 and e_hh < 1e-4
+    assert np.max(np.abs(s_cq - s_hh) / s_hh) < 2e-5
+    assert M.max_sine(cq.V.double().cpu().numpy(), hh.V.double().cpu().numpy()) < 1e-4
+    assert M.max_sine(cq.V.double().cpu().numpy(), sp["V"]) < 1e-4
+
+
+def test_spca_falls_back_to_householder_on_rank_deficient_u(ctx):
+    """An X of rank 5 (up to its FP32 rounding) sketched to k = 16: U^T U is
+    singular to working precision, the first Cholesky stops, and the
+    Householder TSQR gives R; R^-T F drops the directions whose pivots are
+    below 1e-4 of the largest (dividing F's rounding error by them took the
+    rank to k and buried the signal), and the fit recovers the rank-5
+    subspace exactly."""
+    X, B = S.rank_r_exact(4000, 1000, 5, seed=3)
+    Xg = X.float().cuda()
+    r = ctx.spca(Xg, 16, L.omega("gaussian", 9))
+    assert r.report["qr_path"] == 2
+    V = r.V.double().cpu().numpy()
+    assert np.all(np.isfinite(V)) and np.all(np.isfinite(r.sigma.cpu().numpy()))
+    assert int(r.rank.item()) == 5
+    assert M.max_sine(B.numpy(), V[:, :5]) < 1e-4
+
+
 # ------------------------------------------------------------------ projection
 
 @pytest.mark.parametrize("wl,tol", [(C1, 1e-13), (C2S, 2e-6), (C2R, 2e-6)])
