@@ -280,14 +280,16 @@ def serve_bench(L, S, torch, local: int, seconds: float, loads=(0.5, 0.8, 0.95),
     return out
 
 
-# DRAM bytes (read + write) per row of X of one launch, from one ncu capture
-# of the same kernel on a smaller case of the same workload (traffic grows in
-# proportion to the rows).  None until captured, and reset to None whenever
-# the kernel changes.
+# DRAM bytes (read + write) per row of X from one ncu capture of each kernel
+# on 400,000 rows of the e4m3_binary recipe (`bench.py --quick --m 400000`;
+# dram__bytes_read.sum + dram__bytes_write.sum over 400,000; the kernels
+# stream X, so traffic grows with the rows): f8_sketch_kernel 1,641,817,088 +
+# 100,861,696, f8_chain_kernel 1,741,043,968 + 225,536, xproj_kernel
+# 1,658,828,544 + 379,153,152.
 TRAFFIC_PER_ROW = {
-    ("e4m3_binary", "sketch"): None,
-    ("e4m3_binary", "chain_main"): None,
-    ("e4m3_binary", "project"): None,
+    ("e4m3_binary", "sketch"): (1_641_817_088 + 100_861_696) / 400_000,
+    ("e4m3_binary", "chain_main"): (1_741_043_968 + 225_536) / 400_000,
+    ("e4m3_binary", "project"): (1_658_828_544 + 379_153_152) / 400_000,
 }
 
 

@@ -135,10 +135,10 @@ __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volati
   return __all_sync(0xffffffffu, ok);
 }
 
-// The X box (and its V tiles) that tile t takes j-th: every tile walks K in
-// its own rotation, so the CTAs, which hold consecutive tiles, read different
-// V tiles at any moment instead of all loading the same one from the same
-// L2 slices.  A row's result depends only on its tile.
+// The X box (and its V tiles) taken j-th: every CTA pair walks K in its own
+// rotation, (tile / 2) mod boxes, so the pairs, which hold consecutive tiles,
+// read different V tiles at any moment instead of all loading the same one
+// from the same L2 slices.  A row's result depends only on its tile.
 __device__ __forceinline__ int box_rotation(int64_t t, int nboxes) { return (int)(t % nboxes); }
 __device__ __forceinline__ int rotated_box(int rot, int j, int nboxes) {
   const int b = j + rot;
