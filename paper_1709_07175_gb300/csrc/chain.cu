@@ -64,7 +64,10 @@ constexpr int kConvBuffers = 2;
 template <int MODE, int MH, int NACC>
 struct Cfg {
   static_assert(NACC == 1 || (NACC == 2 && MH == 1), "double-buffered A with one M half only");
-  static constexpr int BN = (MH == 2 || NACC == 2) ? 128 : 256;
+  // The Gram with k <= 128: B = U is the A tile itself (the same rows, the
+  // same MN-major layout), so it is loaded once and read as both operands
+  static constexpr bool SHARE_B = MODE == M_GRAM && MH == 1;
+  static constexpr int BN = (SHARE_B || MH == 2 || NACC == 2) ? 128 : 256;
   static constexpr int WA = 128 * MH;
   static constexpr bool CONV = (MODE == M_F32 || MODE == M_E4M3);
   static constexpr bool F16 = (MODE == M_F32 || MODE == M_GRAM);  // FP16 pairs, else BF16
@@ -79,9 +82,9 @@ struct Cfg {
   static constexpr uint32_t BOX = BK * 128;        // one TMA box: BK rows x 64 16-bit columns
   static constexpr uint32_t A_BYTES = BK * WA * 2;  // one part of A
   static constexpr uint32_t B_BYTES = BK * BN * 2;  // one part of B
-  static constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + NB * B_BYTES;
+  static constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + (SHARE_B ? 0u : NB * B_BYTES);
   static constexpr int STAGES = STAGE_BYTES <= 24576 ? 8 : STAGE_BYTES <= 32768 ? 6 : 4;
-  static constexpr uint32_t TX = 2 * A_BYTES + (CONV ? 0u : NB * B_BYTES);
+  static constexpr uint32_t TX = 2 * A_BYTES + ((CONV || SHARE_B) ? 0u : NB * B_BYTES);
   static constexpr uint32_t SBO_B = (BN / 64) * 1024;  // converter layout of B: K atom groups
   static constexpr int ELEM = (MODE == M_F32) ? 4 : 1;  // converter modes: bytes per X element
   static constexpr int B_VEC = CONV ? BK * BN * ELEM / 16 / CT : 1;  // 16-byte loads per thread per step
@@ -275,7 +278,7 @@ __global__ void __launch_bounds__(Cfg<MODE, MH, NACC>::THREADS, 1)
             ptx::tma_load_2d(st + b * C::BOX, &tm_ahi, 64 * b, y, &tfull[s]);
             ptx::tma_load_2d(st + C::A_BYTES + b * C::BOX, &tm_alo, 64 * b, y, &tfull[s]);
           }
-          if (!C::CONV) {
+          if (!C::CONV && !C::SHARE_B) {
             const uint32_t bst = st + 2 * C::A_BYTES;
 #pragma unroll
             for (int b = 0; b < C::BN / 64; ++b) {
@@ -434,7 +437,7 @@ __global__ void __launch_bounds__(Cfg<MODE, MH, NACC>::THREADS, 1)
           }
           ptx::tc_fence_after();
           const uint32_t st = sbase + s * C::STAGE_BYTES;
-          const uint32_t a_hi = st, b_hi = st + 2 * C::A_BYTES;
+          const uint32_t a_hi = st, b_hi = C::SHARE_B ? st : st + 2 * C::A_BYTES;
           // descriptors of the stage's operands; K slices and M halves are offsets
           const uint64_t adh0 = ptx::desc_sw128(a_hi, C::BOX, 1024);
           const uint64_t bdh0 = C::CONV ? ptx::desc_sw128(b_hi, 1024, C::SBO_B) : ptx::desc_sw128(b_hi, C::BOX, 1024);
@@ -442,7 +445,7 @@ __global__ void __launch_bounds__(Cfg<MODE, MH, NACC>::THREADS, 1)
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk) {
             const uint64_t bdh = ptx::desc_advance(bdh0, kk * B_KSTEP);
-            const uint64_t bdl = ptx::desc_advance(bdh, C::B_BYTES);
+            const uint64_t bdl = ptx::desc_advance(bdh, C::SHARE_B ? C::A_BYTES : C::B_BYTES);
 #pragma unroll
             for (int h = 0; h < MH; ++h) {
               const uint32_t d = tmem + (uint32_t)(ab * C::ACC_COLS + h * C::BN);
@@ -554,8 +557,9 @@ __global__ void __launch_bounds__(Cfg<MODE, MH, NACC>::THREADS, 1)
 }
 
 // about four units per CTA, chunks of >= 512 rows, a multiple of BK rows
-void choose_chunks(int64_t m, int tiles, int num_sms, int& chunks, int64_t& rows) {
-  int64_t c = (4LL * num_sms + tiles - 1) / tiles;
+// About `per_sm` units per SM (tiles x chunks), chunks of at least 512 rows.
+void choose_chunks(int64_t m, int tiles, int num_sms, int& chunks, int64_t& rows, int per_sm = 4) {
+  int64_t c = ((int64_t)per_sm * num_sms + tiles - 1) / tiles;
   const int64_t cmax = (m + 511) / 512;
   if (c > cmax) c = cmax;
   if (c < 1) c = 1;
@@ -588,7 +592,9 @@ template <int MODE>
 bool launch_k(Launcher& L, int k, const CUtensorMap& ahi, const CUtensorMap& alo, const CUtensorMap& bhi,
               const CUtensorMap& blo, const Params& p) {
   if (k > 128) return launch<MODE, 2, 1>(L, ahi, alo, bhi, blo, p);
-  return launch<MODE, 1, 1>(L, ahi, alo, bhi, blo, p);
+  // the Gram's 128-column tile leaves TMEM room for a second accumulator
+  if constexpr (MODE == M_GRAM) return launch<MODE, 1, 2>(L, ahi, alo, bhi, blo, p);
+  else return launch<MODE, 1, 1>(L, ahi, alo, bhi, blo, p);
 }
 
 int64_t pitch16(int k) { return ((int64_t)k + 7) / 8 * 8; }
@@ -622,7 +628,9 @@ void plan_tc_chain(char* base, TcChainWs& w, int xt, int64_t m, int64_t n, int k
     const int gt = (k + BN - 1) / BN;
     int gc;
     int64_t grows;
-    pf::choose_chunks(m, gt, num_sms, gc, grows);
+    // one unit per SM: the Gram has a single tile, so short chunks would each
+    // pay the pipeline's fill and drain and write a k x k partial
+    pf::choose_chunks(m, gt, num_sms, gc, grows, 1);
     w.gchunks = gc;
     w.grows_per_chunk = grows;
     w.Gpart = (double*)take((size_t)gc * k * k * 4);

@@ -480,6 +480,8 @@ __global__ void reduce_f32_parts_kernel(const float* __restrict__ part, int chun
   if (gate && *gate == 0) return;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
     float s = 0.f, c = 0.f;
+    // unrolled so the independent loads run ahead of the dependent adds
+#pragma unroll 8
     for (int q = 0; q < chunks; ++q) {
       const float x = part[(int64_t)q * count + e];
       const float t = s + x;
