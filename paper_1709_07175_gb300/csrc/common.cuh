@@ -19,6 +19,17 @@ enum : int {
   ST_BADINDEX = 8,    // a sparse X's column index outside [0, n)
 };
 
+// Programmatic dependent launch.  A kernel launched with launch_pdl is set up
+// by the GPU while its predecessor in the stream still runs and starts as the
+// predecessor ends; pdl_wait blocks until the predecessor has completed and
+// its writes are visible.  Every such kernel calls pdl_wait first and
+// unconditionally (also on paths that return early), so completion stays
+// ordered along the chain: kernel i ends only after kernel i - 1 ended.
+// (Letting successors be scheduled early with griddepcontrol.launch_dependents
+// was slower: their waiting CTAs took SMs from the running kernels.)  A no-op
+// for a kernel launched without PDL.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Element access: every X element type decodes exactly to float (F32/BF16/E4M3)
 // or double (F64).
 template <int DT> struct XType;

@@ -95,6 +95,7 @@ template <int NC>
 __global__ void __launch_bounds__(4 * NC, 1) seed_tri_kernel(const double* __restrict__ M, int k, int level,
                                                             int32_t* lvl, float* __restrict__ gV,
                                                             float* __restrict__ tri, double* scal) {
+  pdl_wait();  // first, on every path: completion stays ordered along the chain
   using C = TriCfg<NC>;
   constexpr int NR = C::NR, NRR = C::NRR, NRS = C::NRS, GW = C::GW;
   extern __shared__ __align__(16) float sm[];
@@ -368,6 +369,7 @@ __global__ void __launch_bounds__(4 * NC, 1) seed_tri_kernel(const double* __res
 // 2. Eigenvalues of T, ascending: one warp per eigenvalue idx.
 __global__ void __launch_bounds__(128) seed_bisect_kernel(int k, int level, const int32_t* __restrict__ lvl,
                                                           float* tri) {
+  pdl_wait();  // first, on every path: completion stays ordered along the chain
   const int s = level_size(lvl, level, k);
   if (level > 0 && s < 2) return;
   __shared__ float d[256], e2[256];
@@ -414,6 +416,7 @@ constexpr int kIIThreads = 32;
 
 __global__ void __launch_bounds__(kIIThreads) seed_ii_kernel(int k, int level, const int32_t* __restrict__ lvl,
                                                              const float* __restrict__ tri, float* __restrict__ Zc) {
+  pdl_wait();  // first, on every path: completion stays ordered along the chain
   const int s = level_size(lvl, level, k);
   if (level > 0 && s < 2) return;
   extern __shared__ float zsm[];
@@ -553,6 +556,7 @@ __global__ void __launch_bounds__(kOrthThreads, 1) seed_orth_kernel(int k, int l
                                                                    const float* __restrict__ tri, float* Zc,
                                                                    float* U, float* Wk, int32_t* stats,
                                                                    int32_t* cid) {
+  pdl_wait();  // first, on every path: completion stays ordered along the chain
   const int s = level_size(lvl, level, k);
   if (level > 0 && s < 2) return;
   __shared__ float lam[256];
@@ -630,6 +634,7 @@ __global__ void __launch_bounds__(kBackWarps * 32) seed_back_kernel(int k, int l
                                                                     const float* __restrict__ tri,
                                                                     double* __restrict__ Xout,
                                                                     double* __restrict__ lam_out) {
+  pdl_wait();  // first, on every path: completion stays ordered along the chain
   const int s = level_size(lvl, level, k);
   if (level > 0 && s < 2) return;
   extern __shared__ __align__(16) float P[];  // packed reflectors
@@ -681,7 +686,7 @@ static void launch_tri(Launcher& L, const double* M, int k, int level, int32_t* 
                        double* scal) {
   const size_t smem = (size_t)TriCfg<NC>::SMEM_FLOATS * sizeof(float);
   cudaFuncSetAttribute(seed_tri_kernel<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  seed_tri_kernel<NC><<<1, TriCfg<NC>::THREADS, smem, L.stream>>>(M, k, level, lvl, gV, tri, scal);
+  launch_pdl(L, seed_tri_kernel<NC>, dim3(1), dim3(TriCfg<NC>::THREADS), smem, M, k, level, lvl, gV, tri, scal);
 }
 
 void launch_seed_level(Launcher& L, const double* M, int k, int level, int32_t* lvl, float* gV, float* Zc, float* U,
@@ -691,15 +696,14 @@ void launch_seed_level(Launcher& L, const double* M, int k, int level, int32_t* 
     launch_tri<128>(L, M, k, level, lvl, gV, tri, scal);
   else
     launch_tri<256>(L, M, k, level, lvl, gV, tri, scal);
-  seed_bisect_kernel<<<(k + 3) / 4, 128, 0, L.stream>>>(k, level, lvl, tri);
+  launch_pdl(L, seed_bisect_kernel, dim3((k + 3) / 4), dim3(128), 0, k, level, lvl, tri);
   const size_t sii = (size_t)2 * 33 * 256 * sizeof(float);
   cudaFuncSetAttribute(seed_ii_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sii);
-  seed_ii_kernel<<<(k + kIIThreads - 1) / kIIThreads, kIIThreads, sii, L.stream>>>(k, level, lvl, tri, Zc);
-  seed_orth_kernel<<<1, kOrthThreads, 0, L.stream>>>(k, level, lvl, tri, Zc, U, Wk, stats, cid);
+  launch_pdl(L, seed_ii_kernel, dim3((k + kIIThreads - 1) / kIIThreads), dim3(kIIThreads), sii, k, level, lvl, tri, Zc);
+  launch_pdl(L, seed_orth_kernel, dim3(1), dim3(kOrthThreads), 0, k, level, lvl, tri, Zc, U, Wk, stats, cid);
   const size_t sback = (size_t)((k * (k - 1)) / 2 + 4) * sizeof(float);
   cudaFuncSetAttribute(seed_back_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sback);
-  seed_back_kernel<<<(k + kBackWarps - 1) / kBackWarps, kBackWarps * 32, sback, L.stream>>>(k, level, lvl, gV, Zc,
-                                                                                            tri, Xout, lam);
+  launch_pdl(L, seed_back_kernel, dim3((k + kBackWarps - 1) / kBackWarps), dim3(kBackWarps * 32), sback, k, level, lvl, gV, Zc, tri, Xout, lam);
   L.count(5);
 }
 

@@ -16,6 +16,23 @@ struct Launcher {
   void count(int n) { *counter += n; }
 };
 
+// Launch with programmatic stream serialization (the kernel must start with
+// pdl_wait(); see common.cuh): its launch overlaps the predecessor's run.
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(Launcher& L, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = L.stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 // ---- K0: Omega ------------------------------------------------------------
 void launch_omega_dense(Launcher& L, const lspca_omega& om, int64_t n, int k, int out_dt, void* out, int64_t ld,
                         bool transposed, bool bf16_round);

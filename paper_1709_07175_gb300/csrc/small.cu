@@ -95,6 +95,7 @@ __device__ double block_sum(double v, double* red) {
 // the kernel leaves its outputs as they are.
 __global__ void rayleigh_kernel(const double* __restrict__ Rm, const double* __restrict__ S, int k, double* lam,
                                 const int32_t* act) {
+  pdl_wait();  // first, on every path: completion stays ordered along the chain
   if (act && *act < 2) return;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x)
     lam[i] = S[(int64_t)i * k + i] / Rm[(int64_t)i * k + i];
@@ -124,6 +125,7 @@ __device__ __forceinline__ int rr_cluster(const int32_t* __restrict__ cid, int k
 // FP64 they may well be distinct.
 __global__ void __launch_bounds__(32) cluster_rr_kernel(const double* __restrict__ S, const int32_t* __restrict__ cid,
                                                         int k, double* __restrict__ Zr, const int32_t* act) {
+  pdl_wait();  // first, on every path: completion stays ordered along the chain
   if (act && *act < 2) return;
   const int c = blockIdx.x, lane = threadIdx.x;
   int i0 = 0;
@@ -210,6 +212,7 @@ __global__ void __launch_bounds__(32) cluster_rr_kernel(const double* __restrict
 __global__ void cluster_rotate_kernel(double* __restrict__ X, double* __restrict__ A1, double* __restrict__ A2,
                                       const int32_t* __restrict__ cid, const double* __restrict__ Zr, int k,
                                       const int32_t* act) {
+  pdl_wait();  // first, on every path: completion stays ordered along the chain
   if (act && *act < 2) return;
   double* M = blockIdx.y == 0 ? X : (blockIdx.y == 1 ? A1 : A2);
   if (!M) return;
@@ -235,6 +238,7 @@ __global__ void cluster_rotate_kernel(double* __restrict__ X, double* __restrict
 __global__ void cluster_rotate_rows_kernel(double* __restrict__ A1, double* __restrict__ A2,
                                            const int32_t* __restrict__ cid, const double* __restrict__ Zr, int k,
                                            const int32_t* act) {
+  pdl_wait();  // first, on every path: completion stays ordered along the chain
   if (act && *act < 2) return;
   double* M = blockIdx.y == 0 ? A1 : A2;
   const int col = blockIdx.x;
@@ -272,6 +276,7 @@ __global__ void cluster_rotate_rows_kernel(double* __restrict__ A1, double* __re
 __global__ void refine_e_kernel(const double* __restrict__ Rm, const double* __restrict__ S,
                                 const double* __restrict__ scal, const int32_t* __restrict__ cid, int k,
                                 double* __restrict__ E, const int32_t* act) {
+  pdl_wait();  // first, on every path: completion stays ordered along the chain
   if (act && *act < 2) return;
   const int i = blockIdx.x;
   const double noise = 64.0 * 0x1p-52 * scal[1];
@@ -308,6 +313,7 @@ __global__ void refine_e_kernel(const double* __restrict__ Rm, const double* __r
 // exactly diagonalising W this is the paper's D^-1.
 __global__ void sort_rank_kernel(const double* __restrict__ lam, const double* __restrict__ S, int k, int64_t m,
                                  int64_t n, double* __restrict__ sigma, int32_t* rank, double* scal) {
+  pdl_wait();  // first, on every path: completion stays ordered along the chain
   __shared__ double key[256];
   __shared__ int src[256];
   __shared__ double wmax[32];
@@ -372,6 +378,7 @@ __global__ void sort_rank_kernel(const double* __restrict__ lam, const double* _
 __global__ void ws_tinv_kernel(const double* __restrict__ W, const double* __restrict__ S,
                                const double* __restrict__ scal, int k, double* __restrict__ Ws,
                                double* __restrict__ Tinv) {
+  pdl_wait();  // first, on every path: completion stays ordered along the chain
   const int a = blockIdx.x;
   const int32_t* src = reinterpret_cast<const int32_t*>(scal + 8 + 2 * k);
   const double* sd = scal + 8 + k;
@@ -391,6 +398,7 @@ __global__ void ws_tinv_kernel(const double* __restrict__ W, const double* __res
 // Sign rule and FP32 output: one block per column of Vd (n x k FP64).
 template <typename VT>
 __global__ void finalize_v_kernel(const double* __restrict__ Vd, int64_t n, int k, VT* __restrict__ V) {
+  pdl_wait();  // first, on every path: completion stays ordered along the chain
   __shared__ double bv[32];
   __shared__ int64_t bi[32];
   __shared__ double sgn_s;
@@ -501,12 +509,14 @@ __device__ __forceinline__ void dgemm_tile_body(const DgemmArgs& g, int z) {
 // blockIdx.z: the K split.
 template <int TM, int TN, int KS>
 __global__ void __launch_bounds__(TM* TN) dgemm_tile_kernel(const DgemmArgs g) {
+  pdl_wait();  // first, on every path: completion stays ordered along the chain
   dgemm_tile_body<TM, TN, KS>(g, blockIdx.z);
 }
 
 // Two independent products in one launch (blockIdx.z selects), K unsplit.
 template <int TM, int TN, int KS>
 __global__ void __launch_bounds__(TM* TN) dgemm_pair_kernel(const DgemmArgs g0, const DgemmArgs g1) {
+  pdl_wait();  // first, on every path: completion stays ordered along the chain
   dgemm_tile_body<TM, TN, KS>(blockIdx.z == 0 ? g0 : g1, 0);
 }
 
@@ -537,7 +547,7 @@ static DgemmArgs dargs(int64_t M, int64_t N, int64_t K, const double* A, int64_t
 // Both products are M x N.
 static void dgemm2(Launcher& L, const DgemmArgs& g0, const DgemmArgs& g1) {
   dim3 grid((unsigned)((g0.M + 7) / 8), (unsigned)((g0.N + 7) / 8), 2);
-  dgemm_pair_kernel<8, 8, 64><<<grid, 64, 0, L.stream>>>(g0, g1);
+  launch_pdl(L, dgemm_pair_kernel<8, 8, 64>, dim3(grid), dim3(64), 0, g0, g1);
   L.count(1);
 }
 
@@ -547,7 +557,7 @@ static void dgemm(Launcher& L, int64_t M, int64_t N, int64_t K, const double* A,
   dim3 grid((unsigned)((M + 7) / 8), (unsigned)((N + 7) / 8), 1);
   DgemmArgs g = dargs(M, N, K, A, lda, at, B, ldb, bt, C, ldc, Cin, act, dflt);
   g.sym = sym ? 1 : 0;
-  dgemm_tile_kernel<8, 8, 64><<<grid, 64, 0, L.stream>>>(g);
+  launch_pdl(L, dgemm_tile_kernel<8, 8, 64>, dim3(grid), dim3(64), 0, g);
   L.count(1);
 }
 
@@ -567,7 +577,7 @@ void launch_decompose(Launcher& L, SmallWs& w, const double* F, int k, int64_t n
     g.c_split_stride = kk;
     g.kchunk = kchunk;
     g.sym = 1;
-    dgemm_tile_kernel<16, 16, 64><<<grid, 256, 0, L.stream>>>(g);
+    launch_pdl(L, dgemm_tile_kernel<16, 16, 64>, dim3(grid), dim3(256), 0, g);
     L.count(1);
   }
   launch_reduce_splits(L, w.Hpart, w.h_splits, kk, kk, w.H);
@@ -598,19 +608,19 @@ void launch_decompose(Launcher& L, SmallWs& w, const double* F, int k, int64_t n
       if (it == kRefineIters) {
         // last pass: a final Rayleigh-Ritz rotation of the small clusters,
         // applied to X, S and X^T X alike (B^T S B), then lambda
-        cluster_rr_kernel<<<k, 32, 0, L.stream>>>(w.S, w.cid, k, w.T, act);
-        cluster_rotate_kernel<<<dim3(k, 3), 64, 0, L.stream>>>(X, w.S, w.Rm, w.cid, w.T, k, act);
-        cluster_rotate_rows_kernel<<<dim3(k, 2), 64, 0, L.stream>>>(w.S, w.Rm, w.cid, w.T, k, act);
-        rayleigh_kernel<<<1, 256, 0, L.stream>>>(w.Rm, w.S, k, w.lam, act);
+        launch_pdl(L, cluster_rr_kernel, dim3(k), dim3(32), 0, w.S, w.cid, k, w.T, act);
+        launch_pdl(L, cluster_rotate_kernel, dim3(k, 3), dim3(64), 0, X, w.S, w.Rm, w.cid, w.T, k, act);
+        launch_pdl(L, cluster_rotate_rows_kernel, dim3(k, 2), dim3(64), 0, w.S, w.Rm, w.cid, w.T, k, act);
+        launch_pdl(L, rayleigh_kernel, dim3(1), dim3(256), 0, w.Rm, w.S, k, w.lam, act);
         L.count(4);
         break;
       }
       // T (H X) is free once S is formed: it holds the clusters' Rayleigh-Ritz vectors
-      cluster_rr_kernel<<<k, 32, 0, L.stream>>>(w.S, w.cid, k, w.T, act);
-      refine_e_kernel<<<k, 128, 0, L.stream>>>(w.Rm, w.S, w.scal, w.cid, k, w.E, act);
+      launch_pdl(L, cluster_rr_kernel, dim3(k), dim3(32), 0, w.S, w.cid, k, w.T, act);
+      launch_pdl(L, refine_e_kernel, dim3(k), dim3(128), 0, w.Rm, w.S, w.scal, w.cid, k, w.E, act);
       L.count(2);
       dgemm(L, k, k, k, X, k, false, w.E, k, false, Xn, k, X, act, X);  // X + X E
-      cluster_rotate_kernel<<<dim3(k, 1), 64, 0, L.stream>>>(Xn, nullptr, nullptr, w.cid, w.T, k, act);
+      launch_pdl(L, cluster_rotate_kernel, dim3(k, 1), dim3(64), 0, Xn, nullptr, nullptr, w.cid, w.T, k, act);
       L.count(1);
       double* t = X;
       X = Xn;
@@ -618,8 +628,8 @@ void launch_decompose(Launcher& L, SmallWs& w, const double* F, int k, int64_t n
     }
   }
   // order, rank rule, Ws and Tinv (S of the final X is in w.S)
-  sort_rank_kernel<<<1, 256, 0, L.stream>>>(w.lam, w.S, k, m, n, sigma, rank, w.scal);
-  ws_tinv_kernel<<<k, 128, 0, L.stream>>>(X, w.S, w.scal, k, w.T, w.E);
+  launch_pdl(L, sort_rank_kernel, dim3(1), dim3(256), 0, w.lam, w.S, k, m, n, sigma, rank, w.scal);
+  launch_pdl(L, ws_tinv_kernel, dim3(k), dim3(128), 0, X, w.S, w.scal, k, w.T, w.E);
   L.count(2);
   dgemm(L, k, k, k, w.T, k, false, w.E, k, false, w.Rm, k);  // Ws Tinv
   // V = F^T (Ws Tinv)  (n x k): FP64 for an FP64 V; for an FP32 V (the result
@@ -631,9 +641,9 @@ void launch_decompose(Launcher& L, SmallWs& w, const double* F, int k, int64_t n
   else
     launch_gemm_simt(L, n, k, k, F, LSPCA_F64, n, true, w.Rm, LSPCA_F64, k, false, w.Vd, true, k, 0, 1, false, false);
   if (v_f64)
-    finalize_v_kernel<double><<<k, 256, 0, L.stream>>>(w.Vd, n, k, (double*)V);
+    launch_pdl(L, finalize_v_kernel<double>, dim3(k), dim3(256), 0, w.Vd, n, k, (double*)V);
   else
-    finalize_v_kernel<float><<<k, 256, 0, L.stream>>>(w.Vd, n, k, (float*)V);
+    launch_pdl(L, finalize_v_kernel<float>, dim3(k), dim3(256), 0, w.Vd, n, k, (float*)V);
   L.count(1);
 }
 
