@@ -577,8 +577,10 @@ def measure_sparse(L, S, torch, local, stream):
 
 def measure_e2e(L, torch, w, X, ctx, stream, reps):
     """The headline step end to end through the public API with host buffers:
-    X copied from pinned host memory, the fit and the reduction map of every
-    row, then V, sigma and Y copied back."""
+    lspca_fit_project_host streams X from pinned host memory into device
+    memory while the slices already copied are sketched and folded into F
+    (Alg. 4), runs the k x k step, and projects every row slice by slice while
+    the previous slice of Y is copied back; then V and sigma are copied back."""
     dev = X.device
     Xh = torch.empty(X.shape, dtype=X.dtype, pin_memory=True)
     Xh.copy_(X)
@@ -586,30 +588,25 @@ def measure_e2e(L, torch, w, X, ctx, stream, reps):
     V = torch.empty(w.n, w.k, dtype=torch.float32, device=dev)
     sig = torch.empty(w.k, dtype=torch.float64, device=dev)
     rk = torch.empty(1, dtype=torch.int32, device=dev)
-    Y = torch.empty(w.m, w.k, dtype=torch.float32, device=dev)
     Vh = torch.empty(V.shape, dtype=V.dtype, pin_memory=True)
     sh = torch.empty(sig.shape, dtype=sig.dtype, pin_memory=True)
-    Yh = torch.empty(Y.shape, dtype=Y.dtype, pin_memory=True)
+    Yh = torch.empty((w.m, w.k), dtype=torch.float32, pin_memory=True)
 
     def step():
-        X.copy_(Xh, non_blocking=True)
-        rc = L.lspca_fit(ctx.handle, X, w.k, om, 0, V, sig, None, rk, stream)
+        rc = L.lspca_fit_project_host(ctx.handle, Xh, w.k, om, 0, 0, X, V, sig, Yh, rk, stream)
         if rc != L.OK:
-            raise L.LspcaError(rc, "lspca_fit")
-        rc = L.lspca_project(ctx.handle, X, V, w.k, Y, stream)
-        if rc != L.OK:
-            raise L.LspcaError(rc, "lspca_project")
+            raise L.LspcaError(rc, "lspca_fit_project_host")
         Vh.copy_(V, non_blocking=True)
         sh.copy_(sig, non_blocking=True)
-        Yh.copy_(Y, non_blocking=True)
     h2d_ms = _time(torch, stream, lambda: X.copy_(Xh, non_blocking=True), 1)
     ms = _time(torch, stream, step, reps)
     xb = Xh.numel() * Xh.element_size()
     out = {"value": w.m / (ms / 1e3), "unit": "samples/s", "h2d_bytes_per_step": xb,
            "d2h_bytes_per_step": Vh.numel() * 4 + sh.numel() * 8 + Yh.numel() * 4, "ms_per_step": ms,
-           "api": "lspca_fit + lspca_project, X from pinned host memory, V / sigma / Y back to pinned host memory",
+           "api": "lspca_fit_project_host (X from pinned host memory, Y to pinned host memory), then V and sigma "
+                  "copied back",
            "h2d_copy_ms": h2d_ms, "h2d_copy_gbs": xb / (h2d_ms / 1e3) / 1e9}
-    del Xh, Yh, Y
+    del Xh, Yh
     return out
 
 

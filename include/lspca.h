@@ -233,6 +233,27 @@ int lspca_fit_host(lspca_ctx* ctx, const void* Xh, int32_t xt, int64_t m, int64_
                    lspca_omega om, uint32_t flags, int64_t slice_rows, void* V, double* sigma, int32_t* rank,
                    void* stream, lspca_report* rep);
 
+/* Fit and reduction map of a host-resident X in one call, the whole step of
+ * Experiment 1 from host memory (Algorithm 4 for the fit, Sec. III-B.2 for
+ * Y = X V): X is copied in row slices on a second stream into Xd while each
+ * slice already copied is sketched and folded into F, as in lspca_fit_host;
+ * after the k x k step, Y is computed slice by slice (slices of about 128 MB
+ * of Y) into two device staging buffers, and each slice is copied back into
+ * Yh while the next one is projected.
+ * Xh [host] m x n (xt F32, BF16 or E4M3; pinned memory for overlapped
+ * copies), ldx as in lspca_fit; Xd [dev] m x ldx elements of xt, 16-byte
+ * aligned, owned by the caller, receives X (and keeps it); V [dev] n x k FP32,
+ * sigma [dev] k FP64, rank [dev] nullable, outputs as in lspca_fit; Yh [host]
+ * m x k FP32 output (pinned memory for overlapped copies).  k a multiple of 4,
+ * slice_rows and flags as lspca_fit_host.  Everything is asynchronous on
+ * `stream`: Yh is complete when the stream has completed.  With rep, ms_qr
+ * holds the time of the reduction map and its copies.
+ * Errors: as lspca_fit_host; LSPCA_ERR_INVALID also for NULL Xd or Yh or a
+ * misaligned Xd.                                                           */
+int lspca_fit_project_host(lspca_ctx* ctx, const void* Xh, int32_t xt, int64_t m, int64_t n, int64_t ldx, int32_t k,
+                           lspca_omega om, uint32_t flags, int64_t slice_rows, void* Xd, void* V, double* sigma,
+                           int32_t* rank, float* Yh, void* stream, lspca_report* rep);
+
 /* Reduction map pi(x) = V^T x for every row: Y = X V (Sec. III-B.2).
  * X [dev] m x n (xt, ldx); V [dev] n x k and Y [dev] m x k (output), both
  * in the result type.  F32 X, k <= 128: X and V each split into three exact

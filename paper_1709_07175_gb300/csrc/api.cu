@@ -595,10 +595,18 @@ int lspca_fit_oversampled(lspca_ctx* ctx, const void* X, int32_t xt, int64_t m, 
   return st;
 }
 
-int lspca_fit_host(lspca_ctx* ctx, const void* Xh, int32_t xt, int64_t m, int64_t n, int64_t ldx, int32_t k,
-                   lspca_omega om, uint32_t flags, int64_t slice_rows, void* V, double* sigma, int32_t* rank,
-                   void* stream, lspca_report* rep) {
+namespace {
+// Algorithm 4 over a host-resident X (lspca_fit_host).  Xd (nullable): a
+// device buffer of m rows x ldx that receives the slices, so X stays resident
+// (no staging buffers); Yh (nullable, needs Xd): afterwards the reduction map
+// of every row, slice by slice into two device staging buffers, each slice
+// copied back into Yh on the copy stream while the next is projected.
+int fit_host_impl(lspca_ctx* ctx, const void* Xh, int32_t xt, int64_t m, int64_t n, int64_t ldx, int32_t k,
+                  lspca_omega om, uint32_t flags, int64_t slice_rows, void* V, double* sigma, int32_t* rank,
+                  void* stream, lspca_report* rep, void* Xd, float* Yh) {
   if (!ctx || !Xh || !V || !sigma) return LSPCA_ERR_INVALID;
+  if (Yh && !Xd) return LSPCA_ERR_INVALID;
+  if (Xd && ((uintptr_t)Xd & 15u)) return LSPCA_ERR_INVALID;
   if (xt != LSPCA_F32 && xt != LSPCA_BF16 && xt != LSPCA_E4M3) return LSPCA_ERR_INVALID;
   if (m < 1 || n < 1 || ldx < n || (ldx * (int64_t)dtype_size(xt)) % 16 != 0) return LSPCA_ERR_INVALID;
   int st;
@@ -618,13 +626,25 @@ int lspca_fit_host(lspca_ctx* ctx, const void* Xh, int32_t xt, int64_t m, int64_
   const int64_t nslices = (m + slice_rows - 1) / slice_rows;
   const bool exact = om.kind == LSPCA_OMEGA_VERY_SPARSE;
 
+  // projection slices: about 128 MB of Y each, whole 128-row tiles
+  int64_t proj_rows = (((int64_t)128 << 20) / ((int64_t)k * 4) + 127) / 128 * 128;
+  if (proj_rows > m) proj_rows = (m + 127) / 128 * 128;
   void *stage[2] = {nullptr, nullptr}, *U = nullptr, *omega_d = nullptr, *tiles = nullptr, *small = nullptr;
   float* scal = nullptr;
+  float* ystage[2] = {nullptr, nullptr};
   double* Facc = nullptr;
   char* chain_base = nullptr;
   TcChainWs cw_max;
+  TcProjectWs pw;
   auto plan = [&](Plan& P) {
-    for (auto& b : stage) b = P.take((size_t)slice_rows * (size_t)row_bytes);
+    if (!Xd)
+      for (auto& b : stage) b = P.take((size_t)slice_rows * (size_t)row_bytes);
+    if (Yh) {
+      for (auto& b : ystage) b = (float*)P.take((size_t)proj_rows * k * 4);
+      char* base = P.base ? P.base + ((P.off + 255) & ~(size_t)255) : nullptr;
+      plan_tc_project(base, pw, xt, n, k);
+      P.take(pw.bytes);
+    }
     U = P.take((size_t)slice_rows * k * 4);
     omega_d = P.take((size_t)n * k * 4);
     tiles = P.take(tc_tile_v_bytes(n, k));
@@ -662,20 +682,22 @@ int lspca_fit_host(lspca_ctx* ctx, const void* Xh, int32_t xt, int64_t m, int64_
     const int b = (int)(si & 1);
     const int64_t r0 = si * slice_rows;
     const int64_t rows = (r0 + slice_rows <= m) ? slice_rows : m - r0;
-    // Algorithm 4: copy slice si while the previous slice is computed
-    if (si >= 2) cudaStreamWaitEvent(ctx->cstream, ctx->consumed[b], 0);
-    if (cudaMemcpyAsync(stage[b], (const char*)Xh + r0 * row_bytes, (size_t)(rows * row_bytes),
-                        cudaMemcpyHostToDevice, ctx->cstream) != cudaSuccess)
+    // Algorithm 4: copy slice si while the previous slice is computed (into
+    // the resident X, or into the staging buffer the slice before last freed)
+    void* xs = Xd ? (void*)((char*)Xd + r0 * row_bytes) : stage[b];
+    if (!Xd && si >= 2) cudaStreamWaitEvent(ctx->cstream, ctx->consumed[b], 0);
+    if (cudaMemcpyAsync(xs, (const char*)Xh + r0 * row_bytes, (size_t)(rows * row_bytes), cudaMemcpyHostToDevice,
+                        ctx->cstream) != cudaSuccess)
       return LSPCA_ERR_CUDA;
     cudaEventRecord(ctx->copied[b], ctx->cstream);
     cudaStreamWaitEvent(s, ctx->copied[b], 0);
     // U_s = X_s Omega (max|X_s|, NaN / Inf, max|U_s| taken on the way); F += U_s^T X_s
     cudaMemsetAsync(ctx->d_absmax, 0, 2 * sizeof(float), s);
-    tc_project_pretiled(L, stage[b], xt, rows, n, ldx, tiles, scal + 1, k, (float*)U, ctx->d_status, exact,
+    tc_project_pretiled(L, xs, xt, rows, n, ldx, tiles, scal + 1, k, (float*)U, ctx->d_status, exact,
                         ctx->d_absmax, ctx->d_absmax + 1);
     TcChainWs cw;
     plan_tc_chain(chain_base, cw, xt, rows, n, k, false, ctx->num_sms);
-    if (!tc_chain_main(L, stage[b], xt, rows, n, ldx, (const float*)U, k, cw, ctx->d_absmax, ctx->d_status, false))
+    if (!tc_chain_main(L, xs, xt, rows, n, ldx, (const float*)U, k, cw, ctx->d_absmax, ctx->d_status, false))
       return LSPCA_ERR_CUDA;
     tc_chain_reduce(L, n, k, cw, Facc, nullptr, si > 0);
     cudaEventRecord(ctx->consumed[b], s);
@@ -684,6 +706,34 @@ int lspca_fit_host(lspca_ctx* ctx, const void* Xh, int32_t xt, int64_t m, int64_
   int32_t* rk = rank ? rank : ctx->d_rank;
   launch_decompose(L, sw, Facc, k, n, m, false, V, sigma, rk, ctx->d_status);
   if (rep) cudaEventRecord(ctx->ev[4], s);
+  if (Yh) {
+    // Y = X V slice by slice; slice q is copied back on the copy stream while
+    // slice q + 1 is projected (two staging buffers)
+    const bool pre = tc_xproj_tile_v(L, xt, (const float*)V, n, k, pw, ctx->d_status);
+    const int64_t npslices = (m + proj_rows - 1) / proj_rows;
+    for (int64_t q = 0; q < npslices; ++q) {
+      const int b = (int)(q & 1);
+      const int64_t r0 = q * proj_rows;
+      const int64_t rows = (r0 + proj_rows <= m) ? proj_rows : m - r0;
+      const void* xs = (const char*)Xd + r0 * row_bytes;
+      if (q >= 2) cudaStreamWaitEvent(s, ctx->consumed[b], 0);  // staging buffer b copied out
+      if (!(pre && tc_xproj(L, xs, xt, rows, n, ldx, pw.vhi, (const float*)pw.vlo + 1, k, false, ystage[b],
+                            ctx->d_status, nullptr, false))) {
+        if (pre) return LSPCA_ERR_CUDA;
+        tc_project(L, xs, xt, rows, n, ldx, (const float*)V, k, pw, ystage[b], ctx->d_status);
+      }
+      cudaEventRecord(ctx->copied[b], s);
+      cudaStreamWaitEvent(ctx->cstream, ctx->copied[b], 0);
+      if (cudaMemcpyAsync(Yh + r0 * k, ystage[b], (size_t)rows * k * 4, cudaMemcpyDeviceToHost, ctx->cstream) !=
+          cudaSuccess)
+        return LSPCA_ERR_CUDA;
+      cudaEventRecord(ctx->consumed[b], ctx->cstream);
+    }
+    // the caller's stream completes only after the last copy of Y
+    cudaEventRecord(ctx->consumed[0], ctx->cstream);
+    cudaStreamWaitEvent(s, ctx->consumed[0], 0);
+    if (rep) cudaEventRecord(ctx->ev[5], s);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return LSPCA_ERR_CUDA;
   if (!rep) return LSPCA_OK;
@@ -691,6 +741,7 @@ int lspca_fit_host(lspca_ctx* ctx, const void* Xh, int32_t xt, int64_t m, int64_
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return LSPCA_ERR_CUDA;
   rep->ms_chain = ev_ms(ctx->ev[0], ctx->ev[2]);  // copies, sketches and pass F of all slices
   rep->ms_small = ev_ms(ctx->ev[2], ctx->ev[4]);
+  if (Yh) rep->ms_qr = ev_ms(ctx->ev[4], ctx->ev[5]);  // the reduction map and the copies of Y
   rep->bytes_x = (double)m * n * dtype_size(xt);
   int32_t hr = 0, hst = 0, hsw = 0;
   cudaMemcpy(&hr, rk, 4, cudaMemcpyDeviceToHost);
@@ -707,6 +758,21 @@ int lspca_fit_host(lspca_ctx* ctx, const void* Xh, int32_t xt, int64_t m, int64_
   if (hst & ST_NUMERIC) return LSPCA_ERR_NUMERIC;
   if (hr < k) return LSPCA_WARN_RANK_DEFICIENT;
   return LSPCA_OK;
+}
+}  // namespace
+
+int lspca_fit_host(lspca_ctx* ctx, const void* Xh, int32_t xt, int64_t m, int64_t n, int64_t ldx, int32_t k,
+                   lspca_omega om, uint32_t flags, int64_t slice_rows, void* V, double* sigma, int32_t* rank,
+                   void* stream, lspca_report* rep) {
+  return fit_host_impl(ctx, Xh, xt, m, n, ldx, k, om, flags, slice_rows, V, sigma, rank, stream, rep, nullptr,
+                       nullptr);
+}
+
+int lspca_fit_project_host(lspca_ctx* ctx, const void* Xh, int32_t xt, int64_t m, int64_t n, int64_t ldx, int32_t k,
+                           lspca_omega om, uint32_t flags, int64_t slice_rows, void* Xd, void* V, double* sigma,
+                           int32_t* rank, float* Yh, void* stream, lspca_report* rep) {
+  if (!Xd || !Yh) return LSPCA_ERR_INVALID;
+  return fit_host_impl(ctx, Xh, xt, m, n, ldx, k, om, flags, slice_rows, V, sigma, rank, stream, rep, Xd, Yh);
 }
 
 int lspca_project(lspca_ctx* ctx, const void* X, int32_t xt, int64_t m, int64_t n, int64_t ldx, const void* V,

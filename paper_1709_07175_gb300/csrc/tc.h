@@ -86,6 +86,9 @@ void tc_project_batch(Launcher& L, int xt, int k, const TcProjUnit* d_units, con
 // Y sets ST_NONFINITE.  False (nothing launched) when X's alignment or pitch
 // does not allow the tensor map.
 bool tc_xproj_ok(const void* X, int xt, int64_t ldx, bool exact_v);
+// V split and tiled once (into w.vhi, its scale at w.vlo[1]) for several
+// tc_xproj launches over row ranges of one BF16 / E4M3 X; false for other types.
+bool tc_xproj_tile_v(Launcher& L, int xt, const float* V, int64_t n, int k, TcProjectWs& w, int* status);
 bool tc_xproj(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_t ldx, const void* vtiles,
               const float* vscale, int k, bool exact_v, float* Y, int* status, float* ymax, bool check_y);
 void tc_project(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_t ldx, const float* V, int k,

@@ -1176,6 +1176,22 @@ void tc_project(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_
   tcp::launch_xt(L, p, xt, npad / 64, 0, exact_v);
 }
 
+bool tc_xproj_tile_v(Launcher& L, int xt, const float* V, int64_t n, int k, TcProjectWs& w, int* status) {
+  if (xt != LSPCA_BF16 && xt != LSPCA_E4M3) return false;
+  const int npad = (k + 63) / 64 * 64;
+  float* scal = (float*)w.vlo;
+  const bool f16 = xt == LSPCA_E4M3;
+  cudaMemsetAsync(scal, 0, 8, L.stream);
+  if (f16) launch_scan_x(L, V, LSPCA_F32, n, k, k, scal, status);
+  const int64_t nks = (n + tcp::BK - 1) / tcp::BK;
+  const int64_t total = nks * tcp::BK * npad;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 16 * L.num_sms) blocks = 16 * L.num_sms;
+  tcp::tile_v_kernel<<<blocks, 256, 0, L.stream>>>(V, n, k, npad, f16 ? 1 : 0, scal, scal + 1, (uint8_t*)w.vhi);
+  L.count(1);
+  return true;
+}
+
 void tc_project_pretiled(Launcher& L, const void* X, int xt, int64_t m, int64_t n, int64_t ldx, const void* tiles,
                          const float* vscale, int k, float* Y, int* status, bool exact_v, float* xmax,
                          float* ymax) {

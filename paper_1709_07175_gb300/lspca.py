@@ -65,6 +65,8 @@ _SIGS = {
                                 ctypes.POINTER(lspca_report)]),
     "lspca_fit_host": (ctypes.c_int, [_P, _P, _I32, _I64, _I64, _I64, _I32, lspca_omega, _U32, _I64, _P, _P, _P,
                                       _P, ctypes.POINTER(lspca_report)]),
+    "lspca_fit_project_host": (ctypes.c_int, [_P, _P, _I32, _I64, _I64, _I64, _I32, lspca_omega, _U32, _I64, _P,
+                                              _P, _P, _P, _P, _P, ctypes.POINTER(lspca_report)]),
     "lspca_fit_oversampled": (ctypes.c_int, [_P, _P, _I32, _I64, _I64, _I64, _I32, _I32, lspca_omega, _U32, _P,
                                              _P, _P, _P, ctypes.POINTER(lspca_report)]),
     "lspca_fit_csr": (ctypes.c_int, [_P, _P, _P, _P, _I64, _I64, _I64, _I32, lspca_omega, _U32, _P, _P, _P, _P,
@@ -211,6 +213,15 @@ def spca_fit(ctx, X, k, om, flags, V, sigma, gram=None, rank=None, stream=None, 
     rp = ctypes.byref(report) if report is not None else None
     return load().spca_fit(ctx, x, xt, m, n, ldx, k, om, flags, _ptr(V), _ptr(sigma), _ptr(gram), _ptr(rank),
                            _stream(stream), rp)
+
+
+def lspca_fit_project_host(ctx, Xh, k, om, flags, slice_rows, Xd, V, sigma, Yh, rank=None, stream=None,
+                           report=None) -> int:
+    """Xh, Yh: CPU tensors (pinned for overlapped copies); Xd, V, sigma, rank: CUDA tensors."""
+    x, xt, m, n, ldx = _xargs(Xh)
+    rep = ctypes.byref(report) if report is not None else None
+    return load().lspca_fit_project_host(ctx, x, xt, m, n, ldx, k, om, flags, int(slice_rows), _ptr(Xd), _ptr(V),
+                                         _ptr(sigma), _ptr(rank), _ptr(Yh), _stream(stream), rep)
 
 
 def lspca_project(ctx, X, V, k, Y, stream=None) -> int:

@@ -103,3 +103,37 @@ def test_fit_host_invalid_and_nonfinite(ctx):
     rc = L.lspca_fit_host(ctx.handle, Xn.pin_memory(), w.k, _om(w), 0, 256, V, sig, None, None, rep)
     assert rc == L.ERR_NUMERIC
     assert ctx.sync_status() == L.OK
+
+
+@pytest.mark.parametrize("wname,m,n,k,slice_rows", [("e4m3_binary", 300_001, 512, 256, 65_536),
+                                                    ("bf16_dense", 20_000, 1024, 64, 6_000),
+                                                    ("fp32_sparse", 5_000, 1024, 128, 2_048)])
+def test_fit_project_host(ctx, wname, m, n, k, slice_rows):
+    """lspca_fit_project_host: the fit equals lspca_fit_host's bit for bit (the
+    same slices and kernels), X lands in the device buffer unchanged, and Y
+    (projected in slices of about 128 MB and copied back while the next slice
+    runs; three slices with a ragged last one at k = 256) matches the
+    reduction map of the whole resident X within 1e-6 of its norm."""
+    w = S.WORKLOADS[wname].scaled(m=m, n=n, k=k)
+    X = S.generate(w)
+    Xh = X.pin_memory()
+    om = _om(w)
+    ref = ctx.fit_host(Xh, w.k, om, slice_rows=slice_rows)
+    Xd = torch.empty(X.shape, dtype=X.dtype, device="cuda")
+    V = torch.empty(n, k, dtype=torch.float32, device="cuda")
+    sig = torch.empty(k, dtype=torch.float64, device="cuda")
+    rk = torch.empty(1, dtype=torch.int32, device="cuda")
+    Yh = torch.full((m, k), float("nan"), dtype=torch.float32).pin_memory()
+    rep = L.lspca_report()
+    rc = L.lspca_fit_project_host(ctx.handle, Xh, k, om, 0, slice_rows, Xd, V, sig, Yh, rk, report=rep)
+    assert rc == L.OK, L.lspca_strerror(rc)
+    torch.cuda.synchronize()
+    assert torch.equal(Xd.cpu().view(torch.uint8), X.view(torch.uint8))
+    assert torch.equal(V, ref.V) and torch.equal(sig, ref.sigma)
+    Yd = ctx.project(Xd, V)
+    torch.cuda.synchronize()
+    Yd = Yd.cpu()
+    assert torch.isfinite(Yh).all()
+    rel = ((Yh.double() - Yd.double()).norm() / Yd.double().norm()).item()
+    assert rel < 1e-6, rel
+    assert L.lspca_fit_project_host(ctx.handle, Xh, k, om, 0, slice_rows, None, V, sig, Yh, rk) == L.ERR_INVALID
