@@ -533,7 +533,11 @@ def measure_form(L, S, torch, name, stream, local, pk, reps, m=None, spca=False,
         out["kernels"] = {
             "sketch": roofline("sketch", per["sketch"], w.m * (w.n + w.k) * 4, 0, 1.0, pk, w.m, name),
             "chain_main": roofline("chain_main", per["chain_main"], w.m * (w.n + w.k) * 4, 0, 1.0, pk, w.m, name),
-            "project": roofline("project", proj_ms, w.m * (w.n + w.k) * 4, 0, 1.0, pk, w.m, name)}
+            # FP32 X against V split into three exact BF16 pieces: six products
+            # (k <= 128, n a multiple of 8), else three; tensor-bound at six
+            "project": roofline("project", proj_ms, w.m * (w.n + w.k) * 4,
+                                (6 if w.k <= 128 and w.n % 8 == 0 else 3) * 2.0 * w.m * w.n * w.k,
+                                pk["bf16_sustained"], pk, w.m, name)}
     if gram:
         G = torch.empty(w.k, w.k, dtype=torch.float64, device=dev)
         out["gram"] = {"ms_per_fit_on": _time(torch, stream, lambda: fit(L.WANT_GRAM, G), reps),

@@ -62,7 +62,9 @@ constexpr uint32_t A_BYTES = 128 * BK * 2;  // one A tile: 16 KB
 constexpr uint32_t RAW_BYTES = 128 * 128;   // one E4M3 box: 128 rows x 128 bytes (two k-steps)
 constexpr uint64_t kWaitNs = 2000000000ull;
 constexpr uint64_t kDrainNs = 100000000ull;
-constexpr int SEG = 8;                      // k-steps per accumulation segment
+// k-steps per accumulation segment: 8 where two accumulators alternate; 16
+// where one 256-column accumulator must wait for each fold's loads (k > 128)
+constexpr int SEG2 = 8, SEG1 = 16;
 constexpr int kSmemBudget = 220 * 1024;
 
 struct Params {
@@ -107,6 +109,7 @@ struct Cfg {
   static constexpr int B_STAGES_FIT = (int)((kSmemBudget - FIXED) / B_STAGE);
   static constexpr int B_STAGES = B_STAGES_FIT > 8 ? 8 : B_STAGES_FIT;
   static constexpr int NACC = NPAD <= 128 ? 2 : 1;
+  static constexpr int SEG = NACC == 2 ? SEG2 : SEG1;
   static constexpr uint32_t S_COL = NACC * NPAD;
   static constexpr uint32_t TMEM_COLS = S_COL + NPAD <= 256 ? 256 : 512;
   static constexpr int WCOLS = NPAD / 2;                     // columns folded per epilogue warp
@@ -372,7 +375,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Cfg<E4M3, NT, EXACT_
       bool ok = true;
       for (int64_t t0 = t0_first; t0 < p.tiles && ok; t0 += gridDim.x) {
         for (int ks = 0; ks < nks && ok; ++ks) {
-          const bool seg_start = (ks % SEG) == 0;
+          const bool seg_start = (ks % C::SEG) == 0;
           if (seg_start) {
             // the epilogue has read the segment that last used accumulator ab
             if (!wait_or_abort(&acce[ab], accph ^ 1u, abort, p.status)) {
@@ -416,7 +419,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Cfg<E4M3, NT, EXACT_
             as = 0;
             aph ^= 1u;
           }
-          if ((ks % SEG) == SEG - 1 || ks == nks - 1) {
+          if ((ks % C::SEG) == C::SEG - 1 || ks == nks - 1) {
             ptx::mma_commit(&accf[ab]);
             if (++ab == C::NACC) {
               ab = 0;
@@ -436,7 +439,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Cfg<E4M3, NT, EXACT_
     const uint32_t lane_base = (uint32_t)(32 * e) << 16;
     const float us = p.vscale ? 1.f / *p.vscale : 1.f;
     uint32_t yb = 0u;  // max|Y| written, as FP32 bits
-    const int nseg = (nks + SEG - 1) / SEG;
+    const int nseg = (nks + C::SEG - 1) / C::SEG;
     int64_t seg = 0;
     bool ok = true;
     for (int64_t t0 = t0_first; t0 < p.tiles && ok; t0 += gridDim.x) {
