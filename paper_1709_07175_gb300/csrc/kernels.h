@@ -115,6 +115,7 @@ void launch_csc_passf(Launcher& L, const CscView& c, int64_t n, int64_t nnz, con
 
 struct SmallWs {
   double* Hpart;   // splits x k x k
+  void* oz;        // workspace of the tensor-core H = F F^T (ozaki.cu)
   double* H;       // k x k
   float* h32;      // k x k: the seed's tridiagonalisation reflectors
   float* w32;      // k x k: the seed's eigenvectors of T (column-major)
@@ -129,6 +130,7 @@ struct SmallWs {
   double* lam;     // k
   double* scal;    // 8 scalars, sigma copy (k), sqrt(S_rr) (k), order (k int32)
   double* Vd;      // n x k
+  void* vaux;      // FP32 V: per-tile column maxima, column signs, tile counters
   int32_t* sweeps; // 1: levels of the graded eigen seed that ran
   int32_t* lvl;    // kSeedLevels + 1: block size of each seed level
   int32_t* cid;    // k: seed cluster of each eigenvector column (level * 1024 + cluster)
@@ -148,6 +150,11 @@ void launch_seed_level(Launcher& L, const double* M, int k, int level, int32_t* 
                        float* Wk, float* tri, double* Xout, double* lam, double* scal, int32_t* stats,
                        int32_t* cid);
 void carve_small_ws(SmallWs& w, void* base, int k, int64_t n);
+// H = F F^T (F k x n FP64, row-major; k <= 256) on the BF16 tensor cores from
+// exact digit planes of F, summed in integers (ozaki.cu): the FP64 result up
+// to one final rounding and digits below 2^-57 of each row's largest entry.
+size_t oz_gram_ws_bytes(int k, int64_t n);
+void launch_oz_gram(Launcher& L, const double* F, int k, int64_t n, void* ws, double* H, int* status);
 void launch_decompose(Launcher& L, SmallWs& w, const double* F, int k, int64_t n, int64_t m, bool v_f64, void* V,
                       double* sigma, int32_t* rank, int* status);
 

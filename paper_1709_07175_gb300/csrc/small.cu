@@ -23,6 +23,11 @@
 namespace lspca {
 
 constexpr int kRefineIters = 2;
+constexpr int kVT = 64;  // V tile of vprod_kernel (rows and columns)
+
+static size_t vaux_bytes(int k, int64_t n) {
+  return (size_t)((n + kVT - 1) / kVT) * k * 8 + 256 + (size_t)k * 4 + 256 + 64;
+}
 
 size_t small_ws_bytes(int k, int64_t n, int* h_splits) {
   int hs = (int)((n + 511) / 512);
@@ -32,16 +37,18 @@ size_t small_ws_bytes(int k, int64_t n, int* h_splits) {
   const size_t kk = (size_t)k * k;
   size_t b = 0;
   b += (size_t)hs * kk * 8;            // Hpart
+  b += oz_gram_ws_bytes(k, n);          // tensor-core H
   b += kk * 8;                          // H
   b += kk * 4 * 4;                      // seed scratch: reflectors, Z, pivots / Householder vectors, QR copy
   b += kk * 8 * 6;                      // Xa Xb Rm T S E
   b += (size_t)k * 8 + 64 + (size_t)k * 24;  // lam, scal (+ src, sd)
   b += (size_t)n * k * 8;               // Vd
+  b += vaux_bytes(k, n);                // V column maxima, signs, counters
   b += 64;                              // sweeps
   b += 64;                              // seed level sizes
   b += (size_t)k * 4;                   // seed cluster ids
   b += (size_t)k * 4 * 5 + 64;          // seed scratch: d, e, e^2, beta, eigenvalues of T, scalars
-  return b + 20 * 256;                  // alignment slack
+  return b + 24 * 256;                  // alignment slack
 }
 
 static char* align256(char* p) { return (char*)(((uintptr_t)p + 255) & ~(uintptr_t)255); }
@@ -54,6 +61,7 @@ void carve_small_ws(SmallWs& w, void* base, int k, int64_t n) {
   char* p = align256((char*)base);
   auto take = [&](size_t bytes) { char* r = p; p = align256(p + bytes); return r; };
   w.Hpart = (double*)take((size_t)hs * kk * 8);
+  w.oz = take(oz_gram_ws_bytes(k, n));
   w.H = (double*)take(kk * 8);
   w.h32 = (float*)take(kk * 4);
   w.w32 = (float*)take(kk * 4);
@@ -68,6 +76,7 @@ void carve_small_ws(SmallWs& w, void* base, int k, int64_t n) {
   w.lam = (double*)take((size_t)k * 8);
   w.scal = (double*)take(64 + (size_t)k * 24);
   w.Vd = (double*)take((size_t)n * k * 8);
+  w.vaux = take(vaux_bytes(k, n));
   w.sweeps = (int32_t*)take(64);
   w.lvl = (int32_t*)take(64);
   w.cid = (int32_t*)take((size_t)k * 4);
@@ -377,9 +386,11 @@ __global__ void sort_rank_kernel(const double* __restrict__ lam, const double* _
 // gaps).  For an exactly diagonalising W this is the paper's D^-1.
 __global__ void ws_tinv_kernel(const double* __restrict__ W, const double* __restrict__ S,
                                const double* __restrict__ scal, int k, double* __restrict__ Ws,
-                               double* __restrict__ Tinv) {
+                               double* __restrict__ Tinv, int* vcount) {
   pdl_wait();  // first, on every path: completion stays ordered along the chain
   const int a = blockIdx.x;
+  // the arrival counters of vprod_kernel's column tiles start each call at zero
+  if (vcount && a == 0 && threadIdx.x < (k + kVT - 1) / kVT) vcount[threadIdx.x] = 0;
   const int32_t* src = reinterpret_cast<const int32_t*>(scal + 8 + 2 * k);
   const double* sd = scal + 8 + k;
   const double sa = sd[a];
@@ -393,6 +404,123 @@ __global__ void ws_tinv_kernel(const double* __restrict__ W, const double* __res
     }
     Tinv[(int64_t)a * k + b] = t;
   }
+}
+
+// FP32 V = F^T M (F k x n FP64, M = Ws Tinv k x k FP64) with the sign rule,
+// in two launches.  vprod_kernel: one CTA per 64 x 64 tile of V; F^T and M
+// staged whole over K = k in shared memory as FP32, 4 x 4 outputs per thread,
+// products summed over 16-term slabs and the slab sums added to the running
+// sum (the rounding of the previous SIMT product).  The tile is written
+// unsigned, and each column's entry of largest magnitude over the tile (ties
+// to the lowest row) goes to a partial; the last CTA of a column tile to
+// arrive (a counter, zeroed by ws_tinv_kernel) reduces the partials of its
+// columns in row order and writes each column's sign.  vsign_kernel negates
+// the columns whose chosen entry is negative.
+struct ColMax {
+  float v;  // signed value of the largest-magnitude entry
+  int i;    // its row
+};
+
+__global__ void __launch_bounds__(256) vprod_kernel(const double* __restrict__ F, int64_t n, int k,
+                                                    const double* __restrict__ M, float* __restrict__ V,
+                                                    ColMax* __restrict__ part, int* vcount, float* __restrict__ sgn) {
+  pdl_wait();  // first, on every path: completion stays ordered along the chain
+  extern __shared__ float vsm[];
+  constexpr int LD = kVT + 4;
+  float* As = vsm;            // [k][LD]: As[q][r] = F[q][r0 + r]
+  float* Bs = vsm + k * LD;   // [k][LD]: Bs[q][c] = M[q][c0 + c]
+  __shared__ ColMax red[16][kVT];
+  __shared__ int last_s;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int64_t r0 = (int64_t)blockIdx.x * kVT;
+  const int c0 = blockIdx.y * kVT;
+  for (int e = tid; e < k * kVT; e += 256) {
+    const int q = e / kVT, r = e % kVT;
+    As[q * LD + r] = (r0 + r < n) ? (float)F[(int64_t)q * n + r0 + r] : 0.f;
+    Bs[q * LD + r] = (c0 + r < k) ? (float)M[(int64_t)q * k + c0 + r] : 0.f;
+  }
+  __syncthreads();
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  for (int q0 = 0; q0 < k; q0 += 16) {
+    float pt[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) pt[i][j] = 0.f;
+    const int qe = min(k, q0 + 16);
+    for (int q = q0; q < qe; ++q) {
+      const float4 a = *reinterpret_cast<const float4*>(As + q * LD + ty * 4);
+      const float4 b = *reinterpret_cast<const float4*>(Bs + q * LD + tx * 4);
+      const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) pt[i][j] = fmaf(av[i], bv[j], pt[i][j]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] += pt[i][j];
+  }
+  // write the tile; per column the largest |v| of this thread's rows
+  ColMax best[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) best[j] = ColMax{0.f, -1};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t gr = r0 + ty * 4 + i;
+    if (gr >= n) break;
+    const int gc = c0 + tx * 4;
+    if (gc + 4 <= k && (k & 3) == 0 && ((uintptr_t)V & 15) == 0) {
+      *reinterpret_cast<float4*>(V + gr * k + gc) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (gc + j < k) V[gr * k + gc + j] = acc[i][j];
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (best[j].i < 0 || fabsf(acc[i][j]) > fabsf(best[j].v)) best[j] = ColMax{acc[i][j], (int)gr};
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) red[ty][tx * 4 + j] = best[j];
+  __syncthreads();
+  if (tid < kVT) {
+    ColMax b{0.f, -1};
+    for (int y = 0; y < 16; ++y) {
+      const ColMax o = red[y][tid];
+      if (o.i >= 0 && (b.i < 0 || fabsf(o.v) > fabsf(b.v))) b = o;
+    }
+    if (c0 + tid < k) part[(int64_t)blockIdx.x * k + c0 + tid] = b;
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) last_s = atomicAdd(&vcount[blockIdx.y], 1) == (int)gridDim.x - 1;
+  __syncthreads();
+  if (!last_s) return;
+  __threadfence();
+  if (tid < kVT && c0 + tid < k) {
+    const int c = c0 + tid;
+    ColMax b{0.f, -1};
+    for (unsigned rt = 0; rt < gridDim.x; ++rt) {
+      const ColMax* pp = part + (int64_t)rt * k + c;
+      const ColMax o{__ldcg(&pp->v), __ldcg(&pp->i)};
+      if (o.i >= 0 && (b.i < 0 || fabsf(o.v) > fabsf(b.v))) b = o;
+    }
+    sgn[c] = (b.v < 0.f) ? -1.f : 1.f;
+  }
+}
+
+__global__ void __launch_bounds__(256) vsign_kernel(float* __restrict__ V, int64_t n, int k,
+                                                    const float* __restrict__ sgn) {
+  pdl_wait();  // first, on every path: completion stays ordered along the chain
+  const int64_t total = n * k;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+    if (sgn[e % k] < 0.f) V[e] = -V[e];
 }
 
 // Sign rule and FP32 output: one block per column of Vd (n x k FP64).
@@ -569,8 +697,12 @@ static DgemmArgs sym_args(DgemmArgs g) {
 void launch_decompose(Launcher& L, SmallWs& w, const double* F, int k, int64_t n, int64_t m, bool v_f64, void* V,
                       double* sigma, int32_t* rank, int* status) {
   const int64_t kk = (int64_t)k * k;
-  // H = F F^T in FP64, split over n, upper tiles mirrored, reduced in fixed order.
-  {
+  // H = F F^T.  FP32-class results (FP32 V): on the tensor cores from exact
+  // digit planes of F (ozaki.cu).  FP64 V: FP64 SIMT products split over n,
+  // upper tiles mirrored, reduced in fixed order.
+  if (!v_f64) {
+    launch_oz_gram(L, F, k, n, w.oz, w.H, status);
+  } else {
     const int64_t kchunk = ((n + w.h_splits - 1) / w.h_splits + 63) / 64 * 64;
     dim3 grid((unsigned)((k + 15) / 16), (unsigned)((k + 15) / 16), (unsigned)w.h_splits);
     DgemmArgs g = dargs(k, k, n, F, n, false, F, n, true, w.Hpart, k);
@@ -579,8 +711,8 @@ void launch_decompose(Launcher& L, SmallWs& w, const double* F, int k, int64_t n
     g.sym = 1;
     launch_pdl(L, dgemm_tile_kernel<16, 16, 64>, dim3(grid), dim3(256), 0, g);
     L.count(1);
+    launch_reduce_splits(L, w.Hpart, w.h_splits, kk, kk, w.H);
   }
-  launch_reduce_splits(L, w.Hpart, w.h_splits, kk, kk, w.H);
   // Graded eigensolve: level 0 seeds H; each later level seeds the tail block
   // of S = X^T H X left unresolved by the level before, and rotates those
   // columns of X; every level ends with the FP64 refinement.
@@ -629,22 +761,34 @@ void launch_decompose(Launcher& L, SmallWs& w, const double* F, int k, int64_t n
   }
   // order, rank rule, Ws and Tinv (S of the final X is in w.S)
   launch_pdl(L, sort_rank_kernel, dim3(1), dim3(256), 0, w.lam, w.S, k, m, n, sigma, rank, w.scal);
-  launch_pdl(L, ws_tinv_kernel, dim3(k), dim3(128), 0, X, w.S, w.scal, k, w.T, w.E);
+  // FP32 V: the fused product and sign rule (vprod_kernel, vsign_kernel)
+  const int nct = (k + kVT - 1) / kVT;
+  const int64_t nrt = (n + kVT - 1) / kVT;
+  ColMax* vpart = (ColMax*)w.vaux;
+  float* vsgn = (float*)((char*)w.vaux + ((nrt * k * 8 + 255) / 256) * 256);
+  int* vcount = (int*)((char*)vsgn + (((size_t)k * 4 + 255) / 256) * 256);
+  launch_pdl(L, ws_tinv_kernel, dim3(k), dim3(128), 0, X, w.S, w.scal, k, w.T, w.E, v_f64 ? nullptr : vcount);
   L.count(2);
   dgemm(L, k, k, k, w.T, k, false, w.E, k, false, w.Rm, k);  // Ws Tinv
   // V = F^T (Ws Tinv)  (n x k): FP64 for an FP64 V; for an FP32 V (the result
   // type of FP32 / BF16 / E4M3 X) an FP32 product of the FP64 factors rounded
   // to FP32, summed over K in 16-term slabs (relative error ~1e-7 of an
   // FP32-rounded result); the factorisation itself stays FP64
-  if (v_f64)
+  if (v_f64) {
     launch_gemm_simt(L, n, k, k, F, LSPCA_F64, n, true, w.Rm, LSPCA_F64, k, false, w.Vd, true, k, 0, 1, true, true);
-  else
-    launch_gemm_simt(L, n, k, k, F, LSPCA_F64, n, true, w.Rm, LSPCA_F64, k, false, w.Vd, true, k, 0, 1, false, false);
-  if (v_f64)
     launch_pdl(L, finalize_v_kernel<double>, dim3(k), dim3(256), 0, w.Vd, n, k, (double*)V);
-  else
-    launch_pdl(L, finalize_v_kernel<float>, dim3(k), dim3(256), 0, w.Vd, n, k, (float*)V);
-  L.count(1);
+    L.count(1);
+  } else {
+    const size_t smem = (size_t)2 * k * (kVT + 4) * sizeof(float);
+    cudaFuncSetAttribute(vprod_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    launch_pdl(L, vprod_kernel, dim3((unsigned)nrt, (unsigned)nct), dim3(256), smem, F, n, k, (const double*)w.Rm,
+               (float*)V, vpart, vcount, vsgn);
+    int blocks = (int)((n * k + 255) / 256);
+    if (blocks > 4 * L.num_sms) blocks = 4 * L.num_sms;
+    if (blocks < 1) blocks = 1;
+    launch_pdl(L, vsign_kernel, dim3(blocks), dim3(256), 0, (float*)V, n, k, (const float*)vsgn);
+    L.count(2);
+  }
 }
 
 }  // namespace lspca
