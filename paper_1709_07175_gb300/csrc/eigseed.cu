@@ -365,6 +365,234 @@ __global__ void __launch_bounds__(4 * NC, 1) seed_tri_kernel(const double* __res
   }
 }
 
+// Tridiagonalisation for blocks of at most 128 (k <= 128), the columns held
+// in registers: thread t owns column c = t / 2 and, of its row groups of four,
+// those of parity h = t & 1 (rows 8 i + 4 h .. 8 i + 4 h + 3).  A stays
+// symmetric under the two-sided update, so the next reflector's source row
+// j + 1 is column j + 1, which its two owners store from static registers;
+// their warp then forms the reflector for the whole CTA (the norm of the
+// tail, alpha, and the Householder vector v with the rows at or above j
+// zeroed), so no register is ever indexed at run time.  Per step: q = A u
+// over the active columns (u = v / |v|), u^T q (one block reduction),
+// w = 2 q - 2 (u^T q) u, and A -= u w^T + w u^T with two FMAs per entry;
+// three block barriers.  Outputs are those of seed_tri_kernel.
+constexpr int kTC = 256;
+
+__global__ void __launch_bounds__(kTC, 1) seed_tri_col_kernel(const double* __restrict__ M, int k, int level,
+                                                              int32_t* lvl, float* __restrict__ gV,
+                                                              float* __restrict__ tri, double* scal) {
+  pdl_wait();  // first, on every path: completion stays ordered along the chain
+  __shared__ __align__(16) float xs[2][128];  // v of the step (ping-pong)
+  __shared__ __align__(16) float ws[128];     // w of the step
+  __shared__ float invv_s[2];
+  __shared__ float red[8];
+  __shared__ float dv[128], ev[128], bv[128];
+  __shared__ double redd[8];
+  __shared__ double hmax_s;
+
+  const int s = level_size(lvl, level, k);
+  if (level > 0 && s < 2) return;  // uniform: nothing to resolve at this level
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int c = tid >> 1, h = tid & 1;
+  if (level == 0 && tid < 3) lvl[1 + tid] = 0;
+
+  // scale by 1 / max |M_ii| over the block; ||H||_F at level 0 (refinement noise floor)
+  {
+    double mx = 0.0;
+    for (int i = tid; i < s; i += kTC) mx = fmax(mx, fabs(M[(int64_t)i * k + i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) redd[warp] = mx;
+    __syncthreads();
+    if (tid == 0) {
+      double m2 = 0.0;
+      for (int i = 0; i < kTC / 32; ++i) m2 = fmax(m2, redd[i]);
+      hmax_s = m2 > 0.0 ? m2 : 1.0;
+    }
+    __syncthreads();
+    if (level == 0) {
+      double hf = 0.0;
+      for (int e = tid; e < s * s; e += kTC) {
+        const double v = M[(int64_t)(e / s) * k + (e % s)];
+        hf += v * v;
+      }
+      hf = warp_sum(hf);
+      if (lane == 0) redd[warp] = hf;
+      __syncthreads();
+      if (tid == 0) {
+        double sum = 0.0;
+        for (int i = 0; i < kTC / 32; ++i) sum += redd[i];
+        scal[1] = sqrt(sum);
+      }
+    }
+  }
+  const double sc = 1.0 / hmax_s;
+  float a[16][4];
+#pragma unroll
+  for (int i = 0; i < 16; ++i)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int r = 8 * i + 4 * h + e;
+      a[i][e] = (r < s && c < s) ? (float)(M[(int64_t)r * k + c] * sc) : 0.f;
+    }
+  auto store_col = [&](float* dst) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+      *reinterpret_cast<float4*>(dst + 8 * i + 4 * h) = make_float4(a[i][0], a[i][1], a[i][2], a[i][3]);
+  };
+  // reflector of step jn from column jn (all lanes of the warp owning it)
+  auto prepare = [&](int jn, int b) {
+    float* x = xs[b];
+    if (c == jn) store_col(x);
+    __syncwarp();
+    const float4 x4 = *reinterpret_cast<const float4*>(x + 4 * lane);
+    const float x0 = x[jn + 1], dj = x[jn];
+    const float xe[4] = {x4.x, x4.y, x4.z, x4.w};
+    float sq = 0.f;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int r = 4 * lane + e;
+      if (r > jn + 1 && r < s) sq = fmaf(xe[e], xe[e], sq);
+    }
+    sq = warp_sumf(sq);
+    // the reflector as a unit vector u = v / |v|; a column below 1e-18 of the
+    // scaled block is taken as reduced (u = 0)
+    const float nrm = sqrtf(x0 * x0 + sq);
+    float alpha = 0.f, invv = 0.f;
+    if (nrm > 1e-18f) {
+      alpha = x0 >= 0.f ? -nrm : nrm;
+      const float v0 = x0 - alpha;
+      invv = rsqrtf(v0 * v0 + sq);
+    }
+    __syncwarp();  // every lane has read x before it is masked
+    float m[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int r = 4 * lane + e;
+      m[e] = r <= jn ? 0.f : (r == jn + 1 ? x0 - alpha : xe[e]);
+    }
+    *reinterpret_cast<float4*>(x + 4 * lane) = make_float4(m[0], m[1], m[2], m[3]);
+    if (lane == 0) {
+      invv_s[b] = invv;
+      dv[jn] = dj;
+      ev[jn] = invv > 0.f ? alpha : x0;
+      bv[jn] = invv > 0.f ? 2.f : 0.f;
+    }
+  };
+  if (s >= 3 && warp == 0) prepare(0, 0);
+  __syncthreads();
+
+  for (int j = 0; j + 2 < s; ++j) {
+    const int b = j & 1;
+    const float* x = xs[b];
+    const float invv = invv_s[b];
+    const bool act = c > j && c < s;
+    // q_c = (A u)_c; the column pair adds its two halves.  Rows go in
+    // segments of 32 (four groups per thread), skipped when they lie at or
+    // above j; warps whose columns are all finished skip the products (both
+    // tests are uniform over the warp; inactive lanes of an active warp
+    // compute values that are never used)
+    const bool wact = (16 * warp + 15 > j) && (16 * warp < s);
+    float pc = 0.f;
+    if (wact) {
+      float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+#pragma unroll
+      for (int sg = 0; sg < 4; ++sg) {
+        if (32 * sg + 31 <= j) continue;
+#pragma unroll
+        for (int ii = 0; ii < 4; ++ii) {
+          const int i = 4 * sg + ii;
+          const float4 v = *reinterpret_cast<const float4*>(x + 8 * i + 4 * h);
+          p0 = fmaf(a[i][0], v.x, p0);
+          p1 = fmaf(a[i][1], v.y, p1);
+          p2 = fmaf(a[i][2], v.z, p2);
+          p3 = fmaf(a[i][3], v.w, p3);
+        }
+      }
+      pc = act ? (p0 + p1) + (p2 + p3) : 0.f;
+    }
+    pc += __shfl_xor_sync(0xffffffffu, pc, 1);
+    const float q = pc * invv;
+    const float uc = act ? x[c] * invv : 0.f;
+    if (h == 0 && act) gV[packed_off(j, s) + (c - j - 1)] = uc;
+    float t = warp_sumf((h == 0 && act) ? uc * q : 0.f);
+    if (lane == 0) red[warp] = t;
+    __syncthreads();
+    float uau = 0.f;
+#pragma unroll
+    for (int w = 0; w < kTC / 32; ++w) uau += red[w];
+    const float wc = act ? 2.f * q - 2.f * uau * uc : 0.f;
+    if (h == 0) ws[c] = wc;
+    __syncthreads();
+    // A -= u w^T + w u^T (rows through v / |v|); rows at or above j have
+    // v = w = 0 and stay as they are
+    if (wact) {
+      const float wci = wc * invv;
+#pragma unroll
+      for (int sg = 0; sg < 4; ++sg) {
+        if (32 * sg + 31 <= j) continue;
+#pragma unroll
+        for (int ii = 0; ii < 4; ++ii) {
+          const int i = 4 * sg + ii;
+          const float4 v = *reinterpret_cast<const float4*>(x + 8 * i + 4 * h);
+          const float4 w = *reinterpret_cast<const float4*>(ws + 8 * i + 4 * h);
+          a[i][0] = fmaf(-v.x, wci, fmaf(-w.x, uc, a[i][0]));
+          a[i][1] = fmaf(-v.y, wci, fmaf(-w.y, uc, a[i][1]));
+          a[i][2] = fmaf(-v.z, wci, fmaf(-w.z, uc, a[i][2]));
+          a[i][3] = fmaf(-v.w, wci, fmaf(-w.w, uc, a[i][3]));
+        }
+      }
+    }
+    if (j + 3 < s && warp == ((j + 1) >> 4)) prepare(j + 1, b ^ 1);
+    __syncthreads();
+  }
+  // the last 2 x 2 block (rows s-2, s-1), or the 1 x 1 matrix
+  if (s >= 2) {
+    if (c == s - 2) store_col(xs[0]);
+    if (c == s - 1) store_col(xs[1]);
+  } else if (c == 0) {
+    store_col(xs[1]);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    if (s >= 2) {
+      dv[s - 2] = xs[0][s - 2];
+      ev[s - 2] = xs[0][s - 1];
+      dv[s - 1] = xs[1][s - 1];
+      bv[s - 2] = 0.f;
+      bv[s - 1] = 0.f;
+    } else {
+      dv[0] = xs[1][0];
+      bv[0] = 0.f;
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < s; i += kTC) {
+    tri[i] = dv[i];
+    tri[k + i] = (i + 1 < s) ? ev[i] : 0.f;
+    tri[2 * k + i] = (i + 1 < s) ? ev[i] * ev[i] : 0.f;
+    tri[3 * k + i] = bv[i];
+  }
+  if (tid == 0) {
+    float gl = 1e30f, gu = -1e30f, tn = 0.f;
+    for (int i = 0; i < s; ++i) {
+      const float off = (i > 0 ? fabsf(ev[i - 1]) : 0.f) + (i + 1 < s ? fabsf(ev[i]) : 0.f);
+      gl = fminf(gl, dv[i] - off);
+      gu = fmaxf(gu, dv[i] + off);
+      tn = fmaxf(tn, fabsf(dv[i]) + off);
+    }
+    const float pad = 2.f * 1.2e-7f * tn + 1e-30f;
+    float* cst = tri + 5 * k;
+    cst[0] = gl - pad;
+    cst[1] = gu + pad;
+    cst[2] = tn;
+    cst[3] = fmaxf(1e-30f, 1.2e-7f * 1e-6f * tn);  // pivmin
+    const float hi = (float)hmax_s;
+    cst[4] = hi;
+    cst[5] = (float)(hmax_s - (double)hi);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // 2. Eigenvalues of T, ascending: one warp per eigenvalue idx.
 __global__ void __launch_bounds__(128) seed_bisect_kernel(int k, int level, const int32_t* __restrict__ lvl,
@@ -693,7 +921,7 @@ void launch_seed_level(Launcher& L, const double* M, int k, int level, int32_t* 
                        float* Wk, float* tri, double* Xout, double* lam, double* scal, int32_t* stats,
                        int32_t* cid) {
   if (k <= 128)
-    launch_tri<128>(L, M, k, level, lvl, gV, tri, scal);
+    launch_pdl(L, seed_tri_col_kernel, dim3(1), dim3(kTC), 0, M, k, level, lvl, gV, tri, scal);
   else
     launch_tri<256>(L, M, k, level, lvl, gV, tri, scal);
   launch_pdl(L, seed_bisect_kernel, dim3((k + 3) / 4), dim3(128), 0, k, level, lvl, tri);
