@@ -383,7 +383,8 @@ __global__ void __launch_bounds__(kTC, 1) seed_tri_col_kernel(const double* __re
                                                               float* __restrict__ tri, double* scal) {
   pdl_wait();  // first, on every path: completion stays ordered along the chain
   __shared__ __align__(16) float xs[2][128];  // v of the step (ping-pong)
-  __shared__ __align__(16) float ws[128];     // w of the step
+  __shared__ __align__(16) float qs[128];     // q = A u of the step
+  __shared__ __align__(16) float cs[2][128];  // lookahead column (ping-pong)
   __shared__ float invv_s[2];
   __shared__ float red[8];
   __shared__ float dv[128], ev[128], bv[128];
@@ -479,7 +480,11 @@ __global__ void __launch_bounds__(kTC, 1) seed_tri_col_kernel(const double* __re
       bv[jn] = invv > 0.f ? 2.f : 0.f;
     }
   };
-  if (s >= 3 && warp == 0) prepare(0, 0);
+  // before step 0: its reflector from column 0, and column 1 for the lookahead
+  if (warp == 0) {
+    if (s >= 3) prepare(0, 0);
+    if (s >= 4 && c == 1) store_col(cs[0]);
+  }
   __syncthreads();
 
   for (int j = 0; j + 2 < s; ++j) {
@@ -514,20 +519,22 @@ __global__ void __launch_bounds__(kTC, 1) seed_tri_col_kernel(const double* __re
     pc += __shfl_xor_sync(0xffffffffu, pc, 1);
     const float q = pc * invv;
     const float uc = act ? x[c] * invv : 0.f;
-    if (h == 0 && act) gV[packed_off(j, s) + (c - j - 1)] = uc;
-    float t = warp_sumf((h == 0 && act) ? uc * q : 0.f);
+    if (h == 0) {
+      qs[c] = q;  // zero for finished and padding columns
+      if (act) gV[packed_off(j, s) + (c - j - 1)] = uc;
+    }
+    const float t = warp_sumf((h == 0 && act) ? uc * q : 0.f);
     if (lane == 0) red[warp] = t;
     __syncthreads();
+    // K = 2 u^T q, w = 2 q - K u.  A -= u w^T + w u^T is, entry by entry,
+    // a -= v_r al_c + q_r be_c with al_c = (w_c - K u_c) / |v|, be_c = 2 u_c
+    // (rows at or above j and padding rows have v = q = 0)
     float uau = 0.f;
 #pragma unroll
     for (int w = 0; w < kTC / 32; ++w) uau += red[w];
-    const float wc = act ? 2.f * q - 2.f * uau * uc : 0.f;
-    if (h == 0) ws[c] = wc;
-    __syncthreads();
-    // A -= u w^T + w u^T (rows through v / |v|); rows at or above j have
-    // v = w = 0 and stay as they are
+    const float K = 2.f * uau;
     if (wact) {
-      const float wci = wc * invv;
+      const float al = invv * (2.f * q - 2.f * K * uc), be = 2.f * uc;
 #pragma unroll
       for (int sg = 0; sg < 4; ++sg) {
         if (32 * sg + 31 <= j) continue;
@@ -535,15 +542,58 @@ __global__ void __launch_bounds__(kTC, 1) seed_tri_col_kernel(const double* __re
         for (int ii = 0; ii < 4; ++ii) {
           const int i = 4 * sg + ii;
           const float4 v = *reinterpret_cast<const float4*>(x + 8 * i + 4 * h);
-          const float4 w = *reinterpret_cast<const float4*>(ws + 8 * i + 4 * h);
-          a[i][0] = fmaf(-v.x, wci, fmaf(-w.x, uc, a[i][0]));
-          a[i][1] = fmaf(-v.y, wci, fmaf(-w.y, uc, a[i][1]));
-          a[i][2] = fmaf(-v.z, wci, fmaf(-w.z, uc, a[i][2]));
-          a[i][3] = fmaf(-v.w, wci, fmaf(-w.w, uc, a[i][3]));
+          const float4 w = *reinterpret_cast<const float4*>(qs + 8 * i + 4 * h);
+          a[i][0] = fmaf(-v.x, al, fmaf(-w.x, be, a[i][0]));
+          a[i][1] = fmaf(-v.y, al, fmaf(-w.y, be, a[i][1]));
+          a[i][2] = fmaf(-v.z, al, fmaf(-w.z, be, a[i][2]));
+          a[i][3] = fmaf(-v.w, al, fmaf(-w.w, be, a[i][3]));
         }
       }
     }
-    if (j + 3 < s && warp == ((j + 1) >> 4)) prepare(j + 1, b ^ 1);
+    // column j + 2 (now as after step j) for the next step's lookahead
+    if (c == j + 2 && j + 2 < s) store_col(cs[(j + 1) & 1]);
+    // warp 0: the reflector of step j + 1 from column j + 1 as before this
+    // step plus this step's update, while the other warps update
+    if (warp == 0 && j + 3 < s) {
+      const int jn = j + 1, bn = b ^ 1;
+      const float* cp = cs[b];
+      const float un = x[jn] * invv, qn = qs[jn];
+      const float aln = invv * (2.f * qn - 2.f * K * un), ben = 2.f * un;
+      const float4 c4 = *reinterpret_cast<const float4*>(cp + 4 * lane);
+      const float4 v4 = *reinterpret_cast<const float4*>(x + 4 * lane);
+      const float4 q4 = *reinterpret_cast<const float4*>(qs + 4 * lane);
+      const float xe[4] = {fmaf(-v4.x, aln, fmaf(-q4.x, ben, c4.x)), fmaf(-v4.y, aln, fmaf(-q4.y, ben, c4.y)),
+                           fmaf(-v4.z, aln, fmaf(-q4.z, ben, c4.z)), fmaf(-v4.w, aln, fmaf(-q4.w, ben, c4.w))};
+      const float x0 = fmaf(-x[jn + 1], aln, fmaf(-qs[jn + 1], ben, cp[jn + 1]));
+      const float dj = fmaf(-x[jn], aln, fmaf(-qn, ben, cp[jn]));
+      float sq = 0.f;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int r = 4 * lane + e;
+        if (r > jn + 1 && r < s) sq = fmaf(xe[e], xe[e], sq);
+      }
+      sq = warp_sumf(sq);
+      const float nrm = sqrtf(x0 * x0 + sq);
+      float alpha = 0.f, iv = 0.f;
+      if (nrm > 1e-18f) {
+        alpha = x0 >= 0.f ? -nrm : nrm;
+        const float v0 = x0 - alpha;
+        iv = rsqrtf(v0 * v0 + sq);
+      }
+      float m[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int r = 4 * lane + e;
+        m[e] = r <= jn ? 0.f : (r == jn + 1 ? x0 - alpha : xe[e]);
+      }
+      *reinterpret_cast<float4*>(xs[bn] + 4 * lane) = make_float4(m[0], m[1], m[2], m[3]);
+      if (lane == 0) {
+        invv_s[bn] = iv;
+        dv[jn] = dj;
+        ev[jn] = iv > 0.f ? alpha : x0;
+        bv[jn] = iv > 0.f ? 2.f : 0.f;
+      }
+    }
     __syncthreads();
   }
   // the last 2 x 2 block (rows s-2, s-1), or the 1 x 1 matrix
