@@ -18,12 +18,14 @@
 // and a level whose block has fewer than two columns does nothing.
 //
 // One level of the seed, on the s x s block (s <= 256), scaled by 1/max|M_ii|:
-//   1. seed_tri_kernel (one CTA): Householder tridiagonalisation M = Q T Q^T.
-//      Thread (g, c) owns column c and rows g + 4i; rows below 128 in
-//      registers, the rest in shared memory.  Every thread derives the
-//      reflector of step j from row j (published by its owners with per-warp
-//      partial norms), so a step needs three block barriers and no phase
-//      runs on a single warp.
+//   1. Householder tridiagonalisation M = Q T Q^T on one CTA:
+//      seed_tri_col_kernel for k <= 128 (each column in the registers of a
+//      thread pair, two block barriers per step, the next reflector formed
+//      by one warp during the update); seed_tri_kernel above (thread (g, c)
+//      owns column c and rows g + 4i; rows below 128 in registers, the rest
+//      in shared memory; every thread derives the reflector of step j from
+//      row j, published by its owners with per-warp partial norms; three
+//      block barriers per step).
 //   2. seed_bisect_kernel: one warp per eigenvalue, Sturm counts at 32
 //      interior points per round, 6 rounds (33^6 >= 2^30: the resolution of
 //      30 halvings of the Gershgorin interval).
@@ -369,13 +371,15 @@ __global__ void __launch_bounds__(4 * NC, 1) seed_tri_kernel(const double* __res
 // in registers: thread t owns column c = t / 2 and, of its row groups of four,
 // those of parity h = t & 1 (rows 8 i + 4 h .. 8 i + 4 h + 3).  A stays
 // symmetric under the two-sided update, so the next reflector's source row
-// j + 1 is column j + 1, which its two owners store from static registers;
-// their warp then forms the reflector for the whole CTA (the norm of the
-// tail, alpha, and the Householder vector v with the rows at or above j
-// zeroed), so no register is ever indexed at run time.  Per step: q = A u
-// over the active columns (u = v / |v|), u^T q (one block reduction),
-// w = 2 q - 2 (u^T q) u, and A -= u w^T + w u^T with two FMAs per entry;
-// three block barriers.  Outputs are those of seed_tri_kernel.
+// j + 1 is column j + 1, and no register is ever indexed at run time.  Per
+// step j: q = A u over the active columns (u = v / |v|, v the Householder
+// vector with the rows at or above j zeroed), the block sum K = 2 u^T q, and
+// the rank-2 update A -= u w^T + w u^T (w = 2 q - K u) written as
+// a -= v_r al_c + q_r be_c, so only q and K are exchanged: two block
+// barriers.  Warp 0 forms the next step's reflector (norm, alpha, masked v)
+// from column j + 1 as it was before the step -- stored one step ahead by
+// its owners -- plus this step's update, while the other warps apply it.
+// Outputs are those of seed_tri_kernel.
 constexpr int kTC = 256;
 
 __global__ void __launch_bounds__(kTC, 1) seed_tri_col_kernel(const double* __restrict__ M, int k, int level,
