@@ -27,7 +27,8 @@
 //      while the tensor core fills the other accumulator set.
 //   3. oz_fin_kernel: sums the splits' integers (exact, so in any order) and
 //      writes H[i][j] = H[j][i] = 2^(e_i + e_j - 63) (hi 2^28 + lo), one
-//      rounding.
+//      rounding (|hi| stays below about n 2^35, so it converts to FP64
+//      exactly for n < 2^18; the int64 sums cannot overflow for n < 2^27).
 //
 // The digits drop below 2^-57 of each row's largest entry and the pairs
 // t + u >= 8 (below 2^-55 of the product of the two rows' scales); the rest
